@@ -1,0 +1,251 @@
+/*
+ * rfcmp.h -- C ABI of the GB300 library for the RWG-discretised EFIE and the
+ * refinement-free Calderon multiplicative preconditioner (RF-CMP) of
+ * Adrian, Andriulli, Eibert, "On a refinement-free Calderon multiplicative
+ * preconditioner for the electric field integral equation" (arXiv 1803.08333).
+ *
+ * Problem (Sec. 2): a closed PEC surface Gamma, triangulated; RWG functions
+ * f_n (not divided by the edge length, Eq. RWGdef); wavenumber k; e^{-i w t};
+ * current j normalised by the wave impedance.  With
+ *   [T_A]_mn  = int int f_m(r) . f_n(r') G(r,r'),    G = e^{ikR}/(4 pi R),
+ *   V_st      = int int p_s(r) p_t(r') G(r,r'),      p_s = 1/A_s on cell s,
+ *   T_Phi     = Sigma V Sigma^T                       (Sec. 3, Eq. TPhiandV),
+ *   T         = i k T_A + T_Phi / (i k),
+ *   e_n       = int f_n . E^i,
+ * the EFIE is T j = -e.  RF-CMP (Sec. 3 Eq. NewFormulation, with the
+ * numerical variant of Sec. 4) solves the Hermitian positive definite system
+ *   P_o^H T^H P_m T P_o i = -P_o^H T^H P_m e,   j = P_o i,
+ *   P_o  = P_LH / alpha + i P_S / beta,
+ *   P_m  = Lambda G_ll^{-1} Lambda^T / alpha^2 + P_LH / gamma
+ *        + Sigma (Sigma^T Sigma)^+ G_pp^{-1} (Sigma^T Sigma)^+ Sigma^T / beta^2,
+ *   P_S  = Sigma (Sigma^T Sigma)^+ Sigma^T,  P_LH = I - P_S      (Sec. 2),
+ * by conjugate gradients (Sec. 4).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: 0 (RFCMP_OK) on success, a negative rfcmp_status otherwise;
+ *    rfcmp_last_error() gives a message for the calling thread.
+ *  - Mesh arrays are HOST pointers; the library copies them.  Triangles are
+ *    int32 vertex triples, counter-clockwise about the outward normal.
+ *  - Edge numbering: edges sorted by (smaller vertex id, larger vertex id);
+ *    c_n^+ is the lower-index cell of edge n, c_n^- the other.
+ *    Sigma[n, c^+] = +1, Sigma[n, c^-] = -1; with c^+ listed
+ *    counter-clockwise as (v1, v2, r^+), Lambda[n, v1] = +1, Lambda[n, v2] = -1.
+ *  - Vectors passed to apply / precondition / solve are DEVICE pointers to
+ *    complex128 (rfcmp_c128), column-major with nrhs columns of length N
+ *    (edges) unless stated otherwise; the caller owns them.  Work is queued
+ *    on `stream` (a cudaStream_t, NULL = legacy default stream); entry points
+ *    that return host results synchronise that stream.
+ *  - An rfcmp_op is not thread-safe; different ops may be used from
+ *    different threads.  rfcmp_ctx create/destroy are thread-safe.
+ *  - Device memory of an op is allocated by the library (cudaMalloc) on the
+ *    context's device and counted against the context's HBM budget.
+ */
+#ifndef RFCMP_H
+#define RFCMP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rfcmp_ctx rfcmp_ctx;
+typedef struct rfcmp_op rfcmp_op;
+typedef struct { double re, im; } rfcmp_c128;
+
+typedef enum {
+  RFCMP_OK = 0,
+  RFCMP_ERR_INVALID_ARG = -1,
+  RFCMP_ERR_MESH_NOT_MANIFOLD = -2, /* an edge not shared by exactly two cells, or a bad index */
+  RFCMP_ERR_MESH_ORIENTATION = -3,  /* neighbouring cells not consistently oriented */
+  RFCMP_ERR_OUT_OF_BUDGET = -4,     /* the op would exceed the context's HBM budget */
+  RFCMP_ERR_CUDA = -5,              /* a CUDA call failed (message in rfcmp_last_error) */
+  RFCMP_ERR_DEVICE_TIMEOUT = -6,    /* a bounded device-side wait gave up */
+  RFCMP_ERR_NOT_CONVERGED = -7,     /* only with rfcmp_solve_opts.fail_on_nonconvergence */
+  RFCMP_ERR_NO_DEVICE = -8          /* no usable CUDA device of compute capability 10.3 */
+} rfcmp_status;
+
+/* which operator rfcmp_apply applies */
+typedef enum {
+  RFCMP_APPLY_T = 0,     /* y = T x = (i k T_A + Sigma V Sigma^T / (i k)) x          (Sec. 2) */
+  RFCMP_APPLY_T_A = 1,   /* y = T_A x                                                 (Sec. 2) */
+  RFCMP_APPLY_T_PHI = 2, /* y = Sigma V Sigma^T x                          (Sec. 3, Eq. TPhiandV) */
+  RFCMP_APPLY_T_ADJ = 3, /* y = T^H x = conj(T conj(x))                    (Sec. 3.4, T^dagger) */
+  RFCMP_APPLY_A = 4      /* y = P_o^H T^H P_m T P_o x (low-frequency-stable order)   (Sec. 3, Sec. 4) */
+} rfcmp_apply_which;
+
+/* which preconditioner factor rfcmp_precondition applies */
+typedef enum {
+  RFCMP_PREC_P_O = 0,     /* P_o                 (Sec. 4, first display) */
+  RFCMP_PREC_P_O_ADJ = 1, /* P_o^H */
+  RFCMP_PREC_P_M = 2,     /* P_m = P_mL + P_mS   (Sec. 4, first display) */
+  RFCMP_PREC_P_SIGMA = 3, /* P_S = Sigma (Sigma^T Sigma)^+ Sigma^T   (Sec. 2) */
+  RFCMP_PREC_P_LAMBDAH = 4 /* P_LH = I - P_S                          (Sec. 2) */
+} rfcmp_prec_which;
+
+/* how alpha, beta, gamma are chosen */
+typedef enum {
+  RFCMP_SCALE_POWER = 0, /* norms by power iteration (Sec. 4, second display); the default */
+  RFCMP_SCALE_K = 1,     /* alpha = sqrt k, beta = 1/sqrt k, gamma = k (Sec. 4, third display) */
+  RFCMP_SCALE_FIXED = 2  /* the values given in rfcmp_op_opts */
+} rfcmp_scaling;
+
+/* arithmetic of the solve */
+typedef enum {
+  RFCMP_PREC_MIXED = 0, /* FP32-data / FP32-accumulate inner CG, float-float residual refinement */
+  RFCMP_PREC_FF = 1     /* every application float-float accurate (FP64-equivalent), no refinement */
+} rfcmp_precision;
+
+typedef struct {
+  int32_t scaling;      /* rfcmp_scaling; default RFCMP_SCALE_POWER */
+  int32_t power_steps;  /* power-iteration steps for each norm; default 30 */
+  double alpha, beta, gamma; /* used with RFCMP_SCALE_FIXED */
+  double factor_tol;    /* relative residual of the dense-inverse builds of (Sigma^T Sigma)^+
+                           and G_ll^{-1}; default 1e-13 */
+  int32_t reserved[8];  /* must be zero */
+} rfcmp_op_opts;
+
+typedef struct {
+  double tol;           /* stop when ||b - A i|| / ||b|| <= tol on the preconditioned system; default 1e-6 */
+  int32_t max_iter;     /* total CG iterations per right-hand side; default 2000 */
+  int32_t max_refine;   /* refinement sweeps (MIXED); default 8 */
+  double inner_tol;     /* relative reduction asked of each inner CG (MIXED); default 1e-4 */
+  int32_t precision;    /* rfcmp_precision; default RFCMP_PREC_MIXED */
+  int32_t fail_on_nonconvergence; /* nonzero: return RFCMP_ERR_NOT_CONVERGED if any column fails */
+  int32_t reserved[8];  /* must be zero */
+} rfcmp_solve_opts;
+
+typedef struct {
+  int32_t converged;    /* 1 if the column reached tol */
+  int32_t iterations;   /* CG iterations spent on this column (all sweeps) */
+  int32_t refinements;  /* refinement sweeps (accurate residual evaluations) */
+  int32_t reserved;
+  double residual;      /* final ||b - A i|| / ||b||, float-float accurate */
+} rfcmp_solve_report;
+
+typedef struct {
+  int64_t n_edges, n_vertices, n_cells;
+  int32_t genus;
+  int32_t reserved0;
+  double k, alpha, beta, gamma;
+  uint64_t device_bytes;    /* device memory held by the op */
+  double ms_assembly;       /* T_A and V assembly (device time) */
+  double ms_factors;        /* dense (Sigma^T Sigma)^+ and G_ll^{-1} (0 when shared from the context cache) */
+  double ms_scaling;        /* alpha, beta, gamma power iterations */
+  int32_t factor_iterations_lplus; /* block-CG iterations of the (Sigma^T Sigma)^+ build */
+  int32_t factor_iterations_gll;   /* block-CG iterations of the G_ll^{-1} build */
+} rfcmp_op_info;
+
+/* ----------------------------------------------------------------------------
+ * Context: one CUDA device, an HBM budget, and a cache of the k-independent
+ * topology factors ((Sigma^T Sigma)^+ depends on the mesh connectivity only,
+ * G_ll^{-1} on the mesh geometry) shared by ops on the same mesh.
+ *  device            CUDA ordinal; the device must be sm_103 (GB300).
+ *  hbm_budget_bytes  upper bound on device memory held by all ops of this
+ *                    context (0 = no bound).
+ * Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_NO_DEVICE, RFCMP_ERR_CUDA.
+ */
+int rfcmp_ctx_create(int device, uint64_t hbm_budget_bytes, rfcmp_ctx** out);
+/* Frees the factor cache.  Every op of the context must be destroyed first. */
+int rfcmp_ctx_destroy(rfcmp_ctx* ctx);
+/* Drops the cached topology factors (ops keep their own references). */
+int rfcmp_ctx_clear_cache(rfcmp_ctx* ctx);
+/* Bytes currently held by the ops and the cache of this context. */
+uint64_t rfcmp_ctx_bytes_in_use(const rfcmp_ctx* ctx);
+
+/* ----------------------------------------------------------------------------
+ * Operator: mesh + wavenumber -> resident T_A (N x N) and V (N_C x N_C),
+ * complex64, row-major (both complex symmetric); dense (Sigma^T Sigma)^+
+ * (N_C x N_C) and G_ll^{-1} (N_V x N_V) as FP32 hi + lo planes; alpha, beta,
+ * gamma.  Assembly (Sec. 2 definitions): 7 x 7 product of the 7-point rule
+ * on far cell pairs in FP32; on near pairs (a shared vertex) closed-form
+ * integration of 1/(4 pi R) over the source cell plus the 7-point rule for
+ * (e^{ikR} - 1)/(4 pi R), in FP64, averaged over both orders.
+ *  verts  N_V x 3 float64 (host), tris N_C x 3 int32 (host).
+ *  k      wavenumber > 0 (rad/m, c = 1).
+ *  opts   NULL for the defaults.
+ * All work runs on the context device's legacy default stream; the call
+ * returns when the op is ready.
+ * Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_MESH_NOT_MANIFOLD,
+ * RFCMP_ERR_MESH_ORIENTATION, RFCMP_ERR_OUT_OF_BUDGET, RFCMP_ERR_CUDA.
+ */
+int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nc,
+                    double k, const rfcmp_op_opts* opts, rfcmp_op** out);
+int rfcmp_op_info_get(const rfcmp_op* op, rfcmp_op_info* out);
+int rfcmp_op_destroy(rfcmp_op* op);
+
+/* Copies an internal matrix to a caller-owned DEVICE buffer of dst_bytes bytes.
+ *  which 0: T_A, N x N complex64 row-major      (8 N^2 bytes)
+ *        1: V, N_C x N_C complex64 row-major    (8 N_C^2 bytes)
+ *        2: (Sigma^T Sigma)^+, N_C x N_C float64 (hi + lo)  (8 N_C^2 bytes)
+ *        3: G_ll^{-1}, N_V x N_V float64 (hi + lo)         (8 N_V^2 bytes)
+ * Errors: RFCMP_ERR_INVALID_ARG (unknown which, dst_bytes too small), RFCMP_ERR_CUDA. */
+int rfcmp_op_export(const rfcmp_op* op, int which, void* dst, uint64_t dst_bytes, void* stream);
+
+/* Topology read-back for tests: edge table in the library's numbering.
+ *  edge_verts  N x 2 int32 (v1, v2)    edge_cells  N x 2 int32 (c^+, c^-)   (host, caller-owned) */
+int rfcmp_op_edges(const rfcmp_op* op, int32_t* edge_verts, int32_t* edge_cells);
+
+/* Plane-wave excitation e_n = int f_n . pol e^{i k khat . r} dS (Sec. 2), 7-point rule, FP64.
+ *  khat, pol  nrhs x 3 float64 (host); khat unit vectors, pol real polarisations.
+ *  e          DEVICE, N x nrhs complex128, column-major. */
+int rfcmp_rhs_planewave(rfcmp_op* op, const double* khat, const double* pol, int64_t nrhs,
+                        rfcmp_c128* e, void* stream);
+
+/* y = op(x) for nrhs columns (see rfcmp_apply_which).  Float-float accurate
+ * accumulation over the stored complex64 matrices.  x and y must not alias. */
+int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* x, rfcmp_c128* y, int64_t nrhs, void* stream);
+
+/* y = P(x) (see rfcmp_prec_which); float-float accurate.  x and y must not alias. */
+int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* x, rfcmp_c128* y, int64_t nrhs,
+                       void* stream);
+
+/* Solves T j = -e through the RF-CMP system by CG (Sec. 4), nrhs columns.
+ *  e  DEVICE N x nrhs; j DEVICE N x nrhs (output); report HOST nrhs entries (output, may be NULL).
+ *  opts NULL for the defaults.  Synchronises `stream` before returning.
+ * Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_CUDA, RFCMP_ERR_NOT_CONVERGED (opt-in). */
+int rfcmp_solve(rfcmp_op* op, const rfcmp_c128* e, rfcmp_c128* j, int64_t nrhs, const rfcmp_solve_opts* opts,
+                rfcmp_solve_report* report, void* stream);
+
+/* The same solve with HOST e and j (copies inside the call; pinned memory is faster). */
+int rfcmp_solve_host(rfcmp_op* op, const rfcmp_c128* e_host, rfcmp_c128* j_host, int64_t nrhs,
+                     const rfcmp_solve_opts* opts, rfcmp_solve_report* report, void* stream);
+
+/* Bistatic radar cross section sigma = (k^2 / 4 pi) |N - rhat (rhat . N)|^2,
+ * N(rhat) = int j e^{-i k rhat . r} dS (7-point rule, FP64), in dBsm.
+ *  j DEVICE N x nrhs; dirs HOST ndir x 3 unit vectors; rcs_dbsm HOST ndir x nrhs (column-major). */
+int rfcmp_farfield(rfcmp_op* op, const rfcmp_c128* j, int64_t nrhs, const double* dirs, int64_t ndir,
+                   double* rcs_dbsm, void* stream);
+
+/* ----------------------------------------------------------------------------
+ * Profiling counters (the paper has no counterpart; measurement support).
+ * When enabled, every launch of an instrumented kernel family is bracketed by
+ * CUDA events on the stream it is launched on; rfcmp_profile_read
+ * synchronises the device and reports per family the launch count, the sum
+ * of the event durations and the algorithmic bytes and FLOPs of those
+ * launches (GEMV: the matrix plus the vectors it reads and writes; far-pair
+ * assembly: 49 kernel evaluations per unique pair at 54 FLOPs each).
+ */
+typedef struct {
+  char name[40];
+  int64_t launches;
+  double total_ms;
+  double bytes;
+  double flops;
+} rfcmp_profile_entry;
+/* Clears the counters; nonzero enables, zero disables. */
+int rfcmp_profile_enable(int enable);
+/* Copies up to max_entries families into out (host) and their number into *n_entries. */
+int rfcmp_profile_read(rfcmp_profile_entry* out, int max_entries, int* n_entries);
+
+const char* rfcmp_strerror(int status);
+const char* rfcmp_last_error(void);
+
+/* Fills opts with the defaults documented above. */
+void rfcmp_op_opts_default(rfcmp_op_opts* opts);
+void rfcmp_solve_opts_default(rfcmp_solve_opts* opts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFCMP_H */

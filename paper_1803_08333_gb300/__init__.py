@@ -1,0 +1,336 @@
+"""Python binding of librfcmp, the GB300 library for the RWG EFIE and the
+refinement-free Calderon multiplicative preconditioner (arXiv 1803.08333).
+
+Argument marshalling only: every step of assembly, preconditioning and the
+solve runs in the library's CUDA kernels (include/rfcmp.h).  PyTorch provides
+device memory and streams.  Vectors are torch.complex128 CUDA tensors of
+shape (nrhs, N): row r is column r of the column-major N x nrhs block the C
+ABI expects.  The library must be built (``build.build()``); importing the
+binding without it raises at first use, there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librfcmp.so")
+
+APPLY = {"T": 0, "T_A": 1, "T_PHI": 2, "T_ADJ": 3, "A": 4}
+PREC = {"P_O": 0, "P_O_ADJ": 1, "P_M": 2, "P_SIGMA": 3, "P_LAMBDAH": 4}
+SCALING = {"power": 0, "k": 1, "fixed": 2}
+PRECISION = {"mixed": 0, "ff": 1}
+EXPORT = {"T_A": 0, "V": 1, "LPLUS": 2, "GLL_INV": 3}
+
+# every symbol include/rfcmp.h declares
+EXPORTED_SYMBOLS = [
+    "rfcmp_ctx_create", "rfcmp_ctx_destroy", "rfcmp_ctx_clear_cache", "rfcmp_ctx_bytes_in_use",
+    "rfcmp_op_create", "rfcmp_op_info_get", "rfcmp_op_destroy", "rfcmp_op_export", "rfcmp_op_edges",
+    "rfcmp_rhs_planewave", "rfcmp_apply", "rfcmp_precondition", "rfcmp_solve", "rfcmp_solve_host",
+    "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
+    "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read",
+]
+
+
+class OpOpts(ctypes.Structure):
+    _fields_ = [
+        ("scaling", ctypes.c_int32), ("power_steps", ctypes.c_int32),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("factor_tol", ctypes.c_double), ("reserved", ctypes.c_int32 * 8),
+    ]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32),
+        ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int32),
+        ("fail_on_nonconvergence", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8),
+    ]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [
+        ("converged", ctypes.c_int32), ("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("residual", ctypes.c_double),
+    ]
+
+
+class OpInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_edges", ctypes.c_int64), ("n_vertices", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+        ("genus", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("k", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("device_bytes", ctypes.c_uint64), ("ms_assembly", ctypes.c_double), ("ms_factors", ctypes.c_double),
+        ("ms_scaling", ctypes.c_double), ("factor_iterations_lplus", ctypes.c_int32),
+        ("factor_iterations_gll", ctypes.c_int32),
+    ]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+        ("bytes", ctypes.c_double), ("flops", ctypes.c_double),
+    ]
+
+
+class RfcmpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("rfcmp status %d: %s" % (status, msg))
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded shared library (raises if it was never built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "librfcmp.so is missing (%s): build it with paper_1803_08333_gb300.build.build()" % LIB_PATH
+            )
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.rfcmp_ctx_create.argtypes = [i32, ctypes.c_uint64, ctypes.POINTER(vp)]
+        L.rfcmp_ctx_destroy.argtypes = [vp]
+        L.rfcmp_ctx_clear_cache.argtypes = [vp]
+        L.rfcmp_ctx_bytes_in_use.argtypes = [vp]
+        L.rfcmp_ctx_bytes_in_use.restype = ctypes.c_uint64
+        L.rfcmp_op_create.argtypes = [vp, vp, i64, vp, i64, dbl, ctypes.POINTER(OpOpts), ctypes.POINTER(vp)]
+        L.rfcmp_op_info_get.argtypes = [vp, ctypes.POINTER(OpInfo)]
+        L.rfcmp_op_destroy.argtypes = [vp]
+        L.rfcmp_op_export.argtypes = [vp, i32, vp, ctypes.c_uint64, vp]
+        L.rfcmp_op_edges.argtypes = [vp, vp, vp]
+        L.rfcmp_rhs_planewave.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.rfcmp_apply.argtypes = [vp, i32, vp, vp, i64, vp]
+        L.rfcmp_precondition.argtypes = [vp, i32, vp, vp, i64, vp]
+        L.rfcmp_solve.argtypes = [vp, vp, vp, i64, ctypes.POINTER(SolveOpts), vp, vp]
+        L.rfcmp_solve_host.argtypes = [vp, vp, vp, i64, ctypes.POINTER(SolveOpts), vp, vp]
+        L.rfcmp_farfield.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+        L.rfcmp_strerror.argtypes = [i32]
+        L.rfcmp_strerror.restype = ctypes.c_char_p
+        L.rfcmp_last_error.restype = ctypes.c_char_p
+        L.rfcmp_op_opts_default.argtypes = [ctypes.POINTER(OpOpts)]
+        L.rfcmp_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
+        L.rfcmp_profile_enable.argtypes = [i32]
+        L.rfcmp_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int):
+    if status != 0:
+        raise RfcmpError(status, lib().rfcmp_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def profile_enable(enable: bool = True):
+    """Clears and (de)activates the per-kernel-family launch counters."""
+    _check(lib().rfcmp_profile_enable(1 if enable else 0))
+
+
+def profile_read() -> dict:
+    """{family: {launches, total_ms, bytes, flops}}; synchronises the device."""
+    n = ctypes.c_int()
+    buf = (ProfileEntry * 64)()
+    _check(lib().rfcmp_profile_read(buf, 64, ctypes.byref(n)))
+    out = {}
+    for i in range(min(n.value, 64)):
+        e = buf[i]
+        out[e.name.decode()] = {"launches": e.launches, "total_ms": e.total_ms, "bytes": e.bytes, "flops": e.flops}
+    return out
+
+
+class Context:
+    """One CUDA device with an HBM budget and the cache of topology factors."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib().rfcmp_ctx_create(int(device), int(hbm_budget_bytes), ctypes.byref(self._h)))
+        self.device = device
+
+    def clear_cache(self):
+        _check(lib().rfcmp_ctx_clear_cache(self._h))
+
+    def bytes_in_use(self) -> int:
+        return int(lib().rfcmp_ctx_bytes_in_use(self._h))
+
+    def close(self):
+        if self._h:
+            _check(lib().rfcmp_ctx_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().rfcmp_ctx_destroy(self._h)
+        except Exception:
+            pass
+
+
+@dataclass
+class Report:
+    converged: bool
+    iterations: int
+    refinements: int
+    residual: float
+
+
+class Operator:
+    """Mesh + wavenumber -> resident EFIE blocks, RF-CMP factors and scaling."""
+
+    def __init__(self, ctx: Context, verts, tris, k: float, scaling: str = "power", power_steps: int = 30,
+                 alpha: float = 1.0, beta: float = 1.0, gamma: float = 1.0, factor_tol: float = 1e-13):
+        self.ctx = ctx
+        self.verts = np.ascontiguousarray(verts, dtype=np.float64)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32)
+        o = OpOpts()
+        lib().rfcmp_op_opts_default(ctypes.byref(o))
+        o.scaling = SCALING[scaling]
+        o.power_steps = int(power_steps)
+        o.alpha, o.beta, o.gamma = float(alpha), float(beta), float(gamma)
+        o.factor_tol = float(factor_tol)
+        self._h = ctypes.c_void_p()
+        _check(
+            lib().rfcmp_op_create(
+                ctx._h, self.verts.ctypes.data_as(ctypes.c_void_p), self.verts.shape[0],
+                self.tris.ctypes.data_as(ctypes.c_void_p), self.tris.shape[0], float(k), ctypes.byref(o),
+                ctypes.byref(self._h),
+            )
+        )
+        self.k = float(k)
+        inf = self.info()
+        self.N, self.nc, self.nv = int(inf.n_edges), int(inf.n_cells), int(inf.n_vertices)
+
+    def info(self) -> OpInfo:
+        out = OpInfo()
+        _check(lib().rfcmp_op_info_get(self._h, ctypes.byref(out)))
+        return out
+
+    @property
+    def scaling(self):
+        i = self.info()
+        return i.alpha, i.beta, i.gamma
+
+    def export(self, which: str):
+        """T_A, V (complex64 n x n) or LPLUS, GLL_INV (float64 n x n from the hi + lo planes) as CUDA tensors."""
+        import torch
+
+        n = {"T_A": self.N, "V": self.nc, "LPLUS": self.nc, "GLL_INV": self.nv}[which]
+        if which in ("T_A", "V"):
+            t = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+            _check(lib().rfcmp_op_export(self._h, EXPORT[which], _ptr(t), n * n * 8, _stream()))
+            return t
+        t = torch.empty((2, n, n), dtype=torch.float32, device="cuda")
+        _check(lib().rfcmp_op_export(self._h, EXPORT[which], _ptr(t), n * n * 8, _stream()))
+        return t[0].double() + t[1].double()
+
+    def edges(self):
+        ev = np.empty((self.N, 2), np.int32)
+        ec = np.empty((self.N, 2), np.int32)
+        _check(lib().rfcmp_op_edges(self._h, ev.ctypes.data_as(ctypes.c_void_p), ec.ctypes.data_as(ctypes.c_void_p)))
+        return ev, ec
+
+    def rhs_planewave(self, khat, pol):
+        import torch
+
+        khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+        pol = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.float64)
+        nr = khat.shape[0]
+        e = torch.empty((nr, self.N), dtype=torch.complex128, device="cuda")
+        _check(lib().rfcmp_rhs_planewave(self._h, khat.ctypes.data_as(ctypes.c_void_p),
+                                         pol.ctypes.data_as(ctypes.c_void_p), nr, _ptr(e), _stream()))
+        return e
+
+    def _vec(self, x):
+        import torch
+
+        x = x.to(device="cuda", dtype=torch.complex128)
+        if x.dim() == 1:
+            x = x[None]
+        return x.contiguous()
+
+    def apply(self, which: str, x):
+        import torch
+
+        x = self._vec(x)
+        y = torch.empty_like(x)
+        _check(lib().rfcmp_apply(self._h, APPLY[which], _ptr(x), _ptr(y), x.shape[0], _stream()))
+        return y
+
+    def precondition(self, which: str, x):
+        import torch
+
+        x = self._vec(x)
+        y = torch.empty_like(x)
+        _check(lib().rfcmp_precondition(self._h, PREC[which], _ptr(x), _ptr(y), x.shape[0], _stream()))
+        return y
+
+    @staticmethod
+    def _solve_opts(tol, max_iter, max_refine, inner_tol, precision):
+        o = SolveOpts()
+        lib().rfcmp_solve_opts_default(ctypes.byref(o))
+        o.tol, o.max_iter, o.max_refine, o.inner_tol = float(tol), int(max_iter), int(max_refine), float(inner_tol)
+        o.precision = PRECISION[precision]
+        return o
+
+    def solve(self, e, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 8, inner_tol: float = 1e-4,
+              precision: str = "mixed"):
+        """j with T j = -e via RF-CMP + CG; returns (j, [Report per column])."""
+        import torch
+
+        e = self._vec(e)
+        j = torch.empty_like(e)
+        nr = e.shape[0]
+        rep = (SolveReport * nr)()
+        o = self._solve_opts(tol, max_iter, max_refine, inner_tol, precision)
+        _check(lib().rfcmp_solve(self._h, _ptr(e), _ptr(j), nr, ctypes.byref(o), rep, _stream()))
+        return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]
+
+    def solve_host(self, e: np.ndarray, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 8,
+                   inner_tol: float = 1e-4, precision: str = "mixed", stream=None):
+        """Same solve with host arrays (nrhs, N) complex128; copies happen inside the C call."""
+        e = np.ascontiguousarray(np.atleast_2d(e), dtype=np.complex128)
+        j = np.empty_like(e)
+        nr = e.shape[0]
+        rep = (SolveReport * nr)()
+        o = self._solve_opts(tol, max_iter, max_refine, inner_tol, precision)
+        _check(lib().rfcmp_solve_host(self._h, e.ctypes.data_as(ctypes.c_void_p), j.ctypes.data_as(ctypes.c_void_p),
+                                      nr, ctypes.byref(o), rep, _stream(stream)))
+        return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]
+
+    def farfield(self, j, dirs) -> np.ndarray:
+        """Bistatic RCS in dBsm, shape (nrhs, ndir)."""
+        j = self._vec(j)
+        dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        out = np.empty((j.shape[0], dirs.shape[0]), np.float64)
+        _check(lib().rfcmp_farfield(self._h, _ptr(j), j.shape[0], dirs.ctypes.data_as(ctypes.c_void_p),
+                                    dirs.shape[0], out.ctypes.data_as(ctypes.c_void_p), _stream()))
+        return out
+
+    def close(self):
+        if self._h:
+            _check(lib().rfcmp_op_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().rfcmp_op_destroy(self._h)
+        except Exception:
+            pass

@@ -1,0 +1,1293 @@
+// C ABI of librfcmp (include/rfcmp.h): context, operator lifecycle, the
+// RF-CMP application (Sec. 3 Eq. NewFormulation, numerical variant of Sec. 4),
+// power-iteration scaling (Sec. 4) and the CG solve with float-float
+// residual refinement.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rfcmp_internal.h"
+
+namespace rfcmp {
+int padded_ld(int n);
+}
+
+using namespace rfcmp;
+
+// ---------------------------------------------------------------- errors
+namespace {
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define RF_CUDA(call)                                                                                  \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess)                                                                             \
+      return set_error(RFCMP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+#define RF_TRY(call)            \
+  do {                          \
+    int rc_ = (call);           \
+    if (rc_ != RFCMP_OK) return rc_; \
+  } while (0)
+
+// Radon's 7-point degree-5 rule in barycentric coordinates (weights sum to 1)
+struct Rule7 {
+  double bary[7][3];
+  double w[7];
+  Rule7() {
+    const double s15 = std::sqrt(15.0);
+    const double a = (6.0 - s15) / 21.0, b = (6.0 + s15) / 21.0;
+    const double wa = (155.0 - s15) / 1200.0, wb = (155.0 + s15) / 1200.0;
+    const double pts[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {a, a, 1 - 2 * a}, {a, 1 - 2 * a, a}, {1 - 2 * a, a, a},
+                              {b, b, 1 - 2 * b},          {b, 1 - 2 * b, b}, {1 - 2 * b, b, b}};
+    const double ws[7] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
+    for (int q = 0; q < 7; ++q) {
+      for (int i = 0; i < 3; ++i) bary[q][i] = pts[q][i];
+      w[q] = ws[q];
+    }
+  }
+};
+
+template <class T>
+int dalloc(T** p, size_t count, std::vector<void*>& owned) {
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return set_error(RFCMP_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  owned.push_back(q);
+  *p = static_cast<T*>(q);
+  return RFCMP_OK;
+}
+
+template <class T>
+int upload(T** p, const std::vector<T>& h, std::vector<void*>& owned) {
+  RF_TRY(dalloc(p, h.size(), owned));
+  if (!h.empty()) RF_CUDA(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return RFCMP_OK;
+}
+
+double2 c2(double re, double im) { return make_double2(re, im); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- profiling
+namespace {
+struct ProfFamily {
+  std::string name;
+  int64_t launches = 0;
+  double bytes = 0.0, flops = 0.0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  double ms = 0.0;
+};
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+std::vector<ProfFamily> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t pool_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_resolve_locked() {
+  for (auto& f : g_prof) {
+    for (auto& pr : f.pending) {
+      cudaEventSynchronize(pr.second);
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) f.ms += ms;
+      g_event_pool.push_back(pr.first);
+      g_event_pool.push_back(pr.second);
+    }
+    f.pending.clear();
+  }
+}
+}  // namespace
+
+namespace rfcmp {
+ProfScope::ProfScope(const char* family, double bytes, double flops, cudaStream_t s) : s_(s) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  int idx = -1;
+  for (size_t i = 0; i < g_prof.size(); ++i)
+    if (g_prof[i].name == family) idx = (int)i;
+  if (idx < 0) {
+    g_prof.push_back(ProfFamily());
+    g_prof.back().name = family;
+    idx = (int)g_prof.size() - 1;
+  }
+  ProfFamily& f = g_prof[idx];
+  f.launches++;
+  f.bytes += bytes;
+  f.flops += flops;
+  cudaEvent_t a = pool_event(), b = pool_event();
+  cudaEventRecord(a, s);
+  f.pending.push_back({a, b});
+  slot_ = idx;
+  if (f.pending.size() > 4096) prof_resolve_locked();
+}
+ProfScope::~ProfScope() {
+  if (slot_ < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot_ < (int)g_prof.size() && !g_prof[slot_].pending.empty())
+    cudaEventRecord(g_prof[slot_].pending.back().second, s_);
+}
+}  // namespace rfcmp
+
+// ---------------------------------------------------------------- factor cache
+struct DenseFactor {
+  int n = 0;
+  float* hi = nullptr;
+  float* lo = nullptr;
+  size_t bytes = 0;
+  int iterations = 0;
+  double ms = 0.0;
+  ~DenseFactor() {
+    if (hi) cudaFree(hi);
+    if (lo) cudaFree(lo);
+  }
+};
+
+struct rfcmp_ctx {
+  int device = 0;
+  uint64_t budget = 0;
+  std::atomic<uint64_t> bytes{0};
+  std::mutex mu;
+  std::map<uint64_t, std::shared_ptr<DenseFactor>> lplus_cache;  // key: connectivity hash
+  std::map<uint64_t, std::shared_ptr<DenseFactor>> gll_cache;    // key: connectivity + coordinates hash
+  std::atomic<int> live_ops{0};
+};
+
+struct Workspace {
+  int cols = 0;
+  std::vector<void*> owned;
+  // edge space (N)
+  double2 *v = nullptr, *u = nullptr, *y = nullptr, *up = nullptr, *tmpN = nullptr;
+  // cell space (N_C)
+  double2 *s = nullptr, *z = nullptr, *w = nullptr, *zu = nullptr, *q0 = nullptr, *q = nullptr, *Lq = nullptr,
+          *vp = nullptr;
+  // vertex space (N_V)
+  double2 *t = nullptr, *tg = nullptr;
+  double* mean = nullptr;  // 4 x cols
+  ~Workspace() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+struct SolveBuffers {
+  int cols = 0;
+  std::vector<void*> owned;
+  double2 *b = nullptr, *i = nullptr, *r = nullptr, *d = nullptr, *rin = nullptr, *p = nullptr, *Ap = nullptr,
+          *tmp = nullptr, *eh = nullptr, *jh = nullptr;
+  double2* dots = nullptr;  // cols
+  double *rho = nullptr, *alpha = nullptr, *beta = nullptr;
+  int* active = nullptr;
+  ~SolveBuffers() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+struct rfcmp_op {
+  rfcmp_ctx* ctx = nullptr;
+  Topology top;
+  std::vector<double> verts;
+  DeviceGeometry g;
+  std::vector<void*> owned;  // geometry + matrices
+  float2* TA = nullptr;
+  float2* V = nullptr;
+  int ldN = 0, ldC = 0;
+  std::shared_ptr<DenseFactor> lplus, gll;
+  double k = 0.0, alpha = 1.0, beta = 1.0, gamma = 1.0;
+  uint64_t bytes = 0;
+  rfcmp_op_info info{};
+  std::unique_ptr<Workspace> ws;
+  std::unique_ptr<SolveBuffers> sb;
+  ~rfcmp_op() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+namespace {
+
+uint64_t mix(uint64_t h, uint64_t v) {
+  uint64_t z = h ^ (v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2));
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int ensure_workspace(rfcmp_op* op, int cols) {
+  if (op->ws && op->ws->cols >= cols) return RFCMP_OK;
+  auto ws = std::make_unique<Workspace>();
+  ws->cols = cols;
+  const size_t N = op->top.ne, C = op->top.nc, NV = op->top.nv;
+  for (double2** p : {&ws->v, &ws->u, &ws->y, &ws->up, &ws->tmpN}) RF_TRY(dalloc(p, N * cols, ws->owned));
+  for (double2** p : {&ws->s, &ws->z, &ws->w, &ws->zu, &ws->q0, &ws->q, &ws->Lq, &ws->vp})
+    RF_TRY(dalloc(p, C * cols, ws->owned));
+  for (double2** p : {&ws->t, &ws->tg}) RF_TRY(dalloc(p, NV * cols, ws->owned));
+  RF_TRY(dalloc(&ws->mean, 4 * (size_t)cols, ws->owned));  // pgp_apply uses 4 per column
+  op->ws = std::move(ws);
+  return RFCMP_OK;
+}
+
+int ensure_solve_buffers(rfcmp_op* op, int cols) {
+  if (op->sb && op->sb->cols >= cols) return RFCMP_OK;
+  auto sb = std::make_unique<SolveBuffers>();
+  sb->cols = cols;
+  const size_t N = op->top.ne;
+  for (double2** p : {&sb->b, &sb->i, &sb->r, &sb->d, &sb->rin, &sb->p, &sb->Ap, &sb->tmp})
+    RF_TRY(dalloc(p, N * cols, sb->owned));
+  RF_TRY(dalloc(&sb->dots, cols, sb->owned));
+  RF_TRY(dalloc(&sb->rho, cols, sb->owned));
+  RF_TRY(dalloc(&sb->alpha, cols, sb->owned));
+  RF_TRY(dalloc(&sb->beta, cols, sb->owned));
+  RF_TRY(dalloc(&sb->active, cols, sb->owned));
+  op->sb = std::move(sb);
+  return RFCMP_OK;
+}
+
+#define RF_K(call)                                                                                      \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return set_error(RFCMP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---- building blocks of the application, nrhs columns, column-major ----
+// z = (Sigma^T Sigma)^+ Sigma^T x  (N_C) using s as scratch for Sigma^T x
+int star_coeff(rfcmp_op* op, const double2* x, double2* s, double2* z, int nr, GemvMode m, cudaStream_t st) {
+  RF_K(sigma_t(op->g, x, s, nr, st));
+  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, (int)op->top.nc, s, z, nr, 1.0, false, m, st));
+  return RFCMP_OK;
+}
+
+// out = A x (Sec. 3 Eq. NewFormulation, numerical variant of Sec. 4) in the
+// low-frequency-stable order: analytically vanishing products are not formed.
+int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cudaStream_t st) {
+  RF_TRY(ensure_workspace(op, nr));
+  Workspace& W = *op->ws;
+  const DeviceGeometry& g = op->g;
+  const double k = op->k, a = op->alpha, b = op->beta, gm = op->gamma;
+  const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
+  // s = Sigma^T x, z = L^+ s
+  RF_TRY(star_coeff(op, x, W.s, W.z, nr, m, st));
+  // v = (ik/a) x - (ik/a + k/b) Sigma z      = i k x_L / a - k x_S / b
+  {
+    EdgeCombo c;
+    c.x = x;
+    c.a = c2(0.0, k / a);
+    c.zs = W.z;
+    c.b = c2(-k / b, -k / a);
+    RF_K(edge_combo(g, c, W.v, nr, st));
+  }
+  // u = T_A v ; w = V Sigma^T x / (k b)
+  RF_K(gemv_c64(op->TA, N, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, st));
+  RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, st));
+  // zu = L^+ Sigma^T u ; tg = G_ll^{-1} Lambda^T u
+  RF_TRY(star_coeff(op, W.u, W.s, W.zu, nr, m, st));
+  RF_K(lambda_t(g, W.u, W.t, nr, st));
+  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, st));
+  // q = L^+ G_pp^{-1} (zu + w - mean(w)) / b^2
+  RF_K(star_middle(g, W.zu, W.w, 1.0, W.q0, nr, W.mean, st));
+  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+  // y = Lambda tg / a^2 + (u - Sigma zu) / gamma + Sigma q
+  {
+    EdgeCombo c;
+    c.zl = W.tg;
+    c.c = c2(1.0 / (a * a), 0.0);
+    c.x = W.u;
+    c.a = c2(1.0 / gm, 0.0);
+    c.zs = W.zu;
+    c.b = c2(-1.0 / gm, 0.0);
+    c.zs2 = W.q;
+    c.d = c2(1.0, 0.0);
+    RF_K(edge_combo(g, c, W.y, nr, st));
+  }
+  // up = conj(T_A) y ; vp = conj(V) (Sigma^T Sigma) q / (k b)
+  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
+  RF_K(lap_apply(g, W.q, W.Lq, nr, st));
+  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, st));
+  // zp = L^+ Sigma^T up
+  RF_TRY(star_coeff(op, W.up, W.s, W.z, nr, m, st));
+  // out = -(ik/a) up + (ik/a - k/b) Sigma zp + Sigma vp
+  {
+    EdgeCombo c;
+    c.x = W.up;
+    c.a = c2(0.0, -k / a);
+    c.zs = W.z;
+    c.b = c2(-k / b, k / a);
+    c.zs2 = W.vp;
+    c.d = c2(1.0, 0.0);
+    RF_K(edge_combo(g, c, out, nr, st));
+  }
+  return RFCMP_OK;
+}
+
+// b = -P_o^H T^H P_m e in the same order
+int apply_rhs(rfcmp_op* op, const double2* e, double2* out, int nr, GemvMode m, cudaStream_t st) {
+  RF_TRY(ensure_workspace(op, nr));
+  Workspace& W = *op->ws;
+  const DeviceGeometry& g = op->g;
+  const double k = op->k, a = op->alpha, b = op->beta, gm = op->gamma;
+  const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
+  RF_TRY(star_coeff(op, e, W.s, W.zu, nr, m, st));  // ze
+  RF_K(star_middle(g, W.zu, nullptr, 1.0, W.q0, nr, W.mean, st));
+  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+  RF_K(lambda_t(g, e, W.t, nr, st));
+  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, st));
+  {
+    EdgeCombo c;
+    c.zl = W.tg;
+    c.c = c2(1.0 / (a * a), 0.0);
+    c.x = e;
+    c.a = c2(1.0 / gm, 0.0);
+    c.zs = W.zu;
+    c.b = c2(-1.0 / gm, 0.0);
+    c.zs2 = W.q;
+    c.d = c2(1.0, 0.0);
+    RF_K(edge_combo(g, c, W.y, nr, st));
+  }
+  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
+  RF_K(lap_apply(g, W.q, W.Lq, nr, st));
+  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0, 0.0), false, m, st));
+  {  // th = -ik up + (i/k) Sigma vp
+    EdgeCombo c;
+    c.x = W.up;
+    c.a = c2(0.0, -k);
+    c.zs = W.vp;
+    c.b = c2(0.0, 1.0 / k);
+    RF_K(edge_combo(g, c, W.tmpN, nr, st));
+  }
+  RF_TRY(star_coeff(op, W.tmpN, W.s, W.z, nr, m, st));
+  {  // out = -th / a + Sigma zt (1/a + i/b)
+    EdgeCombo c;
+    c.x = W.tmpN;
+    c.a = c2(-1.0 / a, 0.0);
+    c.zs = W.z;
+    c.b = c2(1.0 / a, 1.0 / b);
+    RF_K(edge_combo(g, c, out, nr, st));
+  }
+  return RFCMP_OK;
+}
+
+// P_o x (adj: P_o^H x) = x / a + Sigma z (-1/a +- i/b)
+int apply_Po(rfcmp_op* op, const double2* x, double2* out, int nr, bool adj, GemvMode m, cudaStream_t st) {
+  RF_TRY(ensure_workspace(op, nr));
+  Workspace& W = *op->ws;
+  RF_TRY(star_coeff(op, x, W.s, W.z, nr, m, st));
+  EdgeCombo c;
+  c.x = x;
+  c.a = c2(1.0 / op->alpha, 0.0);
+  c.zs = W.z;
+  c.b = c2(-1.0 / op->alpha, adj ? -1.0 / op->beta : 1.0 / op->beta);
+  RF_K(edge_combo(op->g, c, out, nr, st));
+  return RFCMP_OK;
+}
+
+// ---- power iteration operators (unscaled by k, module reading of Sec. 4) ----
+// X x = P_LH T_A^H Lambda G^{-1} Lambda^T T_A P_LH x
+int op_X(rfcmp_op* op, const double2* x, double2* out, cudaStream_t st) {
+  Workspace& W = *op->ws;
+  const int N = (int)op->top.ne, NV = (int)op->top.nv;
+  const GemvMode m = GEMV_F32;
+  RF_TRY(star_coeff(op, x, W.s, W.z, 1, m, st));
+  EdgeCombo c;
+  c.x = x;
+  c.a = c2(1, 0);
+  c.zs = W.z;
+  c.b = c2(-1, 0);
+  RF_K(edge_combo(op->g, c, W.v, 1, st));
+  RF_K(gemv_c64(op->TA, N, W.v, W.u, 1, false, c2(1, 0), false, m, st));
+  RF_K(lambda_t(op->g, W.u, W.t, 1, st));
+  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, 1, 1.0, false, m, st));
+  EdgeCombo l;
+  l.zl = W.tg;
+  l.c = c2(1, 0);
+  RF_K(edge_combo(op->g, l, W.y, 1, st));
+  RF_K(gemv_c64(op->TA, N, W.y, W.up, 1, true, c2(1, 0), false, m, st));
+  RF_TRY(star_coeff(op, W.up, W.s, W.z, 1, m, st));
+  EdgeCombo o;
+  o.x = W.up;
+  o.a = c2(1, 0);
+  o.zs = W.z;
+  o.b = c2(-1, 0);
+  RF_K(edge_combo(op->g, o, out, 1, st));
+  return RFCMP_OK;
+}
+
+// Z x = P_LH T_A^H P_LH T_A P_LH x
+int op_Z(rfcmp_op* op, const double2* x, double2* out, cudaStream_t st) {
+  Workspace& W = *op->ws;
+  const int N = (int)op->top.ne;
+  const GemvMode m = GEMV_F32;
+  EdgeCombo c;
+  c.a = c2(1, 0);
+  c.b = c2(-1, 0);
+  RF_TRY(star_coeff(op, x, W.s, W.z, 1, m, st));
+  c.x = x;
+  c.zs = W.z;
+  RF_K(edge_combo(op->g, c, W.v, 1, st));
+  RF_K(gemv_c64(op->TA, N, W.v, W.u, 1, false, c2(1, 0), false, m, st));
+  RF_TRY(star_coeff(op, W.u, W.s, W.z, 1, m, st));
+  c.x = W.u;
+  RF_K(edge_combo(op->g, c, W.y, 1, st));
+  RF_K(gemv_c64(op->TA, N, W.y, W.up, 1, true, c2(1, 0), false, m, st));
+  RF_TRY(star_coeff(op, W.up, W.s, W.z, 1, m, st));
+  c.x = W.up;
+  RF_K(edge_combo(op->g, c, out, 1, st));
+  return RFCMP_OK;
+}
+
+// Y x = P_S T_Phi^H M_S T_Phi P_S x = Sigma conj(V) Pi G_pp^{-1} Pi V Sigma^T x,  Pi = I - 1 1^T / N_C
+// (Sigma^T P_S = Sigma^T, (Sigma^T Sigma)(Sigma^T Sigma)^+ = Pi, P_S Sigma = Sigma)
+int op_Y(rfcmp_op* op, const double2* x, double2* out, cudaStream_t st) {
+  Workspace& W = *op->ws;
+  const int C = (int)op->top.nc;
+  const GemvMode m = GEMV_F32;
+  RF_K(sigma_t(op->g, x, W.s, 1, st));
+  RF_K(gemv_c64(op->V, C, W.s, W.w, 1, false, c2(1, 0), false, m, st));
+  RF_K(pgp_apply(op->g, W.w, W.q0, 1, W.mean, st));
+  RF_K(gemv_c64(op->V, C, W.q0, W.vp, 1, true, c2(1, 0), false, m, st));
+  EdgeCombo c;
+  c.zs = W.vp;
+  c.b = c2(1, 0);
+  RF_K(edge_combo(op->g, c, out, 1, st));
+  return RFCMP_OK;
+}
+
+// deterministic start vector: splitmix64(seed * 2^32 + i) top 53 bits / 2^53 - 1/2 (real)
+void splitmix_start(std::vector<double2>& h, int64_t n, uint64_t seed) {
+  h.resize(n);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t z = seed * (1ull << 32) + (uint64_t)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    h[i] = make_double2((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5, 0.0);
+  }
+}
+
+// largest eigenvalue of an HPSD operator by `steps` normalised power steps (Rayleigh quotient)
+template <class Op>
+int power_norm(rfcmp_op* op, Op apply, uint64_t seed, int steps, double* lam, cudaStream_t st) {
+  const int64_t N = op->top.ne;
+  RF_TRY(ensure_solve_buffers(op, 1));
+  RF_TRY(ensure_workspace(op, 1));
+  SolveBuffers& B = *op->sb;
+  std::vector<double2> h;
+  splitmix_start(h, N, seed);
+  RF_CUDA(cudaMemcpyAsync(B.p, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, st));
+  double2 nn;
+  RF_K(vec_dot(B.p, B.p, N, 1, B.dots, st));
+  RF_CUDA(cudaMemcpyAsync(&nn, B.dots, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  RF_K(vec_scale(B.p, c2(1.0 / std::sqrt(nn.x), 0.0), N, st));
+  double l = 0.0;
+  for (int it = 0; it < steps; ++it) {
+    RF_TRY(apply(op, B.p, B.Ap, st));
+    double2 pr[2];
+    RF_K(vec_dot(B.p, B.Ap, N, 1, B.dots, st));
+    RF_CUDA(cudaMemcpyAsync(&pr[0], B.dots, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    RF_K(vec_dot(B.Ap, B.Ap, N, 1, B.dots, st));
+    RF_CUDA(cudaMemcpyAsync(&pr[1], B.dots, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    RF_CUDA(cudaStreamSynchronize(st));
+    l = pr[0].x;
+    if (!(pr[1].x > 0.0)) break;
+    RF_K(vec_copy(B.Ap, B.p, N, st));
+    RF_K(vec_scale(B.p, c2(1.0 / std::sqrt(pr[1].x), 0.0), N, st));
+  }
+  *lam = l;
+  return RFCMP_OK;
+}
+
+int compute_scaling(rfcmp_op* op, const rfcmp_op_opts& o, cudaStream_t st) {
+  const double k = op->k;
+  if (o.scaling == RFCMP_SCALE_K) {
+    op->alpha = std::sqrt(k);
+    op->beta = 1.0 / std::sqrt(k);
+    op->gamma = k;
+    return RFCMP_OK;
+  }
+  if (o.scaling == RFCMP_SCALE_FIXED) {
+    op->alpha = o.alpha;
+    op->beta = o.beta;
+    op->gamma = o.gamma;
+    return RFCMP_OK;
+  }
+  double nx = 0, ny = 0, nz = 0;
+  RF_TRY(power_norm(op, op_X, 1, o.power_steps, &nx, st));
+  RF_TRY(power_norm(op, op_Y, 2, o.power_steps, &ny, st));
+  RF_TRY(power_norm(op, op_Z, 3, o.power_steps, &nz, st));
+  // alpha^4 = k^2 ||X||, beta^4 = ||Y|| / k^2, gamma = k^2 ||Z|| / alpha^2 (frequency-scaled reading)
+  op->alpha = std::pow(k * k * nx, 0.25);
+  op->beta = std::pow(ny / (k * k), 0.25);
+  op->gamma = k * k / (op->alpha * op->alpha) * nz;
+  if (!(op->alpha > 0) || !(op->beta > 0) || !(op->gamma > 0) || !std::isfinite(op->alpha) ||
+      !std::isfinite(op->beta) || !std::isfinite(op->gamma))
+    return set_error(RFCMP_ERR_CUDA, "power iteration produced a non-positive or non-finite scaling");
+  return RFCMP_OK;
+}
+
+// ---- geometry upload ----
+int upload_geometry(rfcmp_op* op) {
+  const Topology& T = op->top;
+  const int64_t nc = T.nc, nv = T.nv;
+  const double* X = op->verts.data();
+  static const Rule7 R;
+  std::vector<double> area(nc), cen(3 * nc), qp(21 * nc);
+  std::vector<float> cen_hi(3 * nc), cen_lo(3 * nc), rho(21 * nc), wq(7 * nc), aloc(9 * nc), inv_area(nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    const double* P[3] = {X + 3 * T.tris[3 * c], X + 3 * T.tris[3 * c + 1], X + 3 * T.tris[3 * c + 2]};
+    double u[3], v[3];
+    for (int a = 0; a < 3; ++a) {
+      u[a] = P[1][a] - P[0][a];
+      v[a] = P[2][a] - P[0][a];
+    }
+    const double cr0 = u[1] * v[2] - u[2] * v[1], cr1 = u[2] * v[0] - u[0] * v[2], cr2 = u[0] * v[1] - u[1] * v[0];
+    area[c] = 0.5 * std::sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+    if (!(area[c] > 0.0)) return set_error(RFCMP_ERR_MESH_NOT_MANIFOLD, "cell " + std::to_string(c) + " has zero area");
+    for (int a = 0; a < 3; ++a) cen[3 * c + a] = (P[0][a] + P[1][a] + P[2][a]) / 3.0;
+    for (int q = 0; q < 7; ++q)
+      for (int a = 0; a < 3; ++a)
+        qp[21 * c + 3 * q + a] = R.bary[q][0] * P[0][a] + R.bary[q][1] * P[1][a] + R.bary[q][2] * P[2][a];
+    for (int a = 0; a < 3; ++a) {
+      cen_hi[3 * c + a] = (float)cen[3 * c + a];
+      cen_lo[3 * c + a] = (float)(cen[3 * c + a] - (double)cen_hi[3 * c + a]);
+    }
+    for (int q = 0; q < 7; ++q) {
+      for (int a = 0; a < 3; ++a) rho[21 * c + 3 * q + a] = (float)(qp[21 * c + 3 * q + a] - cen[3 * c + a]);
+      wq[7 * c + q] = (float)(R.w[q] * area[c]);
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < 3; ++a) aloc[9 * c + 3 * i + a] = (float)(P[i][a] - cen[3 * c + a]);
+    inv_area[c] = (float)(1.0 / area[c]);
+  }
+  DeviceGeometry& g = op->g;
+  g.nc = (int32_t)nc;
+  g.ne = (int32_t)T.ne;
+  g.nv = (int32_t)nv;
+  g.ldN = padded_ld((int)T.ne);
+  g.ldC = padded_ld((int)nc);
+  auto& own = op->owned;
+  RF_TRY(upload(&g.cen_hi, cen_hi, own));
+  RF_TRY(upload(&g.cen_lo, cen_lo, own));
+  RF_TRY(upload(&g.rho, rho, own));
+  RF_TRY(upload(&g.wq, wq, own));
+  RF_TRY(upload(&g.aloc, aloc, own));
+  RF_TRY(upload(&g.inv_area, inv_area, own));
+  RF_TRY(upload(&g.verts, op->verts, own));
+  RF_TRY(upload(&g.cen64, cen, own));
+  RF_TRY(upload(&g.area64, area, own));
+  RF_TRY(upload(&g.qp64, qp, own));
+  RF_TRY(upload(&g.tris, T.tris, own));
+  RF_TRY(upload(&g.cell_edges, T.cell_edges, own));
+  RF_TRY(upload(&g.cell_sign, T.cell_sign, own));
+  RF_TRY(upload(&g.edge_cells, T.edge_cells, own));
+  RF_TRY(upload(&g.edge_verts, T.edge_verts, own));
+  RF_TRY(upload(&g.edge_free, T.edge_free, own));
+  RF_TRY(upload(&g.vtx_ptr, T.vtx_ptr, own));
+  RF_TRY(upload(&g.vtx_edge, T.vtx_edge, own));
+  RF_TRY(upload(&g.vtx_sign, T.vtx_sign, own));
+  RF_TRY(upload(&g.lap_ptr, T.lap_ptr, own));
+  RF_TRY(upload(&g.lap_col, T.lap_col, own));
+  RF_TRY(upload(&g.near_pairs, T.near_pairs, own));
+  g.n_near = (int32_t)(T.near_pairs.size() / 2);
+  return RFCMP_OK;
+}
+
+// dense inverse of a sparse SPD matrix (CSR on the host), FP32 hi + lo planes
+int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col, const std::vector<double>& val,
+                 int n, bool project, double tol, std::shared_ptr<DenseFactor>& out) {
+  auto f = std::make_shared<DenseFactor>();
+  f->n = n;
+  const size_t ld = (size_t)padded_ld(n);
+  f->bytes = 2 * ld * (size_t)n * sizeof(float);
+  RF_CUDA(cudaMalloc(&f->hi, ld * n * sizeof(float)));
+  RF_CUDA(cudaMalloc(&f->lo, ld * n * sizeof(float)));
+  RF_CUDA(cudaMemset(f->hi, 0, ld * n * sizeof(float)));
+  RF_CUDA(cudaMemset(f->lo, 0, ld * n * sizeof(float)));
+  std::vector<void*> tmp;
+  int32_t *dptr = nullptr, *dcol = nullptr;
+  double* dval = nullptr;
+  int rc = upload(&dptr, ptr, tmp);
+  if (rc == RFCMP_OK) rc = upload(&dcol, col, tmp);
+  if (rc == RFCMP_OK) rc = upload(&dval, val, tmp);
+  if (rc != RFCMP_OK) {
+    for (void* p : tmp) cudaFree(p);
+    return rc;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, 0);
+  int iters = 0;
+  cudaError_t err = dense_inverse_block_cg(dptr, dcol, dval, n, project, tol, 20000, f->hi, f->lo, &iters, 0);
+  cudaEventRecord(e1, 0);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (void* p : tmp) cudaFree(p);
+  if (err != cudaSuccess) return set_error(RFCMP_ERR_CUDA, std::string("dense inverse: ") + cudaGetErrorString(err));
+  f->iterations = iters;
+  f->ms = ms;
+  out = f;
+  return RFCMP_OK;
+}
+
+int check_device(int device) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0)
+    return set_error(RFCMP_ERR_NO_DEVICE, "no CUDA device visible");
+  if (device < 0 || device >= count) return set_error(RFCMP_ERR_INVALID_ARG, "device ordinal out of range");
+  cudaDeviceProp p;
+  RF_CUDA(cudaGetDeviceProperties(&p, device));
+  if (p.major != 10 || p.minor != 3)
+    return set_error(RFCMP_ERR_NO_DEVICE, std::string("device is sm_") + std::to_string(p.major) +
+                                              std::to_string(p.minor) + ", this library is built for sm_103a");
+  return RFCMP_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* rfcmp_strerror(int st) {
+  switch (st) {
+    case RFCMP_OK: return "ok";
+    case RFCMP_ERR_INVALID_ARG: return "invalid argument";
+    case RFCMP_ERR_MESH_NOT_MANIFOLD: return "mesh is not a closed 2-manifold";
+    case RFCMP_ERR_MESH_ORIENTATION: return "mesh is not consistently oriented";
+    case RFCMP_ERR_OUT_OF_BUDGET: return "HBM budget exceeded";
+    case RFCMP_ERR_CUDA: return "CUDA error";
+    case RFCMP_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case RFCMP_ERR_NOT_CONVERGED: return "solve did not converge";
+    case RFCMP_ERR_NO_DEVICE: return "no usable sm_103 device";
+    default: return "unknown status";
+  }
+}
+
+const char* rfcmp_last_error(void) { return g_last_error.c_str(); }
+
+int rfcmp_profile_enable(int enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_resolve_locked();
+  g_prof.clear();
+  g_prof_on.store(enable != 0);
+  return RFCMP_OK;
+}
+
+int rfcmp_profile_read(rfcmp_profile_entry* out, int max_entries, int* n_entries) {
+  if (!n_entries || (max_entries > 0 && !out)) return set_error(RFCMP_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_resolve_locked();
+  *n_entries = (int)g_prof.size();
+  for (int i = 0; i < max_entries && i < (int)g_prof.size(); ++i) {
+    std::memset(&out[i], 0, sizeof(out[i]));
+    std::strncpy(out[i].name, g_prof[i].name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = g_prof[i].launches;
+    out[i].total_ms = g_prof[i].ms;
+    out[i].bytes = g_prof[i].bytes;
+    out[i].flops = g_prof[i].flops;
+  }
+  return RFCMP_OK;
+}
+
+void rfcmp_op_opts_default(rfcmp_op_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->scaling = RFCMP_SCALE_POWER;
+  o->power_steps = 30;
+  o->alpha = o->beta = o->gamma = 1.0;
+  o->factor_tol = 1e-13;
+}
+
+void rfcmp_solve_opts_default(rfcmp_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->max_iter = 2000;
+  o->max_refine = 8;
+  o->inner_tol = 1e-4;
+  o->precision = RFCMP_PREC_MIXED;
+}
+
+int rfcmp_ctx_create(int device, uint64_t budget, rfcmp_ctx** out) {
+  if (!out) return set_error(RFCMP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  RF_TRY(check_device(device));
+  RF_CUDA(cudaSetDevice(device));
+  RF_CUDA(cudaFree(0));
+  auto* c = new rfcmp_ctx();
+  c->device = device;
+  c->budget = budget;
+  *out = c;
+  return RFCMP_OK;
+}
+
+int rfcmp_ctx_destroy(rfcmp_ctx* ctx) {
+  if (!ctx) return RFCMP_OK;
+  if (ctx->live_ops.load() != 0) return set_error(RFCMP_ERR_INVALID_ARG, "context still has live ops");
+  cudaSetDevice(ctx->device);
+  delete ctx;
+  return RFCMP_OK;
+}
+
+int rfcmp_ctx_clear_cache(rfcmp_ctx* ctx) {
+  if (!ctx) return set_error(RFCMP_ERR_INVALID_ARG, "ctx is NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  for (auto& kv : ctx->lplus_cache)
+    if (kv.second.use_count() == 1) ctx->bytes -= kv.second->bytes;
+  for (auto& kv : ctx->gll_cache)
+    if (kv.second.use_count() == 1) ctx->bytes -= kv.second->bytes;
+  ctx->lplus_cache.clear();
+  ctx->gll_cache.clear();
+  return RFCMP_OK;
+}
+
+uint64_t rfcmp_ctx_bytes_in_use(const rfcmp_ctx* ctx) { return ctx ? ctx->bytes.load() : 0; }
+
+int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nc, double k,
+                    const rfcmp_op_opts* opts_in, rfcmp_op** out) {
+  if (!ctx || !verts || !tris || !out) return set_error(RFCMP_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (!(k > 0.0) || !std::isfinite(k)) return set_error(RFCMP_ERR_INVALID_ARG, "k must be positive and finite");
+  rfcmp_op_opts o;
+  rfcmp_op_opts_default(&o);
+  if (opts_in) o = *opts_in;
+  for (int i = 0; i < 8; ++i)
+    if (o.reserved[i] != 0) return set_error(RFCMP_ERR_INVALID_ARG, "opts.reserved must be zero");
+  if (o.scaling < 0 || o.scaling > 2 || o.power_steps < 1 || !(o.factor_tol > 0.0))
+    return set_error(RFCMP_ERR_INVALID_ARG, "invalid op options");
+  if (o.scaling == RFCMP_SCALE_FIXED && !(o.alpha > 0 && o.beta > 0 && o.gamma > 0))
+    return set_error(RFCMP_ERR_INVALID_ARG, "fixed scaling needs positive alpha, beta, gamma");
+  for (int64_t i = 0; i < 3 * nv; ++i)
+    if (!std::isfinite(verts[i])) return set_error(RFCMP_ERR_INVALID_ARG, "non-finite vertex coordinate");
+  RF_CUDA(cudaSetDevice(ctx->device));
+  auto op = std::make_unique<rfcmp_op>();
+  op->ctx = ctx;
+  op->k = k;
+  std::string err;
+  int rc = build_topology(tris, nc, nv, op->top, err);
+  if (rc != RFCMP_OK) return set_error(rc, err);
+  if (op->top.ne >= (1ll << 31) / 1 || (double)op->top.ne * op->top.ne > 9e18)
+    return set_error(RFCMP_ERR_INVALID_ARG, "mesh too large");
+  op->verts.assign(verts, verts + 3 * nv);
+  const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
+  op->ldN = padded_ld(N);
+  op->ldC = padded_ld(C);
+  const uint64_t mat_bytes = (uint64_t)op->ldN * N * 8 + (uint64_t)op->ldC * C * 8;
+  // factor cache lookups
+  uint64_t geo_hash = op->top.hash;
+  for (int64_t i = 0; i < 3 * nv; ++i) {
+    uint64_t b;
+    std::memcpy(&b, &verts[i], 8);
+    geo_hash = mix(geo_hash, b);
+  }
+  std::shared_ptr<DenseFactor> lp, gl;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto a = ctx->lplus_cache.find(op->top.hash);
+    if (a != ctx->lplus_cache.end()) lp = a->second;
+    auto b = ctx->gll_cache.find(geo_hash);
+    if (b != ctx->gll_cache.end()) gl = b->second;
+  }
+  uint64_t need = mat_bytes;
+  if (!lp) need += 2ull * padded_ld(C) * C * 4;
+  if (!gl) need += 2ull * padded_ld(NV) * NV * 4;
+  if (ctx->budget && ctx->bytes.load() + need > ctx->budget)
+    return set_error(RFCMP_ERR_OUT_OF_BUDGET, "op needs " + std::to_string(need) + " bytes, budget has " +
+                                                  std::to_string(ctx->budget - std::min(ctx->budget, ctx->bytes.load())));
+  RF_TRY(upload_geometry(op.get()));
+  // topology factors
+  op->info.ms_factors = 0.0;
+  if (!lp) {
+    RF_TRY(build_factor(op->top.lap_ptr, op->top.lap_col, op->top.lap_val, C, true, o.factor_tol, lp));
+    op->info.ms_factors += lp->ms;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->lplus_cache[op->top.hash] = lp;
+    ctx->bytes += lp->bytes;
+  }
+  if (!gl) {
+    std::vector<int32_t> mp, mc;
+    std::vector<double> mv;
+    mass_matrix_csr(op->top, op->verts.data(), mp, mc, mv);
+    RF_TRY(build_factor(mp, mc, mv, NV, false, o.factor_tol, gl));
+    op->info.ms_factors += gl->ms;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->gll_cache[geo_hash] = gl;
+    ctx->bytes += gl->bytes;
+  }
+  op->lplus = lp;
+  op->gll = gl;
+  op->info.factor_iterations_lplus = lp->iterations;
+  op->info.factor_iterations_gll = gl->iterations;
+  // assembly
+  RF_CUDA(cudaMalloc(&op->TA, (size_t)op->ldN * N * sizeof(float2)));
+  op->owned.push_back(op->TA);
+  RF_CUDA(cudaMalloc(&op->V, (size_t)op->ldC * C * sizeof(float2)));
+  op->owned.push_back(op->V);
+  op->bytes = mat_bytes;
+  rfcmp_op* raw = op.get();
+  cudaEvent_t e0, e1, e2;
+  RF_CUDA(cudaEventCreate(&e0));
+  RF_CUDA(cudaEventCreate(&e1));
+  RF_CUDA(cudaEventCreate(&e2));
+  RF_CUDA(cudaEventRecord(e0, 0));
+  RF_CUDA(cudaMemsetAsync(op->TA, 0, (size_t)op->ldN * N * sizeof(float2), 0));
+  RF_CUDA(cudaMemsetAsync(op->V, 0, (size_t)op->ldC * C * sizeof(float2), 0));
+  RF_K(launch_assemble_far(op->g, (float)k, op->TA, op->V, 0));
+  RF_K(launch_assemble_near(op->g, k, op->TA, op->V, 0));
+  RF_CUDA(cudaEventRecord(e1, 0));
+  rc = compute_scaling(raw, o, 0);
+  RF_CUDA(cudaEventRecord(e2, 0));
+  RF_CUDA(cudaEventSynchronize(e2));
+  float ms_a = 0.f, ms_s = 0.f;
+  cudaEventElapsedTime(&ms_a, e0, e1);
+  cudaEventElapsedTime(&ms_s, e1, e2);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (rc != RFCMP_OK) return rc;
+  RF_CUDA(cudaGetLastError());
+  ctx->bytes += op->bytes;
+  ctx->live_ops++;
+  op->info.n_edges = N;
+  op->info.n_vertices = NV;
+  op->info.n_cells = C;
+  op->info.genus = op->top.genus;
+  op->info.k = k;
+  op->info.alpha = op->alpha;
+  op->info.beta = op->beta;
+  op->info.gamma = op->gamma;
+  op->info.ms_assembly = ms_a;
+  op->info.ms_scaling = ms_s;
+  *out = op.release();
+  return RFCMP_OK;
+}
+
+int rfcmp_op_info_get(const rfcmp_op* op, rfcmp_op_info* out) {
+  if (!op || !out) return set_error(RFCMP_ERR_INVALID_ARG, "NULL argument");
+  *out = op->info;
+  uint64_t ws = 0;
+  if (op->ws) ws += (uint64_t)op->ws->cols * (5 * op->top.ne + 8 * op->top.nc + 2 * op->top.nv) * 16;
+  if (op->sb) ws += (uint64_t)op->sb->cols * 8 * op->top.ne * 16;
+  out->device_bytes = op->bytes + ws;
+  return RFCMP_OK;
+}
+
+int rfcmp_op_destroy(rfcmp_op* op) {
+  if (!op) return RFCMP_OK;
+  rfcmp_ctx* ctx = op->ctx;
+  cudaSetDevice(ctx->device);
+  ctx->bytes -= op->bytes;
+  ctx->live_ops--;
+  delete op;
+  return RFCMP_OK;
+}
+
+int rfcmp_op_export(const rfcmp_op* op, int which, void* dst, uint64_t dst_bytes, void* stream) {
+  if (!op || !dst) return set_error(RFCMP_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
+  if (which == 0 || which == 1) {
+    const int n = which == 0 ? N : C;
+    const int ld = which == 0 ? op->ldN : op->ldC;
+    if (dst_bytes < (uint64_t)n * n * 8) return set_error(RFCMP_ERR_INVALID_ARG, "destination too small");
+    const float2* M = which == 0 ? op->TA : op->V;
+    RF_CUDA(cudaMemcpy2DAsync(dst, (size_t)n * 8, M, (size_t)ld * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice, st));
+    return RFCMP_OK;
+  }
+  if (which == 2 || which == 3) {
+    const DenseFactor& f = which == 2 ? *op->lplus : *op->gll;
+    const int n = which == 2 ? C : NV;
+    if (dst_bytes < (uint64_t)n * n * 8) return set_error(RFCMP_ERR_INVALID_ARG, "destination too small");
+    // hi and lo planes side by side: first n*n floats hi, then n*n floats lo
+    float* d = static_cast<float*>(dst);
+    const int ld = padded_ld(n);
+    RF_CUDA(cudaMemcpy2DAsync(d, (size_t)n * 4, f.hi, (size_t)ld * 4, (size_t)n * 4, n, cudaMemcpyDeviceToDevice, st));
+    RF_CUDA(cudaMemcpy2DAsync(d + (size_t)n * n, (size_t)n * 4, f.lo, (size_t)ld * 4, (size_t)n * 4, n,
+                              cudaMemcpyDeviceToDevice, st));
+    return RFCMP_OK;
+  }
+  return set_error(RFCMP_ERR_INVALID_ARG, "unknown matrix id");
+}
+
+int rfcmp_op_edges(const rfcmp_op* op, int32_t* edge_verts, int32_t* edge_cells) {
+  if (!op || !edge_verts || !edge_cells) return set_error(RFCMP_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(edge_verts, op->top.edge_verts.data(), op->top.edge_verts.size() * 4);
+  std::memcpy(edge_cells, op->top.edge_cells.data(), op->top.edge_cells.size() * 4);
+  return RFCMP_OK;
+}
+
+int rfcmp_rhs_planewave(rfcmp_op* op, const double* khat, const double* pol, int64_t nrhs, rfcmp_c128* e,
+                        void* stream) {
+  if (!op || !khat || !pol || !e || nrhs <= 0 || nrhs > 65535)
+    return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* d = nullptr;
+  RF_CUDA(cudaMallocAsync(&d, sizeof(double) * 6 * nrhs, st));
+  RF_CUDA(cudaMemcpyAsync(d, khat, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, st));
+  RF_CUDA(cudaMemcpyAsync(d + 3 * nrhs, pol, sizeof(double) * 3 * nrhs, cudaMemcpyHostToDevice, st));
+  RF_K(launch_rhs_planewave(op->g, op->k, d, d + 3 * nrhs, (int)nrhs, reinterpret_cast<double2*>(e), st));
+  RF_CUDA(cudaFreeAsync(d, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  return RFCMP_OK;
+}
+
+int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout, int64_t nrhs, void* stream) {
+  if (!op || !xin || !yout || nrhs <= 0 || nrhs > 4096) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double2* x = reinterpret_cast<const double2*>(xin);
+  double2* y = reinterpret_cast<double2*>(yout);
+  const int nr = (int)nrhs;
+  const int N = (int)op->top.ne, C = (int)op->top.nc;
+  const double k = op->k;
+  const GemvMode m = GEMV_FF;
+  RF_TRY(ensure_workspace(op, nr));
+  Workspace& W = *op->ws;
+  switch (which) {
+    case RFCMP_APPLY_T_A:
+      RF_K(gemv_c64(op->TA, N, x, y, nr, false, c2(1, 0), false, m, st));
+      return RFCMP_OK;
+    case RFCMP_APPLY_T_PHI: {
+      RF_K(sigma_t(op->g, x, W.s, nr, st));
+      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1, 0), false, m, st));
+      EdgeCombo c;
+      c.zs = W.w;
+      c.b = c2(1, 0);
+      RF_K(edge_combo(op->g, c, y, nr, st));
+      return RFCMP_OK;
+    }
+    case RFCMP_APPLY_T:
+    case RFCMP_APPLY_T_ADJ: {
+      const bool adj = which == RFCMP_APPLY_T_ADJ;
+      RF_K(sigma_t(op->g, x, W.s, nr, st));
+      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, adj, c2(1, 0), false, m, st));
+      RF_K(gemv_c64(op->TA, N, x, W.u, nr, adj, c2(1, 0), false, m, st));
+      // T x = i k T_A x - (i/k) Sigma V Sigma^T x ; T^H x = -i k conj(T_A) x + (i/k) Sigma conj(V) Sigma^T x
+      EdgeCombo c;
+      c.x = W.u;
+      c.a = c2(0.0, adj ? -k : k);
+      c.zs = W.w;
+      c.b = c2(0.0, adj ? 1.0 / k : -1.0 / k);
+      RF_K(edge_combo(op->g, c, y, nr, st));
+      return RFCMP_OK;
+    }
+    case RFCMP_APPLY_A:
+      return apply_A(op, x, y, nr, m, st);
+    default:
+      return set_error(RFCMP_ERR_INVALID_ARG, "unknown operator id");
+  }
+}
+
+int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout, int64_t nrhs, void* stream) {
+  if (!op || !xin || !yout || nrhs <= 0 || nrhs > 4096) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double2* x = reinterpret_cast<const double2*>(xin);
+  double2* y = reinterpret_cast<double2*>(yout);
+  const int nr = (int)nrhs;
+  const GemvMode m = GEMV_FF;
+  RF_TRY(ensure_workspace(op, nr));
+  Workspace& W = *op->ws;
+  const double a = op->alpha, b = op->beta, gm = op->gamma;
+  switch (which) {
+    case RFCMP_PREC_P_O:
+      return apply_Po(op, x, y, nr, false, m, st);
+    case RFCMP_PREC_P_O_ADJ:
+      return apply_Po(op, x, y, nr, true, m, st);
+    case RFCMP_PREC_P_SIGMA:
+    case RFCMP_PREC_P_LAMBDAH: {
+      RF_TRY(star_coeff(op, x, W.s, W.z, nr, m, st));
+      EdgeCombo c;
+      c.zs = W.z;
+      if (which == RFCMP_PREC_P_SIGMA) {
+        c.b = c2(1, 0);
+      } else {
+        c.x = x;
+        c.a = c2(1, 0);
+        c.b = c2(-1, 0);
+      }
+      RF_K(edge_combo(op->g, c, y, nr, st));
+      return RFCMP_OK;
+    }
+    case RFCMP_PREC_P_M: {
+      const int C = (int)op->top.nc, NV = (int)op->top.nv;
+      RF_TRY(star_coeff(op, x, W.s, W.zu, nr, m, st));
+      RF_K(star_middle(op->g, W.zu, nullptr, 1.0, W.q0, nr, W.mean, st));
+      RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+      RF_K(lambda_t(op->g, x, W.t, nr, st));
+      RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, st));
+      EdgeCombo c;
+      c.zl = W.tg;
+      c.c = c2(1.0 / (a * a), 0.0);
+      c.x = x;
+      c.a = c2(1.0 / gm, 0.0);
+      c.zs = W.zu;
+      c.b = c2(-1.0 / gm, 0.0);
+      c.zs2 = W.q;
+      c.d = c2(1.0, 0.0);
+      RF_K(edge_combo(op->g, c, y, nr, st));
+      return RFCMP_OK;
+    }
+    default:
+      return set_error(RFCMP_ERR_INVALID_ARG, "unknown preconditioner id");
+  }
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- the solve
+namespace {
+
+// column norms^2 (host) of a device block
+int col_norms2(rfcmp_op* op, const double2* x, int nr, std::vector<double>& out, cudaStream_t st) {
+  SolveBuffers& B = *op->sb;
+  RF_K(vec_dot(x, x, op->top.ne, nr, B.dots, st));
+  std::vector<double2> h(nr);
+  RF_CUDA(cudaMemcpyAsync(h.data(), B.dots, sizeof(double2) * nr, cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  out.resize(nr);
+  for (int r = 0; r < nr; ++r) out[r] = h[r].x;
+  return RFCMP_OK;
+}
+
+// CG on A d = r for the columns in `active` (host mask); d starts at 0.
+// Stops a column when ||r_inner|| <= rel_tol * ||r||.  Counts iterations per column.
+int inner_cg(rfcmp_op* op, const double2* r, double2* d, int nr, std::vector<int>& active, double rel_tol,
+             std::vector<int>& iters, int max_iter_total, GemvMode m, cudaStream_t st) {
+  SolveBuffers& B = *op->sb;
+  const int64_t N = op->top.ne;
+  RF_CUDA(cudaMemsetAsync(d, 0, sizeof(double2) * N * nr, st));
+  RF_K(vec_copy(r, B.rin, N * nr, st));
+  RF_K(vec_copy(r, B.p, N * nr, st));
+  std::vector<double> r0;
+  RF_TRY(col_norms2(op, r, nr, r0, st));
+  std::vector<double2> hd(nr);
+  std::vector<double> rho(nr);
+  for (int c = 0; c < nr; ++c) {
+    rho[c] = r0[c];
+    if (r0[c] == 0.0) active[c] = 0;
+  }
+  RF_CUDA(cudaMemcpyAsync(B.rho, rho.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+  RF_CUDA(cudaMemcpyAsync(B.active, active.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+  for (;;) {
+    bool any = false;
+    for (int c = 0; c < nr; ++c)
+      if (active[c] && iters[c] < max_iter_total) any = true;
+    if (!any) break;
+    RF_TRY(apply_A(op, B.p, B.Ap, nr, m, st));
+    RF_K(vec_dot(B.p, B.Ap, N, nr, B.dots, st));
+    RF_K(cg_scalars_alpha(B.rho, B.dots, B.alpha, B.active, nr, st));
+    RF_K(vec_axpy_cols(B.alpha, false, B.p, d, N, nr, B.active, st));
+    RF_K(vec_axpy_cols(B.alpha, true, B.Ap, B.rin, N, nr, B.active, st));
+    RF_K(vec_dot(B.rin, B.rin, N, nr, B.dots, st));
+    RF_K(cg_scalars_beta(B.dots, B.rho, B.beta, B.active, nr, st));
+    RF_K(vec_xpby_cols(B.rin, B.beta, B.p, N, nr, B.active, st));
+    RF_CUDA(cudaMemcpyAsync(rho.data(), B.rho, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    RF_CUDA(cudaStreamSynchronize(st));
+    bool changed = false;
+    for (int c = 0; c < nr; ++c) {
+      if (!active[c]) continue;
+      iters[c]++;
+      if (std::sqrt(rho[c]) <= rel_tol * std::sqrt(r0[c]) || iters[c] >= max_iter_total || !std::isfinite(rho[c])) {
+        active[c] = 0;
+        changed = true;
+      }
+    }
+    if (changed)
+      RF_CUDA(cudaMemcpyAsync(B.active, active.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+  }
+  return RFCMP_OK;
+}
+
+int solve_impl(rfcmp_op* op, const double2* e, double2* j, int nr, const rfcmp_solve_opts& o,
+               rfcmp_solve_report* rep, cudaStream_t st) {
+  RF_TRY(ensure_workspace(op, nr));
+  RF_TRY(ensure_solve_buffers(op, nr));
+  SolveBuffers& B = *op->sb;
+  const int64_t N = op->top.ne;
+  // b = -P_o^H T^H P_m e (float-float accurate)
+  RF_TRY(apply_rhs(op, e, B.b, nr, GEMV_FF, st));
+  std::vector<double> bb, rr;
+  RF_TRY(col_norms2(op, B.b, nr, bb, st));
+  RF_CUDA(cudaMemsetAsync(B.i, 0, sizeof(double2) * N * nr, st));
+  RF_K(vec_copy(B.b, B.r, N * nr, st));
+  std::vector<int> iters(nr, 0), sweeps(nr, 0), conv(nr, 0);
+  std::vector<double> res(nr, 1.0);
+  const bool mixed = o.precision == RFCMP_PREC_MIXED;
+  const GemvMode inner_mode = mixed ? GEMV_F32 : GEMV_FF;
+  const int max_sweeps = mixed ? o.max_refine : 1;
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+    if (sweep > 0) {
+      // r = b - A i, float-float accurate
+      RF_TRY(apply_A(op, B.i, B.tmp, nr, GEMV_FF, st));
+      RF_K(vec_copy(B.b, B.r, N * nr, st));
+      std::vector<double> ones(nr, 1.0);
+      RF_CUDA(cudaMemcpyAsync(B.alpha, ones.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+      RF_K(vec_axpy_cols(B.alpha, true, B.tmp, B.r, N, nr, nullptr, st));
+      for (int c = 0; c < nr; ++c) sweeps[c]++;
+    }
+    RF_TRY(col_norms2(op, B.r, nr, rr, st));
+    std::vector<int> active(nr, 0);
+    bool any = false;
+    for (int c = 0; c < nr; ++c) {
+      res[c] = bb[c] > 0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
+      conv[c] = res[c] <= o.tol;
+      active[c] = !conv[c] && iters[c] < o.max_iter;
+      any |= active[c] != 0;
+    }
+    if (!any || sweep == max_sweeps) break;
+    // inner tolerance: mixed asks inner_tol per sweep (never below what reaches tol); ff solves to tol
+    std::vector<double> dummy;
+    double rel = mixed ? o.inner_tol : o.tol * 0.5;
+    if (mixed) {
+      double worst = 0.0;
+      for (int c = 0; c < nr; ++c)
+        if (active[c]) worst = std::max(worst, res[c]);
+      rel = std::max(o.inner_tol, 0.5 * o.tol / std::max(worst, 1e-300));
+      rel = std::min(rel, 0.5);
+    }
+    RF_TRY(inner_cg(op, B.r, B.d, nr, active, rel, iters, o.max_iter, inner_mode, st));
+    // i += d
+    std::vector<double> ones(nr, 1.0);
+    RF_CUDA(cudaMemcpyAsync(B.alpha, ones.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+    RF_K(vec_axpy_cols(B.alpha, false, B.d, B.i, N, nr, nullptr, st));
+    if (!mixed) {
+      // FF: one accurate residual to report
+      RF_TRY(apply_A(op, B.i, B.tmp, nr, GEMV_FF, st));
+      RF_K(vec_copy(B.b, B.r, N * nr, st));
+      RF_K(vec_axpy_cols(B.alpha, true, B.tmp, B.r, N, nr, nullptr, st));
+      RF_TRY(col_norms2(op, B.r, nr, rr, st));
+      for (int c = 0; c < nr; ++c) {
+        res[c] = bb[c] > 0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
+        conv[c] = res[c] <= o.tol;
+        sweeps[c] = 1;
+      }
+      break;
+    }
+  }
+  // j = P_o i
+  RF_TRY(apply_Po(op, B.i, j, nr, false, GEMV_FF, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  bool all = true;
+  for (int c = 0; c < nr; ++c) {
+    if (rep) {
+      rep[c].converged = conv[c];
+      rep[c].iterations = iters[c];
+      rep[c].refinements = sweeps[c];
+      rep[c].reserved = 0;
+      rep[c].residual = res[c];
+    }
+    all &= conv[c] != 0;
+  }
+  if (!all && o.fail_on_nonconvergence) return set_error(RFCMP_ERR_NOT_CONVERGED, "a column did not reach tol");
+  return RFCMP_OK;
+}
+
+int check_solve_opts(const rfcmp_solve_opts* in, rfcmp_solve_opts& o) {
+  rfcmp_solve_opts_default(&o);
+  if (in) o = *in;
+  for (int i = 0; i < 8; ++i)
+    if (o.reserved[i] != 0) return set_error(RFCMP_ERR_INVALID_ARG, "opts.reserved must be zero");
+  if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_refine < 0 || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 ||
+      (o.precision != RFCMP_PREC_MIXED && o.precision != RFCMP_PREC_FF))
+    return set_error(RFCMP_ERR_INVALID_ARG, "invalid solve options");
+  return RFCMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rfcmp_solve(rfcmp_op* op, const rfcmp_c128* e, rfcmp_c128* j, int64_t nrhs, const rfcmp_solve_opts* opts,
+                rfcmp_solve_report* report, void* stream) {
+  if (!op || !e || !j || nrhs <= 0 || nrhs > 4096) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  rfcmp_solve_opts o;
+  RF_TRY(check_solve_opts(opts, o));
+  RF_CUDA(cudaSetDevice(op->ctx->device));
+  return solve_impl(op, reinterpret_cast<const double2*>(e), reinterpret_cast<double2*>(j), (int)nrhs, o, report,
+                    (cudaStream_t)stream);
+}
+
+int rfcmp_solve_host(rfcmp_op* op, const rfcmp_c128* e_host, rfcmp_c128* j_host, int64_t nrhs,
+                     const rfcmp_solve_opts* opts, rfcmp_solve_report* report, void* stream) {
+  if (!op || !e_host || !j_host || nrhs <= 0 || nrhs > 4096)
+    return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  rfcmp_solve_opts o;
+  RF_TRY(check_solve_opts(opts, o));
+  RF_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double2) * (size_t)op->top.ne * nrhs;
+  double2 *de = nullptr, *dj = nullptr;
+  RF_CUDA(cudaMallocAsync(&de, bytes, st));
+  RF_CUDA(cudaMallocAsync(&dj, bytes, st));
+  RF_CUDA(cudaMemcpyAsync(de, e_host, bytes, cudaMemcpyHostToDevice, st));
+  int rc = solve_impl(op, de, dj, (int)nrhs, o, report, st);
+  if (rc == RFCMP_OK) {
+    cudaError_t err = cudaMemcpyAsync(j_host, dj, bytes, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) rc = set_error(RFCMP_ERR_CUDA, std::string("copy back: ") + cudaGetErrorString(err));
+  }
+  cudaFreeAsync(de, st);
+  cudaFreeAsync(dj, st);
+  return rc;
+}
+
+int rfcmp_farfield(rfcmp_op* op, const rfcmp_c128* j, int64_t nrhs, const double* dirs, int64_t ndir,
+                   double* rcs_dbsm, void* stream) {
+  if (!op || !j || !dirs || !rcs_dbsm || nrhs <= 0 || ndir <= 0 || nrhs > 65535 || ndir > (1 << 20))
+    return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* dd = nullptr;
+  double2* dn = nullptr;
+  RF_CUDA(cudaMallocAsync(&dd, sizeof(double) * 3 * ndir, st));
+  RF_CUDA(cudaMallocAsync(&dn, sizeof(double2) * 3 * ndir * nrhs, st));
+  RF_CUDA(cudaMemcpyAsync(dd, dirs, sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, st));
+  RF_K(launch_farfield(op->g, op->k, reinterpret_cast<const double2*>(j), (int)nrhs, dd, (int)ndir, dn, st));
+  std::vector<double2> h(3 * ndir * nrhs);
+  RF_CUDA(cudaMemcpyAsync(h.data(), dn, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaFreeAsync(dd, st));
+  RF_CUDA(cudaFreeAsync(dn, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  const double k = op->k;
+  for (int64_t r = 0; r < nrhs; ++r)
+    for (int64_t d = 0; d < ndir; ++d) {
+      const double* u = dirs + 3 * d;
+      const double2* n = &h[(r * ndir + d) * 3];
+      double2 dot = make_double2(u[0] * n[0].x + u[1] * n[1].x + u[2] * n[2].x,
+                                 u[0] * n[0].y + u[1] * n[1].y + u[2] * n[2].y);
+      double s = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double pr = n[a].x - u[a] * dot.x, pi = n[a].y - u[a] * dot.y;
+        s += pr * pr + pi * pi;
+      }
+      const double sigma = k * k / (4.0 * M_PI) * s;
+      rcs_dbsm[r * ndir + d] = 10.0 * std::log10(std::max(sigma, 1e-300));
+    }
+  return RFCMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,503 @@
+// Assembly kernels: the EFIE blocks T_A and V (Sec. 2), the plane-wave
+// excitation e and the radiation vector for the far field.
+//
+// Every cell pair (s, t) is reduced to four moments in centroid-local
+// coordinates rho = r - c_s, rho' = r' - c_t:
+//   I0 = int int G,  Ir = int int rho G,  Irp = int int rho' G,  Irr = int int rho.rho' G,
+// G = e^{ikR} / (4 pi R).  The local RWG half-function of cell s opposite its
+// vertex i is sigma (r - P_i) / (2 A_s) (Eq. RWGdef), so the pair contributes
+//   sigma_i sigma_j [Irr - b_j.Ir - a_i.Irp + (a_i.b_j) I0] / (4 A_s A_t)
+// to [T_A]_{m_i n_j} (a_i = P_i - c_s, b_j = P_j - c_t), and I0 / (A_s A_t)
+// to V_st (p = 1/A, Eq. patchstddef).
+//
+// Far pairs (no shared vertex): 7 x 7 product of the 7-point rule, FP32,
+// one unordered pair per thread, both (s,t) and (t,s) written.
+// Near pairs (a shared vertex): FP64, G split as 1/(4 pi R) + (e^{ikR}-1)/(4 pi R);
+// the first term integrated over the source cell in closed form (integrals of
+// 1/R and (r'-p)/R over a flat triangle by Stokes' theorem, Wilton et al. 1984),
+// the second by the 7-point rule; the result is the mean of both orders.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "rfcmp_internal.h"
+
+namespace rfcmp {
+
+namespace {
+
+constexpr int TILE = 32;          // cells per tile side
+constexpr int FAR_THREADS = 256;  // 32 s-cells x 8 t-lanes
+constexpr float INV_4PI_F = 0.0795774715459476679f;
+constexpr double INV_4PI = 0.0795774715459476679;
+
+__device__ __forceinline__ void atomic_add_c64(float2* p, float re, float im) {
+  atomicAdd(p, make_float2(re, im));
+}
+
+// shared-memory image of one tile of cells
+struct TileCells {
+  float rho[TILE][21];
+  float wq4[TILE][7];   // weight x area / (4 pi)
+  float wq[TILE][7];    // weight x area
+  float cen_hi[TILE][3];
+  float cen_lo[TILE][3];
+  float aloc[TILE][9];
+  float inv_area[TILE];
+  int32_t vid[TILE][3];
+  int32_t edge[TILE][3];
+  float sign[TILE][3];
+};
+
+__device__ void load_tile(TileCells& T, const DeviceGeometry g, int base) {
+  for (int q = threadIdx.x; q < TILE; q += blockDim.x) {
+    int c = base + q;
+    bool ok = c < g.nc;
+    int cc = ok ? c : 0;
+    for (int e = 0; e < 21; ++e) T.rho[q][e] = g.rho[21 * cc + e];
+    for (int e = 0; e < 7; ++e) {
+      float w = g.wq[7 * cc + e];
+      T.wq[q][e] = w;
+      T.wq4[q][e] = w * INV_4PI_F;
+    }
+    for (int e = 0; e < 3; ++e) {
+      T.cen_hi[q][e] = g.cen_hi[3 * cc + e];
+      T.cen_lo[q][e] = g.cen_lo[3 * cc + e];
+      T.vid[q][e] = ok ? g.tris[3 * cc + e] : -1 - q;
+      T.edge[q][e] = g.cell_edges[3 * cc + e];
+      T.sign[q][e] = (float)g.cell_sign[3 * cc + e];
+    }
+    for (int e = 0; e < 9; ++e) T.aloc[q][e] = g.aloc[9 * cc + e];
+    T.inv_area[q] = g.inv_area[cc];
+  }
+}
+
+__global__ void __launch_bounds__(FAR_THREADS, 2)
+far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float2* __restrict__ V, int nb) {
+  __shared__ TileCells S, Tt;
+  // linear tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
+  long long tix = blockIdx.x;
+  int bi = 0;
+  {
+    long long rem = tix;
+    while (rem >= nb - bi) {
+      rem -= nb - bi;
+      ++bi;
+    }
+    tix = rem;
+  }
+  const int bj = bi + (int)tix;
+  load_tile(S, g, bi * TILE);
+  load_tile(Tt, g, bj * TILE);
+  __syncthreads();
+
+  const int sl = threadIdx.x >> 3;
+  const int s = bi * TILE + sl;
+  if (s >= g.nc) return;
+  float rs[21], ws[7];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) rs[e] = S.rho[sl][e];
+#pragma unroll
+  for (int e = 0; e < 7; ++e) ws[e] = S.wq[sl][e];
+  const size_t ldN = g.ldN, ldC = g.ldC;
+  const int NC = g.nc;
+
+  for (int q = 0; q < 4; ++q) {
+    const int tl = (threadIdx.x & 7) + 8 * q;
+    const int t = bj * TILE + tl;
+    if (t >= NC) continue;
+    if (bi == bj && t <= s) continue;
+    // near pairs (a shared vertex) belong to the FP64 kernel
+    bool near = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) near |= (S.vid[sl][a] == Tt.vid[tl][b]);
+    if (near) continue;
+
+    float rt[21], wt[7];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) rt[e] = Tt.rho[tl][e];
+#pragma unroll
+    for (int e = 0; e < 7; ++e) wt[e] = Tt.wq4[tl][e];
+    float d[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) d[e] = (S.cen_hi[sl][e] - Tt.cen_hi[tl][e]) + (S.cen_lo[sl][e] - Tt.cen_lo[tl][e]);
+
+    float I0r = 0.f, I0i = 0.f, Irr_r = 0.f, Irr_i = 0.f;
+    float Ir_r[3] = {0.f, 0.f, 0.f}, Ir_i[3] = {0.f, 0.f, 0.f};
+    float Ip_r[3] = {0.f, 0.f, 0.f}, Ip_i[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      const float dx = d[0] + rs[3 * i], dy = d[1] + rs[3 * i + 1], dz = d[2] + rs[3 * i + 2];
+      float s0r = 0.f, s0i = 0.f;
+      float s1r[3] = {0.f, 0.f, 0.f}, s1i[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const float ex = dx - rt[3 * j], ey = dy - rt[3 * j + 1], ez = dz - rt[3 * j + 2];
+        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float rinv = rsqrtf(r2);
+        const float R = r2 * rinv;
+        float sn, cs;
+        sincosf(k * R, &sn, &cs);
+        const float gw = wt[j] * rinv;
+        const float gr = gw * cs, gi = gw * sn;
+        s0r += gr;
+        s0i += gi;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          s1r[e] = fmaf(gr, rt[3 * j + e], s1r[e]);
+          s1i[e] = fmaf(gi, rt[3 * j + e], s1i[e]);
+        }
+      }
+      const float w = ws[i];
+      I0r = fmaf(w, s0r, I0r);
+      I0i = fmaf(w, s0i, I0i);
+      float dr = 0.f, di = 0.f;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const float wr = w * rs[3 * i + e];
+        Ir_r[e] = fmaf(wr, s0r, Ir_r[e]);
+        Ir_i[e] = fmaf(wr, s0i, Ir_i[e]);
+        Ip_r[e] = fmaf(w, s1r[e], Ip_r[e]);
+        Ip_i[e] = fmaf(w, s1i[e], Ip_i[e]);
+        dr = fmaf(wr, s1r[e], dr);
+        di = fmaf(wr, s1i[e], di);
+      }
+      Irr_r += dr;
+      Irr_i += di;
+    }
+    const float inv_aa = S.inv_area[sl] * Tt.inv_area[tl];
+    V[(size_t)s * ldC + t] = make_float2(I0r * inv_aa, I0i * inv_aa);
+    V[(size_t)t * ldC + s] = make_float2(I0r * inv_aa, I0i * inv_aa);
+    const float quarter = 0.25f * inv_aa;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float ax = S.aloc[sl][3 * a], ay = S.aloc[sl][3 * a + 1], az = S.aloc[sl][3 * a + 2];
+      // Irr - a.Irp (shared by the three j)
+      const float pa_r = Irr_r - (ax * Ip_r[0] + ay * Ip_r[1] + az * Ip_r[2]);
+      const float pa_i = Irr_i - (ax * Ip_i[0] + ay * Ip_i[1] + az * Ip_i[2]);
+      const int m = S.edge[sl][a];
+      const float sa = S.sign[sl][a] * quarter;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float bx = Tt.aloc[tl][3 * b], by = Tt.aloc[tl][3 * b + 1], bz = Tt.aloc[tl][3 * b + 2];
+        const float ab = ax * bx + ay * by + az * bz;
+        const float vr = pa_r - (bx * Ir_r[0] + by * Ir_r[1] + bz * Ir_r[2]) + ab * I0r;
+        const float vi = pa_i - (bx * Ir_i[0] + by * Ir_i[1] + bz * Ir_i[2]) + ab * I0i;
+        const float f = sa * Tt.sign[tl][b];
+        const int n = Tt.edge[tl][b];
+        atomic_add_c64(&TA[(size_t)m * ldN + n], f * vr, f * vi);
+        atomic_add_c64(&TA[(size_t)n * ldN + m], f * vr, f * vi);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- near pairs (FP64)
+struct Pot {
+  double S;       // int 1/R
+  double V[3];    // int (r' - p)/R
+  double p[3];    // projection of r on the plane
+};
+
+__device__ __forceinline__ double rpl(double R, double l, double R02) {
+  // R + l without cancellation (R >= |l|)
+  return l > 0.0 ? R + l : R02 / (R - l);
+}
+
+// closed-form integrals over the flat triangle (P0, P1, P2), counter-clockwise
+__device__ Pot triangle_potentials(const double r[3], const double* P0, const double* P1, const double* P2) {
+  double e1[3], e2[3], n[3];
+  for (int a = 0; a < 3; ++a) {
+    e1[a] = P1[a] - P0[a];
+    e2[a] = P2[a] - P0[a];
+  }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int a = 0; a < 3; ++a) n[a] /= nn;
+  double d = (r[0] - P0[0]) * n[0] + (r[1] - P0[1]) * n[1] + (r[2] - P0[2]) * n[2];
+  Pot out;
+  for (int a = 0; a < 3; ++a) {
+    out.p[a] = r[a] - d * n[a];
+    out.V[a] = 0.0;
+  }
+  out.S = 0.0;
+  const double ad = fabs(d);
+  const double* P[3] = {P0, P1, P2};
+  for (int i = 0; i < 3; ++i) {
+    const double* A = P[i];
+    const double* B = P[(i + 1) % 3];
+    double lv[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    double le = sqrt(lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2]);
+    for (int a = 0; a < 3; ++a) lv[a] /= le;
+    // outward in-plane normal u = l x n
+    double u[3] = {lv[1] * n[2] - lv[2] * n[1], lv[2] * n[0] - lv[0] * n[2], lv[0] * n[1] - lv[1] * n[0]};
+    double lp = 0, lm = 0, P0d = 0;
+    for (int a = 0; a < 3; ++a) {
+      lp += (B[a] - out.p[a]) * lv[a];
+      lm += (A[a] - out.p[a]) * lv[a];
+      P0d += (A[a] - out.p[a]) * u[a];
+    }
+    const double R02 = P0d * P0d + d * d;
+    const double Rp = sqrt(lp * lp + R02), Rm = sqrt(lm * lm + R02);
+    double F = 0.0;
+    if (R02 > 1e-30 * le * le) F = log(rpl(Rp, lp, R02) / rpl(Rm, lm, R02));
+    double at = 0.0;
+    if (ad > 0.0) at = atan2(P0d * lp, R02 + ad * Rp) - atan2(P0d * lm, R02 + ad * Rm);
+    out.S += P0d * F - ad * at;
+    const double c = 0.5 * (R02 * F + lp * Rp - lm * Rm);
+    for (int a = 0; a < 3; ++a) out.V[a] += c * u[a];
+  }
+  return out;
+}
+
+constexpr int NEAR_PAIRS_PER_BLOCK = 8;
+constexpr int NEAR_THREADS = NEAR_PAIRS_PER_BLOCK * 16;
+
+// 16 slots per pair: slot = order * 7 + outer point, slots 14, 15 idle
+__global__ void __launch_bounds__(NEAR_THREADS)
+near_pairs_kernel(const DeviceGeometry g, double k, float2* __restrict__ TA, float2* __restrict__ V) {
+  __shared__ double mom[NEAR_PAIRS_PER_BLOCK][16][16];  // per slot: I0(2) Iouter(6) Iinner(6) Irr(2)
+  const int lp = threadIdx.x >> 4;
+  const int slot = threadIdx.x & 15;
+  const int pair = blockIdx.x * NEAR_PAIRS_PER_BLOCK + lp;
+  double acc[16];
+  for (int e = 0; e < 16; ++e) acc[e] = 0.0;
+  if (pair < g.n_near && slot < 14) {
+    const int order = slot / 7, i = slot % 7;
+    const int s = g.near_pairs[2 * pair], t = g.near_pairs[2 * pair + 1];
+    const int so = order == 0 ? s : t;  // outer (test) cell
+    const int si = order == 0 ? t : s;  // inner (source) cell
+    double r[3], rho_o[3];
+    for (int a = 0; a < 3; ++a) {
+      r[a] = g.qp64[21 * so + 3 * i + a];
+      rho_o[a] = r[a] - g.cen64[3 * so + a];
+    }
+    const double* P0 = g.verts + 3 * g.tris[3 * si];
+    const double* P1 = g.verts + 3 * g.tris[3 * si + 1];
+    const double* P2 = g.verts + 3 * g.tris[3 * si + 2];
+    Pot pt = triangle_potentials(r, P0, P1, P2);
+    // singular part: J0 = S / 4pi, J1 = (Vv + (p - c_si) S) / 4pi (relative to the inner centroid)
+    double J0r = pt.S * INV_4PI, J0i = 0.0;
+    double J1r[3], J1i[3];
+    for (int a = 0; a < 3; ++a) {
+      J1r[a] = (pt.V[a] + (pt.p[a] - g.cen64[3 * si + a]) * pt.S) * INV_4PI;
+      J1i[a] = 0.0;
+    }
+    // smooth part (e^{ikR} - 1)/(4 pi R) on the inner 7-point rule; value i k / 4pi at R = 0
+    const double Ai = g.area64[si];
+    for (int j = 0; j < 7; ++j) {
+      double rr[3], rhoi[3], R2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        rr[a] = g.qp64[21 * si + 3 * j + a];
+        rhoi[a] = rr[a] - g.cen64[3 * si + a];
+        double dd = r[a] - rr[a];
+        R2 += dd * dd;
+      }
+      const double w = (j == 0 ? 9.0 / 40.0 : (j < 4 ? (155.0 - sqrt(15.0)) / 1200.0 : (155.0 + sqrt(15.0)) / 1200.0)) * Ai;
+      double gr, gi;
+      if (R2 > 0.0) {
+        const double R = sqrt(R2);
+        double sh, ch, sn, cs;
+        sincos(0.5 * k * R, &sh, &ch);
+        sincos(k * R, &sn, &cs);
+        gr = -2.0 * sh * sh * INV_4PI / R;
+        gi = sn * INV_4PI / R;
+      } else {
+        gr = 0.0;
+        gi = k * INV_4PI;
+      }
+      J0r += w * gr;
+      J0i += w * gi;
+      for (int a = 0; a < 3; ++a) {
+        J1r[a] += w * gr * rhoi[a];
+        J1i[a] += w * gi * rhoi[a];
+      }
+    }
+    const double wo = (i == 0 ? 9.0 / 40.0 : (i < 4 ? (155.0 - sqrt(15.0)) / 1200.0 : (155.0 + sqrt(15.0)) / 1200.0)) *
+                      g.area64[so];
+    acc[0] = wo * J0r;
+    acc[1] = wo * J0i;
+    double dr = 0.0, di = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      acc[2 + a] = wo * rho_o[a] * J0r;   // outer moment
+      acc[5 + a] = wo * rho_o[a] * J0i;
+      acc[8 + a] = wo * J1r[a];           // inner moment
+      acc[11 + a] = wo * J1i[a];
+      dr += rho_o[a] * J1r[a];
+      di += rho_o[a] * J1i[a];
+    }
+    acc[14] = wo * dr;
+    acc[15] = wo * di;
+  }
+  for (int e = 0; e < 16; ++e) mom[lp][slot][e] = acc[e];
+  __syncthreads();
+  if (slot != 0 || pair >= g.n_near) return;
+  // sum each order over its 7 points, then average the two orders in the (s, t) frame
+  double o0[16], o1[16];
+  for (int e = 0; e < 16; ++e) {
+    o0[e] = 0.0;
+    o1[e] = 0.0;
+    for (int i = 0; i < 7; ++i) {
+      o0[e] += mom[lp][i][e];
+      o1[e] += mom[lp][7 + i][e];
+    }
+  }
+  const int s = g.near_pairs[2 * pair], t = g.near_pairs[2 * pair + 1];
+  double I0r = 0.5 * (o0[0] + o1[0]), I0i = 0.5 * (o0[1] + o1[1]);
+  double Isr[3], Isi[3], Itr[3], Iti[3];
+  for (int a = 0; a < 3; ++a) {
+    Isr[a] = 0.5 * (o0[2 + a] + o1[8 + a]);  // int rho_s G
+    Isi[a] = 0.5 * (o0[5 + a] + o1[11 + a]);
+    Itr[a] = 0.5 * (o0[8 + a] + o1[2 + a]);  // int rho_t G
+    Iti[a] = 0.5 * (o0[11 + a] + o1[5 + a]);
+  }
+  double Irr_r = 0.5 * (o0[14] + o1[14]), Irr_i = 0.5 * (o0[15] + o1[15]);
+  const size_t ldN = g.ldN, ldC = g.ldC;
+  const double inv_aa = 1.0 / (g.area64[s] * g.area64[t]);
+  V[(size_t)s * ldC + t] = make_float2((float)(I0r * inv_aa), (float)(I0i * inv_aa));
+  if (s != t) V[(size_t)t * ldC + s] = make_float2((float)(I0r * inv_aa), (float)(I0i * inv_aa));
+  for (int a = 0; a < 3; ++a) {
+    double ai[3], pr = Irr_r, pi = Irr_i;
+    for (int x = 0; x < 3; ++x) {
+      ai[x] = g.verts[3 * g.tris[3 * s + a] + x] - g.cen64[3 * s + x];
+      pr -= ai[x] * Itr[x];
+      pi -= ai[x] * Iti[x];
+    }
+    const int m = g.cell_edges[3 * s + a];
+    const double sa = (double)g.cell_sign[3 * s + a] * 0.25 * inv_aa;
+    for (int b = 0; b < 3; ++b) {
+      double vr = pr, vi = pi, ab = 0.0;
+      for (int x = 0; x < 3; ++x) {
+        const double bx = g.verts[3 * g.tris[3 * t + b] + x] - g.cen64[3 * t + x];
+        vr -= bx * Isr[x];
+        vi -= bx * Isi[x];
+        ab += ai[x] * bx;
+      }
+      vr += ab * I0r;
+      vi += ab * I0i;
+      const double f = sa * (double)g.cell_sign[3 * t + b];
+      const int n = g.cell_edges[3 * t + b];
+      atomic_add_c64(&TA[(size_t)m * ldN + n], (float)(f * vr), (float)(f * vi));
+      if (s != t) atomic_add_c64(&TA[(size_t)n * ldN + m], (float)(f * vr), (float)(f * vi));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- excitation (FP64)
+__global__ void rhs_kernel(const DeviceGeometry g, double k, const double* __restrict__ khat,
+                           const double* __restrict__ pol, int nrhs, double2* __restrict__ e) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (n >= g.ne || r >= nrhs) return;
+  const double kx = khat[3 * r], ky = khat[3 * r + 1], kz = khat[3 * r + 2];
+  const double px = pol[3 * r], py = pol[3 * r + 1], pz = pol[3 * r + 2];
+  double accr = 0.0, acci = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    const int c = g.edge_cells[2 * n + side];
+    const int fv = g.edge_free[2 * n + side];
+    const double sg = side == 0 ? 0.5 : -0.5;  // sigma / (2 A) times the area of the rule
+    for (int q = 0; q < 7; ++q) {
+      const double* rq = g.qp64 + 21 * c + 3 * q;
+      const double w = q == 0 ? 9.0 / 40.0 : (q < 4 ? (155.0 - sqrt(15.0)) / 1200.0 : (155.0 + sqrt(15.0)) / 1200.0);
+      const double dot = (rq[0] - g.verts[3 * fv]) * px + (rq[1] - g.verts[3 * fv + 1]) * py +
+                         (rq[2] - g.verts[3 * fv + 2]) * pz;
+      double sn, cs;
+      sincos(k * (kx * rq[0] + ky * rq[1] + kz * rq[2]), &sn, &cs);
+      accr += sg * w * dot * cs;
+      acci += sg * w * dot * sn;
+    }
+  }
+  e[(size_t)r * g.ne + n] = make_double2(accr, acci);
+}
+
+// ---------------------------------------------------------------- radiation vector (FP64)
+constexpr int FF_THREADS = 256;
+
+__global__ void __launch_bounds__(FF_THREADS)
+farfield_kernel(const DeviceGeometry g, double k, const double2* __restrict__ j, const double* __restrict__ dirs,
+                int ndir, double2* __restrict__ out) {
+  const int d = blockIdx.x;
+  const int r = blockIdx.y;
+  const double ux = dirs[3 * d], uy = dirs[3 * d + 1], uz = dirs[3 * d + 2];
+  const double2* jr = j + (size_t)r * g.ne;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int c = threadIdx.x; c < g.nc; c += blockDim.x) {
+    double jl_r[3], jl_i[3];
+    for (int i = 0; i < 3; ++i) {
+      const double2 v = jr[g.cell_edges[3 * c + i]];
+      const double sg = (double)g.cell_sign[3 * c + i];
+      jl_r[i] = sg * v.x;
+      jl_i[i] = sg * v.y;
+    }
+    for (int q = 0; q < 7; ++q) {
+      const double* rq = g.qp64 + 21 * c + 3 * q;
+      const double w = 0.5 * (q == 0 ? 9.0 / 40.0 : (q < 4 ? (155.0 - sqrt(15.0)) / 1200.0 : (155.0 + sqrt(15.0)) / 1200.0));
+      double sn, cs;
+      sincos(-k * (ux * rq[0] + uy * rq[1] + uz * rq[2]), &sn, &cs);
+      for (int x = 0; x < 3; ++x) {
+        double cr = 0.0, ci = 0.0;
+        for (int i = 0; i < 3; ++i) {
+          const double rel = rq[x] - g.verts[3 * g.tris[3 * c + i] + x];
+          cr += jl_r[i] * rel;
+          ci += jl_i[i] * rel;
+        }
+        acc[2 * x] += w * (cr * cs - ci * sn);
+        acc[2 * x + 1] += w * (cr * sn + ci * cs);
+      }
+    }
+  }
+  __shared__ double red[FF_THREADS / 32][6];
+  for (int e = 0; e < 6; ++e) {
+    double v = acc[e];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][e] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < FF_THREADS / 32; ++w) v += red[w][threadIdx.x];
+    double* o = reinterpret_cast<double*>(out + ((size_t)r * ndir + d) * 3);
+    o[threadIdx.x] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, float2* V, cudaStream_t s) {
+  const int nb = (g.nc + TILE - 1) / TILE;
+  const long long tiles = (long long)nb * (nb + 1) / 2;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  // far pairs: all unordered pairs minus the near ones (n_near counts s <= t, including s == t)
+  const double far = (double)g.nc * (g.nc + 1) / 2.0 - (double)g.n_near;
+  ProfScope prof("assemble_far", 8.0 * (double)g.nc * g.nc + 8.0 * (double)g.ne * g.ne, far * 49.0 * 54.0, s);
+  far_pairs_kernel<<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_near(const DeviceGeometry& g, double k, float2* TA, float2* V, cudaStream_t s) {
+  if (g.n_near == 0) return cudaSuccess;
+  const int blocks = (g.n_near + NEAR_PAIRS_PER_BLOCK - 1) / NEAR_PAIRS_PER_BLOCK;
+  ProfScope prof("assemble_near", 0.0, 0.0, s);
+  near_pairs_kernel<<<blocks, NEAR_THREADS, 0, s>>>(g, k, TA, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_planewave(const DeviceGeometry& g, double k, const double* khat, const double* pol, int nrhs,
+                                 double2* e, cudaStream_t s) {
+  dim3 grid((g.ne + 255) / 256, nrhs);
+  rhs_kernel<<<grid, 256, 0, s>>>(g, k, khat, pol, nrhs, e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_farfield(const DeviceGeometry& g, double k, const double2* j, int nrhs, const double* dirs,
+                            int ndir, double2* out, cudaStream_t s) {
+  dim3 grid(ndir, nrhs);
+  farfield_kernel<<<grid, FF_THREADS, 0, s>>>(g, k, j, dirs, ndir, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rfcmp

@@ -1,0 +1,160 @@
+// Internal declarations shared by the translation units of librfcmp.
+// Host topology (topology.cpp), kernels (k_assembly.cu, k_linalg.cu) and the
+// C ABI (capi.cu).  Nothing here is part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rfcmp.h"
+
+namespace rfcmp {
+
+// ---------------------------------------------------------------- profiling
+// RAII bracket of one launch by CUDA events on its stream (no-op when disabled).
+class ProfScope {
+ public:
+  ProfScope(const char* family, double bytes, double flops, cudaStream_t s);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  int slot_ = -1;
+  cudaStream_t s_ = nullptr;
+};
+
+// ---------------------------------------------------------------- host topology
+// Edge numbering and signs follow include/rfcmp.h (Sec. 2, Eq. RWGdef, Eq. qHofj).
+struct Topology {
+  int64_t nv = 0, nc = 0, ne = 0;
+  int genus = 0;
+  std::vector<int32_t> tris;        // nc x 3
+  std::vector<int32_t> edge_verts;  // ne x 2 (v1, v2): c^+ traverses v1 -> v2
+  std::vector<int32_t> edge_cells;  // ne x 2 (c^+, c^-)
+  std::vector<int32_t> edge_free;   // ne x 2 (r^+, r^-)
+  std::vector<int32_t> cell_edges;  // nc x 3, edge opposite local vertex i
+  std::vector<int8_t> cell_sign;    // nc x 3, +1 if the cell is c^+ of that edge
+  // Lambda^T gather: for vertex v, entries [vtx_ptr[v], vtx_ptr[v+1]) of vtx_edge / vtx_sign
+  std::vector<int32_t> vtx_ptr, vtx_edge;
+  std::vector<int8_t> vtx_sign;
+  // Sigma^T Sigma as CSR (cell graph Laplacian: 3 on the diagonal, -1 per shared edge)
+  std::vector<int32_t> lap_ptr, lap_col;
+  std::vector<double> lap_val;
+  // unordered near pairs (s <= t) of cells sharing at least one vertex
+  std::vector<int32_t> near_pairs;  // P x 2
+  uint64_t hash = 0;                // of the connectivity only
+};
+
+// Builds the topology; returns RFCMP_OK or a mesh error with a message.
+int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& out, std::string& err);
+
+// G_ll (P1 mass matrix) as CSR over the vertices, local block A/12 [[2,1,1],[1,2,1],[1,1,2]].
+void mass_matrix_csr(const Topology& top, const double* verts, std::vector<int32_t>& ptr,
+                     std::vector<int32_t>& col, std::vector<double>& val);
+
+// ---------------------------------------------------------------- device geometry
+// Per-cell data for the assembly kernels; structure of arrays, FP32 copies of
+// quantities relative to the centroid plus FP64 copies for the near pairs.
+struct DeviceGeometry {
+  int32_t nc = 0, ne = 0, nv = 0;
+  int32_t ldN = 0, ldC = 0;  // padded row strides (elements) of T_A and V
+  // FP32 (far pairs)
+  float* cen_hi = nullptr;   // nc x 3 (centroid rounded to FP32)
+  float* cen_lo = nullptr;   // nc x 3 (centroid - cen_hi)
+  float* rho = nullptr;      // nc x 7 x 3 quadrature points minus centroid
+  float* wq = nullptr;       // nc x 7 weight x area
+  float* aloc = nullptr;     // nc x 3 x 3 free vertex of local basis i minus centroid
+  float* inv_area = nullptr; // nc
+  // FP64 (near pairs, excitation, far field)
+  double* verts = nullptr;    // nv x 3
+  double* cen64 = nullptr;    // nc x 3
+  double* area64 = nullptr;   // nc
+  double* qp64 = nullptr;     // nc x 7 x 3 quadrature points
+  // topology
+  int32_t* tris = nullptr;        // nc x 3
+  int32_t* cell_edges = nullptr;  // nc x 3
+  int8_t* cell_sign = nullptr;    // nc x 3
+  int32_t* edge_cells = nullptr;  // ne x 2
+  int32_t* edge_verts = nullptr;  // ne x 2
+  int32_t* edge_free = nullptr;   // ne x 2
+  int32_t* vtx_ptr = nullptr;     // nv + 1
+  int32_t* vtx_edge = nullptr;
+  int8_t* vtx_sign = nullptr;
+  int32_t* lap_ptr = nullptr;     // nc + 1
+  int32_t* lap_col = nullptr;
+  int32_t* near_pairs = nullptr;  // n_near x 2
+  int32_t n_near = 0;
+};
+
+// ---------------------------------------------------------------- kernels (k_assembly.cu)
+// T_A (ne x ne) and V (nc x nc), complex64 row-major, must be zeroed by the caller.
+cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, float2* V, cudaStream_t s);
+cudaError_t launch_assemble_near(const DeviceGeometry& g, double k, float2* TA, float2* V, cudaStream_t s);
+// e (ne x nrhs complex128), khat/pol device nrhs x 3
+cudaError_t launch_rhs_planewave(const DeviceGeometry& g, double k, const double* khat, const double* pol,
+                                 int nrhs, double2* e, cudaStream_t s);
+// radiation vector N(rhat) for nrhs currents and ndir directions -> out (ndir x nrhs x 3 complex)
+cudaError_t launch_farfield(const DeviceGeometry& g, double k, const double2* j, int nrhs, const double* dirs,
+                            int ndir, double2* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- kernels (k_linalg.cu)
+enum GemvMode { GEMV_F32 = 0, GEMV_FF = 1 };
+
+// y[:, r] = beta_y * y + scale * op(M) x[:, r], r < nrhs; M n x n complex64 row-major
+// (symmetric, so rows are columns); op = conj if conjugate.  x, y complex128 column-major
+// with leading dimension n.  scale is complex.
+cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate,
+                     double2 scale, bool accumulate, GemvMode mode, cudaStream_t s);
+// y = scale * (Mhi [+ Mlo]) x with a real symmetric n x n matrix in FP32 hi/lo planes.
+cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x, double2* y, int nrhs,
+                     double scale, bool accumulate, GemvMode mode, cudaStream_t s);
+
+// sparse transforms (Sec. 2, Eq. qHofj); all complex128, nrhs columns
+cudaError_t sigma_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s);   // N_C
+cudaError_t lambda_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s);  // N_V
+cudaError_t lap_apply(const DeviceGeometry& g, const double2* z, double2* out, int nrhs, cudaStream_t s); // Sigma^T Sigma z
+
+// Fused edge-space combination: out = a*x + b*(Sigma zs) + c*(Lambda zl) + d*(Sigma zs2) + e*w
+// with complex coefficients; any input may be null (its term is dropped).
+struct EdgeCombo {
+  const double2* x = nullptr;   double2 a{0, 0};
+  const double2* zs = nullptr;  double2 b{0, 0};   // N_C vector through Sigma
+  const double2* zl = nullptr;  double2 c{0, 0};   // N_V vector through Lambda
+  const double2* zs2 = nullptr; double2 d{0, 0};   // second N_C vector through Sigma
+  const double2* w = nullptr;   double2 e{0, 0};   // second edge vector
+};
+cudaError_t edge_combo(const DeviceGeometry& g, const EdgeCombo& c, double2* out, int nrhs, cudaStream_t s);
+
+// q = scale * diag(area) (z + w - mean(w)); mean over each column of w (N_C).  w may be null.
+cudaError_t star_middle(const DeviceGeometry& g, const double2* z, const double2* w, double scale, double2* q,
+                        int nrhs, double* scratch_mean, cudaStream_t s);
+
+// out = Pi diag(area) Pi w, Pi = I - 1 1^T / N_C (per column); scratch holds 4 x nrhs doubles
+cudaError_t pgp_apply(const DeviceGeometry& g, const double2* w, double2* out, int nrhs, double* scratch,
+                      cudaStream_t s);
+
+// vector kernels (length n per column, nrhs columns)
+cudaError_t vec_dot(const double2* a, const double2* b, int64_t n, int nrhs, double2* out, cudaStream_t s);  // out[r] = a^H b
+cudaError_t vec_axpy_cols(const double* coef, bool negate, const double2* x, double2* y, int64_t n, int nrhs,
+                          const int* active, cudaStream_t s);   // y += (+/-coef[r]) x
+cudaError_t vec_xpby_cols(const double2* x, const double* coef, double2* y, int64_t n, int nrhs,
+                          const int* active, cudaStream_t s);   // y = x + coef[r] y
+cudaError_t vec_copy(const double2* x, double2* y, int64_t n, cudaStream_t s);
+cudaError_t vec_scale(double2* y, double2 a, int64_t n, cudaStream_t s);
+// CG scalar step on device: alpha = rr/pAp etc. (see k_linalg.cu)
+cudaError_t cg_scalars_alpha(const double* rr, const double2* pAp, double* alpha, const int* active, int nrhs,
+                             cudaStream_t s);
+cudaError_t cg_scalars_beta(const double2* rr_new2, double* rr, double* beta, const int* active, int nrhs,
+                            cudaStream_t s);
+
+// Dense inverse of a sparse SPD (or singular Laplacian) matrix by Jacobi-preconditioned block CG.
+// A in CSR (n x n, FP64); rhs columns e_c - (project ? 1/n : 0); output X (FP32 hi + lo planes, n x n).
+// Returns the iterations used in *iters; work buffers are allocated inside.
+cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const double* val, int n, bool project,
+                                   double tol, int max_iter, float* Xhi, float* Xlo, int* iters, cudaStream_t s);
+
+}  // namespace rfcmp

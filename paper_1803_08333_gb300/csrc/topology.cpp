@@ -1,0 +1,226 @@
+// Host-side mesh topology for RWG functions and the quasi-Helmholtz transforms.
+//
+// Sec. 2, Eq. RWGdef: edge n carries the RWG function supported on its two
+// cells c_n^+ and c_n^- with free vertices r_n^+ and r_n^-.
+// Sec. 2, Eq. qHofj: Sigma (N x N_C) and Lambda (N x N_V) with entries +-1,
+// Lambda^T Sigma = 0.  Sec. 2 (graph Laplacians): Sigma^T Sigma is the cell
+// graph Laplacian, 3 on the diagonal and -1 for each pair of cells sharing an
+// edge.  Numbering and sign conventions: include/rfcmp.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_set>
+
+#include "rfcmp_internal.h"
+
+namespace rfcmp {
+
+namespace {
+
+struct HalfEdge {
+  int32_t lo, hi;   // sorted vertex pair
+  int32_t cell;     // owning cell
+  int32_t local;    // local index of the opposite vertex
+  int32_t a, b;     // the cell traverses a -> b
+};
+
+uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std::string& err) {
+  if (nc <= 0 || nv <= 0 || nc > (int64_t)1 << 28 || nv > (int64_t)1 << 28) {
+    err = "mesh sizes out of range";
+    return RFCMP_ERR_INVALID_ARG;
+  }
+  T = Topology();
+  T.nc = nc;
+  T.nv = nv;
+  T.tris.assign(tris, tris + 3 * nc);
+  std::vector<HalfEdge> he;
+  he.reserve(3 * nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    for (int i = 0; i < 3; ++i) {
+      int32_t a = tris[3 * c + (i + 1) % 3], b = tris[3 * c + (i + 2) % 3];
+      if (a < 0 || a >= nv || b < 0 || b >= nv) {
+        err = "vertex index out of range in cell " + std::to_string(c);
+        return RFCMP_ERR_MESH_NOT_MANIFOLD;
+      }
+      if (a == b) {
+        err = "degenerate cell " + std::to_string(c);
+        return RFCMP_ERR_MESH_NOT_MANIFOLD;
+      }
+      he.push_back({std::min(a, b), std::max(a, b), (int32_t)c, i, a, b});
+    }
+  }
+  std::sort(he.begin(), he.end(), [](const HalfEdge& x, const HalfEdge& y) {
+    if (x.lo != y.lo) return x.lo < y.lo;
+    if (x.hi != y.hi) return x.hi < y.hi;
+    return x.cell < y.cell;
+  });
+  if (he.size() % 2 != 0) {
+    err = "odd number of half-edges: the surface is not closed";
+    return RFCMP_ERR_MESH_NOT_MANIFOLD;
+  }
+  const int64_t ne = (int64_t)he.size() / 2;
+  T.ne = ne;
+  T.edge_verts.resize(2 * ne);
+  T.edge_cells.resize(2 * ne);
+  T.edge_free.resize(2 * ne);
+  T.cell_edges.assign(3 * nc, -1);
+  T.cell_sign.assign(3 * nc, 0);
+  for (int64_t n = 0; n < ne; ++n) {
+    const HalfEdge& p = he[2 * n];
+    const HalfEdge& m = he[2 * n + 1];
+    if (p.lo != m.lo || p.hi != m.hi || (2 * n + 2 < (int64_t)he.size() && he[2 * n + 2].lo == p.lo &&
+                                         he[2 * n + 2].hi == p.hi)) {
+      err = "edge (" + std::to_string(p.lo) + "," + std::to_string(p.hi) +
+            ") is not shared by exactly two cells";
+      return RFCMP_ERR_MESH_NOT_MANIFOLD;
+    }
+    if (!(p.a == m.b && p.b == m.a)) {
+      err = "cells " + std::to_string(p.cell) + " and " + std::to_string(m.cell) +
+            " are not consistently oriented";
+      return RFCMP_ERR_MESH_ORIENTATION;
+    }
+    T.edge_cells[2 * n] = p.cell;
+    T.edge_cells[2 * n + 1] = m.cell;
+    T.edge_verts[2 * n] = p.a;
+    T.edge_verts[2 * n + 1] = p.b;
+    T.edge_free[2 * n] = tris[3 * p.cell + p.local];
+    T.edge_free[2 * n + 1] = tris[3 * m.cell + m.local];
+    T.cell_edges[3 * p.cell + p.local] = (int32_t)n;
+    T.cell_sign[3 * p.cell + p.local] = 1;
+    T.cell_edges[3 * m.cell + m.local] = (int32_t)n;
+    T.cell_sign[3 * m.cell + m.local] = -1;
+  }
+  // every vertex must be used; Euler characteristic of a closed orientable surface
+  std::vector<int32_t> deg(nv, 0);
+  for (int64_t i = 0; i < 3 * nc; ++i) deg[tris[i]]++;
+  for (int64_t v = 0; v < nv; ++v)
+    if (deg[v] == 0) {
+      err = "vertex " + std::to_string(v) + " is not used by any cell";
+      return RFCMP_ERR_MESH_NOT_MANIFOLD;
+    }
+  int64_t chi = nv - ne + nc;
+  if (chi > 2 || (chi % 2) != 0) {
+    err = "Euler characteristic " + std::to_string(chi) + " is not that of a closed orientable surface";
+    return RFCMP_ERR_MESH_NOT_MANIFOLD;
+  }
+  T.genus = (int)((2 - chi) / 2);
+
+  // Lambda^T gather lists
+  T.vtx_ptr.assign(nv + 1, 0);
+  for (int64_t n = 0; n < ne; ++n) {
+    T.vtx_ptr[T.edge_verts[2 * n] + 1]++;
+    T.vtx_ptr[T.edge_verts[2 * n + 1] + 1]++;
+  }
+  for (int64_t v = 0; v < nv; ++v) T.vtx_ptr[v + 1] += T.vtx_ptr[v];
+  T.vtx_edge.resize(2 * ne);
+  T.vtx_sign.resize(2 * ne);
+  {
+    std::vector<int32_t> fill(T.vtx_ptr.begin(), T.vtx_ptr.end() - 1);
+    for (int64_t n = 0; n < ne; ++n) {
+      int32_t v1 = T.edge_verts[2 * n], v2 = T.edge_verts[2 * n + 1];
+      T.vtx_edge[fill[v1]] = (int32_t)n;
+      T.vtx_sign[fill[v1]++] = 1;
+      T.vtx_edge[fill[v2]] = (int32_t)n;
+      T.vtx_sign[fill[v2]++] = -1;
+    }
+  }
+  // Sigma^T Sigma (duplicates merged: two cells sharing two edges get -2)
+  T.lap_ptr.assign(nc + 1, 0);
+  T.lap_col.clear();
+  T.lap_val.clear();
+  for (int64_t c = 0; c < nc; ++c) {
+    int32_t nb[3];
+    for (int i = 0; i < 3; ++i) {
+      int32_t n = T.cell_edges[3 * c + i];
+      nb[i] = T.edge_cells[2 * n] == c ? T.edge_cells[2 * n + 1] : T.edge_cells[2 * n];
+    }
+    std::vector<std::pair<int32_t, double>> row = {{(int32_t)c, 3.0}};
+    for (int i = 0; i < 3; ++i) {
+      bool merged = false;
+      for (auto& e : row)
+        if (e.first == nb[i]) {
+          e.second -= 1.0;
+          merged = true;
+        }
+      if (!merged) row.push_back({nb[i], -1.0});
+    }
+    std::sort(row.begin(), row.end());
+    for (auto& e : row) {
+      T.lap_col.push_back(e.first);
+      T.lap_val.push_back(e.second);
+    }
+    T.lap_ptr[c + 1] = (int32_t)T.lap_col.size();
+  }
+  // near pairs: cells sharing a vertex
+  std::vector<int32_t> vc_ptr(nv + 1, 0), vc_cell(3 * nc);
+  for (int64_t i = 0; i < 3 * nc; ++i) vc_ptr[tris[i] + 1]++;
+  for (int64_t v = 0; v < nv; ++v) vc_ptr[v + 1] += vc_ptr[v];
+  {
+    std::vector<int32_t> fill(vc_ptr.begin(), vc_ptr.end() - 1);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int i = 0; i < 3; ++i) vc_cell[fill[tris[3 * c + i]]++] = (int32_t)c;
+  }
+  T.near_pairs.clear();
+  for (int64_t s = 0; s < nc; ++s) {
+    std::vector<int32_t> nbrs;
+    for (int i = 0; i < 3; ++i) {
+      int32_t v = tris[3 * s + i];
+      for (int32_t q = vc_ptr[v]; q < vc_ptr[v + 1]; ++q)
+        if (vc_cell[q] >= s) nbrs.push_back(vc_cell[q]);
+    }
+    std::sort(nbrs.begin(), nbrs.end());
+    nbrs.erase(std::unique(nbrs.begin(), nbrs.end()), nbrs.end());
+    for (int32_t t : nbrs) {
+      T.near_pairs.push_back((int32_t)s);
+      T.near_pairs.push_back(t);
+    }
+  }
+  uint64_t h = mix64((uint64_t)nv) ^ mix64((uint64_t)nc << 1);
+  for (int64_t i = 0; i < 3 * nc; ++i) h = mix64(h ^ (uint64_t)(uint32_t)tris[i]);
+  T.hash = h;
+  return RFCMP_OK;
+}
+
+void mass_matrix_csr(const Topology& T, const double* verts, std::vector<int32_t>& ptr, std::vector<int32_t>& col,
+                     std::vector<double>& val) {
+  const int64_t nv = T.nv, nc = T.nc;
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(nv);
+  for (int64_t c = 0; c < nc; ++c) {
+    const int32_t* t = &T.tris[3 * c];
+    const double* p0 = verts + 3 * t[0];
+    const double* p1 = verts + 3 * t[1];
+    const double* p2 = verts + 3 * t[2];
+    double u[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+    double w[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+    double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) rows[t[i]].push_back({t[j], area * (i == j ? 2.0 : 1.0) / 12.0});
+  }
+  ptr.assign(nv + 1, 0);
+  col.clear();
+  val.clear();
+  for (int64_t v = 0; v < nv; ++v) {
+    auto& r = rows[v];
+    std::sort(r.begin(), r.end());
+    for (size_t q = 0; q < r.size();) {
+      int32_t cidx = r[q].first;
+      double s = 0.0;
+      while (q < r.size() && r[q].first == cidx) s += r[q++].second;
+      col.push_back(cidx);
+      val.push_back(s);
+    }
+    ptr[v + 1] = (int32_t)col.size();
+  }
+}
+
+}  // namespace rfcmp

@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads and exports every entry point include/rfcmp.h declares.
+
+No compute calls: these run without a GPU.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1803_08333_gb300 as rf
+from paper_1803_08333_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "rfcmp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rfcmp_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build.build()
+
+
+def test_header_declarations_match_binding_list():
+    assert _declared() == sorted(rf.EXPORTED_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_defaults(libpath):
+    L = rf.lib()
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert L.rfcmp_strerror(code)
+    o = rf.OpOpts()
+    L.rfcmp_op_opts_default(ctypes.byref(o))
+    assert o.power_steps == 30 and o.scaling == 0 and o.factor_tol == 1e-13
+    s = rf.SolveOpts()
+    L.rfcmp_solve_opts_default(ctypes.byref(s))
+    assert s.tol == 1e-6 and s.precision == 0 and s.max_refine == 8
+
+
+def test_struct_layouts_match_header(libpath):
+    # sizes implied by include/rfcmp.h on LP64
+    assert ctypes.sizeof(rf.OpOpts) == 4 + 4 + 8 * 4 + 4 * 8
+    assert ctypes.sizeof(rf.SolveOpts) == 8 + 4 + 4 + 8 + 4 + 4 + 4 * 8
+    assert ctypes.sizeof(rf.SolveReport) == 4 * 4 + 8
+    assert ctypes.sizeof(rf.OpInfo) == 3 * 8 + 2 * 4 + 4 * 8 + 8 + 3 * 8 + 2 * 4
+
+
+def test_no_device_is_an_error_not_a_fallback(libpath):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = rf.lib().rfcmp_ctx_create(0, 0, ctypes.byref(h))
+    assert st == -8  # RFCMP_ERR_NO_DEVICE
+    assert not h.value

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated in the spec contract of this library): matrix
+entries <= 1e-5 relative (Frobenius, real and imaginary parts separately),
+solution currents <= 1e-6 relative, RCS <= 1e-3 dB where sigma is within 40 dB
+of its peak.  Float-float applications of the stored complex64 operator are
+checked against FP64 products of the same stored matrices at 1e-12.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import efie, farfield, krylov, rfcmp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1803_08333_gb300 as rf  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1803_08333_gb300 import build
+
+    build.build()
+    c = rf.Context(0)
+    yield c
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _parts(a, b):
+    return _rel(a.real, b.real), _rel(a.imag, b.imag)
+
+
+MESHES = {
+    "ico": lambda: synth.geodesic_sphere(1, seed=9),  # 20 cells: a single partial tile
+    "l2": lambda: synth.geodesic_sphere(4, seed=1),  # 320 cells: ragged tiles
+    "l3": lambda: synth.geodesic_sphere(8, seed=1),  # 1280 cells, N = 1920
+    "torus": lambda: synth.torus(3, 5, jitter=0.02),  # genus 1, N = 45 (odd, padded rows)
+    "cube": lambda: synth.cube(3),  # sharp edges
+}
+
+
+def _oracle(memo, name, k):
+    m = MESHES[name]()
+    D = memo(("gdisc", name), lambda: efie.discretize(m.verts, m.tris))
+    TA, V = memo(("gop", name, k), lambda: efie.assemble(D, k))
+    return m, D, TA, V
+
+
+@pytest.mark.parametrize("name", ["ico", "l2", "torus", "cube"])
+def test_topology_numbering_matches_oracle(ctx, memo, name):
+    m, D, _, _ = _oracle(memo, name, 1.0)
+    op = rf.Operator(ctx, m.verts, m.tris, 1.0, scaling="k")
+    ev, ec = op.edges()
+    assert np.array_equal(ev, D.top.edge_verts)
+    assert np.array_equal(ec, D.top.edge_cells)
+    assert op.info().genus == D.top.genus
+
+
+@pytest.mark.parametrize("name,k", [("ico", 1.0), ("l2", 1.0), ("l2", 1e-5), ("torus", 2.0), ("cube", 0.7), ("l3", 1.0)])
+def test_matrix_entries(ctx, memo, name, k):
+    m, D, TA, V = _oracle(memo, name, k)
+    op = rf.Operator(ctx, m.verts, m.tris, k, scaling="k")
+    gTA = op.export("T_A").cpu().numpy().astype(np.complex128)
+    gV = op.export("V").cpu().numpy().astype(np.complex128)
+    for got, ref in ((gTA, TA), (gV, V)):
+        re, im = _parts(got, ref)
+        assert re <= 1e-5 and im <= 1e-5, (re, im)
+    # near-pair entries (FP64 path): entrywise
+    near = D.near
+    ent = np.abs(gV[near[:, 0], near[:, 1]] - V[near[:, 0], near[:, 1]]) / np.abs(V[near[:, 0], near[:, 1]])
+    assert ent.max() <= 1e-6
+
+
+def test_factors(ctx, memo):
+    m, D, _, _ = _oracle(memo, "l2", 1.0)
+    F = memo(("gfac", "l2"), lambda: rfcmp.factors(D))
+    op = rf.Operator(ctx, m.verts, m.tris, 1.0, scaling="k")
+    Lp = op.export("LPLUS").cpu().numpy()
+    Gi = op.export("GLL_INV").cpu().numpy()
+    assert _rel(Lp, F.Lplus) <= 1e-11
+    assert _rel(Gi, F.Gll_inv) <= 1e-11
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_excitation(ctx, memo, nrhs):
+    m, D, _, _ = _oracle(memo, "l2", 1.3)
+    op = rf.Operator(ctx, m.verts, m.tris, 1.3, scaling="k")
+    kh, pol = synth.random_plane_waves(nrhs, seed=4)
+    e = op.rhs_planewave(kh, pol).cpu().numpy()
+    ref = efie.excitation(D, 1.3, kh, pol).T
+    assert _rel(e, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("name,k", [("l2", 1.0), ("torus", 2.0), ("l2", 1e-4)])
+@pytest.mark.parametrize("nrhs", [1, 2, 5])
+def test_operator_applications_ff_accurate(ctx, memo, name, k, nrhs):
+    """T, T_A, T_Phi, T^H through the library equal FP64 products of its own stored matrices."""
+    m, D, _, _ = _oracle(memo, name, k)
+    op = rf.Operator(ctx, m.verts, m.tris, k, scaling="k")
+    gTA = op.export("T_A").cpu().numpy().astype(np.complex128)
+    gV = op.export("V").cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(nrhs)
+    x = rng.standard_normal((nrhs, op.N)) + 1j * rng.standard_normal((nrhs, op.N))
+    xt = torch.from_numpy(x)
+    S = D.Sigma.toarray()
+    T = 1j * k * gTA + S @ gV @ S.T / (1j * k)
+    refs = {"T_A": gTA @ x.T, "T_PHI": S @ gV @ S.T @ x.T, "T": T @ x.T, "T_ADJ": T.conj().T @ x.T}
+    for which, ref in refs.items():
+        got = op.apply(which, xt).cpu().numpy().T
+        assert _rel(got, ref) <= 1e-12, which
+
+
+@pytest.mark.parametrize("name,k", [("l2", 1.0), ("l2", 1e-3), ("torus", 1.5), ("cube", 0.5)])
+def test_rfcmp_application_and_preconditioners(ctx, memo, name, k):
+    m, D, TA, V = _oracle(memo, name, k)
+    F = memo(("gfac", name), lambda: rfcmp.factors(D))
+    sc = rfcmp.Scaling(0.37 * np.sqrt(k), 1.3 / np.sqrt(k), 0.8 * k)
+    op = rf.Operator(ctx, m.verts, m.tris, k, scaling="fixed", alpha=sc.alpha, beta=sc.beta, gamma=sc.gamma)
+    gTA = op.export("T_A").cpu().numpy().astype(np.complex128)
+    gV = op.export("V").cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, op.N)) + 1j * rng.standard_normal((2, op.N))
+    got = op.apply("A", torch.from_numpy(x)).cpu().numpy()
+    for c in range(2):
+        # same stored matrices: the composition itself must match to float-float accuracy
+        ref_same = rfcmp.apply_A(F, gTA, gV, k, sc, x[c])
+        assert _rel(got[c], ref_same) <= 1e-9
+        # against the oracle's FP64 matrices: limited by the complex64 operator
+        ref = rfcmp.apply_A(F, TA, V, k, sc, x[c])
+        assert _rel(got[c], ref) <= 1e-5
+    Po, Pm = rfcmp.preconditioners(F, sc)
+    for which, M in (("P_O", Po), ("P_O_ADJ", Po.conj().T), ("P_M", Pm), ("P_SIGMA", F.P_S), ("P_LAMBDAH", F.P_LH)):
+        y = op.precondition(which, torch.from_numpy(x)).cpu().numpy()
+        assert _rel(y.T, M @ x.T) <= 1e-11, which
+
+
+@pytest.mark.parametrize("k", [1.0, 1e-2, 1e-5])
+def test_power_iteration_scaling(ctx, memo, k):
+    m, D, TA, V = _oracle(memo, "l2", k)
+    F = memo(("gfac", "l2"), lambda: rfcmp.factors(D))
+    op = rf.Operator(ctx, m.verts, m.tris, k, scaling="power", power_steps=30)
+    ref = rfcmp.power_scaling(F, TA, V, k, steps=30)
+    a, b, g = op.scaling
+    assert abs(a / ref.alpha - 1) < 1e-4
+    assert abs(b / ref.beta - 1) < 1e-4
+    assert abs(g / ref.gamma - 1) < 1e-3
+
+
+@pytest.mark.parametrize("name,k,prec", [("l2", 1.0, "mixed"), ("l2", 1e-5, "mixed"), ("torus", 2.0, "mixed"),
+                                          ("cube", 0.5, "ff"), ("l3", 1.0, "mixed"), ("ico", 1.0, "mixed")])
+def test_solution_currents(ctx, memo, name, k, prec):
+    m, D, TA, V = _oracle(memo, name, k)
+    F = memo(("gfac", name), lambda: rfcmp.factors(D))
+    kh, pol = synth.plane_wave_z()
+    e_ref = efie.excitation(D, k, kh, pol)[:, 0]
+    if k >= 1e-2:
+        j_ref = krylov.lu_solve(efie.efie_matrix(D, TA, V, k), -e_ref)
+    else:
+        j_ref, _, _ = rfcmp.solve(F, TA, V, k, rfcmp.power_scaling(F, TA, V, k), e_ref, 1e-13)
+    op = rf.Operator(ctx, m.verts, m.tris, k)
+    e = op.rhs_planewave(kh, pol)
+    j, rep = op.solve(e, tol=1e-10, precision=prec)
+    assert rep[0].converged and rep[0].residual <= 1e-10
+    jg = j.cpu().numpy()[0]
+    assert _rel(jg, j_ref) <= 1e-6
+    # per component (loop part and star part; the star part is O(k) smaller at low k)
+    zs = lambda v: F.Sigma @ (F.Lplus @ (F.Sigma.T @ v))  # noqa: E731
+    assert _rel(zs(jg), zs(j_ref)) <= 1e-6
+    assert _rel(jg - zs(jg), j_ref - zs(j_ref)) <= 1e-6
+
+
+def test_rcs_matches_oracle(ctx, memo):
+    m, D, TA, V = _oracle(memo, "l3", 1.0)
+    kh, pol = synth.plane_wave_z()
+    e_ref = efie.excitation(D, 1.0, kh, pol)[:, 0]
+    j_ref = krylov.lu_solve(efie.efie_matrix(D, TA, V, 1.0), -e_ref)
+    op = rf.Operator(ctx, m.verts, m.tris, 1.0)
+    j, rep = op.solve(op.rhs_planewave(kh, pol), tol=1e-8)
+    th = np.linspace(0, np.pi, 181)
+    for phi in (0.0, np.pi / 2):
+        dirs = farfield.cut_directions(th, phi)
+        ref = farfield.bistatic_rcs(D, j_ref, 1.0, dirs)
+        got = op.farfield(j, dirs)[0]
+        keep = ref > ref.max() * 1e-4
+        assert np.abs(got[keep] - 10 * np.log10(ref[keep])).max() <= 1e-3
+
+
+def test_multi_rhs_columns_independent(ctx, memo):
+    """Each column of a batched solve equals its single-column solve."""
+    m, D, _, _ = _oracle(memo, "l2", 1.2)
+    op = rf.Operator(ctx, m.verts, m.tris, 1.2)
+    kh, pol = synth.random_plane_waves(5, seed=8)
+    e = op.rhs_planewave(kh, pol)
+    jb, rb = op.solve(e, tol=1e-10)
+    for c in (0, 3):
+        j1, r1 = op.solve(e[c : c + 1], tol=1e-10)
+        assert _rel(jb[c].cpu().numpy(), j1[0].cpu().numpy()) <= 1e-8
+    assert all(r.converged for r in rb)
+
+
+def test_solve_host_buffers(ctx, memo):
+    m, D, _, _ = _oracle(memo, "l2", 1.0)
+    op = rf.Operator(ctx, m.verts, m.tris, 1.0)
+    e = op.rhs_planewave(*synth.plane_wave_z())
+    jd, _ = op.solve(e, tol=1e-9)
+    jh, rep = op.solve_host(e.cpu().numpy(), tol=1e-9)
+    assert _rel(jh[0], jd.cpu().numpy()[0]) <= 1e-12
+
+
+def test_error_codes(ctx):
+    m = synth.geodesic_sphere(2)
+    with pytest.raises(rf.RfcmpError) as ei:
+        rf.Operator(ctx, m.verts, m.tris[:-1], 1.0)
+    assert ei.value.status == -2
+    bad = m.tris.copy()
+    bad[0] = bad[0, [0, 2, 1]]
+    with pytest.raises(rf.RfcmpError) as ei:
+        rf.Operator(ctx, m.verts, bad, 1.0)
+    assert ei.value.status == -3
+    with pytest.raises(rf.RfcmpError) as ei:
+        rf.Operator(ctx, m.verts, m.tris, -1.0)
+    assert ei.value.status == -1
+    small = rf.Context(0, hbm_budget_bytes=1 << 20)
+    with pytest.raises(rf.RfcmpError) as ei:
+        rf.Operator(small, m.verts, m.tris, 1.0)
+    assert ei.value.status == -4
