@@ -53,10 +53,13 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+MESH_N = 32
+
+
 def _mesh():
     import synth
 
-    return synth.geodesic_sphere(32, seed=2)
+    return synth.geodesic_sphere(MESH_N, seed=2)
 
 
 def _cut_dirs():
@@ -387,7 +390,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh-n", type=int, default=32,
+                    help="geodesic frequency of the sphere (32 = the workload; smaller for profiling captures)")
+    ap.add_argument("--ka", type=float, nargs="*", default=None, help="override the wavenumber sweep")
     args = ap.parse_args()
+    global MESH_N, KA, WORKLOAD
+    if args.mesh_n != 32 or args.ka:
+        MESH_N = args.mesh_n
+        KA = args.ka or KA
+        WORKLOAD = "profiling_case_sphere_f%d" % MESH_N
     if args.impl == "reference":
         bench_reference(args)
     else:

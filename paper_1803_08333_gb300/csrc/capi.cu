@@ -860,6 +860,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   RF_CUDA(cudaMemsetAsync(op->V, 0, (size_t)op->ldC * C * sizeof(float2), 0));
   RF_K(launch_assemble_far(op->g, (float)k, op->TA, op->V, 0));
   RF_K(launch_assemble_near(op->g, k, op->TA, op->V, 0));
+  RF_K(launch_mirror_upper(op->TA, N, op->ldN, 0));
   RF_CUDA(cudaEventRecord(e1, 0));
   rc = compute_scaling(raw, o, 0);
   RF_CUDA(cudaEventRecord(e2, 0));

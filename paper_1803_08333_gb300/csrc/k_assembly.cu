@@ -187,8 +187,9 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
         const float vi = pa_i - (bx * Ir_i[0] + by * Ir_i[1] + bz * Ir_i[2]) + ab * I0i;
         const float f = sa * Tt.sign[tl][b];
         const int n = Tt.edge[tl][b];
-        atomic_add_c64(&TA[(size_t)m * ldN + n], f * vr, f * vi);
-        atomic_add_c64(&TA[(size_t)n * ldN + m], f * vr, f * vi);
+        // T_A is complex symmetric: only the upper triangle is accumulated (m != n on far pairs),
+        // the lower one is mirrored afterwards so that both are bit-identical
+        atomic_add_c64(&TA[(size_t)min(m, n) * ldN + max(m, n)], f * vr, f * vi);
       }
     }
   }
@@ -381,9 +382,37 @@ near_pairs_kernel(const DeviceGeometry g, double k, float2* __restrict__ TA, flo
       vi += ab * I0i;
       const double f = sa * (double)g.cell_sign[3 * t + b];
       const int n = g.cell_edges[3 * t + b];
-      atomic_add_c64(&TA[(size_t)m * ldN + n], (float)(f * vr), (float)(f * vi));
-      if (s != t) atomic_add_c64(&TA[(size_t)n * ldN + m], (float)(f * vr), (float)(f * vi));
+      // upper triangle only: a distinct pair reaches (m, n) and (n, m) once each, which is
+      // twice on the diagonal; the self pair lists both (a, b) and (b, a) itself
+      double mult = 1.0;
+      if (s != t) {
+        if (m == n) mult = 2.0;
+      } else if (m > n) {
+        mult = 0.0;
+      }
+      if (mult != 0.0)
+        atomic_add_c64(&TA[(size_t)min(m, n) * ldN + max(m, n)], (float)(mult * f * vr), (float)(mult * f * vi));
     }
+  }
+}
+
+// ---------------------------------------------------------------- mirror upper -> lower
+constexpr int MT = 32;
+
+__global__ void mirror_upper_kernel(float2* __restrict__ M, int n, size_t ld) {
+  // block (bx, by) with by <= bx copies tile (by, bx) of the upper triangle into tile (bx, by)
+  __shared__ float2 tile[MT][MT + 1];
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (by > bx) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < MT; r += 8) {
+    const int row = by * MT + r, col = bx * MT + tx;
+    if (row < n && col < n && row < col) tile[r][tx] = M[(size_t)row * ld + col];
+  }
+  __syncthreads();
+  for (int r = ty; r < MT; r += 8) {
+    const int row = bx * MT + r, col = by * MT + tx;  // lower entry (row, col) = upper (col, row)
+    if (row < n && col < n && col < row) M[(size_t)row * ld + col] = tile[tx][r];
   }
 }
 
@@ -483,6 +512,14 @@ cudaError_t launch_assemble_near(const DeviceGeometry& g, double k, float2* TA, 
   const int blocks = (g.n_near + NEAR_PAIRS_PER_BLOCK - 1) / NEAR_PAIRS_PER_BLOCK;
   ProfScope prof("assemble_near", 0.0, 0.0, s);
   near_pairs_kernel<<<blocks, NEAR_THREADS, 0, s>>>(g, k, TA, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_upper(float2* M, int n, int ld, cudaStream_t s) {
+  const int nb = (n + MT - 1) / MT;
+  dim3 grid(nb, nb), block(MT, 8);
+  ProfScope prof("mirror_upper", 8.0 * (double)n * n, 0.0, s);
+  mirror_upper_kernel<<<grid, block, 0, s>>>(M, n, (size_t)ld);
   return cudaGetLastError();
 }
 

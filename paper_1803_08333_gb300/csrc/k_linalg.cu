@@ -760,13 +760,20 @@ __global__ void bcg_spmm_kernel(const int32_t* __restrict__ ptr, const int32_t* 
   atomicAdd(&pAp[c], dot);
 }
 
-// X += a P, R -= a AP, rr_new += R.R with a = rr / pAp
+// X += a P, R -= a AP, rr_new += R.R with a = rr / pAp.  A column whose residual has
+// reached the tolerance is frozen: continuing CG on it once p^T A p has fallen to rounding
+// level (or below zero on the singular Laplacian) makes the step explode.
 __global__ void bcg_update_kernel(int n, int W, const double* __restrict__ rr, const double* __restrict__ pAp,
-                                  double* __restrict__ X, double* __restrict__ R, const double* __restrict__ P,
+                                  const double* __restrict__ bb, double tol2, double* __restrict__ X,
+                                  double* __restrict__ R, const double* __restrict__ P,
                                   const double* __restrict__ AP, double* __restrict__ rr_new) {
   const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
   const int rsub = threadIdx.x / BCG_COLS;
   if (c >= W) return;
+  if (rr[c] <= tol2 * bb[c]) {
+    if (blockIdx.y == 0 && rsub == 0) rr_new[c] = rr[c];
+    return;
+  }
   const double d = pAp[c];
   const double a = d > 0.0 ? rr[c] / d : 0.0;
   const int r0 = blockIdx.y * BCG_ROWS;
@@ -782,23 +789,24 @@ __global__ void bcg_update_kernel(int n, int W, const double* __restrict__ rr, c
   atomicAdd(&rr_new[c], dot);
 }
 
-// P = R + (rr_new / rr) P; zero pAp and the next accumulator
+// P = R + (rr_new / rr) P (frozen columns keep P); zero pAp and the next accumulator
 __global__ void bcg_direction_kernel(int n, int W, const double* __restrict__ rr, const double* __restrict__ rr_new,
-                                     const double* __restrict__ R, double* __restrict__ P, double* __restrict__ pAp,
-                                     double* __restrict__ rr_next) {
+                                     const double* __restrict__ bb, double tol2, const double* __restrict__ R,
+                                     double* __restrict__ P, double* __restrict__ pAp, double* __restrict__ rr_next) {
   const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
   const int rsub = threadIdx.x / BCG_COLS;
   if (c >= W) return;
+  if (blockIdx.y == 0 && rsub == 0) {
+    pAp[c] = 0.0;
+    rr_next[c] = 0.0;
+  }
+  if (rr_new[c] <= tol2 * bb[c]) return;
   const double b = rr[c] > 0.0 ? rr_new[c] / rr[c] : 0.0;
   const int r0 = blockIdx.y * BCG_ROWS;
   const int r1 = min(n, r0 + BCG_ROWS);
   for (int i = r0 + rsub; i < r1; i += blockDim.x / BCG_COLS) {
     const size_t o = (size_t)i * W + c;
     P[o] = R[o] + b * P[o];
-  }
-  if (blockIdx.y == 0 && rsub == 0) {
-    pAp[c] = 0.0;
-    rr_next[c] = 0.0;
   }
 }
 
@@ -886,11 +894,11 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
       }
       {
         ProfScope prof("factor_bcg_update", 48.0 * n * w, 0.0, s);
-        bcg_update_kernel<<<grid, threads, 0, s>>>(n, w, rr, pAp, X, R, P, AP, rr_new);
+        bcg_update_kernel<<<grid, threads, 0, s>>>(n, w, rr, pAp, bb, tol * tol, X, R, P, AP, rr_new);
       }
       {
         ProfScope prof("factor_bcg_direction", 24.0 * n * w, 0.0, s);
-        bcg_direction_kernel<<<grid, threads, 0, s>>>(n, w, rr, rr_new, R, P, pAp, rr_next);
+        bcg_direction_kernel<<<grid, threads, 0, s>>>(n, w, rr, rr_new, bb, tol * tol, R, P, pAp, rr_next);
       }
       ++it;
       if (it % 16 == 0 || it == max_iter) {

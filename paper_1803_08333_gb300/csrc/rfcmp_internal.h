@@ -94,6 +94,8 @@ struct DeviceGeometry {
 // T_A (ne x ne) and V (nc x nc), complex64 row-major, must be zeroed by the caller.
 cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, float2* V, cudaStream_t s);
 cudaError_t launch_assemble_near(const DeviceGeometry& g, double k, float2* TA, float2* V, cudaStream_t s);
+// T_A is accumulated in its upper triangle; this copies it to the lower one (bit-identical symmetry)
+cudaError_t launch_mirror_upper(float2* M, int n, int ld, cudaStream_t s);
 // e (ne x nrhs complex128), khat/pol device nrhs x 3
 cudaError_t launch_rhs_planewave(const DeviceGeometry& g, double k, const double* khat, const double* pol,
                                  int nrhs, double2* e, cudaStream_t s);

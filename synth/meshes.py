@@ -236,15 +236,11 @@ def torus(nu: int, nv: int, R: float = 1.0, r: float = 0.4, jitter: float = 0.0,
             tris.append((a, b, c))
             tris.append((a, c, d))
     tris = np.array(tris, dtype=np.int64)
-    # outward: normal along the tube's radial direction
+    # the (u, v) grid orders every cell the same way; flip all if the enclosed volume is negative
     p = verts[tris]
-    nrm = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
-    cen = p.mean(axis=1)
-    ring = cen.copy()
-    ring[:, 2] = 0.0
-    ring *= (R / np.linalg.norm(ring, axis=1))[:, None]
-    flip = np.einsum("ij,ij->i", nrm, cen - ring) < 0
-    tris[flip, 1], tris[flip, 2] = tris[flip, 2].copy(), tris[flip, 1].copy()
+    vol = np.einsum("ij,ij->i", p[:, 0], np.cross(p[:, 1], p[:, 2])).sum() / 6.0
+    if vol < 0:
+        tris = tris[:, [0, 2, 1]]
     return Mesh(verts, tris.astype(np.int32), f"torus_{nu}x{nv}_R{R}_r{r}")
 
 

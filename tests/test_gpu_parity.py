@@ -210,7 +210,8 @@ def test_solve_host_buffers(ctx, memo):
     e = op.rhs_planewave(*synth.plane_wave_z())
     jd, _ = op.solve(e, tol=1e-9)
     jh, rep = op.solve_host(e.cpu().numpy(), tol=1e-9)
-    assert _rel(jh[0], jd.cpu().numpy()[0]) <= 1e-12
+    # two solves to 1e-9 differ by the order of the atomic partial sums in their dot products
+    assert _rel(jh[0], jd.cpu().numpy()[0]) <= 1e-8
 
 
 def test_error_codes(ctx):
@@ -226,7 +227,7 @@ def test_error_codes(ctx):
     with pytest.raises(rf.RfcmpError) as ei:
         rf.Operator(ctx, m.verts, m.tris, -1.0)
     assert ei.value.status == -1
-    small = rf.Context(0, hbm_budget_bytes=1 << 20)
+    small = rf.Context(0, hbm_budget_bytes=1 << 16)  # the level-1 sphere needs about 300 KB
     with pytest.raises(rf.RfcmpError) as ei:
         rf.Operator(small, m.verts, m.tris, 1.0)
     assert ei.value.status == -4
