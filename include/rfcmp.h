@@ -98,10 +98,13 @@ typedef enum {
 
 typedef struct {
   int32_t scaling;      /* rfcmp_scaling; default RFCMP_SCALE_POWER */
-  int32_t power_steps;  /* power-iteration steps for each norm; default 30 */
+  int32_t power_steps;  /* maximum power-iteration steps for each norm; default 30 */
   double alpha, beta, gamma; /* used with RFCMP_SCALE_FIXED */
   double factor_tol;    /* relative residual of the dense-inverse builds of (Sigma^T Sigma)^+
                            and G_ll^{-1}; default 1e-13 */
+  double power_rtol;    /* power iteration stops once the Rayleigh quotient changes by at most
+                           power_rtol (relative) between two steps, after at least 2 and at most
+                           power_steps steps; 0 = always power_steps; default 1e-3 */
   int32_t reserved[8];  /* must be zero */
 } rfcmp_op_opts;
 

@@ -22,7 +22,9 @@ so each principal diagonal block of the system has unit norm.  Under the
 closed-form choice alpha = sqrt k, beta = 1/sqrt k, gamma = k (Sec. 4, third
 display) the variant reduces to the theory scaling of Sec. 3.  The norms are
 estimated by power iteration (Sec. 4) from a start vector given by the caller
-(``splitmix_start``), a fixed number of steps, Rayleigh quotient estimate.
+(``splitmix_start``), Rayleigh quotient estimate; at most 30 steps, stopping once
+the estimate changes by at most 1e-3 (relative) between steps (the paper states
+neither; the solution does not depend on these choices).
 
 Low-frequency-stable application (reading of Eq. LastProofBigUmformung with
 the separate storage of T_A and V, Sec. 4): the products that vanish exactly,
@@ -97,15 +99,21 @@ def kscale(k: float) -> Scaling:
     return Scaling(np.sqrt(k), 1.0 / np.sqrt(k), k)
 
 
-def power_norm(apply, x0: np.ndarray, steps: int) -> float:
-    """Largest eigenvalue of an HPSD operator: normalised power steps, Rayleigh quotient."""
+def power_norm(apply, x0: np.ndarray, steps: int, rtol: float = 0.0) -> float:
+    """Largest eigenvalue of an HPSD operator: normalised power steps, Rayleigh quotient.
+
+    Stops after `steps` steps, or earlier (after at least 2) once the Rayleigh quotient
+    changes by at most rtol relative to its value.
+    """
     x = x0.astype(np.complex128)
     x = x / np.linalg.norm(x)
     lam = 0.0
-    for _ in range(steps):
+    for it in range(steps):
         y = apply(x)
-        lam = np.vdot(x, y).real
+        prev, lam = lam, np.vdot(x, y).real
         x = y / np.linalg.norm(y)
+        if rtol > 0 and it >= 1 and abs(lam - prev) <= rtol * abs(lam):
+            break
     return lam
 
 
@@ -121,16 +129,16 @@ def block_operators(F: Factors, TA: np.ndarray, V: np.ndarray):
     return X, Y, Z
 
 
-def power_scaling(F: Factors, TA, V, k: float, steps: int = 30, exact: bool = False) -> Scaling:
+def power_scaling(F: Factors, TA, V, k: float, steps: int = 30, exact: bool = False, rtol: float = 1e-3) -> Scaling:
     """alpha, beta, gamma by power iteration (Sec. 4), or by exact norms (for pins)."""
     X, Y, Z = block_operators(F, TA, V)
     N = TA.shape[0]
     if exact:
         nx, ny, nz = (np.linalg.eigvalsh(0.5 * (M + M.conj().T))[-1] for M in (X, Y, Z))
     else:
-        nx = power_norm(lambda v: X @ v, splitmix_start(N, 1), steps)
-        ny = power_norm(lambda v: Y @ v, splitmix_start(N, 2), steps)
-        nz = power_norm(lambda v: Z @ v, splitmix_start(N, 3), steps)
+        nx = power_norm(lambda v: X @ v, splitmix_start(N, 1), steps, rtol)
+        ny = power_norm(lambda v: Y @ v, splitmix_start(N, 2), steps, rtol)
+        nz = power_norm(lambda v: Z @ v, splitmix_start(N, 3), steps, rtol)
     alpha = (k * k * nx) ** 0.25
     beta = (ny / (k * k)) ** 0.25
     gamma = k * k / (alpha * alpha) * nz

@@ -18,10 +18,6 @@
 
 #include "rfcmp_internal.h"
 
-namespace rfcmp {
-int padded_ld(int n);
-}
-
 using namespace rfcmp;
 
 // ---------------------------------------------------------------- errors
@@ -190,6 +186,7 @@ struct Workspace {
   // vertex space (N_V)
   double2 *t = nullptr, *tg = nullptr;
   double* mean = nullptr;  // 4 x cols
+  GemvScratch gs;
   ~Workspace() {
     for (void* p : owned) cudaFree(p);
   }
@@ -247,6 +244,15 @@ int ensure_workspace(rfcmp_op* op, int cols) {
     RF_TRY(dalloc(p, C * cols, ws->owned));
   for (double2** p : {&ws->t, &ws->tg}) RF_TRY(dalloc(p, NV * cols, ws->owned));
   RF_TRY(dalloc(&ws->mean, 4 * (size_t)cols, ws->owned));  // pgp_apply uses 4 per column
+  {
+    const int capn = (int)std::max<int64_t>(N, std::max<int64_t>(C, NV));
+    ws->gs.cap_n = capn;
+    ws->gs.cap_ld = padded_ld(capn);
+    ws->gs.cap_cols = 4;
+    RF_TRY(dalloc(&ws->gs.xh, (size_t)ws->gs.cap_ld * 4, ws->owned));
+    RF_TRY(dalloc(&ws->gs.xl, (size_t)ws->gs.cap_ld * 4, ws->owned));
+    RF_TRY(dalloc(&ws->gs.acc, (size_t)capn * 4, ws->owned));
+  }
   op->ws = std::move(ws);
   return RFCMP_OK;
 }
@@ -277,7 +283,7 @@ int ensure_solve_buffers(rfcmp_op* op, int cols) {
 // z = (Sigma^T Sigma)^+ Sigma^T x  (N_C) using s as scratch for Sigma^T x
 int star_coeff(rfcmp_op* op, const double2* x, double2* s, double2* z, int nr, GemvMode m, cudaStream_t st) {
   RF_K(sigma_t(op->g, x, s, nr, st));
-  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, (int)op->top.nc, s, z, nr, 1.0, false, m, st));
+  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, (int)op->top.nc, s, z, nr, 1.0, false, m, op->ws->gs, st));
   return RFCMP_OK;
 }
 
@@ -301,15 +307,15 @@ int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cu
     RF_K(edge_combo(g, c, W.v, nr, st));
   }
   // u = T_A v ; w = V Sigma^T x / (k b)
-  RF_K(gemv_c64(op->TA, N, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, st));
-  RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, st));
+  RF_K(gemv_c64(op->TA, N, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, op->ws->gs, st));
+  RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, op->ws->gs, st));
   // zu = L^+ Sigma^T u ; tg = G_ll^{-1} Lambda^T u
   RF_TRY(star_coeff(op, W.u, W.s, W.zu, nr, m, st));
   RF_K(lambda_t(g, W.u, W.t, nr, st));
-  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, st));
+  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, op->ws->gs, st));
   // q = L^+ G_pp^{-1} (zu + w - mean(w)) / b^2
   RF_K(star_middle(g, W.zu, W.w, 1.0, W.q0, nr, W.mean, st));
-  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, op->ws->gs, st));
   // y = Lambda tg / a^2 + (u - Sigma zu) / gamma + Sigma q
   {
     EdgeCombo c;
@@ -324,9 +330,9 @@ int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cu
     RF_K(edge_combo(g, c, W.y, nr, st));
   }
   // up = conj(T_A) y ; vp = conj(V) (Sigma^T Sigma) q / (k b)
-  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
+  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, op->ws->gs, st));
   RF_K(lap_apply(g, W.q, W.Lq, nr, st));
-  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, st));
+  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, op->ws->gs, st));
   // zp = L^+ Sigma^T up
   RF_TRY(star_coeff(op, W.up, W.s, W.z, nr, m, st));
   // out = -(ik/a) up + (ik/a - k/b) Sigma zp + Sigma vp
@@ -352,9 +358,9 @@ int apply_rhs(rfcmp_op* op, const double2* e, double2* out, int nr, GemvMode m, 
   const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
   RF_TRY(star_coeff(op, e, W.s, W.zu, nr, m, st));  // ze
   RF_K(star_middle(g, W.zu, nullptr, 1.0, W.q0, nr, W.mean, st));
-  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, op->ws->gs, st));
   RF_K(lambda_t(g, e, W.t, nr, st));
-  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, st));
+  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, op->ws->gs, st));
   {
     EdgeCombo c;
     c.zl = W.tg;
@@ -367,9 +373,9 @@ int apply_rhs(rfcmp_op* op, const double2* e, double2* out, int nr, GemvMode m, 
     c.d = c2(1.0, 0.0);
     RF_K(edge_combo(g, c, W.y, nr, st));
   }
-  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
+  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, op->ws->gs, st));
   RF_K(lap_apply(g, W.q, W.Lq, nr, st));
-  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0, 0.0), false, m, st));
+  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0, 0.0), false, m, op->ws->gs, st));
   {  // th = -ik up + (i/k) Sigma vp
     EdgeCombo c;
     c.x = W.up;
@@ -404,57 +410,46 @@ int apply_Po(rfcmp_op* op, const double2* x, double2* out, int nr, bool adj, Gem
   return RFCMP_OK;
 }
 
-// ---- power iteration operators (unscaled by k, module reading of Sec. 4) ----
-// X x = P_LH T_A^H Lambda G^{-1} Lambda^T T_A P_LH x
-int op_X(rfcmp_op* op, const double2* x, double2* out, cudaStream_t st) {
+// ---- power iteration operators (unscaled by k, frequency-scaled reading of Sec. 4) ----
+// Columns 0 and 1 of x (N x 2) go through
+//   X = P_LH T_A^H Lambda G_ll^{-1} Lambda^T T_A P_LH   (column 0, for alpha) and
+//   Z = P_LH T_A^H P_LH T_A P_LH                         (column 1, for gamma),
+// sharing each pass over T_A.
+int op_XZ(rfcmp_op* op, const double2* x, double2* out, cudaStream_t st) {
   Workspace& W = *op->ws;
   const int N = (int)op->top.ne, NV = (int)op->top.nv;
   const GemvMode m = GEMV_F32;
-  RF_TRY(star_coeff(op, x, W.s, W.z, 1, m, st));
+  RF_TRY(star_coeff(op, x, W.s, W.z, 2, m, st));
   EdgeCombo c;
   c.x = x;
   c.a = c2(1, 0);
   c.zs = W.z;
   c.b = c2(-1, 0);
-  RF_K(edge_combo(op->g, c, W.v, 1, st));
-  RF_K(gemv_c64(op->TA, N, W.v, W.u, 1, false, c2(1, 0), false, m, st));
+  RF_K(edge_combo(op->g, c, W.v, 2, st));
+  RF_K(gemv_c64(op->TA, N, W.v, W.u, 2, false, c2(1, 0), false, m, op->ws->gs, st));
+  // column 0: Lambda G_ll^{-1} Lambda^T u0
   RF_K(lambda_t(op->g, W.u, W.t, 1, st));
-  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, 1, 1.0, false, m, st));
+  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, 1, 1.0, false, m, op->ws->gs, st));
   EdgeCombo l;
   l.zl = W.tg;
   l.c = c2(1, 0);
   RF_K(edge_combo(op->g, l, W.y, 1, st));
-  RF_K(gemv_c64(op->TA, N, W.y, W.up, 1, true, c2(1, 0), false, m, st));
-  RF_TRY(star_coeff(op, W.up, W.s, W.z, 1, m, st));
+  // column 1: P_LH u1
+  RF_TRY(star_coeff(op, W.u + N, W.s, W.z, 1, m, st));
+  EdgeCombo p1;
+  p1.x = W.u + N;
+  p1.a = c2(1, 0);
+  p1.zs = W.z;
+  p1.b = c2(-1, 0);
+  RF_K(edge_combo(op->g, p1, W.y + N, 1, st));
+  RF_K(gemv_c64(op->TA, N, W.y, W.up, 2, true, c2(1, 0), false, m, op->ws->gs, st));
+  RF_TRY(star_coeff(op, W.up, W.s, W.z, 2, m, st));
   EdgeCombo o;
   o.x = W.up;
   o.a = c2(1, 0);
   o.zs = W.z;
   o.b = c2(-1, 0);
-  RF_K(edge_combo(op->g, o, out, 1, st));
-  return RFCMP_OK;
-}
-
-// Z x = P_LH T_A^H P_LH T_A P_LH x
-int op_Z(rfcmp_op* op, const double2* x, double2* out, cudaStream_t st) {
-  Workspace& W = *op->ws;
-  const int N = (int)op->top.ne;
-  const GemvMode m = GEMV_F32;
-  EdgeCombo c;
-  c.a = c2(1, 0);
-  c.b = c2(-1, 0);
-  RF_TRY(star_coeff(op, x, W.s, W.z, 1, m, st));
-  c.x = x;
-  c.zs = W.z;
-  RF_K(edge_combo(op->g, c, W.v, 1, st));
-  RF_K(gemv_c64(op->TA, N, W.v, W.u, 1, false, c2(1, 0), false, m, st));
-  RF_TRY(star_coeff(op, W.u, W.s, W.z, 1, m, st));
-  c.x = W.u;
-  RF_K(edge_combo(op->g, c, W.y, 1, st));
-  RF_K(gemv_c64(op->TA, N, W.y, W.up, 1, true, c2(1, 0), false, m, st));
-  RF_TRY(star_coeff(op, W.up, W.s, W.z, 1, m, st));
-  c.x = W.up;
-  RF_K(edge_combo(op->g, c, out, 1, st));
+  RF_K(edge_combo(op->g, o, out, 2, st));
   return RFCMP_OK;
 }
 
@@ -465,9 +460,9 @@ int op_Y(rfcmp_op* op, const double2* x, double2* out, cudaStream_t st) {
   const int C = (int)op->top.nc;
   const GemvMode m = GEMV_F32;
   RF_K(sigma_t(op->g, x, W.s, 1, st));
-  RF_K(gemv_c64(op->V, C, W.s, W.w, 1, false, c2(1, 0), false, m, st));
+  RF_K(gemv_c64(op->V, C, W.s, W.w, 1, false, c2(1, 0), false, m, op->ws->gs, st));
   RF_K(pgp_apply(op->g, W.w, W.q0, 1, W.mean, st));
-  RF_K(gemv_c64(op->V, C, W.q0, W.vp, 1, true, c2(1, 0), false, m, st));
+  RF_K(gemv_c64(op->V, C, W.q0, W.vp, 1, true, c2(1, 0), false, m, op->ws->gs, st));
   EdgeCombo c;
   c.zs = W.vp;
   c.b = c2(1, 0);
@@ -487,36 +482,53 @@ void splitmix_start(std::vector<double2>& h, int64_t n, uint64_t seed) {
   }
 }
 
-// largest eigenvalue of an HPSD operator by `steps` normalised power steps (Rayleigh quotient)
+// Largest eigenvalues of `cols` HPSD operators applied together (column c of the block goes
+// through operator c), by normalised power steps from splitmix64 start vectors (seeds[c]);
+// Rayleigh-quotient estimates.  Each column stops once its estimate changes by at most rtol
+// (relative) between steps (after at least 2 steps; rtol = 0: always `steps`).
 template <class Op>
-int power_norm(rfcmp_op* op, Op apply, uint64_t seed, int steps, double* lam, cudaStream_t st) {
+int power_norms(rfcmp_op* op, Op apply, int cols, const uint64_t* seeds, int steps, double rtol, double* lam,
+                cudaStream_t st) {
   const int64_t N = op->top.ne;
-  RF_TRY(ensure_solve_buffers(op, 1));
-  RF_TRY(ensure_workspace(op, 1));
+  RF_TRY(ensure_solve_buffers(op, cols));
+  RF_TRY(ensure_workspace(op, cols));
   SolveBuffers& B = *op->sb;
   std::vector<double2> h;
-  splitmix_start(h, N, seed);
-  RF_CUDA(cudaMemcpyAsync(B.p, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, st));
-  double2 nn;
-  RF_K(vec_dot(B.p, B.p, N, 1, B.dots, st));
-  RF_CUDA(cudaMemcpyAsync(&nn, B.dots, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  for (int c = 0; c < cols; ++c) {
+    splitmix_start(h, N, seeds[c]);
+    RF_CUDA(cudaMemcpyAsync(B.p + c * N, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, st));
+  }
+  std::vector<double2> d1(cols), d2(cols);
+  std::vector<double> coef(cols), prev(cols, 0.0);
+  std::vector<int> done(cols, 0);
+  RF_K(vec_dot(B.p, B.p, N, cols, B.dots, st));
+  RF_CUDA(cudaMemcpyAsync(d1.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
   RF_CUDA(cudaStreamSynchronize(st));
-  RF_K(vec_scale(B.p, c2(1.0 / std::sqrt(nn.x), 0.0), N, st));
-  double l = 0.0;
+  for (int c = 0; c < cols; ++c) coef[c] = 1.0 / std::sqrt(d1[c].x);
+  RF_CUDA(cudaMemcpyAsync(B.alpha, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+  RF_K(vec_copy_scale_cols(B.p, B.alpha, B.p, N, cols, st));
+  for (int c = 0; c < cols; ++c) lam[c] = 0.0;
   for (int it = 0; it < steps; ++it) {
     RF_TRY(apply(op, B.p, B.Ap, st));
-    double2 pr[2];
-    RF_K(vec_dot(B.p, B.Ap, N, 1, B.dots, st));
-    RF_CUDA(cudaMemcpyAsync(&pr[0], B.dots, sizeof(double2), cudaMemcpyDeviceToHost, st));
-    RF_K(vec_dot(B.Ap, B.Ap, N, 1, B.dots, st));
-    RF_CUDA(cudaMemcpyAsync(&pr[1], B.dots, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    RF_K(vec_dot(B.p, B.Ap, N, cols, B.dots, st));
+    RF_CUDA(cudaMemcpyAsync(d1.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
+    RF_K(vec_dot(B.Ap, B.Ap, N, cols, B.dots, st));
+    RF_CUDA(cudaMemcpyAsync(d2.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
     RF_CUDA(cudaStreamSynchronize(st));
-    l = pr[0].x;
-    if (!(pr[1].x > 0.0)) break;
-    RF_K(vec_copy(B.Ap, B.p, N, st));
-    RF_K(vec_scale(B.p, c2(1.0 / std::sqrt(pr[1].x), 0.0), N, st));
+    bool all = true;
+    for (int c = 0; c < cols; ++c) {
+      if (done[c]) continue;
+      prev[c] = lam[c];
+      lam[c] = d1[c].x;
+      if (rtol > 0.0 && it >= 1 && std::fabs(lam[c] - prev[c]) <= rtol * std::fabs(lam[c])) done[c] = 1;
+      if (!(d2[c].x > 0.0)) done[c] = 1;
+      all &= done[c] != 0;
+      coef[c] = d2[c].x > 0.0 ? 1.0 / std::sqrt(d2[c].x) : 0.0;
+    }
+    if (all) break;
+    RF_CUDA(cudaMemcpyAsync(B.alpha, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+    RF_K(vec_copy_scale_cols(B.Ap, B.alpha, B.p, N, cols, st));
   }
-  *lam = l;
   return RFCMP_OK;
 }
 
@@ -534,10 +546,11 @@ int compute_scaling(rfcmp_op* op, const rfcmp_op_opts& o, cudaStream_t st) {
     op->gamma = o.gamma;
     return RFCMP_OK;
   }
-  double nx = 0, ny = 0, nz = 0;
-  RF_TRY(power_norm(op, op_X, 1, o.power_steps, &nx, st));
-  RF_TRY(power_norm(op, op_Y, 2, o.power_steps, &ny, st));
-  RF_TRY(power_norm(op, op_Z, 3, o.power_steps, &nz, st));
+  double lxz[2] = {0, 0}, ly = 0;
+  const uint64_t sxz[2] = {1, 3}, sy = 2;
+  RF_TRY(power_norms(op, op_XZ, 2, sxz, o.power_steps, o.power_rtol, lxz, st));
+  RF_TRY(power_norms(op, op_Y, 1, &sy, o.power_steps, o.power_rtol, &ly, st));
+  const double nx = lxz[0], nz = lxz[1], ny = ly;
   // alpha^4 = k^2 ||X||, beta^4 = ||Y|| / k^2, gamma = k^2 ||Z|| / alpha^2 (frequency-scaled reading)
   op->alpha = std::pow(k * k * nx, 0.25);
   op->beta = std::pow(ny / (k * k), 0.25);
@@ -617,7 +630,7 @@ int upload_geometry(rfcmp_op* op) {
 
 // dense inverse of a sparse SPD matrix (CSR on the host), FP32 hi + lo planes
 int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col, const std::vector<double>& val,
-                 int n, bool project, double tol, std::shared_ptr<DenseFactor>& out) {
+                 int n, bool project, bool multigrid, double tol, std::shared_ptr<DenseFactor>& out) {
   auto f = std::make_shared<DenseFactor>();
   f->n = n;
   const size_t ld = (size_t)padded_ld(n);
@@ -640,8 +653,18 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, 0);
+  AmgHierarchy H;
+  if (multigrid) {
+    std::string err;
+    int rc2 = build_amg(ptr, col, val, n, 64, H, err);
+    if (rc2 != RFCMP_OK) {
+      for (void* p : tmp) cudaFree(p);
+      return set_error(rc2, err);
+    }
+  }
   int iters = 0;
-  cudaError_t err = dense_inverse_block_cg(dptr, dcol, dval, n, project, tol, 20000, f->hi, f->lo, &iters, 0);
+  cudaError_t err = dense_inverse_block_cg(dptr, dcol, dval, n, project, multigrid ? &H : nullptr, tol, 20000, f->hi,
+                                           f->lo, &iters, 0);
   cudaEventRecord(e1, 0);
   cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -722,6 +745,7 @@ void rfcmp_op_opts_default(rfcmp_op_opts* o) {
   o->power_steps = 30;
   o->alpha = o->beta = o->gamma = 1.0;
   o->factor_tol = 1e-13;
+  o->power_rtol = 1e-3;
 }
 
 void rfcmp_solve_opts_default(rfcmp_solve_opts* o) {
@@ -779,7 +803,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   if (opts_in) o = *opts_in;
   for (int i = 0; i < 8; ++i)
     if (o.reserved[i] != 0) return set_error(RFCMP_ERR_INVALID_ARG, "opts.reserved must be zero");
-  if (o.scaling < 0 || o.scaling > 2 || o.power_steps < 1 || !(o.factor_tol > 0.0))
+  if (o.scaling < 0 || o.scaling > 2 || o.power_steps < 1 || !(o.factor_tol > 0.0) || !(o.power_rtol >= 0.0))
     return set_error(RFCMP_ERR_INVALID_ARG, "invalid op options");
   if (o.scaling == RFCMP_SCALE_FIXED && !(o.alpha > 0 && o.beta > 0 && o.gamma > 0))
     return set_error(RFCMP_ERR_INVALID_ARG, "fixed scaling needs positive alpha, beta, gamma");
@@ -824,7 +848,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   // topology factors
   op->info.ms_factors = 0.0;
   if (!lp) {
-    RF_TRY(build_factor(op->top.lap_ptr, op->top.lap_col, op->top.lap_val, C, true, o.factor_tol, lp));
+    RF_TRY(build_factor(op->top.lap_ptr, op->top.lap_col, op->top.lap_val, C, true, true, o.factor_tol, lp));
     op->info.ms_factors += lp->ms;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->lplus_cache[op->top.hash] = lp;
@@ -834,7 +858,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
     std::vector<int32_t> mp, mc;
     std::vector<double> mv;
     mass_matrix_csr(op->top, op->verts.data(), mp, mc, mv);
-    RF_TRY(build_factor(mp, mc, mv, NV, false, o.factor_tol, gl));
+    RF_TRY(build_factor(mp, mc, mv, NV, false, false, o.factor_tol, gl));
     op->info.ms_factors += gl->ms;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->gll_cache[geo_hash] = gl;
@@ -971,11 +995,11 @@ int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout
   Workspace& W = *op->ws;
   switch (which) {
     case RFCMP_APPLY_T_A:
-      RF_K(gemv_c64(op->TA, N, x, y, nr, false, c2(1, 0), false, m, st));
+      RF_K(gemv_c64(op->TA, N, x, y, nr, false, c2(1, 0), false, m, op->ws->gs, st));
       return RFCMP_OK;
     case RFCMP_APPLY_T_PHI: {
       RF_K(sigma_t(op->g, x, W.s, nr, st));
-      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1, 0), false, m, st));
+      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1, 0), false, m, op->ws->gs, st));
       EdgeCombo c;
       c.zs = W.w;
       c.b = c2(1, 0);
@@ -986,8 +1010,8 @@ int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout
     case RFCMP_APPLY_T_ADJ: {
       const bool adj = which == RFCMP_APPLY_T_ADJ;
       RF_K(sigma_t(op->g, x, W.s, nr, st));
-      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, adj, c2(1, 0), false, m, st));
-      RF_K(gemv_c64(op->TA, N, x, W.u, nr, adj, c2(1, 0), false, m, st));
+      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, adj, c2(1, 0), false, m, op->ws->gs, st));
+      RF_K(gemv_c64(op->TA, N, x, W.u, nr, adj, c2(1, 0), false, m, op->ws->gs, st));
       // T x = i k T_A x - (i/k) Sigma V Sigma^T x ; T^H x = -i k conj(T_A) x + (i/k) Sigma conj(V) Sigma^T x
       EdgeCombo c;
       c.x = W.u;
@@ -1038,9 +1062,9 @@ int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c12
       const int C = (int)op->top.nc, NV = (int)op->top.nv;
       RF_TRY(star_coeff(op, x, W.s, W.zu, nr, m, st));
       RF_K(star_middle(op->g, W.zu, nullptr, 1.0, W.q0, nr, W.mean, st));
-      RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+      RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, op->ws->gs, st));
       RF_K(lambda_t(op->g, x, W.t, nr, st));
-      RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, st));
+      RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, op->ws->gs, st));
       EdgeCombo c;
       c.zl = W.tg;
       c.c = c2(1.0 / (a * a), 0.0);

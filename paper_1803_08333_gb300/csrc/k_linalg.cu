@@ -12,6 +12,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "rfcmp_internal.h"
@@ -22,8 +24,8 @@ namespace {
 
 constexpr int GEMV_ROWS_PER_WARP = 4;
 constexpr int GEMV_WARPS = 8;
-constexpr int GEMV_ROWS = GEMV_ROWS_PER_WARP * GEMV_WARPS;  // 32 rows per block
-constexpr int GEMV_CHUNK = 1024;                            // columns staged per pass
+constexpr int GEMV_ROWS = GEMV_ROWS_PER_WARP * GEMV_WARPS;  // 32 rows per work unit
+constexpr int GEMV_CHUNK = 1024;                            // columns per work unit
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -43,51 +45,102 @@ __device__ __forceinline__ void ff_mac(float& hi, float& lo, float a, float bh, 
   lo += err + c;
 }
 
-// ---------------------------------------------------------------- complex64 GEMV
+// streaming load of the matrix: read once, kept out of L1
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// x (complex128, n x nr) -> FP32 hi (and lo) copies padded to ld, and zero the accumulator
+__global__ void gemv_prep_kernel(const double2* __restrict__ x, int n, int ld, int nr, float2* __restrict__ xh,
+                                 float2* __restrict__ xl, double2* __restrict__ acc, int acc_n) {
+  const int r = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x) {
+    const double2 v = i < n ? x[(size_t)r * n + i] : make_double2(0.0, 0.0);
+    const float2 h = make_float2((float)v.x, (float)v.y);
+    xh[(size_t)r * ld + i] = h;
+    if (xl) xl[(size_t)r * ld + i] = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+    if (i < acc_n) acc[(size_t)r * acc_n + i] = make_double2(0.0, 0.0);
+  }
+}
+
+// y = scale * acc (+ y)
+__global__ void gemv_finalize_kernel(const double2* __restrict__ acc, int n, int nr, double2 scale, int accumulate,
+                                     double2* __restrict__ y) {
+  const int r = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 a = acc[(size_t)r * n + i];
+    double2 o = make_double2(scale.x * a.x - scale.y * a.y, scale.x * a.y + scale.y * a.x);
+    if (accumulate) {
+      const double2 p = y[(size_t)r * n + i];
+      o.x += p.x;
+      o.y += p.y;
+    }
+    y[(size_t)r * n + i] = o;
+  }
+}
+
+// Flushes the per-lane FP64 row sums of one row block into the accumulator.
+template <int NR>
+__device__ __forceinline__ void flush_rows(double (&acc)[GEMV_ROWS_PER_WARP][NR][2], int row0, int n, int lane,
+                                           double2* __restrict__ out) {
+#pragma unroll
+  for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const double re = warp_sum(acc[a][r][0]);
+      const double im = warp_sum(acc[a][r][1]);
+      acc[a][r][0] = acc[a][r][1] = 0.0;
+      if (lane == 0 && row0 + a < n) {
+        double* o = reinterpret_cast<double*>(out + (size_t)r * n + row0 + a);
+        atomicAdd(o, re);
+        atomicAdd(o + 1, im);
+      }
+    }
+}
+
+// ---------------------------------------------------------------- complex64 GEMV (persistent)
+// Work unit u = (row block rb, column chunk cc); CTA g owns units [u0, u1) of the
+// row-major unit order, so every CTA streams the same number of matrix bytes.
 template <int NR, bool FF, bool CONJ>
 __global__ void __launch_bounds__(GEMV_WARPS * 32)
-gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const double2* __restrict__ x, double2* __restrict__ y,
-                double2 scale, int accumulate) {
-  __shared__ float4 xs_hi[NR][GEMV_CHUNK / 2];
-  __shared__ float4 xs_lo[FF ? NR : 1][FF ? GEMV_CHUNK / 2 : 1];
+gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
+                const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.x * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP;
+  const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   double acc[GEMV_ROWS_PER_WARP][NR][2];
 #pragma unroll
   for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[a][r][0] = acc[a][r][1] = 0.0;
-
-  for (int cb = 0; cb < ld; cb += GEMV_CHUNK) {
-    const int clen = min(GEMV_CHUNK, ld - cb);  // multiple of 64
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NR * (GEMV_CHUNK / 2); idx += blockDim.x) {
-      const int r = idx / (GEMV_CHUNK / 2), p = idx % (GEMV_CHUNK / 2);
-      const int c0 = cb + 2 * p;
-      double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
-      if (c0 < n) v0 = x[(size_t)r * n + c0];
-      if (c0 + 1 < n) v1 = x[(size_t)r * n + c0 + 1];
-      float4 h = make_float4((float)v0.x, (float)v0.y, (float)v1.x, (float)v1.y);
-      xs_hi[r][p] = h;
-      if (FF)
-        xs_lo[r][p] = make_float4((float)(v0.x - (double)h.x), (float)(v0.y - (double)h.y),
-                                  (float)(v1.x - (double)h.z), (float)(v1.y - (double)h.w));
+  long long cur_rb = -1;
+  for (long long u = u0; u < u1; ++u) {
+    const int rb = (int)(u / upr), cc = (int)(u % upr);
+    const int row0 = rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP;
+    if (rb != cur_rb) {
+      if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
+      cur_rb = rb;
     }
-    __syncthreads();
+    const int cb = cc * GEMV_CHUNK;
+    const int npair = min(GEMV_CHUNK, ld - cb) / 2;
     float fh[GEMV_ROWS_PER_WARP][NR][2], fl[GEMV_ROWS_PER_WARP][NR][2];
 #pragma unroll
     for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
 #pragma unroll
       for (int r = 0; r < NR; ++r) fh[a][r][0] = fh[a][r][1] = fl[a][r][0] = fl[a][r][1] = 0.f;
-    const int npair = clen / 2;
+    const float4* rowp[GEMV_ROWS_PER_WARP];
+#pragma unroll
+    for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
+      rowp[a] = reinterpret_cast<const float4*>(M + (size_t)min(row0 + a, n - 1) * ld + cb);
 #pragma unroll 4
     for (int p = lane; p < npair; p += 32) {
       float4 m[GEMV_ROWS_PER_WARP];
 #pragma unroll
       for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
-        const int row = row0 + a;
-        m[a] = row < n ? __ldg(reinterpret_cast<const float4*>(M + (size_t)row * ld + cb) + p)
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        m[a] = row0 + a < n ? ld_stream(rowp[a] + p) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (CONJ) {
           m[a].y = -m[a].y;
           m[a].w = -m[a].w;
@@ -95,34 +148,34 @@ gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const double2* __re
       }
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        const float4 xh = xs_hi[r][p];
+        const float4 x4 = __ldg(reinterpret_cast<const float4*>(xh + (size_t)r * ld + cb) + p);
         if (!FF) {
 #pragma unroll
           for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
             float re = fh[a][r][0], im = fh[a][r][1];
-            re = fmaf(m[a].x, xh.x, re);
-            re = fmaf(-m[a].y, xh.y, re);
-            re = fmaf(m[a].z, xh.z, re);
-            re = fmaf(-m[a].w, xh.w, re);
-            im = fmaf(m[a].x, xh.y, im);
-            im = fmaf(m[a].y, xh.x, im);
-            im = fmaf(m[a].z, xh.w, im);
-            im = fmaf(m[a].w, xh.z, im);
+            re = fmaf(m[a].x, x4.x, re);
+            re = fmaf(-m[a].y, x4.y, re);
+            re = fmaf(m[a].z, x4.z, re);
+            re = fmaf(-m[a].w, x4.w, re);
+            im = fmaf(m[a].x, x4.y, im);
+            im = fmaf(m[a].y, x4.x, im);
+            im = fmaf(m[a].z, x4.w, im);
+            im = fmaf(m[a].w, x4.z, im);
             fh[a][r][0] = re;
             fh[a][r][1] = im;
           }
         } else {
-          const float4 xl = xs_lo[r][p];
+          const float4 l4 = __ldg(reinterpret_cast<const float4*>(xl + (size_t)r * ld + cb) + p);
 #pragma unroll
           for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
-            ff_mac(fh[a][r][0], fl[a][r][0], m[a].x, xh.x, xl.x);
-            ff_mac(fh[a][r][0], fl[a][r][0], -m[a].y, xh.y, xl.y);
-            ff_mac(fh[a][r][0], fl[a][r][0], m[a].z, xh.z, xl.z);
-            ff_mac(fh[a][r][0], fl[a][r][0], -m[a].w, xh.w, xl.w);
-            ff_mac(fh[a][r][1], fl[a][r][1], m[a].x, xh.y, xl.y);
-            ff_mac(fh[a][r][1], fl[a][r][1], m[a].y, xh.x, xl.x);
-            ff_mac(fh[a][r][1], fl[a][r][1], m[a].z, xh.w, xl.w);
-            ff_mac(fh[a][r][1], fl[a][r][1], m[a].w, xh.z, xl.z);
+            ff_mac(fh[a][r][0], fl[a][r][0], m[a].x, x4.x, l4.x);
+            ff_mac(fh[a][r][0], fl[a][r][0], -m[a].y, x4.y, l4.y);
+            ff_mac(fh[a][r][0], fl[a][r][0], m[a].z, x4.z, l4.z);
+            ff_mac(fh[a][r][0], fl[a][r][0], -m[a].w, x4.w, l4.w);
+            ff_mac(fh[a][r][1], fl[a][r][1], m[a].x, x4.y, l4.y);
+            ff_mac(fh[a][r][1], fl[a][r][1], m[a].y, x4.x, l4.x);
+            ff_mac(fh[a][r][1], fl[a][r][1], m[a].z, x4.w, l4.w);
+            ff_mac(fh[a][r][1], fl[a][r][1], m[a].w, x4.z, l4.z);
           }
         }
       }
@@ -135,80 +188,58 @@ gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const double2* __re
         acc[a][r][1] += (double)fh[a][r][1] + (double)fl[a][r][1];
       }
   }
-#pragma unroll
-  for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
-    const int row = row0 + a;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const double re = warp_sum(acc[a][r][0]);
-      const double im = warp_sum(acc[a][r][1]);
-      if (lane == 0 && row < n) {
-        double2 out = make_double2(scale.x * re - scale.y * im, scale.x * im + scale.y * re);
-        double2* dst = y + (size_t)r * n + row;
-        if (accumulate) {
-          out.x += dst->x;
-          out.y += dst->y;
-        }
-        *dst = out;
-      }
-    }
-  }
+  if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
 }
 
-// ---------------------------------------------------------------- real (hi + lo) GEMV
+// ---------------------------------------------------------------- real (hi + lo) GEMV (persistent)
 template <int NR, bool FF>
 __global__ void __launch_bounds__(GEMV_WARPS * 32)
 gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, int ld, int n,
-                const double2* __restrict__ x, double2* __restrict__ y, double scale, int accumulate) {
-  // x chunk as 4 complex per float4 pair: xs[r][q] holds complex 2q, 2q+1
-  __shared__ float4 xs_hi[NR][GEMV_CHUNK / 2];
-  __shared__ float4 xs_lo[FF ? NR : 1][FF ? GEMV_CHUNK / 2 : 1];
+                const float2* __restrict__ xh, const float2* __restrict__ xl, double2* __restrict__ out,
+                long long units, int upr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.x * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP;
+  const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   double acc[GEMV_ROWS_PER_WARP][NR][2];
 #pragma unroll
   for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[a][r][0] = acc[a][r][1] = 0.0;
-
-  for (int cb = 0; cb < ld; cb += GEMV_CHUNK) {
-    const int clen = min(GEMV_CHUNK, ld - cb);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NR * (GEMV_CHUNK / 2); idx += blockDim.x) {
-      const int r = idx / (GEMV_CHUNK / 2), p = idx % (GEMV_CHUNK / 2);
-      const int c0 = cb + 2 * p;
-      double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
-      if (c0 < n) v0 = x[(size_t)r * n + c0];
-      if (c0 + 1 < n) v1 = x[(size_t)r * n + c0 + 1];
-      float4 h = make_float4((float)v0.x, (float)v0.y, (float)v1.x, (float)v1.y);
-      xs_hi[r][p] = h;
-      if (FF)
-        xs_lo[r][p] = make_float4((float)(v0.x - (double)h.x), (float)(v0.y - (double)h.y),
-                                  (float)(v1.x - (double)h.z), (float)(v1.y - (double)h.w));
+  long long cur_rb = -1;
+  for (long long u = u0; u < u1; ++u) {
+    const int rb = (int)(u / upr), cc = (int)(u % upr);
+    const int row0 = rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP;
+    if (rb != cur_rb) {
+      if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
+      cur_rb = rb;
     }
-    __syncthreads();
+    const int cb = cc * GEMV_CHUNK;
+    const int nquad = min(GEMV_CHUNK, ld - cb) / 4;
     float fh[GEMV_ROWS_PER_WARP][NR][2], fl[GEMV_ROWS_PER_WARP][NR][2];
 #pragma unroll
     for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
 #pragma unroll
       for (int r = 0; r < NR; ++r) fh[a][r][0] = fh[a][r][1] = fl[a][r][0] = fl[a][r][1] = 0.f;
-    const int nquad = clen / 4;
-#pragma unroll 4
+    const float4* rh[GEMV_ROWS_PER_WARP];
+    const float4* rl[GEMV_ROWS_PER_WARP];
+#pragma unroll
+    for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
+      const size_t off = (size_t)min(row0 + a, n - 1) * ld + cb;
+      rh[a] = reinterpret_cast<const float4*>(Mhi + off);
+      rl[a] = reinterpret_cast<const float4*>(Mlo + off);
+    }
+#pragma unroll 2
     for (int q = lane; q < nquad; q += 32) {
       float4 mh[GEMV_ROWS_PER_WARP], ml[GEMV_ROWS_PER_WARP];
 #pragma unroll
       for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
-        const int row = row0 + a;
-        const bool ok = row < n;
-        mh[a] = ok ? __ldg(reinterpret_cast<const float4*>(Mhi + (size_t)row * ld + cb) + q)
-                   : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (FF)
-          ml[a] = ok ? __ldg(reinterpret_cast<const float4*>(Mlo + (size_t)row * ld + cb) + q)
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = row0 + a < n;
+        mh[a] = ok ? ld_stream(rh[a] + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (FF) ml[a] = ok ? ld_stream(rl[a] + q) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        const float4 x0 = xs_hi[r][2 * q], x1 = xs_hi[r][2 * q + 1];
+        const float4* xr = reinterpret_cast<const float4*>(xh + (size_t)r * ld + cb);
+        const float4 x0 = __ldg(xr + 2 * q), x1 = __ldg(xr + 2 * q + 1);
         if (!FF) {
 #pragma unroll
           for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
@@ -225,10 +256,11 @@ gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, in
             fh[a][r][1] = im;
           }
         } else {
-          const float4 l0 = xs_lo[r][2 * q], l1 = xs_lo[r][2 * q + 1];
+          const float4* lr = reinterpret_cast<const float4*>(xl + (size_t)r * ld + cb);
+          const float4 l0 = __ldg(lr + 2 * q), l1 = __ldg(lr + 2 * q + 1);
 #pragma unroll
           for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
-            // (mh + ml)(xh + xl): mh*xh exact in ff, mh*xl + ml*xh folded into the low word
+            // (mh + ml)(xh + xl): mh*xh exact in float-float, mh*xl + ml*xh folded into the low word
             ff_mac(fh[a][r][0], fl[a][r][0], mh[a].x, x0.x, l0.x);
             ff_mac(fh[a][r][1], fl[a][r][1], mh[a].x, x0.y, l0.y);
             ff_mac(fh[a][r][0], fl[a][r][0], mh[a].y, x0.z, l0.z);
@@ -257,58 +289,80 @@ gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, in
         acc[a][r][1] += (double)fh[a][r][1] + (double)fl[a][r][1];
       }
   }
-#pragma unroll
-  for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a) {
-    const int row = row0 + a;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const double re = warp_sum(acc[a][r][0]);
-      const double im = warp_sum(acc[a][r][1]);
-      if (lane == 0 && row < n) {
-        double2 out = make_double2(scale * re, scale * im);
-        double2* dst = y + (size_t)r * n + row;
-        if (accumulate) {
-          out.x += dst->x;
-          out.y += dst->y;
-        }
-        *dst = out;
-      }
-    }
-  }
+  if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
 }
 
-template <int NR>
-cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, const double2* x, double2* y, bool conj, double2 scale,
-                              bool acc, GemvMode mode, cudaStream_t s) {
-  const int blocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
-  const int a = acc ? 1 : 0;
-  ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", 8.0 * n * n + 32.0 * n * NR,
-                 8.0 * n * n * NR, s);
-  if (mode == GEMV_FF) {
-    if (conj)
-      gemv_c64_kernel<NR, true, true><<<blocks, GEMV_WARPS * 32, 0, s>>>(M, ld, n, x, y, scale, a);
-    else
-      gemv_c64_kernel<NR, true, false><<<blocks, GEMV_WARPS * 32, 0, s>>>(M, ld, n, x, y, scale, a);
-  } else {
-    if (conj)
-      gemv_c64_kernel<NR, false, true><<<blocks, GEMV_WARPS * 32, 0, s>>>(M, ld, n, x, y, scale, a);
-    else
-      gemv_c64_kernel<NR, false, false><<<blocks, GEMV_WARPS * 32, 0, s>>>(M, ld, n, x, y, scale, a);
-  }
+// persistent grid: SMs x resident CTAs of this kernel (cached per kernel and device)
+template <class K>
+int persistent_grid(K kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, GEMV_WARPS * 32, 0);
+  const int g = std::max(1, sms * std::max(1, per));
+  cache[key] = g;
+  return g;
+}
+
+cudaError_t gemv_prep(const double2* x, int n, int ld, int nr, bool ff, GemvScratch& w, cudaStream_t s) {
+  dim3 grid(std::min((ld + 255) / 256, 4 * 152), nr);
+  gemv_prep_kernel<<<grid, 256, 0, s>>>(x, n, ld, nr, w.xh, ff ? w.xl : nullptr, w.acc, n);
+  return cudaGetLastError();
+}
+
+cudaError_t gemv_finalize(int n, int nr, double2 scale, bool acc, double2* y, GemvScratch& w, cudaStream_t s) {
+  dim3 grid(std::min((n + 255) / 256, 4 * 152), nr);
+  gemv_finalize_kernel<<<grid, 256, 0, s>>>(w.acc, n, nr, scale, acc ? 1 : 0, y);
   return cudaGetLastError();
 }
 
 template <int NR>
-cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n, const double2* x, double2* y,
-                              double scale, bool acc, GemvMode mode, cudaStream_t s) {
-  const int blocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
-  const int a = acc ? 1 : 0;
+cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, bool conj, GemvMode mode, GemvScratch& w,
+                              cudaStream_t s) {
+  const int rowblocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
+  const int upr = (ld + GEMV_CHUNK - 1) / GEMV_CHUNK;
+  const long long units = (long long)rowblocks * upr;
+  ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", 8.0 * n * n + 32.0 * n * NR,
+                 8.0 * n * n * NR, s);
+#define RF_LAUNCH_C(FFV, CJ)                                                                      \
+  {                                                                                               \
+    auto k = gemv_c64_kernel<NR, FFV, CJ>;                                                        \
+    const int grid = (int)std::min<long long>(units, persistent_grid(k));                         \
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr);                  \
+  }
+  if (mode == GEMV_FF) {
+    if (conj) RF_LAUNCH_C(true, true) else RF_LAUNCH_C(true, false)
+  } else {
+    if (conj) RF_LAUNCH_C(false, true) else RF_LAUNCH_C(false, false)
+  }
+#undef RF_LAUNCH_C
+  return cudaGetLastError();
+}
+
+template <int NR>
+cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n, GemvMode mode, GemvScratch& w,
+                              cudaStream_t s) {
+  const int rowblocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
+  const int upr = (ld + GEMV_CHUNK - 1) / GEMV_CHUNK;
+  const long long units = (long long)rowblocks * upr;
   ProfScope prof(mode == GEMV_FF ? "gemv_r32_ff" : "gemv_r32_f32",
                  (mode == GEMV_FF ? 8.0 : 4.0) * n * n + 32.0 * n * NR, 4.0 * n * n * NR, s);
-  if (mode == GEMV_FF)
-    gemv_r32_kernel<NR, true><<<blocks, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, x, y, scale, a);
-  else
-    gemv_r32_kernel<NR, false><<<blocks, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, x, y, scale, a);
+  if (mode == GEMV_FF) {
+    auto k = gemv_r32_kernel<NR, true>;
+    const int grid = (int)std::min<long long>(units, persistent_grid(k));
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr);
+  } else {
+    auto k = gemv_r32_kernel<NR, false>;
+    const int grid = (int)std::min<long long>(units, persistent_grid(k));
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr);
+  }
   return cudaGetLastError();
 }
 
@@ -316,48 +370,41 @@ cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n,
 
 int padded_ld(int n) { return (n + 63) / 64 * 64; }
 
+// y = scale * op(M) x (+ y): prep (x -> FP32 hi/lo, zero accumulator), persistent GEMV, finalize.
 cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate, double2 scale,
-                     bool accumulate, GemvMode mode, cudaStream_t s) {
+                     bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s) {
   const int ld = padded_ld(n);
-  int r = 0;
   cudaError_t err = cudaSuccess;
-  while (r < nrhs && err == cudaSuccess) {
-    const int left = nrhs - r;
+  for (int r = 0; r < nrhs && err == cudaSuccess;) {
+    const int nr = std::min(4, nrhs - r) >= 4 ? 4 : (nrhs - r >= 2 ? 2 : 1);
+    if (n > w.cap_n || ld > w.cap_ld || nr > w.cap_cols) return cudaErrorInvalidValue;
     const double2* xr = x + (size_t)r * n;
     double2* yr = y + (size_t)r * n;
-    if (left >= 4) {
-      err = gemv_c64_dispatch<4>(M, ld, n, xr, yr, conjugate, scale, accumulate, mode, s);
-      r += 4;
-    } else if (left >= 2) {
-      err = gemv_c64_dispatch<2>(M, ld, n, xr, yr, conjugate, scale, accumulate, mode, s);
-      r += 2;
-    } else {
-      err = gemv_c64_dispatch<1>(M, ld, n, xr, yr, conjugate, scale, accumulate, mode, s);
-      r += 1;
-    }
+    if ((err = gemv_prep(xr, n, ld, nr, mode == GEMV_FF, w, s)) != cudaSuccess) break;
+    if (nr == 4) err = gemv_c64_dispatch<4>(M, ld, n, conjugate, mode, w, s);
+    else if (nr == 2) err = gemv_c64_dispatch<2>(M, ld, n, conjugate, mode, w, s);
+    else err = gemv_c64_dispatch<1>(M, ld, n, conjugate, mode, w, s);
+    if (err == cudaSuccess) err = gemv_finalize(n, nr, scale, accumulate, yr, w, s);
+    r += nr;
   }
   return err;
 }
 
 cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x, double2* y, int nrhs, double scale,
-                     bool accumulate, GemvMode mode, cudaStream_t s) {
+                     bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s) {
   const int ld = padded_ld(n);
-  int r = 0;
   cudaError_t err = cudaSuccess;
-  while (r < nrhs && err == cudaSuccess) {
-    const int left = nrhs - r;
+  for (int r = 0; r < nrhs && err == cudaSuccess;) {
+    const int nr = nrhs - r >= 4 ? 4 : (nrhs - r >= 2 ? 2 : 1);
+    if (n > w.cap_n || ld > w.cap_ld || nr > w.cap_cols) return cudaErrorInvalidValue;
     const double2* xr = x + (size_t)r * n;
     double2* yr = y + (size_t)r * n;
-    if (left >= 4) {
-      err = gemv_r32_dispatch<4>(Mhi, Mlo, ld, n, xr, yr, scale, accumulate, mode, s);
-      r += 4;
-    } else if (left >= 2) {
-      err = gemv_r32_dispatch<2>(Mhi, Mlo, ld, n, xr, yr, scale, accumulate, mode, s);
-      r += 2;
-    } else {
-      err = gemv_r32_dispatch<1>(Mhi, Mlo, ld, n, xr, yr, scale, accumulate, mode, s);
-      r += 1;
-    }
+    if ((err = gemv_prep(xr, n, ld, nr, mode == GEMV_FF, w, s)) != cudaSuccess) break;
+    if (nr == 4) err = gemv_r32_dispatch<4>(Mhi, Mlo, ld, n, mode, w, s);
+    else if (nr == 2) err = gemv_r32_dispatch<2>(Mhi, Mlo, ld, n, mode, w, s);
+    else err = gemv_r32_dispatch<1>(Mhi, Mlo, ld, n, mode, w, s);
+    if (err == cudaSuccess) err = gemv_finalize(n, nr, make_double2(scale, 0.0), accumulate, yr, w, s);
+    r += nr;
   }
   return err;
 }
@@ -632,6 +679,16 @@ __global__ void copy_kernel(const double2* __restrict__ x, double2* __restrict__
     y[i] = x[i];
 }
 
+__global__ void copy_scale_cols_kernel(const double2* __restrict__ x, const double* __restrict__ coef,
+                                       double2* __restrict__ y, int64_t n) {
+  const int r = blockIdx.y;
+  const double a = coef[r];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 u = x[(size_t)r * n + i];
+    y[(size_t)r * n + i] = make_double2(a * u.x, a * u.y);
+  }
+}
+
 __global__ void scale_kernel(double2* __restrict__ y, double2 a, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = y[i];
@@ -694,6 +751,13 @@ cudaError_t vec_copy(const double2* x, double2* y, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t vec_copy_scale_cols(const double2* x, const double* coef, double2* y, int64_t n, int nrhs,
+                               cudaStream_t s) {
+  dim3 grid(grid_for(n), nrhs);
+  copy_scale_cols_kernel<<<grid, 256, 0, s>>>(x, coef, y, n);
+  return cudaGetLastError();
+}
+
 cudaError_t vec_scale(double2* y, double2 a, int64_t n, cudaStream_t s) {
   scale_kernel<<<grid_for(n), 256, 0, s>>>(y, a, n);
   return cudaGetLastError();
@@ -711,203 +775,447 @@ cudaError_t cg_scalars_beta(const double2* rr_new2, double* rr, double* beta, co
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- dense inverse by block CG
-// X = A^{-1} B for the sparse SPD A (or, with project, the graph Laplacian
-// restricted to 1^perp: B = I - 1 1^T / n, X = A^+ by Sec. 3.2), W columns at a
-// time; every column runs plain CG with its own scalars.  Arrays are row-major
-// n x W so that consecutive threads read consecutive columns.
+// ---------------------------------------------------------------- dense inverse by block (P)CG
+// X = A^{-1} B for the sparse SPD A (or, with project, the graph Laplacian restricted to
+// 1^perp: B = I - 1 1^T / n, X = A^+ by the identity of Sec. 3.2), W columns at a time;
+// every column runs its own (P)CG with its own scalars.  Arrays are row-major n x W so that
+// consecutive threads read consecutive columns.  A column whose residual reached the
+// tolerance is frozen: continuing CG on it after p^T A p has fallen to rounding level (or
+// below zero on the singular Laplacian) makes the step explode.
 namespace {
 
-constexpr int BCG_COLS = 128;  // columns per thread block
+constexpr int BCG_COLS = 128;  // columns per thread block (64 threads x 2 adjacent columns)
 constexpr int BCG_ROWS = 256;  // rows per thread block
+constexpr int BCG_THREADS = 256;
+constexpr int BCG_RLANES = BCG_THREADS / (BCG_COLS / 2);  // 4 interleaved row lanes
 
+// Thread (column pair, row lane) of a block-CG kernel: columns c, c + 1 (c even), rows
+// r0, r0 + 4, ... < r1.  Arrays are row-major n x W with W a multiple of 128.
+struct RowIter {
+  int c, r0, r1;
+  __device__ RowIter(int n) {
+    c = 2 * (blockIdx.x * (BCG_COLS / 2) + (threadIdx.x % (BCG_COLS / 2)));
+    r0 = blockIdx.y * BCG_ROWS + threadIdx.x / (BCG_COLS / 2);
+    r1 = min(n, (int)(blockIdx.y * BCG_ROWS + BCG_ROWS));
+  }
+  __device__ bool first() const { return blockIdx.y == 0 && threadIdx.x < BCG_COLS / 2; }
+};
+
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
+
+// columns c0 + c >= n (padding of the last block) get b = 0: they are frozen from the start
 __global__ void bcg_init_kernel(int n, int W, int c0, bool project, double* __restrict__ X, double* __restrict__ R,
-                                double* __restrict__ P, double* __restrict__ rr0) {
-  const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
-  const int rsub = threadIdx.x / BCG_COLS;
-  if (c >= W) return;
-  const int r0 = blockIdx.y * BCG_ROWS;
-  const int r1 = min(n, r0 + BCG_ROWS);
+                                double* __restrict__ rr0) {
+  RowIter it(n);
   const double off = project ? 1.0 / n : 0.0;
-  double dot = 0.0;
-  for (int i = r0 + rsub; i < r1; i += blockDim.x / BCG_COLS) {
-    const double b = (i == c0 + c ? 1.0 : 0.0) - off;
-    const size_t o = (size_t)i * W + c;
-    X[o] = 0.0;
-    R[o] = b;
-    P[o] = b;
-    dot += b * b;
+  const bool v0 = c0 + it.c < n, v1 = c0 + it.c + 1 < n;
+  double d0 = 0.0, d1 = 0.0;
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    const double b0 = v0 ? (i == c0 + it.c ? 1.0 : 0.0) - off : 0.0;
+    const double b1 = v1 ? (i == c0 + it.c + 1 ? 1.0 : 0.0) - off : 0.0;
+    const size_t o = (size_t)i * W + it.c;
+    st2(X + o, make_double2(0.0, 0.0));
+    st2(R + o, make_double2(b0, b1));
+    d0 += b0 * b0;
+    d1 += b1 * b1;
   }
-  atomicAdd(&rr0[c], dot);
+  atomicAdd(&rr0[it.c], d0);
+  atomicAdd(&rr0[it.c + 1], d1);
 }
 
-// AP = A P, pAp += P.AP
-__global__ void bcg_spmm_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                const double* __restrict__ val, int n, int W, const double* __restrict__ P,
-                                double* __restrict__ AP, double* __restrict__ pAp) {
-  const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
-  const int rsub = threadIdx.x / BCG_COLS;
-  if (c >= W) return;
-  const int r0 = blockIdx.y * BCG_ROWS;
-  const int r1 = min(n, r0 + BCG_ROWS);
-  double dot = 0.0;
-  for (int i = r0 + rsub; i < r1; i += blockDim.x / BCG_COLS) {
-    double acc = 0.0;
-    for (int q = ptr[i]; q < ptr[i + 1]; ++q) acc += val[q] * P[(size_t)col[q] * W + c];
-    AP[(size_t)i * W + c] = acc;
-    dot += P[(size_t)i * W + c] * acc;
+// out = A in (CSR); with acc, out += A in; with dot, dotp += in . out (per column)
+__global__ void __launch_bounds__(BCG_THREADS)
+bcg_spmm_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+                int n, int W, const double* __restrict__ in, double* __restrict__ out, int accumulate,
+                double* __restrict__ dotp) {
+  RowIter it(n);
+  double d0 = 0.0, d1 = 0.0;
+#pragma unroll 4
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int q = ptr[i]; q < ptr[i + 1]; ++q) {
+      const double v = val[q];
+      const double2 x = ld2(in + (size_t)col[q] * W + it.c);
+      a.x += v * x.x;
+      a.y += v * x.y;
+    }
+    const size_t o = (size_t)i * W + it.c;
+    if (accumulate) {
+      const double2 p = ld2(out + o);
+      a.x += p.x;
+      a.y += p.y;
+    }
+    st2(out + o, a);
+    if (dotp) {
+      const double2 x = ld2(in + o);
+      d0 += x.x * a.x;
+      d1 += x.y * a.y;
+    }
   }
-  atomicAdd(&pAp[c], dot);
+  if (dotp) {
+    atomicAdd(&dotp[it.c], d0);
+    atomicAdd(&dotp[it.c + 1], d1);
+  }
 }
 
-// X += a P, R -= a AP, rr_new += R.R with a = rr / pAp.  A column whose residual has
-// reached the tolerance is frozen: continuing CG on it once p^T A p has fallen to rounding
-// level (or below zero on the singular Laplacian) makes the step explode.
-__global__ void bcg_update_kernel(int n, int W, const double* __restrict__ rr, const double* __restrict__ pAp,
-                                  const double* __restrict__ bb, double tol2, double* __restrict__ X,
-                                  double* __restrict__ R, const double* __restrict__ P,
-                                  const double* __restrict__ AP, double* __restrict__ rr_new) {
-  const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
-  const int rsub = threadIdx.x / BCG_COLS;
-  if (c >= W) return;
-  if (rr[c] <= tol2 * bb[c]) {
-    if (blockIdx.y == 0 && rsub == 0) rr_new[c] = rr[c];
-    return;
+// X = w D^{-1} B
+__global__ void __launch_bounds__(BCG_THREADS)
+mg_smooth0_kernel(int n, int W, double w, const double* __restrict__ diag, const double* __restrict__ B,
+                  double* __restrict__ X) {
+  RowIter it(n);
+#pragma unroll 4
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    const size_t o = (size_t)i * W + it.c;
+    const double f = w / diag[i];
+    const double2 b = ld2(B + o);
+    st2(X + o, make_double2(f * b.x, f * b.y));
   }
-  const double d = pAp[c];
-  const double a = d > 0.0 ? rr[c] / d : 0.0;
-  const int r0 = blockIdx.y * BCG_ROWS;
-  const int r1 = min(n, r0 + BCG_ROWS);
-  double dot = 0.0;
-  for (int i = r0 + rsub; i < r1; i += blockDim.x / BCG_COLS) {
-    const size_t o = (size_t)i * W + c;
-    X[o] += a * P[o];
-    const double rv = R[o] - a * AP[o];
-    R[o] = rv;
-    dot += rv * rv;
-  }
-  atomicAdd(&rr_new[c], dot);
 }
 
-// P = R + (rr_new / rr) P (frozen columns keep P); zero pAp and the next accumulator
-__global__ void bcg_direction_kernel(int n, int W, const double* __restrict__ rr, const double* __restrict__ rr_new,
-                                     const double* __restrict__ bb, double tol2, const double* __restrict__ R,
-                                     double* __restrict__ P, double* __restrict__ pAp, double* __restrict__ rr_next) {
-  const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
-  const int rsub = threadIdx.x / BCG_COLS;
-  if (c >= W) return;
-  if (blockIdx.y == 0 && rsub == 0) {
-    pAp[c] = 0.0;
-    rr_next[c] = 0.0;
+// T = B - A X   (mode 0)   or   T = X + w D^{-1} (B - A X)   (mode 1)
+__global__ void __launch_bounds__(BCG_THREADS)
+mg_resid_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const double* __restrict__ val,
+                const double* __restrict__ diag, int n, int W, double w, int mode, const double* __restrict__ B,
+                const double* __restrict__ X, double* __restrict__ T) {
+  RowIter it(n);
+#pragma unroll 4
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int q = ptr[i]; q < ptr[i + 1]; ++q) {
+      const double v = val[q];
+      const double2 x = ld2(X + (size_t)col[q] * W + it.c);
+      a.x += v * x.x;
+      a.y += v * x.y;
+    }
+    const size_t o = (size_t)i * W + it.c;
+    const double2 b = ld2(B + o);
+    double2 r = make_double2(b.x - a.x, b.y - a.y);
+    if (mode != 0) {
+      const double2 x = ld2(X + o);
+      const double f = w / diag[i];
+      r = make_double2(x.x + f * r.x, x.y + f * r.y);
+    }
+    st2(T + o, r);
   }
-  if (rr_new[c] <= tol2 * bb[c]) return;
-  const double b = rr[c] > 0.0 ? rr_new[c] / rr[c] : 0.0;
-  const int r0 = blockIdx.y * BCG_ROWS;
-  const int r1 = min(n, r0 + BCG_ROWS);
-  for (int i = r0 + rsub; i < r1; i += blockDim.x / BCG_COLS) {
-    const size_t o = (size_t)i * W + c;
-    P[o] = R[o] + b * P[o];
+}
+
+// Xc = Cinv Bc (dense m x m times m x W)
+__global__ void mg_coarse_kernel(int m, int W, const double* __restrict__ Cinv, const double* __restrict__ Bc,
+                                 double* __restrict__ Xc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (c >= W || i >= m) return;
+  double a = 0.0;
+  for (int k = 0; k < m; ++k) a += Cinv[(size_t)i * m + k] * Bc[(size_t)k * W + c];
+  Xc[(size_t)i * W + c] = a;
+}
+
+__device__ __forceinline__ bool frozen(const double* rr, const double* bb, double tol2, int c) {
+  return rr[c] <= tol2 * bb[c];
+}
+
+// X += a P, R -= a AP, rr_new += R.R with a = rz / pAp (frozen columns untouched)
+__global__ void __launch_bounds__(BCG_THREADS)
+bcg_update_kernel(int n, int W, const double* __restrict__ rz, const double* __restrict__ rr,
+                  const double* __restrict__ pAp, const double* __restrict__ bb, double tol2, double* __restrict__ X,
+                  double* __restrict__ R, const double* __restrict__ P, const double* __restrict__ AP,
+                  double* __restrict__ rr_new) {
+  RowIter it(n);
+  const bool f0 = frozen(rr, bb, tol2, it.c), f1 = frozen(rr, bb, tol2, it.c + 1);
+  if (it.first()) {
+    if (f0) rr_new[it.c] = rr[it.c];
+    if (f1) rr_new[it.c + 1] = rr[it.c + 1];
+  }
+  if (f0 && f1) return;
+  const double a0 = f0 || !(pAp[it.c] > 0.0) ? 0.0 : rz[it.c] / pAp[it.c];
+  const double a1 = f1 || !(pAp[it.c + 1] > 0.0) ? 0.0 : rz[it.c + 1] / pAp[it.c + 1];
+  double d0 = 0.0, d1 = 0.0;
+#pragma unroll 4
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    const size_t o = (size_t)i * W + it.c;
+    double2 x = ld2(X + o), r = ld2(R + o);
+    const double2 p = ld2(P + o), ap = ld2(AP + o);
+    x.x += a0 * p.x;
+    x.y += a1 * p.y;
+    r.x -= a0 * ap.x;
+    r.y -= a1 * ap.y;
+    st2(X + o, x);
+    st2(R + o, r);
+    d0 += r.x * r.x;
+    d1 += r.y * r.y;
+  }
+  if (!f0) atomicAdd(&rr_new[it.c], d0);
+  if (!f1) atomicAdd(&rr_new[it.c + 1], d1);
+}
+
+// out += R.Z (per column)
+__global__ void __launch_bounds__(BCG_THREADS)
+bcg_dot_kernel(int n, int W, const double* __restrict__ R, const double* __restrict__ Z, double* __restrict__ out) {
+  RowIter it(n);
+  double d0 = 0.0, d1 = 0.0;
+#pragma unroll 4
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    const size_t o = (size_t)i * W + it.c;
+    const double2 r = ld2(R + o), z = ld2(Z + o);
+    d0 += r.x * z.x;
+    d1 += r.y * z.y;
+  }
+  atomicAdd(&out[it.c], d0);
+  atomicAdd(&out[it.c + 1], d1);
+}
+
+// P = Z + (rz_new / rz) P (frozen columns keep P); zero the accumulators of the next iteration
+__global__ void __launch_bounds__(BCG_THREADS)
+bcg_direction_kernel(int n, int W, const double* __restrict__ rz, const double* __restrict__ rz_new,
+                     const double* __restrict__ rr_new, const double* __restrict__ bb, double tol2,
+                     const double* __restrict__ Z, double* __restrict__ P, double* __restrict__ pAp,
+                     double* __restrict__ zero_a, double* __restrict__ zero_b) {
+  RowIter it(n);
+  if (it.first()) {
+    for (int k = 0; k < 2; ++k) {
+      pAp[it.c + k] = 0.0;
+      zero_a[it.c + k] = 0.0;
+      zero_b[it.c + k] = 0.0;
+    }
+  }
+  const bool f0 = frozen(rr_new, bb, tol2, it.c), f1 = frozen(rr_new, bb, tol2, it.c + 1);
+  if (f0 && f1) return;
+  const double b0 = rz[it.c] > 0.0 ? rz_new[it.c] / rz[it.c] : 0.0;
+  const double b1 = rz[it.c + 1] > 0.0 ? rz_new[it.c + 1] / rz[it.c + 1] : 0.0;
+#pragma unroll 4
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    const size_t o = (size_t)i * W + it.c;
+    const double2 z = ld2(Z + o);
+    double2 p = ld2(P + o);
+    if (!f0) p.x = z.x + b0 * p.x;
+    if (!f1) p.y = z.y + b1 * p.y;
+    st2(P + o, p);
   }
 }
 
 __global__ void bcg_colsum_kernel(int n, int W, const double* __restrict__ X, double* __restrict__ sums) {
-  const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
-  const int rsub = threadIdx.x / BCG_COLS;
-  if (c >= W) return;
-  const int r0 = blockIdx.y * BCG_ROWS;
-  const int r1 = min(n, r0 + BCG_ROWS);
-  double s = 0.0;
-  for (int i = r0 + rsub; i < r1; i += blockDim.x / BCG_COLS) s += X[(size_t)i * W + c];
-  atomicAdd(&sums[c], s);
+  RowIter it(n);
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+    const double2 x = ld2(X + (size_t)i * W + it.c);
+    s0 += x.x;
+    s1 += x.y;
+  }
+  atomicAdd(&sums[it.c], s0);
+  atomicAdd(&sums[it.c + 1], s1);
 }
 
 // Xhi/Xlo[i, c0 + c] = X[i, c] - mean_c (projected case), split into FP32 hi + lo
 __global__ void bcg_store_kernel(int n, int W, int c0, int ld, const double* __restrict__ X,
                                  const double* __restrict__ sums, bool project, float* __restrict__ Xhi,
                                  float* __restrict__ Xlo) {
-  const int c = blockIdx.x * BCG_COLS + (threadIdx.x % BCG_COLS);
-  const int rsub = threadIdx.x / BCG_COLS;
-  if (c >= W) return;
-  const double mean = project ? sums[c] / n : 0.0;
-  const int r0 = blockIdx.y * BCG_ROWS;
-  const int r1 = min(n, r0 + BCG_ROWS);
-  for (int i = r0 + rsub; i < r1; i += blockDim.x / BCG_COLS) {
-    const double v = X[(size_t)i * W + c] - mean;
-    const float h = (float)v;
-    Xhi[(size_t)i * ld + c0 + c] = h;
-    Xlo[(size_t)i * ld + c0 + c] = (float)(v - (double)h);
+  RowIter it(n);
+  for (int k = 0; k < 2; ++k) {
+    const int cc = it.c + k;
+    if (c0 + cc >= n) continue;
+    const double mean = project ? sums[cc] / n : 0.0;
+    for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
+      const double v = X[(size_t)i * W + cc] - mean;
+      const float h = (float)v;
+      Xhi[(size_t)i * ld + c0 + cc] = h;
+      Xlo[(size_t)i * ld + c0 + cc] = (float)(v - (double)h);
+    }
   }
 }
+
+struct DevLevel {
+  int n = 0, nc = 0;
+  double omega = 0.0;
+  double* diag = nullptr;
+  int32_t *A_ptr = nullptr, *A_col = nullptr, *P_ptr = nullptr, *P_col = nullptr, *R_ptr = nullptr, *R_col = nullptr;
+  double *A_val = nullptr, *P_val = nullptr, *R_val = nullptr;
+  double *B = nullptr, *X = nullptr, *T = nullptr;  // n x W work arrays (level 0 uses the CG arrays)
+};
+
+template <class T>
+cudaError_t up(T** d, const std::vector<T>& h, std::vector<void*>& own) {
+  cudaError_t e = cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  own.push_back(*d);
+  if (!h.empty()) e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+inline dim3 bgrid(int n, int w) { return dim3((w + BCG_COLS - 1) / BCG_COLS, (n + BCG_ROWS - 1) / BCG_ROWS); }
+// every kernel of a column block runs over all W columns of the (padded) stride
 
 }  // namespace
 
 cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const double* val, int n, bool project,
-                                   double tol, int max_iter, float* Xhi, float* Xlo, int* iters, cudaStream_t s) {
+                                   const AmgHierarchy* H, double tol, int max_iter, float* Xhi, float* Xlo,
+                                   int* iters, cudaStream_t s) {
   const int ld = padded_ld(n);
-  // column block width: bound the four n x W work arrays to about 16 GB
-  size_t cap = (size_t)16 << 30;
-  int W = (int)std::min<size_t>((size_t)n, cap / (4 * sizeof(double) * (size_t)n));
-  W = std::max(BCG_COLS, W / BCG_COLS * BCG_COLS);
-  W = std::min(W, (n + BCG_COLS - 1) / BCG_COLS * BCG_COLS);
-  double *X = nullptr, *R = nullptr, *P = nullptr, *AP = nullptr, *sc = nullptr;
-  size_t bytes = (size_t)n * W * sizeof(double);
+  std::vector<void*> own;
   cudaError_t err = cudaSuccess;
   auto fail = [&](cudaError_t e) {
-    cudaFree(X);
-    cudaFree(R);
-    cudaFree(P);
-    cudaFree(AP);
-    cudaFree(sc);
+    for (void* p : own) cudaFree(p);
     return e;
   };
-  if ((err = cudaMalloc(&X, bytes)) != cudaSuccess) return fail(err);
-  if ((err = cudaMalloc(&R, bytes)) != cudaSuccess) return fail(err);
-  if ((err = cudaMalloc(&P, bytes)) != cudaSuccess) return fail(err);
-  if ((err = cudaMalloc(&AP, bytes)) != cudaSuccess) return fail(err);
-  // scalars: rr ring of 3, pAp, bb, sums
-  if ((err = cudaMalloc(&sc, sizeof(double) * W * 6)) != cudaSuccess) return fail(err);
-  double* ring = sc;              // 3 W
-  double* pAp = sc + 3 * (size_t)W;
-  double* bb = sc + 4 * (size_t)W;
-  double* sums = sc + 5 * (size_t)W;
+  // device hierarchy
+  std::vector<DevLevel> L;
+  double* Cinv = nullptr;
+  int m = 0;
+  size_t coarse_rows = 0;  // sum of the rows of levels 1.. (plus the coarsest) for the work arrays
+  if (H && !H->levels.empty()) {
+    for (const AmgLevelHost& h : H->levels) {
+      DevLevel d;
+      d.n = h.n;
+      d.nc = h.nc;
+      d.omega = h.omega;
+      if ((err = up(&d.diag, h.diag, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.A_ptr, h.A_ptr, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.A_col, h.A_col, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.A_val, h.A_val, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.P_ptr, h.P_ptr, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.P_col, h.P_col, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.P_val, h.P_val, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.R_ptr, h.R_ptr, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.R_col, h.R_col, own)) != cudaSuccess) return fail(err);
+      if ((err = up(&d.R_val, h.R_val, own)) != cudaSuccess) return fail(err);
+      L.push_back(d);
+      coarse_rows += (size_t)h.nc;
+    }
+    m = H->coarse_n;
+    if ((err = up(&Cinv, H->coarse_inv, own)) != cudaSuccess) return fail(err);
+  }
+  const bool mg = !L.empty();
+  // column block width: bound the work arrays to about 24 GB
+  const size_t fine_arrays = mg ? 6 : 4;
+  const size_t per_col = sizeof(double) * (fine_arrays * (size_t)n + 3 * coarse_rows);
+  const size_t cap = (size_t)24 << 30;
+  const int n_pad = (n + BCG_COLS - 1) / BCG_COLS * BCG_COLS;  // all columns in one block when they fit
+  int W = n_pad;
+  if ((size_t)W * per_col > cap) W = std::max<int>(BCG_COLS, (int)(cap / per_col) / BCG_COLS * BCG_COLS);
+  const size_t bytes = (size_t)n * W * sizeof(double);
+  double *X, *R, *P, *AP, *Z = nullptr, *T0 = nullptr, *sc;
+  for (double** p : {&X, &R, &P, &AP}) {
+    if ((err = cudaMalloc(p, bytes)) != cudaSuccess) return fail(err);
+    own.push_back(*p);
+  }
+  if (mg) {
+    for (double** p : {&Z, &T0}) {
+      if ((err = cudaMalloc(p, bytes)) != cudaSuccess) return fail(err);
+      own.push_back(*p);
+    }
+    // levels 1.. hold B, X, T; the coarsest rhs / solution live in the last level's extra slots
+    for (size_t l = 1; l < L.size(); ++l)
+      for (double** p : {&L[l].B, &L[l].X, &L[l].T}) {
+        if ((err = cudaMalloc(p, (size_t)L[l].n * W * sizeof(double))) != cudaSuccess) return fail(err);
+        own.push_back(*p);
+      }
+  }
+  // coarsest arrays (m x W): rhs and solution
+  double *Bc = nullptr, *Xc = nullptr;
+  if (mg) {
+    for (double** p : {&Bc, &Xc}) {
+      if ((err = cudaMalloc(p, (size_t)m * W * sizeof(double))) != cudaSuccess) return fail(err);
+      own.push_back(*p);
+    }
+  }
+  // scalars: rz ring (3W), rr ring (3W), pAp, bb, sums
+  if ((err = cudaMalloc(&sc, sizeof(double) * W * 9)) != cudaSuccess) return fail(err);
+  own.push_back(sc);
+  double* rzr = sc;
+  double* rrr = sc + 3 * (size_t)W;
+  double* pAp = sc + 6 * (size_t)W;
+  double* bb = sc + 7 * (size_t)W;
+  double* sums = sc + 8 * (size_t)W;
   std::vector<double> h_rr(W), h_bb(W);
   int worst_iters = 0;
-  const int threads = 256;
+  const double tol2 = tol * tol;
   for (int c0 = 0; c0 < n; c0 += W) {
-    const int w = std::min(W, n - c0);
-    dim3 grid((w + BCG_COLS - 1) / BCG_COLS, (n + BCG_ROWS - 1) / BCG_ROWS);
-    if ((err = cudaMemsetAsync(sc, 0, sizeof(double) * W * 6, s)) != cudaSuccess) return fail(err);
-    bcg_init_kernel<<<grid, threads, 0, s>>>(n, w, c0, project, X, R, P, ring);
-    if ((err = cudaMemcpyAsync(bb, ring, sizeof(double) * w, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    const int w = W;  // padding columns (c0 + c >= n) carry b = 0 and stay frozen
+    const int wlive = std::min(W, n - c0);
+    dim3 grid = bgrid(n, w);
+    if ((err = cudaMemsetAsync(sc, 0, sizeof(double) * W * 9, s)) != cudaSuccess) return fail(err);
+    bcg_init_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, project, X, R, rrr);
+    if ((err = cudaMemcpyAsync(bb, rrr, sizeof(double) * w, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return fail(err);
-    if ((err = cudaMemcpyAsync(h_bb.data(), ring, sizeof(double) * w, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if ((err = cudaMemcpyAsync(h_bb.data(), rrr, sizeof(double) * w, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return fail(err);
+    // z0 = M r0 (one V(1,1) cycle; Z = R without a hierarchy), rz0 = r0.z0, p0 = z0
+    auto precond = [&](double* Rin) -> double* {
+      if (!mg) return Rin;
+      ProfScope prof("factor_mg_vcycle", 0.0, 0.0, s);
+      // levels: l = 0 .. nl-1 have operators; the coarse solve sits after the last
+      const size_t nl = L.size();
+      std::vector<double*> Bs(nl + 1), Xs(nl + 1), Ts(nl);
+      for (size_t l = 0; l < nl; ++l) {
+        Bs[l] = l == 0 ? Rin : L[l].B;
+        Xs[l] = l == 0 ? Z : L[l].X;
+        Ts[l] = l == 0 ? T0 : L[l].T;
+      }
+      Bs[nl] = Bc;
+      Xs[nl] = Xc;
+      for (size_t l = 0; l < nl; ++l) {
+        DevLevel& v = L[l];
+        mg_smooth0_kernel<<<bgrid(v.n, w), BCG_THREADS, 0, s>>>(v.n, w, v.omega, v.diag, Bs[l], Xs[l]);
+        mg_resid_kernel<<<bgrid(v.n, w), BCG_THREADS, 0, s>>>(v.A_ptr, v.A_col, v.A_val, v.diag, v.n, w, v.omega,
+                                                             0, Bs[l], Xs[l], Ts[l]);
+        bcg_spmm_kernel<<<bgrid(v.nc, w), BCG_THREADS, 0, s>>>(v.R_ptr, v.R_col, v.R_val, v.nc, w, Ts[l], Bs[l + 1],
+                                                               0, nullptr);
+      }
+      {
+        dim3 g((w + 127) / 128, m);
+        mg_coarse_kernel<<<g, 128, 0, s>>>(m, w, Cinv, Bs[nl], Xs[nl]);
+      }
+      for (size_t li = nl; li-- > 0;) {
+        DevLevel& v = L[li];
+        bcg_spmm_kernel<<<bgrid(v.n, w), BCG_THREADS, 0, s>>>(v.P_ptr, v.P_col, v.P_val, v.n, w, Xs[li + 1], Xs[li],
+                                                              1, nullptr);
+        mg_resid_kernel<<<bgrid(v.n, w), BCG_THREADS, 0, s>>>(v.A_ptr, v.A_col, v.A_val, v.diag, v.n, w, v.omega,
+                                                             1, Bs[li], Xs[li], Ts[li]);
+        // the smoothed iterate is in Ts[li]: swap the roles of the two arrays of this level
+        if (li == 0) {
+          std::swap(Z, T0);
+        } else {
+          std::swap(L[li].X, L[li].T);
+        }
+        Xs[li] = li == 0 ? Z : L[li].X;
+      }
+      return Z;
+    };
+    double* Zp = precond(R);
+    bcg_dot_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, R, Zp, rzr);
+    if ((err = cudaMemcpyAsync(P, Zp, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return fail(err);
     int it = 0;
     bool done = false;
     while (!done && it < max_iter) {
-      double* rr = ring + (size_t)(it % 3) * W;
-      double* rr_new = ring + (size_t)((it + 1) % 3) * W;
-      double* rr_next = ring + (size_t)((it + 2) % 3) * W;
+      double* rz = rzr + (size_t)(it % 3) * W;
+      double* rz_new = rzr + (size_t)((it + 1) % 3) * W;
+      double* rz_next = rzr + (size_t)((it + 2) % 3) * W;
+      double* rr = rrr + (size_t)(it % 3) * W;
+      double* rr_new = rrr + (size_t)((it + 1) % 3) * W;
+      double* rr_next = rrr + (size_t)((it + 2) % 3) * W;
       {
         ProfScope prof("factor_bcg_spmm", 16.0 * n * w, 0.0, s);
-        bcg_spmm_kernel<<<grid, threads, 0, s>>>(ptr, col, val, n, w, P, AP, pAp);
+        bcg_spmm_kernel<<<grid, BCG_THREADS, 0, s>>>(ptr, col, val, n, w, P, AP, 0, pAp);
       }
       {
         ProfScope prof("factor_bcg_update", 48.0 * n * w, 0.0, s);
-        bcg_update_kernel<<<grid, threads, 0, s>>>(n, w, rr, pAp, bb, tol * tol, X, R, P, AP, rr_new);
+        bcg_update_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, rz, rr, pAp, bb, tol2, X, R, P, AP, rr_new);
       }
+      double* Zi = precond(R);
+      bcg_dot_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, R, Zi, rz_new);
       {
         ProfScope prof("factor_bcg_direction", 24.0 * n * w, 0.0, s);
-        bcg_direction_kernel<<<grid, threads, 0, s>>>(n, w, rr, rr_new, bb, tol * tol, R, P, pAp, rr_next);
+        bcg_direction_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, rz, rz_new, rr_new, bb, tol2, Zi, P, pAp, rz_next,
+                                                          rr_next);
       }
       ++it;
-      if (it % 16 == 0 || it == max_iter) {
+      if (it % 8 == 0 || it == max_iter) {
         if ((err = cudaMemcpyAsync(h_rr.data(), rr_new, sizeof(double) * w, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess)
           return fail(err);
         if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);
         double worst = 0.0;
-        for (int c = 0; c < w; ++c) worst = std::max(worst, std::sqrt(h_rr[c] / std::max(h_bb[c], 1e-300)));
+        for (int c = 0; c < wlive; ++c) worst = std::max(worst, std::sqrt(h_rr[c] / std::max(h_bb[c], 1e-300)));
         done = worst <= tol;
       }
     }
@@ -915,9 +1223,9 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
     worst_iters = std::max(worst_iters, it);
     if (project) {
       if ((err = cudaMemsetAsync(sums, 0, sizeof(double) * W, s)) != cudaSuccess) return fail(err);
-      bcg_colsum_kernel<<<grid, threads, 0, s>>>(n, w, X, sums);
+      bcg_colsum_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, X, sums);
     }
-    bcg_store_kernel<<<grid, threads, 0, s>>>(n, w, c0, ld, X, sums, project, Xhi, Xlo);
+    bcg_store_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, X, sums, project, Xhi, Xlo);
     if ((err = cudaGetLastError()) != cudaSuccess) return fail(err);
   }
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);

@@ -106,14 +106,25 @@ cudaError_t launch_farfield(const DeviceGeometry& g, double k, const double2* j,
 // ---------------------------------------------------------------- kernels (k_linalg.cu)
 enum GemvMode { GEMV_F32 = 0, GEMV_FF = 1 };
 
-// y[:, r] = beta_y * y + scale * op(M) x[:, r], r < nrhs; M n x n complex64 row-major
-// (symmetric, so rows are columns); op = conj if conjugate.  x, y complex128 column-major
-// with leading dimension n.  scale is complex.
+// Device scratch of the GEMV: x converted to FP32 hi (and lo) padded to ld, and the FP64
+// accumulator the persistent CTAs add their row sums into.  Calls sharing a scratch must not
+// overlap on the device.
+struct GemvScratch {
+  float2* xh = nullptr;   // cap_cols x cap_ld
+  float2* xl = nullptr;   // cap_cols x cap_ld
+  double2* acc = nullptr; // cap_cols x cap_n
+  int cap_n = 0, cap_ld = 0, cap_cols = 0;
+};
+int padded_ld(int n);
+
+// y[:, r] = scale * op(M) x[:, r] (+ y[:, r] if accumulate), r < nrhs; M n x n complex64
+// row-major with rows padded to padded_ld(n) (symmetric, so rows are columns); op = conj if
+// conjugate.  x, y complex128 column-major with leading dimension n.
 cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate,
-                     double2 scale, bool accumulate, GemvMode mode, cudaStream_t s);
+                     double2 scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s);
 // y = scale * (Mhi [+ Mlo]) x with a real symmetric n x n matrix in FP32 hi/lo planes.
 cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x, double2* y, int nrhs,
-                     double scale, bool accumulate, GemvMode mode, cudaStream_t s);
+                     double scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s);
 
 // sparse transforms (Sec. 2, Eq. qHofj); all complex128, nrhs columns
 cudaError_t sigma_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s);   // N_C
@@ -146,6 +157,8 @@ cudaError_t vec_axpy_cols(const double* coef, bool negate, const double2* x, dou
 cudaError_t vec_xpby_cols(const double2* x, const double* coef, double2* y, int64_t n, int nrhs,
                           const int* active, cudaStream_t s);   // y = x + coef[r] y
 cudaError_t vec_copy(const double2* x, double2* y, int64_t n, cudaStream_t s);
+cudaError_t vec_copy_scale_cols(const double2* x, const double* coef, double2* y, int64_t n, int nrhs,
+                               cudaStream_t s);  // y[:, r] = coef[r] x[:, r]
 cudaError_t vec_scale(double2* y, double2 a, int64_t n, cudaStream_t s);
 // CG scalar step on device: alpha = rr/pAp etc. (see k_linalg.cu)
 cudaError_t cg_scalars_alpha(const double* rr, const double2* pAp, double* alpha, const int* active, int nrhs,
@@ -153,10 +166,29 @@ cudaError_t cg_scalars_alpha(const double* rr, const double2* pAp, double* alpha
 cudaError_t cg_scalars_beta(const double2* rr_new2, double* rr, double* beta, const int* active, int nrhs,
                             cudaStream_t s);
 
-// Dense inverse of a sparse SPD (or singular Laplacian) matrix by Jacobi-preconditioned block CG.
-// A in CSR (n x n, FP64); rhs columns e_c - (project ? 1/n : 0); output X (FP32 hi + lo planes, n x n).
-// Returns the iterations used in *iters; work buffers are allocated inside.
+// Smoothed-aggregation multigrid hierarchy (host side, amg.cpp).
+struct AmgLevelHost {
+  int n = 0, nc = 0;       // rows of this level, rows of the next
+  double omega = 0.0;      // Jacobi weight 4 / (3 rho)
+  std::vector<double> diag;
+  std::vector<int32_t> A_ptr, A_col, P_ptr, P_col, R_ptr, R_col;  // A (n x n), P (n x nc), R = P^T
+  std::vector<double> A_val, P_val, R_val;
+};
+struct AmgHierarchy {
+  std::vector<AmgLevelHost> levels;
+  int coarse_n = 0;
+  std::vector<double> coarse_inv;  // dense pseudo-inverse of the coarsest matrix
+};
+int build_amg(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col, const std::vector<double>& val, int n,
+              int max_coarse, AmgHierarchy& H, std::string& err);
+
+// Dense inverse of a sparse SPD matrix (or of the singular cell Laplacian restricted to 1^perp,
+// with project = true: columns e_c - 1/n, result with zero column means = the pseudo-inverse),
+// by block CG, preconditioned by one multigrid V(1,1) cycle when H is given.  A in CSR (device,
+// n x n, FP64); output in FP32 hi + lo planes (n rows, padded_ld(n) stride).  Work buffers are
+// allocated inside.  *iters receives the iteration count of the slowest column block.
 cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const double* val, int n, bool project,
-                                   double tol, int max_iter, float* Xhi, float* Xlo, int* iters, cudaStream_t s);
+                                   const AmgHierarchy* H, double tol, int max_iter, float* Xhi, float* Xlo,
+                                   int* iters, cudaStream_t s);
 
 }  // namespace rfcmp

@@ -42,7 +42,7 @@ def test_status_strings_and_defaults(libpath):
         assert L.rfcmp_strerror(code)
     o = rf.OpOpts()
     L.rfcmp_op_opts_default(ctypes.byref(o))
-    assert o.power_steps == 30 and o.scaling == 0 and o.factor_tol == 1e-13
+    assert o.power_steps == 30 and o.scaling == 0 and o.factor_tol == 1e-13 and o.power_rtol == 1e-3
     s = rf.SolveOpts()
     L.rfcmp_solve_opts_default(ctypes.byref(s))
     assert s.tol == 1e-6 and s.precision == 0 and s.max_refine == 8
@@ -50,7 +50,7 @@ def test_status_strings_and_defaults(libpath):
 
 def test_struct_layouts_match_header(libpath):
     # sizes implied by include/rfcmp.h on LP64
-    assert ctypes.sizeof(rf.OpOpts) == 4 + 4 + 8 * 4 + 4 * 8
+    assert ctypes.sizeof(rf.OpOpts) == 4 + 4 + 8 * 5 + 4 * 8
     assert ctypes.sizeof(rf.SolveOpts) == 8 + 4 + 4 + 8 + 4 + 4 + 4 * 8
     assert ctypes.sizeof(rf.SolveReport) == 4 * 4 + 8
     assert ctypes.sizeof(rf.OpInfo) == 3 * 8 + 2 * 4 + 4 * 8 + 8 + 3 * 8 + 2 * 4
