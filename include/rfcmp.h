@@ -221,6 +221,27 @@ int rfcmp_farfield(rfcmp_op* op, const rfcmp_c128* j, int64_t nrhs, const double
                    double* rcs_dbsm, void* stream);
 
 /* ----------------------------------------------------------------------------
+ * y = T_A x without allocating anything (the paper has no counterpart).
+ * For callers that cannot allocate device memory where they need this product: a serving
+ * loop whose HBM is partitioned up front by its own pool, or a latency-critical path that
+ * must not call cudaMalloc/cudaFree, which can synchronise the device.  rfcmp_apply
+ * allocates the operator's work buffers on first use; this entry point never does.  Its
+ * scratch (x in FP32 hi/lo and an FP64 row accumulator, 4 MiB) is a file-scope device array
+ * that every GPU which loads the library holds until the process exits.
+ *  op     an operator created earlier (its T_A is read; nothing of op is modified)
+ *  x, y   DEVICE, N x nrhs complex128, column-major; must not alias
+ *  nrhs   1..4, with padded_N x nrhs <= 131072 (padded_N = N rounded up to a multiple of 64;
+ *         N = 30720 allows nrhs <= 4, N = 90750 allows nrhs = 1)
+ * Float-float accurate accumulation, like rfcmp_apply with RFCMP_APPLY_T_A.
+ * The first call on each device (with the op's device current) looks up the scratch
+ * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call shares the one scratch array (it is cleared where it must start at zero):
+ * calls that overlap on the GPU race, so issue them on one stream or serialise them.
+ * Errors: RFCMP_ERR_INVALID_ARG (NULL, nrhs or size beyond the limits), RFCMP_ERR_CUDA.
+ */
+int rfcmp_apply_ta_noalloc(const rfcmp_op* op, const rfcmp_c128* x, rfcmp_c128* y, int64_t nrhs, void* stream);
+
+/* ----------------------------------------------------------------------------
  * Profiling counters (the paper has no counterpart; measurement support).
  * When enabled, every launch of an instrumented kernel family is bracketed by
  * CUDA events on the stream it is launched on; rfcmp_profile_read

@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "rfcmp_op_create", "rfcmp_op_info_get", "rfcmp_op_destroy", "rfcmp_op_export", "rfcmp_op_edges",
     "rfcmp_rhs_planewave", "rfcmp_apply", "rfcmp_precondition", "rfcmp_solve", "rfcmp_solve_host",
     "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
-    "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read",
+    "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
 ]
 
 
@@ -117,6 +117,7 @@ def lib():
         L.rfcmp_last_error.restype = ctypes.c_char_p
         L.rfcmp_op_opts_default.argtypes = [ctypes.POINTER(OpOpts)]
         L.rfcmp_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
+        L.rfcmp_apply_ta_noalloc.argtypes = [vp, vp, vp, i64, vp]
         L.rfcmp_profile_enable.argtypes = [i32]
         L.rfcmp_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
         _LIB = L
@@ -273,6 +274,15 @@ class Operator:
         x = self._vec(x)
         y = torch.empty_like(x)
         _check(lib().rfcmp_apply(self._h, APPLY[which], _ptr(x), _ptr(y), x.shape[0], _stream()))
+        return y
+
+    def apply_ta_noalloc(self, x, out=None):
+        """y = T_A x through the allocation-free entry point; `out` may be preallocated."""
+        import torch
+
+        x = self._vec(x)
+        y = torch.empty_like(x) if out is None else out
+        _check(lib().rfcmp_apply_ta_noalloc(self._h, _ptr(x), _ptr(y), x.shape[0], _stream()))
         return y
 
     def precondition(self, which: str, x):

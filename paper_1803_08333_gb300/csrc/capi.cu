@@ -23,11 +23,16 @@ using namespace rfcmp;
 // ---------------------------------------------------------------- errors
 namespace {
 thread_local std::string g_last_error;
+}  // namespace
 
+namespace rfcmp {
 int set_error(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
 }
+}  // namespace rfcmp
+
+namespace {
 
 #define RF_CUDA(call)                                                                                  \
   do {                                                                                                 \
@@ -693,6 +698,16 @@ int check_device(int device) {
 }
 
 }  // namespace
+
+namespace rfcmp {
+bool op_ta_view(const rfcmp_op* op, OpTaView* out) {
+  if (!op || !out || !op->TA) return false;
+  out->TA = op->TA;
+  out->n = (int)op->top.ne;
+  out->device = op->ctx->device;
+  return true;
+}
+}  // namespace rfcmp
 
 // ============================================================================ C ABI
 extern "C" {

@@ -390,6 +390,54 @@ cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int n
   return err;
 }
 
+// The same complex GEMV without profiling events and without the cached grid map: it
+// performs no allocation of any kind (device, driver or host heap).
+cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate,
+                           GemvMode mode, GemvScratch& w, cudaStream_t s) {
+  const int ld = padded_ld(n);
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int r = 0; r < nrhs && err == cudaSuccess;) {
+    const int nr = nrhs - r >= 4 ? 4 : (nrhs - r >= 2 ? 2 : 1);
+    if (n > w.cap_n || ld > w.cap_ld || nr > w.cap_cols) return cudaErrorInvalidValue;
+    const double2* xr = x + (size_t)r * n;
+    double2* yr = y + (size_t)r * n;
+    if ((err = gemv_prep(xr, n, ld, nr, mode == GEMV_FF, w, s)) != cudaSuccess) break;
+    const int rowblocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
+    const int upr = (ld + GEMV_CHUNK - 1) / GEMV_CHUNK;
+    const long long units = (long long)rowblocks * upr;
+#define RF_PLAIN(NRV, FFV, CJ)                                                                   \
+  {                                                                                              \
+    auto k = gemv_c64_kernel<NRV, FFV, CJ>;                                                      \
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, GEMV_WARPS * 32, 0)) !=     \
+        cudaSuccess)                                                                             \
+      break;                                                                                     \
+    const int grid = (int)std::min<long long>(units, (long long)sms * std::max(1, per));         \
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr);                 \
+  }
+#define RF_PLAIN_NR(NRV)                                           \
+  if (mode == GEMV_FF) {                                           \
+    if (conjugate) RF_PLAIN(NRV, true, true) else RF_PLAIN(NRV, true, false)   \
+  } else {                                                         \
+    if (conjugate) RF_PLAIN(NRV, false, true) else RF_PLAIN(NRV, false, false) \
+  }
+    if (nr == 4) {
+      RF_PLAIN_NR(4)
+    } else if (nr == 2) {
+      RF_PLAIN_NR(2)
+    } else {
+      RF_PLAIN_NR(1)
+    }
+#undef RF_PLAIN_NR
+#undef RF_PLAIN
+    if ((err = cudaGetLastError()) != cudaSuccess) break;
+    err = gemv_finalize(n, nr, make_double2(1.0, 0.0), false, yr, w, s);
+    r += nr;
+  }
+  return err;
+}
+
 cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x, double2* y, int nrhs, double scale,
                      bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s) {
   const int ld = padded_ld(n);

@@ -13,6 +13,17 @@
 
 namespace rfcmp {
 
+// ---------------------------------------------------------------- op accessors
+// Read-only view of an operator's T_A for translation units outside capi.cu.
+struct OpTaView {
+  const float2* TA = nullptr;
+  int n = 0;
+  int device = 0;
+};
+bool op_ta_view(const rfcmp_op* op, OpTaView* out);
+// Records the message returned by rfcmp_last_error() for the calling thread; returns code.
+int set_error(int code, const std::string& msg);
+
 // ---------------------------------------------------------------- profiling
 // RAII bracket of one launch by CUDA events on its stream (no-op when disabled).
 class ProfScope {
@@ -122,6 +133,10 @@ int padded_ld(int n);
 // conjugate.  x, y complex128 column-major with leading dimension n.
 cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate,
                      double2 scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s);
+// y = op(M) x through the same kernels with no allocation of any kind (no profiling events,
+// no cached launch-grid table).
+cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate,
+                           GemvMode mode, GemvScratch& w, cudaStream_t s);
 // y = scale * (Mhi [+ Mlo]) x with a real symmetric n x n matrix in FP32 hi/lo planes.
 cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x, double2* y, int nrhs,
                      double scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s);
