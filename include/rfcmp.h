@@ -221,6 +221,20 @@ int rfcmp_farfield(rfcmp_op* op, const rfcmp_c128* j, int64_t nrhs, const double
                    double* rcs_dbsm, void* stream);
 
 /* ----------------------------------------------------------------------------
+ * D = A B^T (+ D) on the tensor cores in split BF16 (the engine of the multi-RHS products).
+ * The paper has no counterpart; it is exported so the engine can be checked on its own.
+ *  A  DEVICE float32, M x K row-major, row stride lda elements
+ *  B  DEVICE float32, N x K row-major, row stride ldb elements
+ *  D  DEVICE float32, M x N row-major, row stride ldd elements; accumulate != 0 adds to D
+ * Each operand is split into two BF16 planes (hi = bf16(x), lo = bf16(x - hi)); every K step
+ * accumulates hi*hi + hi*lo + lo*hi in FP32 (tcgen05.mma, tensor-memory accumulator), about
+ * 2^-16 relative accuracy per product.  Temporary planes are allocated on `stream`.
+ * Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_CUDA, RFCMP_ERR_DEVICE_TIMEOUT (a bounded wait of
+ * the kernel gave up; the context stays usable). */
+int rfcmp_gemm_bf16x3(const float* A, int64_t lda, const float* B, int64_t ldb, float* D, int64_t ldd, int64_t M,
+                      int64_t N, int64_t K, int accumulate, void* stream);
+
+/* ----------------------------------------------------------------------------
  * y = T_A x without allocating anything (the paper has no counterpart).
  * For callers that cannot allocate device memory where they need this product: a serving
  * loop whose HBM is partitioned up front by its own pool, or a latency-critical path that

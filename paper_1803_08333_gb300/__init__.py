@@ -33,6 +33,7 @@ EXPORTED_SYMBOLS = [
     "rfcmp_rhs_planewave", "rfcmp_apply", "rfcmp_precondition", "rfcmp_solve", "rfcmp_solve_host",
     "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
+    "rfcmp_gemm_bf16x3",
 ]
 
 
@@ -118,6 +119,7 @@ def lib():
         L.rfcmp_op_opts_default.argtypes = [ctypes.POINTER(OpOpts)]
         L.rfcmp_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
         L.rfcmp_apply_ta_noalloc.argtypes = [vp, vp, vp, i64, vp]
+        L.rfcmp_gemm_bf16x3.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, vp]
         L.rfcmp_profile_enable.argtypes = [i32]
         L.rfcmp_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
         _LIB = L
@@ -155,6 +157,20 @@ def profile_read() -> dict:
         e = buf[i]
         out[e.name.decode()] = {"launches": e.launches, "total_ms": e.total_ms, "bytes": e.bytes, "flops": e.flops}
     return out
+
+
+def gemm_bf16x3(A, B, D=None, accumulate=False):
+    """D = A @ B.T (+ D) with float32 CUDA tensors through the split-BF16 tensor-core GEMM."""
+    import torch
+
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    if D is None:
+        D = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().rfcmp_gemm_bf16x3(_ptr(A), K, _ptr(B), K, _ptr(D), N, M, N, K, 1 if accumulate else 0, _stream()))
+    return D
 
 
 class Context:

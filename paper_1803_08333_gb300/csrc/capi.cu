@@ -1296,6 +1296,43 @@ int rfcmp_solve_host(rfcmp_op* op, const rfcmp_c128* e_host, rfcmp_c128* j_host,
   return rc;
 }
 
+int rfcmp_gemm_bf16x3(const float* A, int64_t lda, const float* B, int64_t ldb, float* D, int64_t ldd, int64_t M,
+                      int64_t N, int64_t K, int accumulate, void* stream) {
+  if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || lda < K || ldb < K || ldd < N || M > (1 << 30) ||
+      N > (1 << 30) || K > (1 << 30))
+    return set_error(RFCMP_ERR_INVALID_ARG, "invalid GEMM arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long ldp = (K + 7) / 8 * 8;  // plane row stride: 16-byte multiple
+  __nv_bfloat16* pl = nullptr;
+  int* err = nullptr;
+  const size_t na = (size_t)M * ldp, nb = (size_t)N * ldp;
+  RF_CUDA(cudaMallocAsync(&pl, sizeof(__nv_bfloat16) * 2 * (na + nb), st));
+  RF_CUDA(cudaMallocAsync(&err, sizeof(int), st));
+  RF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  RF_CUDA(cudaMemsetAsync(pl, 0, sizeof(__nv_bfloat16) * 2 * (na + nb), st));
+  SplitOperand a, b;
+  a.hi = pl;
+  a.lo = pl + na;
+  a.rows = (int)M;
+  a.ld = ldp;
+  b.hi = pl + 2 * na;
+  b.lo = pl + 2 * na + nb;
+  b.rows = (int)N;
+  b.ld = ldp;
+  RF_K(split_bf16_f32(A, lda, (int)M, (int)K, const_cast<__nv_bfloat16*>(a.hi), const_cast<__nv_bfloat16*>(a.lo),
+                      ldp, st));
+  RF_K(split_bf16_f32(B, ldb, (int)N, (int)K, const_cast<__nv_bfloat16*>(b.hi), const_cast<__nv_bfloat16*>(b.lo),
+                      ldp, st));
+  RF_K(gemm_bf16x3(&a, &b, nullptr, 1, (int)M, (int)N, (int)K, D, ldd, accumulate != 0, err, st));
+  int h_err = 0;
+  RF_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaFreeAsync(pl, st));
+  RF_CUDA(cudaFreeAsync(err, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  if (h_err) return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "GEMM kernel wait timed out (code " + std::to_string(h_err) + ")");
+  return RFCMP_OK;
+}
+
 int rfcmp_farfield(rfcmp_op* op, const rfcmp_c128* j, int64_t nrhs, const double* dirs, int64_t ndir,
                    double* rcs_dbsm, void* stream) {
   if (!op || !j || !dirs || !rcs_dbsm || nrhs <= 0 || ndir <= 0 || nrhs > 65535 || ndir > (1 << 20))

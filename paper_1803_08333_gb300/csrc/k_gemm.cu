@@ -1,0 +1,320 @@
+// Split-BF16 GEMM on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA loads).
+//
+//   D[M x N] (FP32, row-major) = sum over segments s of  sign_s * A_s[M x K] * B_s[N x K]^T  (+ D)
+//
+// Every operand is given as two BF16 planes (hi = bf16(x), lo = bf16(x - hi)), both K-major
+// (row-major with K contiguous).  Each K step issues the three products hi*hi, hi*lo, lo*hi into
+// one FP32 accumulator in tensor memory ("BF16x3"; the lo*lo term is below the accuracy of the
+// other three).  Used for the multi-RHS complex products with the resident operator blocks and
+// for the dense products of the factor refinement.
+//
+// Kernel layout: one CTA per 128 x 128 output tile, 128 threads.  Thread 0 issues the TMA loads
+// of a 3-stage ring (each stage: A hi, A lo, B hi, B lo tiles of 128 x 64 BF16 with the 128-byte
+// swizzle), thread 32 issues the MMAs (tcgen05.mma kind::f16, M = 128, N = 128, K = 16 per
+// instruction) and commits them to the stage's "empty" barrier, and all four warps drain the
+// accumulator (tcgen05.ld 32x32b) into D.  Every wait is bounded by a clock limit; on timeout the
+// kernel records an error code, still releases its tensor memory, and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "rfcmp_internal.h"
+
+namespace rfcmp {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int TILE_A = BM * BK * 2;                 // 16 KiB per BF16 plane
+constexpr int TILE_B = BN * BK * 2;                 // 16 KiB
+constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // 64 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long WAIT_CYCLES = 4000000000LL;     // about 2 s at the GB300 clock
+
+struct GemmMaps {
+  CUtensorMap a[2][2];  // [segment][hi, lo]
+  CUtensorMap b[2][2];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on one phase of an mbarrier: false after WAIT_CYCLES
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // layout: 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: kind::f16, BF16 A and B, FP32 accumulator, K-major A and B, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n, bool neg_a) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask, int M, int N, int K,
+                   float* __restrict__ D, long long ldd, int accumulate, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kblocks = (K + BK - 1) / BK;
+  const int total = nseg * kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: TMA loads into the stage ring
+      for (int it = 0; it < total; ++it) {
+        const int s = it % STAGES, round = it / STAGES;
+        if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+          atomicExch(err, 1);
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int seg = it / kblocks, kx = (it % kblocks) * BK;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_2d(st, &maps.a[seg][0], &full[s], kx, m0);
+        tma_load_2d(st + TILE_A, &maps.a[seg][1], &full[s], kx, m0);
+        tma_load_2d(st + 2 * TILE_A, &maps.b[seg][0], &full[s], kx, n0);
+        tma_load_2d(st + 2 * TILE_A + TILE_B, &maps.b[seg][1], &full[s], kx, n0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      const uint32_t id_pos = idesc_bf16(BM, BN, false), id_neg = idesc_bf16(BM, BN, true);
+      for (int it = 0; it < total; ++it) {
+        const int s = it % STAGES, round = it / STAGES;
+        if (!mbar_wait(&full[s], round & 1)) {
+          atomicExch(err, 2);
+          break;
+        }
+        tc_fence_after();
+        const int seg = it / kblocks;
+        const uint32_t idesc = (neg_mask >> seg) & 1 ? id_neg : id_pos;
+        const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + TILE_A;
+        const uint32_t b_hi = a_hi + 2 * TILE_A, b_lo = b_hi + TILE_B;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte swizzled row
+          const uint64_t ah = sw128_desc(a_hi + off), al = sw128_desc(a_lo + off);
+          const uint64_t bh = sw128_desc(b_hi + off), bl = sw128_desc(b_lo + off);
+          mma_bf16(tmem, ah, bh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, ah, bl, idesc, 1u);
+          mma_bf16(tmem, al, bh, idesc, 1u);
+        }
+        mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+      }
+      mma_commit(done);  // arrives when every MMA issued above has completed
+    }
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));  // warp-uniform: tcgen05.ld is .sync.aligned
+  if (!ok && lane == 0) atomicExch(err, 3);
+  tc_fence_after();
+  const int row = m0 + 32 * warp + lane;
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+      if (row < M) {
+        float* dst = D + (size_t)row * ldd + n0 + c0;
+        const int cols = min(32, N - (n0 + c0));
+        for (int j = 0; j < cols; ++j) {
+          float v = __uint_as_float(r[j]);
+          if (accumulate) v += dst[j];
+          dst[j] = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+// FP32 (or FP64) -> BF16 hi/lo planes
+template <class T>
+__global__ void split_bf16_kernel(const T* __restrict__ src, long long ld_src, int rows, int cols,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ld_dst) {
+  const long long total = (long long)rows * cols;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx % cols);
+    const float v = (float)src[(size_t)r * ld_src + c];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[(size_t)r * ld_dst + c] = h;
+    lo[(size_t)r * ld_dst + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k, long long ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t split_bf16_f32(const float* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
+                           __nv_bfloat16* lo, long long ld_dst, cudaStream_t s) {
+  const long long total = (long long)rows * cols;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 8 * 152);
+  split_bf16_kernel<float><<<blocks, 256, 0, s>>>(src, ld_src, rows, cols, hi, lo, ld_dst);
+  return cudaGetLastError();
+}
+
+cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
+                           __nv_bfloat16* lo, long long ld_dst, cudaStream_t s) {
+  const long long total = (long long)rows * cols;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 8 * 152);
+  split_bf16_kernel<double><<<blocks, 256, 0, s>>>(src, ld_src, rows, cols, hi, lo, ld_dst);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N,
+                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s) {
+  if (nseg < 1 || nseg > 2 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  GemmMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  int neg_mask = 0;
+  for (int g = 0; g < nseg; ++g) {
+    if (A[g].rows < M || B[g].rows < N) return cudaErrorInvalidValue;
+    if (!make_map(&maps.a[g][0], A[g].hi, M, K, A[g].ld, BM) || !make_map(&maps.a[g][1], A[g].lo, M, K, A[g].ld, BM) ||
+        !make_map(&maps.b[g][0], B[g].hi, N, K, B[g].ld, BN) || !make_map(&maps.b[g][1], B[g].lo, N, K, B[g].ld, BN))
+      return cudaErrorInvalidValue;
+    if (negate && negate[g]) neg_mask |= 1 << g;
+  }
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(gemm_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  ProfScope prof("gemm_bf16x3", 0.0, 6.0 * (double)M * N * K * nseg, s);
+  gemm_bf16x3_kernel<<<grid, 128, SMEM_BYTES, s>>>(maps, nseg, neg_mask, M, N, K, D, ldd, accumulate ? 1 : 0,
+                                                    err_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace rfcmp

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/rfcmp.h"
@@ -113,6 +114,25 @@ cudaError_t launch_rhs_planewave(const DeviceGeometry& g, double k, const double
 // radiation vector N(rhat) for nrhs currents and ndir directions -> out (ndir x nrhs x 3 complex)
 cudaError_t launch_farfield(const DeviceGeometry& g, double k, const double2* j, int nrhs, const double* dirs,
                             int ndir, double2* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- tensor-core GEMM (k_gemm.cu)
+// A BF16 operand split in two planes (hi = bf16(x), lo = bf16(x - hi)), row-major with K
+// contiguous, `rows` rows, row stride `ld` elements (ld * 2 bytes a multiple of 16).
+struct SplitOperand {
+  const __nv_bfloat16* hi = nullptr;
+  const __nv_bfloat16* lo = nullptr;
+  int rows = 0;
+  long long ld = 0;
+};
+// D[M x N] = sum_g (negate[g] ? -1 : 1) A_g B_g^T (+ D), three BF16 products per K step into an
+// FP32 tensor-memory accumulator (tcgen05).  nseg 1 or 2.  err_dev receives a nonzero code if a
+// bounded device-side wait gave up.
+cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N,
+                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s);
+cudaError_t split_bf16_f32(const float* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
+                           __nv_bfloat16* lo, long long ld_dst, cudaStream_t s);
+cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
+                           __nv_bfloat16* lo, long long ld_dst, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels (k_linalg.cu)
 enum GemvMode { GEMV_F32 = 0, GEMV_FF = 1 };
