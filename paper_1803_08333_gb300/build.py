@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librfcmp.so")
-SOURCES = ["k_assembly.cu", "k_linalg.cu", "k_gemm.cu", "capi.cu", "noalloc.cu", "topology.cpp", "amg.cpp"]
+SOURCES = ["k_assembly.cu", "k_linalg.cu", "k_gemm.cu", "k_factor.cu", "capi.cu", "noalloc.cu", "topology.cpp", "amg.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

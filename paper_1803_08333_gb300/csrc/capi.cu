@@ -157,8 +157,15 @@ ProfScope::~ProfScope() {
 }  // namespace rfcmp
 
 // ---------------------------------------------------------------- factor cache
+// (Sigma^T Sigma)^+ of meshes with at least this many cells is refined by Newton-Schulz steps on
+// the tensor cores from a multigrid-PCG start accurate to NS_START_TOL.
+constexpr int NS_MIN_CELLS = 256;
+constexpr double NS_START_TOL = 1e-3;
+
 struct DenseFactor {
   int n = 0;
+  int ns_steps = 0;
+  double ns_residual = 0.0;
   float* hi = nullptr;
   float* lo = nullptr;
   size_t bytes = 0;
@@ -668,8 +675,25 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
     }
   }
   int iters = 0;
-  cudaError_t err = dense_inverse_block_cg(dptr, dcol, dval, n, project, multigrid ? &H : nullptr, tol, 20000, f->hi,
-                                           f->lo, &iters, 0);
+  cudaError_t err;
+  if (multigrid && project && n >= NS_MIN_CELLS) {
+    // multigrid PCG to a loose tolerance, then Newton-Schulz steps on the tensor cores
+    double* Xd = nullptr;
+    err = cudaMalloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
+    if (err == cudaSuccess)
+      err = dense_inverse_block_cg(dptr, dcol, dval, n, project, &H, NS_START_TOL, 20000, f->hi, f->lo, &iters, 0, Xd);
+    int steps = 0;
+    double res = 0.0;
+    if (err == cudaSuccess)
+      err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, Xd, padded_ld(n), 6, std::min(tol, 1e-12), f->hi, f->lo,
+                                         &steps, &res, 0);
+    if (Xd) cudaFree(Xd);
+    f->ns_steps = steps;
+    f->ns_residual = res;
+  } else {
+    err = dense_inverse_block_cg(dptr, dcol, dval, n, project, multigrid ? &H : nullptr, tol, 20000, f->hi, f->lo,
+                                 &iters, 0);
+  }
   cudaEventRecord(e1, 0);
   cudaEventSynchronize(e1);
   float ms = 0.f;

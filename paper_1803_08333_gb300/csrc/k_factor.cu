@@ -1,0 +1,205 @@
+// Dense (Sigma^T Sigma)^+ by Newton-Schulz refinement on the tensor cores.
+//
+// With M = Sigma^T Sigma + 1 1^T / n, the identity of Sec. 3.2 gives
+// (Sigma^T Sigma)^+ = M^{-1} - 1 1^T / n.  A multigrid-preconditioned block CG delivers
+// X0 ~ M^{-1} to a loose tolerance; then
+//     R_k = I - M X_k   (FP64, formed exactly along rows: (X M)_ij = sum_k X_ik M_kj, M sparse),
+//     X_{k+1} = X_k + X_k R_k   (dense product, split-BF16 tensor-core GEMM, FP64 update)
+// converges quadratically: the relative error e_k of X_k obeys e_{k+1} <= e_k^2 + c e_k with
+// c ~ 2^-16 the accuracy of one split product, so three steps take e_0 = 1e-3 to rounding
+// level.  X_k stays symmetric up to rounding (X (2I - M X) is symmetric when X is), and the
+// result is symmetrised once at the end before the 1 1^T / n term is removed.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rfcmp_internal.h"
+
+namespace rfcmp {
+
+namespace {
+
+// Rt[i][j] = delta_ij - (X M)[i][j] with M = L + 1 1^T / n (L symmetric CSR), written as BF16
+// hi/lo planes; rowsum[i] = sum_j X[i][j] is precomputed.  Also tracks max |Rt|.
+__global__ void ns_residual_kernel(const double* __restrict__ X, long long ldx, int n, const int32_t* __restrict__ ptr,
+                                   const int32_t* __restrict__ col, const double* __restrict__ val,
+                                   const double* __restrict__ rowsum, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo, long long ldp,
+                                   unsigned long long* __restrict__ maxbits) {
+  const int i = blockIdx.y;
+  const double* xr = X + (size_t)i * ldx;
+  const double rs = rowsum[i] / n;
+  double mx = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double a = rs;
+    for (int q = ptr[j]; q < ptr[j + 1]; ++q) a += xr[col[q]] * val[q];  // (X L)_ij, L symmetric
+    const double r = (i == j ? 1.0 : 0.0) - a;
+    const float rf = (float)r;
+    const __nv_bfloat16 h = __float2bfloat16_rn(rf);
+    hi[(size_t)i * ldp + j] = h;
+    lo[(size_t)i * ldp + j] = __float2bfloat16_rn(rf - __bfloat162float(h));
+    mx = fmax(mx, fabs(r));
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void row_sum_kernel(const double* __restrict__ X, long long ldx, int n, double* __restrict__ out) {
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s += X[(size_t)i * ldx + j];
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[i] = t;
+  }
+}
+
+__global__ void ns_update_kernel(double* __restrict__ X, long long ldx, const float* __restrict__ D, long long ldd,
+                                 int n) {
+  const long long total = (long long)n * n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    X[(size_t)i * ldx + j] += (double)D[(size_t)i * ldd + j];
+  }
+}
+
+// out = (X + X^T)/2 - 1/n, split into FP32 hi + lo planes (row stride ld)
+constexpr int TT = 32;
+__global__ void symmetrize_store_kernel(const double* __restrict__ X, long long ldx, int n, float* __restrict__ hi,
+                                        float* __restrict__ lo, long long ld) {
+  __shared__ double tile[TT][TT + 1];
+  const int bi = blockIdx.y * TT, bj = blockIdx.x * TT;
+  // load the transposed tile X[bj.., bi..]
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    const int row = bj + r, c = bi + threadIdx.x;
+    tile[r][threadIdx.x] = (row < n && c < n) ? X[(size_t)row * ldx + c] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    const int i = bi + r, j = bj + threadIdx.x;
+    if (i < n && j < n) {
+      const double v = 0.5 * (X[(size_t)i * ldx + j] + tile[threadIdx.x][r]) - 1.0 / n;
+      const float h = (float)v;
+      hi[(size_t)i * ld + j] = h;
+      lo[(size_t)i * ld + j] = (float)(v - (double)h);
+    }
+  }
+}
+
+// X <- (X + X^T) / 2 in place: block (bx, by), by <= bx, averages tile (by, bx) with the
+// transpose of tile (bx, by) and writes both
+__global__ void symmetrize_inplace_kernel(double* __restrict__ X, long long ldx, int n) {
+  __shared__ double a[TT][TT + 1], b[TT][TT + 1];
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (by > bx) return;
+  const int r0 = by * TT, c0 = bx * TT;  // tile a = X[r0.., c0..], tile b = X[c0.., r0..]
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    const int i = r0 + r, j = c0 + threadIdx.x;
+    a[r][threadIdx.x] = (i < n && j < n) ? X[(size_t)i * ldx + j] : 0.0;
+    const int i2 = c0 + r, j2 = r0 + threadIdx.x;
+    b[r][threadIdx.x] = (i2 < n && j2 < n) ? X[(size_t)i2 * ldx + j2] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    const int i = r0 + r, j = c0 + threadIdx.x;
+    const double v = 0.5 * (a[r][threadIdx.x] + b[threadIdx.x][r]);
+    if (i < n && j < n) X[(size_t)i * ldx + j] = v;
+    const int i2 = c0 + r, j2 = r0 + threadIdx.x;
+    const double w = 0.5 * (b[r][threadIdx.x] + a[threadIdx.x][r]);
+    if (i2 < n && j2 < n) X[(size_t)i2 * ldx + j2] = w;
+  }
+}
+
+}  // namespace
+
+cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col, const double* val, int n,
+                                         double* X, long long ldx, int max_steps, double tol, float* Xhi, float* Xlo,
+                                         int* steps_done, double* final_residual, cudaStream_t s) {
+  // X holds an approximation of M^{-1} = L^+ + 1 1^T / n on entry (row-major, stride ldx)
+  const long long ldp = ldx;  // plane stride (elements); ldx is a multiple of 64
+  std::vector<void*> own;
+  auto fail = [&](cudaError_t e) {
+    for (void* p : own) cudaFree(p);
+    return e;
+  };
+  cudaError_t err;
+  __nv_bfloat16 *xh, *xl, *rh, *rl;
+  float* D;
+  double* rowsum;
+  unsigned long long* maxbits;
+  int* gerr;
+  const size_t plane = (size_t)n * ldp;
+  for (__nv_bfloat16** p : {&xh, &xl, &rh, &rl}) {
+    if ((err = cudaMalloc(p, plane * sizeof(__nv_bfloat16))) != cudaSuccess) return fail(err);
+    own.push_back(*p);
+  }
+  if ((err = cudaMalloc(&D, plane * sizeof(float))) != cudaSuccess) return fail(err);
+  own.push_back(D);
+  if ((err = cudaMalloc(&rowsum, n * sizeof(double))) != cudaSuccess) return fail(err);
+  own.push_back(rowsum);
+  if ((err = cudaMalloc(&maxbits, sizeof(unsigned long long))) != cudaSuccess) return fail(err);
+  own.push_back(maxbits);
+  if ((err = cudaMalloc(&gerr, sizeof(int))) != cudaSuccess) return fail(err);
+  own.push_back(gerr);
+  if ((err = cudaMemsetAsync(gerr, 0, sizeof(int), s)) != cudaSuccess) return fail(err);
+  SplitOperand A, B;
+  A.hi = xh;
+  A.lo = xl;
+  A.rows = n;
+  A.ld = ldp;
+  B.hi = rh;
+  B.lo = rl;
+  B.rows = n;
+  B.ld = ldp;
+  double res = 1.0;
+  int k = 0;
+  const dim3 sgrid((n + TT - 1) / TT, (n + TT - 1) / TT), sblock(TT, 8);
+  // the residual below is formed along rows as I - X M, which is R^T only for symmetric X
+  symmetrize_inplace_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, n);
+  for (;; ++k) {
+    row_sum_kernel<<<n, 256, 0, s>>>(X, ldx, n, rowsum);
+    if ((err = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), s)) != cudaSuccess) return fail(err);
+    {
+      ProfScope prof("factor_ns_residual", 16.0 * (double)n * n, 0.0, s);
+      dim3 grid((n + 255) / 256 < 8 ? (n + 255) / 256 : 8, n);
+      ns_residual_kernel<<<grid, 256, 0, s>>>(X, ldx, n, ptr, col, val, rowsum, rh, rl, ldp, maxbits);
+    }
+    unsigned long long hb = 0;
+    if ((err = cudaMemcpyAsync(&hb, maxbits, sizeof(hb), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(err);
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);
+    std::memcpy(&res, &hb, sizeof(res));
+    if (!(res > tol) || k >= max_steps) break;
+    if ((err = split_bf16_f64(X, ldx, n, n, xh, xl, ldp, s)) != cudaSuccess) return fail(err);
+    // D = X R with B = R^T stored row-major (B[j][k] = R[k][j] = Rt[j][k])
+    if ((err = gemm_bf16x3(&A, &B, nullptr, 1, n, n, n, D, ldp, false, gerr, s)) != cudaSuccess) return fail(err);
+    {
+      ProfScope prof("factor_ns_update", 16.0 * (double)n * n, 0.0, s);
+      ns_update_kernel<<<8 * 152, 256, 0, s>>>(X, ldx, D, ldp, n);
+    }
+    symmetrize_inplace_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return fail(err);
+  }
+  int herr = 0;
+  if ((err = cudaMemcpyAsync(&herr, gerr, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(err);
+  {
+    dim3 grid((n + TT - 1) / TT, (n + TT - 1) / TT), block(TT, 8);
+    symmetrize_store_kernel<<<grid, block, 0, s>>>(X, ldx, n, Xhi, Xlo, ldx);
+  }
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);
+  if (herr) return fail(cudaErrorLaunchTimeout);
+  *steps_done = k;
+  *final_residual = res;
+  return fail(cudaSuccess);
+}
+
+}  // namespace rfcmp

@@ -1072,6 +1072,18 @@ __global__ void bcg_store_kernel(int n, int W, int c0, int ld, const double* __r
   }
 }
 
+// Xd[i, c0 + c] = X[i, c] - mean_c + 1/n  (an approximation of (L + 1 1^T / n)^{-1}, FP64)
+__global__ void bcg_store_f64_kernel(int n, int W, int c0, long long ld, const double* __restrict__ X,
+                                     const double* __restrict__ sums, double* __restrict__ Xd) {
+  RowIter it(n);
+  for (int k = 0; k < 2; ++k) {
+    const int cc = it.c + k;
+    if (c0 + cc >= n) continue;
+    const double shift = 1.0 / n - sums[cc] / n;
+    for (int i = it.r0; i < it.r1; i += BCG_RLANES) Xd[(size_t)i * ld + c0 + cc] = X[(size_t)i * W + cc] + shift;
+  }
+}
+
 struct DevLevel {
   int n = 0, nc = 0;
   double omega = 0.0;
@@ -1097,7 +1109,7 @@ inline dim3 bgrid(int n, int w) { return dim3((w + BCG_COLS - 1) / BCG_COLS, (n 
 
 cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const double* val, int n, bool project,
                                    const AmgHierarchy* H, double tol, int max_iter, float* Xhi, float* Xlo,
-                                   int* iters, cudaStream_t s) {
+                                   int* iters, cudaStream_t s, double* Xd) {
   const int ld = padded_ld(n);
   std::vector<void*> own;
   cudaError_t err = cudaSuccess;
@@ -1273,7 +1285,10 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
       if ((err = cudaMemsetAsync(sums, 0, sizeof(double) * W, s)) != cudaSuccess) return fail(err);
       bcg_colsum_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, X, sums);
     }
-    bcg_store_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, X, sums, project, Xhi, Xlo);
+    if (Xd && project)
+      bcg_store_f64_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, X, sums, Xd);
+    else
+      bcg_store_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, X, sums, project, Xhi, Xlo);
     if ((err = cudaGetLastError()) != cudaSuccess) return fail(err);
   }
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);

@@ -222,8 +222,15 @@ int build_amg(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col, 
 // by block CG, preconditioned by one multigrid V(1,1) cycle when H is given.  A in CSR (device,
 // n x n, FP64); output in FP32 hi + lo planes (n rows, padded_ld(n) stride).  Work buffers are
 // allocated inside.  *iters receives the iteration count of the slowest column block.
+// With Xd (and project), the result goes to Xd (FP64, n rows, padded_ld(n) stride) as
+// X - colmean + 1/n, an approximation of (L + 1 1^T / n)^{-1}, instead of the FP32 planes.
 cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const double* val, int n, bool project,
                                    const AmgHierarchy* H, double tol, int max_iter, float* Xhi, float* Xlo,
-                                   int* iters, cudaStream_t s);
+                                   int* iters, cudaStream_t s, double* Xd = nullptr);
+// Newton-Schulz refinement of X ~ (L + 1 1^T / n)^{-1} (k_factor.cu); writes
+// (Sigma^T Sigma)^+ = sym(X) - 1 1^T / n to the FP32 hi + lo planes.
+cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col, const double* val, int n,
+                                         double* X, long long ldx, int max_steps, double tol, float* Xhi, float* Xlo,
+                                         int* steps_done, double* final_residual, cudaStream_t s);
 
 }  // namespace rfcmp
