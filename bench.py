@@ -132,9 +132,13 @@ def run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, copy_back=False):
 
     ctx.clear_cache()  # the topology factors are rebuilt once per step
     h2d = d2h = 0
+    prev = None
     for ka in KA:
         t0 = time.perf_counter()
-        op = rf.Operator(ctx, mesh.verts, mesh.tris, ka)
+        # alpha, beta, gamma power iterations start from the previous wavenumber's iterates
+        op = rf.Operator(ctx, mesh.verts, mesh.tris, ka, scaling_start=prev)
+        if prev is not None:
+            prev.close()
         e = op.rhs_planewave(kh, pol)
         j, rep = op.solve(e, tol=TOL)
         rcs = op.farfield(j, dirs)
@@ -147,7 +151,9 @@ def run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, copy_back=False):
         torch.cuda.synchronize()
         lat.append((time.perf_counter() - t0) * 1e3)
         reports.append((ka, rep[0], op.info()))
-        op.close()
+        prev = op
+    if prev is not None:
+        prev.close()
     return h2d, d2h
 
 

@@ -105,6 +105,9 @@ typedef struct {
   double power_rtol;    /* power iteration stops once the Rayleigh quotient changes by at most
                            power_rtol (relative) between two steps, after at least 2 and at most
                            power_steps steps; 0 = always power_steps; default 1e-3 */
+  const rfcmp_op* scaling_start; /* NULL, or an op on the same mesh: the power iterations start
+                           from its final iterates instead of the splitmix64 vectors (a
+                           frequency sweep converges in a few steps); default NULL */
   int32_t reserved[8];  /* must be zero */
 } rfcmp_op_opts;
 

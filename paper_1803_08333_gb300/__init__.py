@@ -41,7 +41,8 @@ class OpOpts(ctypes.Structure):
     _fields_ = [
         ("scaling", ctypes.c_int32), ("power_steps", ctypes.c_int32),
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
-        ("factor_tol", ctypes.c_double), ("power_rtol", ctypes.c_double), ("reserved", ctypes.c_int32 * 8),
+        ("factor_tol", ctypes.c_double), ("power_rtol", ctypes.c_double), ("scaling_start", ctypes.c_void_p),
+        ("reserved", ctypes.c_int32 * 8),
     ]
 
 
@@ -213,7 +214,7 @@ class Operator:
 
     def __init__(self, ctx: Context, verts, tris, k: float, scaling: str = "power", power_steps: int = 30,
                  alpha: float = 1.0, beta: float = 1.0, gamma: float = 1.0, factor_tol: float = 1e-13,
-                 power_rtol: float = 1e-3):
+                 power_rtol: float = 1e-3, scaling_start: "Operator | None" = None):
         self.ctx = ctx
         self.verts = np.ascontiguousarray(verts, dtype=np.float64)
         self.tris = np.ascontiguousarray(tris, dtype=np.int32)
@@ -224,6 +225,8 @@ class Operator:
         o.alpha, o.beta, o.gamma = float(alpha), float(beta), float(gamma)
         o.factor_tol = float(factor_tol)
         o.power_rtol = float(power_rtol)
+        if scaling_start is not None:
+            o.scaling_start = scaling_start._h
         self._h = ctypes.c_void_p()
         _check(
             lib().rfcmp_op_create(

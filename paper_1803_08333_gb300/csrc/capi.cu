@@ -160,12 +160,17 @@ ProfScope::~ProfScope() {
 // (Sigma^T Sigma)^+ of meshes with at least this many cells is refined by Newton-Schulz steps on
 // the tensor cores from a multigrid-PCG start accurate to NS_START_TOL.
 constexpr int NS_MIN_CELLS = 256;
-constexpr double NS_START_TOL = 1e-3;
+// Products with at least this many right-hand sides in the FP32 inner iterations run on the tensor
+// cores (split-BF16 GEMM) instead of the HBM-bound GEMV.
+constexpr int MRHS_MIN = 16;
+constexpr double NS_START_TOL = 1e-2;
 
 struct DenseFactor {
   int n = 0;
   int ns_steps = 0;
   double ns_residual = 0.0;
+  RealPlanes planes;  // BF16 hi/lo of the FP32 hi plane, built on the first multi-RHS product
+  std::mutex planes_mu;
   float* hi = nullptr;
   float* lo = nullptr;
   size_t bytes = 0;
@@ -174,6 +179,8 @@ struct DenseFactor {
   ~DenseFactor() {
     if (hi) cudaFree(hi);
     if (lo) cudaFree(lo);
+    if (planes.h) cudaFree(planes.h);
+    if (planes.l) cudaFree(planes.l);
   }
 };
 
@@ -199,6 +206,7 @@ struct Workspace {
   double2 *t = nullptr, *tg = nullptr;
   double* mean = nullptr;  // 4 x cols
   GemvScratch gs;
+  MrhsScratch ms;
   ~Workspace() {
     for (void* p : owned) cudaFree(p);
   }
@@ -232,6 +240,8 @@ struct rfcmp_op {
   rfcmp_op_info info{};
   std::unique_ptr<Workspace> ws;
   std::unique_ptr<SolveBuffers> sb;
+  double2* power_vecs = nullptr;  // N x 3: final iterates of the X, Z and Y power iterations
+  CplxPlanes ta_planes, v_planes;  // BF16 planes of T_A and V, built on the first multi-RHS product
   ~rfcmp_op() {
     for (void* p : owned) cudaFree(p);
   }
@@ -264,6 +274,15 @@ int ensure_workspace(rfcmp_op* op, int cols) {
     RF_TRY(dalloc(&ws->gs.xh, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.xl, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.acc, (size_t)capn * 4, ws->owned));
+    if (cols >= MRHS_MIN) {
+      ws->ms.cap_cols = cols;
+      ws->ms.cap_n = capn;
+      ws->ms.cap_ld = padded_ld(capn);
+      RF_TRY(dalloc(&ws->ms.xb, (size_t)4 * cols * ws->ms.cap_ld, ws->owned));
+      RF_TRY(dalloc(&ws->ms.D, (size_t)2 * cols * capn, ws->owned));
+      RF_TRY(dalloc(&ws->ms.err, 1, ws->owned));
+      RF_CUDA(cudaMemset(ws->ms.err, 0, sizeof(int)));
+    }
   }
   op->ws = std::move(ws);
   return RFCMP_OK;
@@ -285,17 +304,84 @@ int ensure_solve_buffers(rfcmp_op* op, int cols) {
   return RFCMP_OK;
 }
 
+int ensure_planes(rfcmp_op* op, cudaStream_t st);
+
 #define RF_K(call)                                                                                      \
   do {                                                                                                  \
     cudaError_t e_ = (call);                                                                            \
     if (e_ != cudaSuccess) return set_error(RFCMP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+int make_cplx_planes(rfcmp_op* op, const float2* M, int n, int ld, CplxPlanes& P, cudaStream_t st) {
+  if (P.rh) return RFCMP_OK;
+  CplxPlanes q;
+  q.n = n;
+  q.ldp = ld;
+  const size_t pl = (size_t)n * ld;
+  for (__nv_bfloat16** p : {&q.rh, &q.rl, &q.ih, &q.il}) RF_TRY(dalloc(p, pl, op->owned));
+  RF_K(split_c64_planes(M, n, ld, q, st));
+  op->bytes += 4 * pl * sizeof(__nv_bfloat16);
+  op->ctx->bytes += 4 * pl * sizeof(__nv_bfloat16);
+  P = q;
+  return RFCMP_OK;
+}
+
+int make_real_planes(rfcmp_op* op, DenseFactor& f, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(f.planes_mu);
+  if (f.planes.h) return RFCMP_OK;
+  RealPlanes q;
+  q.n = f.n;
+  q.ldp = padded_ld(f.n);
+  const size_t pl = (size_t)f.n * q.ldp;
+  RF_CUDA(cudaMalloc(&q.h, pl * sizeof(__nv_bfloat16)));
+  RF_CUDA(cudaMalloc(&q.l, pl * sizeof(__nv_bfloat16)));
+  RF_CUDA(cudaMemsetAsync(q.h, 0, pl * sizeof(__nv_bfloat16), st));
+  RF_CUDA(cudaMemsetAsync(q.l, 0, pl * sizeof(__nv_bfloat16), st));
+  RF_K(split_bf16_f32(f.hi, q.ldp, f.n, f.n, q.h, q.l, q.ldp, st));
+  f.bytes += 2 * pl * sizeof(__nv_bfloat16);
+  op->ctx->bytes += 2 * pl * sizeof(__nv_bfloat16);
+  f.planes = q;
+  return RFCMP_OK;
+}
+
+int ensure_planes(rfcmp_op* op, cudaStream_t st) {
+  RF_TRY(make_cplx_planes(op, op->TA, (int)op->top.ne, op->ldN, op->ta_planes, st));
+  RF_TRY(make_cplx_planes(op, op->V, (int)op->top.nc, op->ldC, op->v_planes, st));
+  RF_TRY(make_real_planes(op, *op->lplus, st));
+  RF_TRY(make_real_planes(op, *op->gll, st));
+  return RFCMP_OK;
+}
+
+// y = scale * op(M) x (+ y) for M = T_A or V: GEMV, or the tensor-core product for wide FP32 blocks
+int prod_c(rfcmp_op* op, bool ta, const double2* x, double2* y, int nr, bool conj, double2 scale, bool acc,
+           GemvMode m, cudaStream_t st) {
+  if (m == GEMV_F32 && nr >= MRHS_MIN) {
+    RF_TRY(ensure_planes(op, st));
+    RF_K(cplx_gemm(ta ? op->ta_planes : op->v_planes, x, y, nr, conj, scale, acc, op->ws->ms, st));
+    return RFCMP_OK;
+  }
+  RF_K(gemv_c64(ta ? op->TA : op->V, ta ? (int)op->top.ne : (int)op->top.nc, x, y, nr, conj, scale, acc, m,
+                op->ws->gs, st));
+  return RFCMP_OK;
+}
+
+// y = scale * F x (+ y) for a dense real factor
+int prod_r(rfcmp_op* op, DenseFactor& f, const double2* x, double2* y, int nr, double scale, bool acc, GemvMode m,
+           cudaStream_t st) {
+  if (m == GEMV_F32 && nr >= MRHS_MIN) {
+    RF_TRY(ensure_planes(op, st));
+    RF_K(real_gemm(f.planes, x, y, nr, scale, acc, op->ws->ms, st));
+    return RFCMP_OK;
+  }
+  RF_K(gemv_r32(f.hi, f.lo, f.n, x, y, nr, scale, acc, m, op->ws->gs, st));
+  return RFCMP_OK;
+}
+
 // ---- building blocks of the application, nrhs columns, column-major ----
 // z = (Sigma^T Sigma)^+ Sigma^T x  (N_C) using s as scratch for Sigma^T x
 int star_coeff(rfcmp_op* op, const double2* x, double2* s, double2* z, int nr, GemvMode m, cudaStream_t st) {
   RF_K(sigma_t(op->g, x, s, nr, st));
-  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, (int)op->top.nc, s, z, nr, 1.0, false, m, op->ws->gs, st));
+  RF_TRY(prod_r(op, *op->lplus, s, z, nr, 1.0, false, m, st));
   return RFCMP_OK;
 }
 
@@ -319,15 +405,15 @@ int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cu
     RF_K(edge_combo(g, c, W.v, nr, st));
   }
   // u = T_A v ; w = V Sigma^T x / (k b)
-  RF_K(gemv_c64(op->TA, N, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, op->ws->gs, st));
-  RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, op->ws->gs, st));
+  RF_TRY(prod_c(op, true, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, st));
+  RF_TRY(prod_c(op, false, W.s, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, st));
   // zu = L^+ Sigma^T u ; tg = G_ll^{-1} Lambda^T u
   RF_TRY(star_coeff(op, W.u, W.s, W.zu, nr, m, st));
   RF_K(lambda_t(g, W.u, W.t, nr, st));
-  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, op->ws->gs, st));
+  RF_TRY(prod_r(op, *op->gll, W.t, W.tg, nr, 1.0, false, m, st));
   // q = L^+ G_pp^{-1} (zu + w - mean(w)) / b^2
   RF_K(star_middle(g, W.zu, W.w, 1.0, W.q0, nr, W.mean, st));
-  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, op->ws->gs, st));
+  RF_TRY(prod_r(op, *op->lplus, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
   // y = Lambda tg / a^2 + (u - Sigma zu) / gamma + Sigma q
   {
     EdgeCombo c;
@@ -342,9 +428,9 @@ int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cu
     RF_K(edge_combo(g, c, W.y, nr, st));
   }
   // up = conj(T_A) y ; vp = conj(V) (Sigma^T Sigma) q / (k b)
-  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, op->ws->gs, st));
+  RF_TRY(prod_c(op, true, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
   RF_K(lap_apply(g, W.q, W.Lq, nr, st));
-  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, op->ws->gs, st));
+  RF_TRY(prod_c(op, false, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, st));
   // zp = L^+ Sigma^T up
   RF_TRY(star_coeff(op, W.up, W.s, W.z, nr, m, st));
   // out = -(ik/a) up + (ik/a - k/b) Sigma zp + Sigma vp
@@ -500,15 +586,19 @@ void splitmix_start(std::vector<double2>& h, int64_t n, uint64_t seed) {
 // (relative) between steps (after at least 2 steps; rtol = 0: always `steps`).
 template <class Op>
 int power_norms(rfcmp_op* op, Op apply, int cols, const uint64_t* seeds, int steps, double rtol, double* lam,
-                cudaStream_t st) {
+                const double2* start, double2* keep, cudaStream_t st) {
   const int64_t N = op->top.ne;
   RF_TRY(ensure_solve_buffers(op, cols));
   RF_TRY(ensure_workspace(op, cols));
   SolveBuffers& B = *op->sb;
-  std::vector<double2> h;
-  for (int c = 0; c < cols; ++c) {
-    splitmix_start(h, N, seeds[c]);
-    RF_CUDA(cudaMemcpyAsync(B.p + c * N, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, st));
+  if (start) {
+    RF_CUDA(cudaMemcpyAsync(B.p, start, sizeof(double2) * N * cols, cudaMemcpyDeviceToDevice, st));
+  } else {
+    std::vector<double2> h;
+    for (int c = 0; c < cols; ++c) {
+      splitmix_start(h, N, seeds[c]);
+      RF_CUDA(cudaMemcpyAsync(B.p + c * N, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, st));
+    }
   }
   std::vector<double2> d1(cols), d2(cols);
   std::vector<double> coef(cols), prev(cols, 0.0);
@@ -541,6 +631,7 @@ int power_norms(rfcmp_op* op, Op apply, int cols, const uint64_t* seeds, int ste
     RF_CUDA(cudaMemcpyAsync(B.alpha, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
     RF_K(vec_copy_scale_cols(B.Ap, B.alpha, B.p, N, cols, st));
   }
+  if (keep) RF_CUDA(cudaMemcpyAsync(keep, B.p, sizeof(double2) * N * cols, cudaMemcpyDeviceToDevice, st));
   return RFCMP_OK;
 }
 
@@ -560,8 +651,17 @@ int compute_scaling(rfcmp_op* op, const rfcmp_op_opts& o, cudaStream_t st) {
   }
   double lxz[2] = {0, 0}, ly = 0;
   const uint64_t sxz[2] = {1, 3}, sy = 2;
-  RF_TRY(power_norms(op, op_XZ, 2, sxz, o.power_steps, o.power_rtol, lxz, st));
-  RF_TRY(power_norms(op, op_Y, 1, &sy, o.power_steps, o.power_rtol, &ly, st));
+  const int64_t N = op->top.ne;
+  if (!op->power_vecs) {
+    RF_CUDA(cudaMalloc(&op->power_vecs, sizeof(double2) * N * 3));
+    op->owned.push_back(op->power_vecs);
+  }
+  const rfcmp_op* from = o.scaling_start;
+  const bool warm = from && from->power_vecs && from->top.ne == N && from->top.hash == op->top.hash;
+  RF_TRY(power_norms(op, op_XZ, 2, sxz, o.power_steps, o.power_rtol, lxz, warm ? from->power_vecs : nullptr,
+                     op->power_vecs, st));
+  RF_TRY(power_norms(op, op_Y, 1, &sy, o.power_steps, o.power_rtol, &ly, warm ? from->power_vecs + 2 * N : nullptr,
+                     op->power_vecs + 2 * N, st));
   const double nx = lxz[0], nz = lxz[1], ny = ly;
   // alpha^4 = k^2 ||X||, beta^4 = ||Y|| / k^2, gamma = k^2 ||Z|| / alpha^2 (frequency-scaled reading)
   op->alpha = std::pow(k * k * nx, 0.25);
@@ -785,6 +885,7 @@ void rfcmp_op_opts_default(rfcmp_op_opts* o) {
   o->alpha = o->beta = o->gamma = 1.0;
   o->factor_tol = 1e-13;
   o->power_rtol = 1e-3;
+  o->scaling_start = nullptr;
 }
 
 void rfcmp_solve_opts_default(rfcmp_solve_opts* o) {
@@ -1256,6 +1357,15 @@ int solve_impl(rfcmp_op* op, const double2* e, double2* j, int nr, const rfcmp_s
   // j = P_o i
   RF_TRY(apply_Po(op, B.i, j, nr, false, GEMV_FF, st));
   RF_CUDA(cudaStreamSynchronize(st));
+  if (op->ws->ms.err) {
+    int h_err = 0;
+    RF_CUDA(cudaMemcpy(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_err) {
+      RF_CUDA(cudaMemset(op->ws->ms.err, 0, sizeof(int)));
+      return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a tensor-core product gave up a bounded wait (code " +
+                                                     std::to_string(h_err) + ")");
+    }
+  }
   bool all = true;
   for (int c = 0; c < nr; ++c) {
     if (rep) {

@@ -28,12 +28,19 @@ namespace rfcmp {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
-constexpr int TILE_A = BM * BK * 2;                 // 16 KiB per BF16 plane
-constexpr int TILE_B = BN * BK * 2;                 // 16 KiB
-constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // 64 KiB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr long long WAIT_CYCLES = 4000000000LL;     // about 2 s at the GB300 clock
+constexpr int BM = 128, BK = 64;
+constexpr int TILE_A = BM * BK * 2;  // 16 KiB per BF16 plane
+constexpr long long WAIT_CYCLES = 4000000000LL;  // about 2 s at the GB300 clock
+
+// N tile (output columns per CTA) and ring depth: narrow tiles for narrow right-hand-side blocks
+template <int BN>
+struct TileCfg {
+  static constexpr int STAGES = BN >= 128 ? 3 : (BN >= 64 ? 4 : 5);
+  static constexpr int TILE_B = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
 
 struct GemmMaps {
   CUtensorMap a[2][2];  // [segment][hi, lo]
@@ -122,9 +129,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
 gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask, int M, int N, int K,
                    float* __restrict__ D, long long ldd, int accumulate, int* __restrict__ err) {
+  using C = TileCfg<BN>;
+  constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, TILE_B = C::TILE_B;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -146,7 +156,7 @@ gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -228,7 +238,7 @@ gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
 // FP32 (or FP64) -> BF16 hi/lo planes
@@ -273,7 +283,150 @@ bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k, long
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int BN>
+cudaError_t gemm_launch(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N, int K,
+                        float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s) {
+  using C = TileCfg<BN>;
+  GemmMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  int neg_mask = 0;
+  for (int g = 0; g < nseg; ++g) {
+    if (A[g].rows < M || B[g].rows < N) return cudaErrorInvalidValue;
+    if (!make_map(&maps.a[g][0], A[g].hi, M, K, A[g].ld, BM) || !make_map(&maps.a[g][1], A[g].lo, M, K, A[g].ld, BM) ||
+        !make_map(&maps.b[g][0], B[g].hi, N, K, B[g].ld, BN) || !make_map(&maps.b[g][1], B[g].lo, N, K, B[g].ld, BN))
+      return cudaErrorInvalidValue;
+    if (negate && negate[g]) neg_mask |= 1 << g;
+  }
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err =
+        cudaFuncSetAttribute(gemm_bf16x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  ProfScope prof("gemm_bf16x3", 0.0, 6.0 * (double)M * N * K * nseg, s);
+  gemm_bf16x3_kernel<BN><<<grid, 128, C::SMEM_BYTES, s>>>(maps, nseg, neg_mask, M, N, K, D, ldd, accumulate ? 1 : 0,
+                                                          err_dev);
+  return cudaGetLastError();
+}
+
+// complex64 matrix (row stride ld) -> BF16 planes Re hi/lo, Im hi/lo (row stride ldp)
+__global__ void split_c64_kernel(const float2* __restrict__ M, int n, long long ld, __nv_bfloat16* __restrict__ rh,
+                                 __nv_bfloat16* __restrict__ rl, __nv_bfloat16* __restrict__ ih,
+                                 __nv_bfloat16* __restrict__ il, long long ldp) {
+  const long long total = (long long)n * n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / n), c = (int)(idx % n);
+    const float2 v = M[(size_t)r * ld + c];
+    const __nv_bfloat16 a = __float2bfloat16_rn(v.x), b = __float2bfloat16_rn(v.y);
+    const size_t o = (size_t)r * ldp + c;
+    rh[o] = a;
+    rl[o] = __float2bfloat16_rn(v.x - __bfloat162float(a));
+    ih[o] = b;
+    il[o] = __float2bfloat16_rn(v.y - __bfloat162float(b));
+  }
+}
+
+// X (complex128, column-major n x nr) -> BF16 planes of Re X^T and Im X^T (nr x ldp each, hi and lo);
+// with stacked, Re and Im share one operand of 2 nr rows (rows nr.. hold Im).
+__global__ void split_x_kernel(const double2* __restrict__ X, int n, int nr, long long ldp, bool stacked,
+                               __nv_bfloat16* __restrict__ rh, __nv_bfloat16* __restrict__ rl,
+                               __nv_bfloat16* __restrict__ ih, __nv_bfloat16* __restrict__ il) {
+  const int r = blockIdx.y;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < ldp; k += (long long)gridDim.x * blockDim.x) {
+    const double2 v = k < n ? X[(size_t)r * n + k] : make_double2(0.0, 0.0);
+    const float re = (float)v.x, im = (float)v.y;
+    const __nv_bfloat16 a = __float2bfloat16_rn(re), b = __float2bfloat16_rn(im);
+    const size_t orow = (size_t)r * ldp + k;
+    const size_t irow = stacked ? (size_t)(nr + r) * ldp + k : orow;
+    rh[orow] = a;
+    rl[orow] = __float2bfloat16_rn(re - __bfloat162float(a));
+    ih[irow] = b;
+    il[irow] = __float2bfloat16_rn(im - __bfloat162float(b));
+  }
+}
+
+// Y[:, r] = scale * (Dr[:, r] + i Di[:, r]) (+ Y); D row-major n x ldd with the real parts in column r and
+// the imaginary parts in column r (Di) or column nr + r (stacked, Di == Dr)
+__global__ void combine_kernel(const float* __restrict__ Dr, const float* __restrict__ Di, long long ldd, int n,
+                               int nr, int im_off, double2 scale, int accumulate, double2* __restrict__ Y) {
+  const int r = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = Dr[(size_t)i * ldd + r], b = Di[(size_t)i * ldd + im_off + r];
+    double2 o = make_double2(scale.x * a - scale.y * b, scale.x * b + scale.y * a);
+    if (accumulate) {
+      const double2 p = Y[(size_t)r * n + i];
+      o.x += p.x;
+      o.y += p.y;
+    }
+    Y[(size_t)r * n + i] = o;
+  }
+}
+
 }  // namespace
+
+cudaError_t split_c64_planes(const float2* M, int n, long long ld, const CplxPlanes& P, cudaStream_t s) {
+  const long long total = (long long)n * n;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 8 * 152);
+  split_c64_kernel<<<blocks, 256, 0, s>>>(M, n, ld, P.rh, P.rl, P.ih, P.il, P.ldp);
+  return cudaGetLastError();
+}
+
+cudaError_t cplx_gemm(const CplxPlanes& T, const double2* X, double2* Y, int nr, bool conj, double2 scale,
+                      bool accumulate, MrhsScratch& w, cudaStream_t s) {
+  const int n = T.n;
+  const long long ldp = T.ldp;
+  if (nr > w.cap_cols || ldp > w.cap_ld || n > w.cap_n) return cudaErrorInvalidValue;
+  __nv_bfloat16* xb = w.xb;
+  const size_t pl = (size_t)nr * ldp;
+  __nv_bfloat16 *xrh = xb, *xrl = xb + pl, *xih = xb + 2 * pl, *xil = xb + 3 * pl;
+  dim3 g1((unsigned)std::min<long long>((ldp + 255) / 256, 64), nr);
+  split_x_kernel<<<g1, 256, 0, s>>>(X, n, nr, ldp, false, xrh, xrl, xih, xil);
+  SplitOperand Tr, Ti, XR, XI;
+  Tr.hi = T.rh; Tr.lo = T.rl; Tr.rows = n; Tr.ld = ldp;
+  Ti.hi = T.ih; Ti.lo = T.il; Ti.rows = n; Ti.ld = ldp;
+  XR.hi = xrh; XR.lo = xrl; XR.rows = nr; XR.ld = ldp;
+  XI.hi = xih; XI.lo = xil; XI.rows = nr; XI.ld = ldp;
+  float* Dr = w.D;
+  float* Di = w.D + (size_t)n * nr;
+  cudaError_t e;
+  // Re Y = Tr Xr -/+ Ti Xi      Im Y = Tr Xi +/- Ti Xr      (lower signs for conj(T))
+  {
+    SplitOperand A[2] = {Tr, Ti}, B[2] = {XR, XI};
+    int neg[2] = {0, conj ? 0 : 1};
+    if ((e = gemm_bf16x3(A, B, neg, 2, n, nr, n, Dr, nr, false, w.err, s)) != cudaSuccess) return e;
+  }
+  {
+    SplitOperand A[2] = {Tr, Ti}, B[2] = {XI, XR};
+    int neg[2] = {0, conj ? 1 : 0};
+    if ((e = gemm_bf16x3(A, B, neg, 2, n, nr, n, Di, nr, false, w.err, s)) != cudaSuccess) return e;
+  }
+  dim3 g2((unsigned)std::min((n + 255) / 256, 64), nr);
+  combine_kernel<<<g2, 256, 0, s>>>(Dr, Di, nr, n, nr, 0, scale, accumulate ? 1 : 0, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t real_gemm(const RealPlanes& P, const double2* X, double2* Y, int nr, double scale, bool accumulate,
+                      MrhsScratch& w, cudaStream_t s) {
+  const int n = P.n;
+  const long long ldp = P.ldp;
+  if (2 * nr > 2 * w.cap_cols || ldp > w.cap_ld || n > w.cap_n) return cudaErrorInvalidValue;
+  __nv_bfloat16* xb = w.xb;
+  const size_t pl = (size_t)2 * nr * ldp;  // stacked Re / Im rows
+  __nv_bfloat16 *bh = xb, *bl = xb + pl;
+  dim3 g1((unsigned)std::min<long long>((ldp + 255) / 256, 64), nr);
+  split_x_kernel<<<g1, 256, 0, s>>>(X, n, nr, ldp, true, bh, bl, bh, bl);
+  SplitOperand A, B;
+  A.hi = P.h; A.lo = P.l; A.rows = n; A.ld = ldp;
+  B.hi = bh; B.lo = bl; B.rows = 2 * nr; B.ld = ldp;
+  cudaError_t e;
+  if ((e = gemm_bf16x3(&A, &B, nullptr, 1, n, 2 * nr, n, w.D, 2 * nr, false, w.err, s)) != cudaSuccess) return e;
+  dim3 g2((unsigned)std::min((n + 255) / 256, 64), nr);
+  combine_kernel<<<g2, 256, 0, s>>>(w.D, w.D, 2 * nr, n, nr, nr, make_double2(scale, 0.0), accumulate ? 1 : 0, Y);
+  return cudaGetLastError();
+}
 
 cudaError_t split_bf16_f32(const float* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
                            __nv_bfloat16* lo, long long ld_dst, cudaStream_t s) {
@@ -294,27 +447,9 @@ cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int co
 cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N,
                         int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s) {
   if (nseg < 1 || nseg > 2 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
-  GemmMaps maps;
-  std::memset(&maps, 0, sizeof(maps));
-  int neg_mask = 0;
-  for (int g = 0; g < nseg; ++g) {
-    if (A[g].rows < M || B[g].rows < N) return cudaErrorInvalidValue;
-    if (!make_map(&maps.a[g][0], A[g].hi, M, K, A[g].ld, BM) || !make_map(&maps.a[g][1], A[g].lo, M, K, A[g].ld, BM) ||
-        !make_map(&maps.b[g][0], B[g].hi, N, K, B[g].ld, BN) || !make_map(&maps.b[g][1], B[g].lo, N, K, B[g].ld, BN))
-      return cudaErrorInvalidValue;
-    if (negate && negate[g]) neg_mask |= 1 << g;
-  }
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(gemm_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  ProfScope prof("gemm_bf16x3", 0.0, 6.0 * (double)M * N * K * nseg, s);
-  gemm_bf16x3_kernel<<<grid, 128, SMEM_BYTES, s>>>(maps, nseg, neg_mask, M, N, K, D, ldd, accumulate ? 1 : 0,
-                                                    err_dev);
-  return cudaGetLastError();
+  if (N <= 32) return gemm_launch<32>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+  if (N <= 64) return gemm_launch<64>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+  return gemm_launch<128>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
 }
 
 }  // namespace rfcmp

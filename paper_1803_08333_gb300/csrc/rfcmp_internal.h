@@ -131,6 +131,34 @@ cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int*
                         int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s);
 cudaError_t split_bf16_f32(const float* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
                            __nv_bfloat16* lo, long long ld_dst, cudaStream_t s);
+
+// BF16 planes of the resident blocks for the multi-right-hand-side products.
+struct CplxPlanes {  // complex n x n: Re hi/lo, Im hi/lo, row stride ldp
+  __nv_bfloat16 *rh = nullptr, *rl = nullptr, *ih = nullptr, *il = nullptr;
+  int n = 0;
+  long long ldp = 0;
+};
+struct RealPlanes {  // real n x n: hi/lo, row stride ldp
+  __nv_bfloat16 *h = nullptr, *l = nullptr;
+  int n = 0;
+  long long ldp = 0;
+};
+// Scratch of the multi-RHS products: BF16 planes of X (4 x cap_cols x cap_ld) and the FP32
+// products (2 x cap_n x cap_cols); err receives device-side timeout codes.
+struct MrhsScratch {
+  __nv_bfloat16* xb = nullptr;
+  float* D = nullptr;
+  int* err = nullptr;
+  int cap_cols = 0, cap_n = 0;
+  long long cap_ld = 0;
+};
+cudaError_t split_c64_planes(const float2* M, int n, long long ld, const CplxPlanes& P, cudaStream_t s);
+// Y = scale * op(T) X (+ Y) with op = conj if conj; X, Y complex128 column-major n x nr.
+cudaError_t cplx_gemm(const CplxPlanes& T, const double2* X, double2* Y, int nr, bool conj, double2 scale,
+                      bool accumulate, MrhsScratch& w, cudaStream_t s);
+// Y = scale * P X (+ Y) with a real P.
+cudaError_t real_gemm(const RealPlanes& P, const double2* X, double2* Y, int nr, double scale, bool accumulate,
+                      MrhsScratch& w, cudaStream_t s);
 cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
                            __nv_bfloat16* lo, long long ld_dst, cudaStream_t s);
 

@@ -50,7 +50,7 @@ def test_status_strings_and_defaults(libpath):
 
 def test_struct_layouts_match_header(libpath):
     # sizes implied by include/rfcmp.h on LP64
-    assert ctypes.sizeof(rf.OpOpts) == 4 + 4 + 8 * 5 + 4 * 8
+    assert ctypes.sizeof(rf.OpOpts) == 4 + 4 + 8 * 5 + 8 + 4 * 8
     assert ctypes.sizeof(rf.SolveOpts) == 8 + 4 + 4 + 8 + 4 + 4 + 4 * 8
     assert ctypes.sizeof(rf.SolveReport) == 4 * 4 + 8
     assert ctypes.sizeof(rf.OpInfo) == 3 * 8 + 2 * 4 + 4 * 8 + 8 + 3 * 8 + 2 * 4

@@ -231,3 +231,45 @@ def test_error_codes(ctx):
     with pytest.raises(rf.RfcmpError) as ei:
         rf.Operator(small, m.verts, m.tris, 1.0)
     assert ei.value.status == -4
+
+
+def test_scaling_warm_start_across_a_sweep(ctx, memo):
+    """alpha, beta, gamma started from the previous wavenumber's iterates match a cold start."""
+    m, D, TA, V = _oracle(memo, "l2", 1e-3)
+    cold = rf.Operator(ctx, m.verts, m.tris, 1e-3)
+    prev = rf.Operator(ctx, m.verts, m.tris, 1e-2)
+    warm = rf.Operator(ctx, m.verts, m.tris, 1e-3, scaling_start=prev)
+    for a, b in zip(warm.scaling, cold.scaling):
+        assert abs(a / b - 1) < 0.02
+    F = memo(("gfac", "l2"), lambda: rfcmp.factors(D))
+    ref = rfcmp.power_scaling(F, TA, V, 1e-3, exact=True)
+    for a, b in zip(warm.scaling, (ref.alpha, ref.beta, ref.gamma)):
+        assert abs(a / b - 1) < 0.05
+    e = warm.rhs_planewave(*synth.plane_wave_z())
+    j, rep = warm.solve(e, tol=1e-10)
+    jc, _ = cold.solve(e, tol=1e-10)
+    assert rep[0].converged and _rel(j.cpu().numpy(), jc.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("name,k", [("l3", 1.0), ("l2", 1e-4)])
+def test_multi_rhs_tensor_core_path(ctx, memo, name, k):
+    """20 right-hand sides: the inner products run on the split-BF16 tensor-core GEMM."""
+    m, D, TA, V = _oracle(memo, name, k)
+    F = memo(("gfac", name), lambda: rfcmp.factors(D))
+    kh, pol = synth.random_plane_waves(20, seed=21)
+    e_ref = efie.excitation(D, k, kh, pol)
+    if k >= 1e-2:
+        j_ref = krylov.lu_solve(efie.efie_matrix(D, TA, V, k), -e_ref).T
+    else:
+        sc = rfcmp.power_scaling(F, TA, V, k)
+        j_ref = np.stack([rfcmp.solve(F, TA, V, k, sc, e_ref[:, c], 1e-13)[0] for c in range(20)])
+    op = rf.Operator(ctx, m.verts, m.tris, k)
+    e = op.rhs_planewave(kh, pol)
+    j, rep = op.solve(e, tol=1e-10)
+    assert all(r.converged and r.residual <= 1e-10 for r in rep)
+    jg = j.cpu().numpy()
+    for c in range(20):
+        assert _rel(jg[c], j_ref[c]) <= 1e-6, c
+    # each column equals its single-column (GEMV) solve
+    j1, _ = op.solve(e[7:8], tol=1e-10)
+    assert _rel(jg[7], j1.cpu().numpy()[0]) <= 1e-8
