@@ -384,6 +384,66 @@ def oracle_sample(budget_s: float = 20.0):
     }
 
 
+def _scene_mesh(shape, n, cache):
+    import synth
+
+    key = (shape, n)
+    if key not in cache:
+        if shape == "sphere":
+            cache[key] = synth.geodesic_sphere(n, seed=40 + n)
+        elif shape == "ellipsoid":
+            cache[key] = synth.ellipsoid(n, seed=40 + n)
+        else:
+            cache[key] = synth.cube(n, seed=40 + n)
+    return cache[key]
+
+
+def bench_serving(args):
+    """Poisson stream of solves (seeded, 20 req/s) through the continuous-batching server."""
+    import threading
+
+    import torch
+
+    import synth
+    from paper_1803_08333_gb300 import build, serve
+
+    build.build()
+    torch.cuda.set_device(0)
+    work = serve.poisson_workload(args.requests, 20.0, seed=4, pool=48)
+    meshes = {}
+    scenes = [(_scene_mesh(sc[0], sc[1], meshes), sc[2], nr) for _, sc, nr in work]
+    budget = int(torch.cuda.mem_get_info()[1] * 0.85)
+    be = serve.GpuBackend(0, hbm_budget=0)
+    srv = serve.Server(be, hbm_budget=budget, workers=args.workers)
+    futs = [None] * len(work)
+
+    def driver():
+        t0 = time.perf_counter()
+        for i, ((t_arr, _, _), (m, ka, nr)) in enumerate(zip(work, scenes)):
+            delay = t_arr - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            kh, pol = synth.random_plane_waves(nr, seed=1000 + i)
+            futs[i] = srv.submit(m.verts, m.tris, ka, kh, pol, tol=TOL)
+
+    th = threading.Thread(target=driver)
+    t0 = time.perf_counter()
+    th.start()
+    th.join()
+    for f in futs:
+        f.result()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    print(json.dumps({
+        "metric": "RF-CMP EFIE serving: solves/s and p50/p99 latency @1e-6 resid", "value": st["solves_per_s"],
+        "unit": "right-hand sides/s", "n_gpus": 1, "higher_is_better": True,
+        "config": {"workload": "poisson_serving_20rps", "requests": args.requests, "scene_pool": 48,
+                   "workers": args.workers, "budget_bytes": budget},
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]}, "requests_per_s": st["requests_per_s"],
+        "mean_batch_columns": st["mean_batch_columns"], "wall_s": round(wall, 2), "data": "synthetic"}))
+
+
 def bench_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -415,6 +475,10 @@ def main():
     ap.add_argument("--mesh-n", type=int, default=32,
                     help="geodesic frequency of the sphere (32 = the workload; smaller for profiling captures)")
     ap.add_argument("--ka", type=float, nargs="*", default=None, help="override the wavenumber sweep")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serving"],
+                    help="sweep: the level-5 low-frequency sweep (default); serving: the Poisson request stream")
+    ap.add_argument("--requests", type=int, default=600)
+    ap.add_argument("--workers", type=int, default=2)
     args = ap.parse_args()
     global MESH_N, KA, WORKLOAD
     if args.mesh_n != 32 or args.ka:
@@ -423,6 +487,8 @@ def main():
         WORKLOAD = "profiling_case_sphere_f%d" % MESH_N
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "serving":
+        bench_serving(args)
     else:
         bench_ours(args)
 

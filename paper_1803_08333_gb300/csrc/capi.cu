@@ -191,6 +191,7 @@ struct rfcmp_ctx {
   std::mutex mu;
   std::map<uint64_t, std::shared_ptr<DenseFactor>> lplus_cache;  // key: connectivity hash
   std::map<uint64_t, std::shared_ptr<DenseFactor>> gll_cache;    // key: connectivity + coordinates hash
+  std::mutex build_mu;  // one factor build at a time, so concurrent ops on one mesh share it
   std::atomic<int> live_ops{0};
 };
 
@@ -971,6 +972,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
     geo_hash = mix(geo_hash, b);
   }
   std::shared_ptr<DenseFactor> lp, gl;
+  std::unique_lock<std::mutex> build_lock(ctx->build_mu);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     auto a = ctx->lplus_cache.find(op->top.hash);
@@ -1006,6 +1008,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   }
   op->lplus = lp;
   op->gll = gl;
+  build_lock.unlock();
   op->info.factor_iterations_lplus = lp->iterations;
   op->info.factor_iterations_gll = gl->iterations;
   // assembly

@@ -1,0 +1,341 @@
+"""Continuous-batching solve server above the C ABI.
+
+Requests (a mesh, a wavenumber, one or more plane waves) arrive at any time.
+The scheduler keeps assembled operators resident (their (Sigma^T Sigma)^+ and
+G_ll^{-1} factors are shared through the context's topology cache), admits a
+request when the HBM footprint of what it still needs fits the budget
+(evicting idle operators least recently used first), merges waiting requests
+for the same operator into one multi-column solve as soon as a worker is free,
+and runs several workers, each on its own CUDA stream, so that solves on
+different operators overlap on the device.  Every request records its latency
+from submission to result; ``Server.stats()`` reports p50 / p99 latency and
+solves (right-hand sides) per second.
+
+The scheduling logic only talks to a backend (``GpuBackend`` for the library,
+``FakeBackend`` for host-side tests), so it is exercised without a GPU.
+"""
+
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import hashlib
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def mesh_key(verts: np.ndarray, tris: np.ndarray) -> str:
+    h = hashlib.sha1()
+    h.update(np.ascontiguousarray(verts, dtype=np.float64).tobytes())
+    h.update(np.ascontiguousarray(tris, dtype=np.int32).tobytes())
+    return h.hexdigest()[:16]
+
+
+def op_footprint(nv: int, nc: int, nrhs: int, with_factors: bool) -> int:
+    """Upper estimate of the device bytes an operator and one solve of nrhs columns need."""
+    ne = 3 * nc // 2
+    pad = lambda n: (n + 63) // 64 * 64  # noqa: E731
+    ops = 8 * pad(ne) * ne + 8 * pad(nc) * nc  # T_A, V complex64
+    if nrhs >= 16:
+        ops *= 2  # BF16 planes for the tensor-core products
+    fac = 8 * pad(nc) * nc + 8 * pad(nv) * nv if with_factors else 0
+    transient = 64 * nc * nc if with_factors else 0  # factor build work arrays
+    vectors = 16 * ne * max(nrhs, 4) * 24
+    return ops + fac + transient + vectors
+
+
+@dataclass
+class Request:
+    rid: int
+    scene: tuple  # (mesh key, k)
+    verts: np.ndarray
+    tris: np.ndarray
+    k: float
+    khat: np.ndarray  # nrhs x 3
+    pol: np.ndarray  # nrhs x 3
+    tol: float
+    t_submit: float
+    future: cf.Future = field(default_factory=cf.Future)
+
+    @property
+    def nrhs(self) -> int:
+        return int(self.khat.shape[0])
+
+
+@dataclass
+class Result:
+    j: np.ndarray  # nrhs x N complex128
+    residuals: list
+    iterations: list
+    latency_s: float
+    batch_columns: int
+
+
+class GpuBackend:
+    """Operators of the library; one context shared by all workers."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, power_steps: int = 30):
+        import paper_1803_08333_gb300 as rf
+
+        self.rf = rf
+        self.ctx = rf.Context(device, hbm_budget)
+        self.device = device
+        self.power_steps = power_steps
+
+    def make_stream(self):
+        import torch
+
+        torch.cuda.set_device(self.device)
+        return torch.cuda.Stream(device=self.device)
+
+    def create(self, req: Request):
+        return self.rf.Operator(self.ctx, req.verts, req.tris, req.k, power_steps=self.power_steps)
+
+    def nbytes(self, op) -> int:
+        return int(op.info().device_bytes)
+
+    def solve(self, op, khat, pol, tol, stream):
+        import torch
+
+        with torch.cuda.stream(stream):
+            e = op.rhs_planewave(khat, pol)
+            j, rep = op.solve(e, tol=tol)
+            jh = j.cpu().numpy()
+        return jh, rep
+
+    def destroy(self, op):
+        op.close()
+
+    def bytes_in_use(self) -> int:
+        return self.ctx.bytes_in_use()
+
+
+class Server:
+    def __init__(self, backend, hbm_budget: int, workers: int = 2, max_batch_columns: int = 64):
+        self.backend = backend
+        self.budget = int(hbm_budget)
+        self.max_cols = int(max_batch_columns)
+        self._lock = threading.Condition()
+        self._pending: collections.OrderedDict = collections.OrderedDict()  # scene -> deque of requests
+        self._ops: collections.OrderedDict = collections.OrderedDict()  # scene -> (op, bytes), LRU order
+        self._busy: set = set()  # scenes being solved
+        self._reserved = 0  # bytes promised to operators being created
+        self._work: "collections.deque" = collections.deque()
+        self._next_id = 0
+        self._closed = False
+        self._latencies = []
+        self._columns = 0
+        self._batches = []
+        self._t0 = None
+        self._t_last = None
+        self._threads = [threading.Thread(target=self._worker, args=(w,), daemon=True) for w in range(workers)]
+        for t in self._threads:
+            t.start()
+
+    # ------------------------------------------------------------------ client side
+    def submit(self, verts, tris, k, khat, pol, tol: float = 1e-6) -> cf.Future:
+        khat = np.atleast_2d(np.asarray(khat, dtype=np.float64))
+        pol = np.atleast_2d(np.asarray(pol, dtype=np.float64))
+        scene = (mesh_key(verts, tris), float(k))
+        with self._lock:
+            if self._closed:
+                raise RuntimeError("server closed")
+            req = Request(self._next_id, scene, verts, tris, float(k), khat, pol, tol, time.perf_counter())
+            self._next_id += 1
+            if self._t0 is None:
+                self._t0 = req.t_submit
+            self._pending.setdefault(scene, collections.deque()).append(req)
+            self._lock.notify_all()
+        return req.future
+
+    def close(self, wait: bool = True):
+        with self._lock:
+            self._closed = True
+            self._lock.notify_all()
+        if wait:
+            for t in self._threads:
+                t.join()
+        for scene, (op, _) in list(self._ops.items()):
+            self.backend.destroy(op)
+        self._ops.clear()
+
+    def stats(self) -> dict:
+        with self._lock:
+            lat = np.array(self._latencies) * 1e3
+            span = (self._t_last - self._t0) if self._t0 is not None and self._t_last is not None else 0.0
+            return {
+                "requests": int(lat.size),
+                "columns": int(self._columns),
+                "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                "requests_per_s": float(lat.size / span) if span > 0 else None,
+                "solves_per_s": float(self._columns / span) if span > 0 else None,
+                "mean_batch_columns": float(np.mean(self._batches)) if self._batches else None,
+                "resident_operators": len(self._ops),
+            }
+
+    # ------------------------------------------------------------------ scheduling
+    def _take_batch(self):
+        """Under the lock: the next runnable batch (scene, requests, needs_create) or None."""
+        for scene, queue in self._pending.items():
+            if scene in self._busy or not queue:
+                continue
+            cols, batch = 0, []
+            while queue and (not batch or cols + queue[0].nrhs <= self.max_cols):
+                r = queue.popleft()
+                batch.append(r)
+                cols += r.nrhs
+            if scene in self._ops:
+                self._ops.move_to_end(scene)
+                need = 0
+            else:
+                r0 = batch[0]
+                nv, nc = r0.verts.shape[0], r0.tris.shape[0]
+                shares_mesh = any(s[0] == scene[0] for s in self._ops)
+                need = op_footprint(nv, nc, cols, with_factors=not shares_mesh)
+                if not self._make_room(need):
+                    for r in reversed(batch):  # put back: wait for memory
+                        queue.appendleft(r)
+                    continue
+            self._busy.add(scene)
+            self._reserved += need
+            if not queue:
+                del self._pending[scene]
+            return scene, batch, need
+        return None
+
+    def _make_room(self, need: int) -> bool:
+        """Evict idle operators (LRU first) until `need` bytes fit; False if they cannot."""
+        if self.budget <= 0:
+            return True
+        while self.backend.bytes_in_use() + self._reserved + need > self.budget:
+            victim = next((s for s in self._ops if s not in self._busy), None)
+            if victim is None:
+                return False
+            op, _ = self._ops.pop(victim)
+            self.backend.destroy(op)
+        return True
+
+    def _worker(self, w: int):
+        stream = self.backend.make_stream()
+        while True:
+            with self._lock:
+                item = None
+                while item is None:
+                    item = self._take_batch()
+                    if item is None:
+                        if self._closed and not self._pending:
+                            return
+                        self._lock.wait(timeout=0.05)
+                scene, batch, need = item
+                entry = self._ops.get(scene)
+            try:
+                if entry is None:
+                    op = self.backend.create(batch[0])
+                    entry = (op, self.backend.nbytes(op))
+                khat = np.concatenate([r.khat for r in batch])
+                pol = np.concatenate([r.pol for r in batch])
+                tol = min(r.tol for r in batch)
+                jh, rep = self.backend.solve(entry[0], khat, pol, tol, stream)
+                t_done = time.perf_counter()
+                out = []
+                c = 0
+                for r in batch:
+                    sl = slice(c, c + r.nrhs)
+                    c += r.nrhs
+                    res = Result(jh[sl].copy(), [x.residual for x in rep[sl]], [x.iterations for x in rep[sl]],
+                                 t_done - r.t_submit, int(khat.shape[0]))
+                    out.append((r, res))
+                with self._lock:
+                    self._ops[scene] = entry
+                    self._ops.move_to_end(scene)
+                    self._busy.discard(scene)
+                    self._reserved -= need
+                    for r, res in out:
+                        self._latencies.append(res.latency_s)
+                    self._columns += int(khat.shape[0])
+                    self._batches.append(int(khat.shape[0]))
+                    self._t_last = t_done
+                    self._lock.notify_all()
+                for r, res in out:
+                    r.future.set_result(res)
+            except Exception as exc:  # a failed batch fails its requests, the server keeps running
+                with self._lock:
+                    self._busy.discard(scene)
+                    self._reserved -= need
+                    self._lock.notify_all()
+                for r in batch:
+                    if not r.future.done():
+                        r.future.set_exception(exc)
+
+
+class FakeBackend:
+    """Host-only stand-in: operators are tokens with a byte size, solves sleep and return zeros."""
+
+    def __init__(self, solve_seconds: float = 0.001, create_seconds: float = 0.002):
+        self.solve_seconds = solve_seconds
+        self.create_seconds = create_seconds
+        self.in_use = 0
+        self.created = []
+        self.destroyed = []
+        self.max_in_use = 0
+        self._lock = threading.Lock()
+
+    def make_stream(self):
+        return None
+
+    def create(self, req: Request):
+        time.sleep(self.create_seconds)
+        nb = op_footprint(req.verts.shape[0], req.tris.shape[0], 1, with_factors=False)
+        with self._lock:
+            self.in_use += nb
+            self.max_in_use = max(self.max_in_use, self.in_use)
+            self.created.append(req.scene)
+        return {"scene": req.scene, "bytes": nb, "n": 3 * req.tris.shape[0] // 2}
+
+    def nbytes(self, op) -> int:
+        return op["bytes"]
+
+    def solve(self, op, khat, pol, tol, stream):
+        time.sleep(self.solve_seconds)
+
+        class _Rep:
+            residual = 0.0
+            iterations = 1
+
+        return np.zeros((khat.shape[0], op["n"]), np.complex128), [_Rep() for _ in range(khat.shape[0])]
+
+    def destroy(self, op):
+        with self._lock:
+            self.in_use -= op["bytes"]
+            self.destroyed.append(op["scene"])
+
+    def bytes_in_use(self) -> int:
+        return self.in_use
+
+
+def poisson_workload(n_requests: int, rate: float, seed: int = 4, pool: int | None = 48):
+    """The seeded serving stream: arrival times and (shape, size, ka, nrhs) per request.
+
+    Shape uniform over sphere / cube / ellipsoid; geodesic frequency 9..31 (spheres, ellipsoids)
+    or cube grid 11..40; ka log-uniform in [1e-3, 3]; nrhs uniform in 1..64.  With `pool`, the
+    (mesh, ka) scenes are drawn from a seeded pool of that many scenes so operators get reused.
+    """
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+
+    def scene():
+        shape = rng.choice(["sphere", "cube", "ellipsoid"])
+        n = int(rng.integers(11, 41)) if shape == "cube" else int(rng.integers(9, 32))
+        ka = float(10 ** rng.uniform(-3, np.log10(3.0)))
+        return (str(shape), n, ka)
+
+    scenes = [scene() for _ in range(pool)] if pool else None
+    out = []
+    for i in range(n_requests):
+        sc = scenes[int(rng.integers(0, pool))] if scenes else scene()
+        out.append((float(t[i]), sc, int(rng.integers(1, 65))))
+    return out

@@ -1,0 +1,43 @@
+"""Serving on the GPU: each result is the same alone and in the mix."""
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1803_08333_gb300 import serve  # noqa: E402
+import paper_1803_08333_gb300 as rf  # noqa: E402
+
+
+def test_results_alone_equal_results_in_the_mix():
+    from paper_1803_08333_gb300 import build
+
+    build.build()
+    meshes = [synth.geodesic_sphere(4, seed=1), synth.cube(4), synth.ellipsoid(3)]
+    rng = np.random.default_rng(12)
+    jobs = []
+    for i in range(12):
+        m = meshes[i % 3]
+        k = [0.5, 1e-3, 1.7][i % 3]
+        nr = int(rng.integers(1, 24))
+        kh, pol = synth.random_plane_waves(nr, seed=100 + i)
+        jobs.append((m, k, kh, pol))
+    be = serve.GpuBackend(0)
+    srv = serve.Server(be, hbm_budget=0, workers=2)
+    futs = [srv.submit(m.verts, m.tris, k, kh, pol, tol=1e-10) for (m, k, kh, pol) in jobs]
+    res = [f.result(timeout=600) for f in futs]
+    st = srv.stats()
+    srv.close()
+    assert st["requests"] == 12 and st["mean_batch_columns"] >= 1
+    ctx = rf.Context(0)
+    for (m, k, kh, pol), r in zip(jobs, res):
+        op = rf.Operator(ctx, m.verts, m.tris, k)
+        j, rep = op.solve(op.rhs_planewave(kh, pol), tol=1e-10)
+        alone = j.cpu().numpy()
+        assert all(x <= 1e-10 for x in r.residuals)
+        err = np.linalg.norm(r.j - alone) / np.linalg.norm(alone)
+        assert err <= 1e-8, err
+        op.close()

@@ -1,0 +1,87 @@
+"""Host-side logic of the continuous-batching server (fake backend, no GPU)."""
+
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from paper_1803_08333_gb300 import serve
+
+
+def _mesh(n, seed=1):
+    m = synth.geodesic_sphere(n, seed=seed)
+    return m.verts, m.tris
+
+
+def test_all_requests_complete_with_their_columns():
+    be = serve.FakeBackend()
+    srv = serve.Server(be, hbm_budget=0, workers=2)
+    v, t = _mesh(2)
+    futs = [srv.submit(v, t, 1.0 + 0.1 * (i % 3), np.tile([[0, 0, 1.0]], (i % 4 + 1, 1)),
+                       np.tile([[1.0, 0, 0]], (i % 4 + 1, 1))) for i in range(20)]
+    for i, f in enumerate(futs):
+        r = f.result(timeout=10)
+        assert r.j.shape == (i % 4 + 1, 3 * t.shape[0] // 2)
+    srv.close()
+    st = srv.stats()
+    assert st["requests"] == 20 and st["columns"] == sum(i % 4 + 1 for i in range(20))
+    assert st["p50_ms"] is not None and st["p99_ms"] >= st["p50_ms"]
+
+
+def test_waiting_requests_of_one_operator_are_merged():
+    be = serve.FakeBackend(solve_seconds=0.05)
+    srv = serve.Server(be, hbm_budget=0, workers=1, max_batch_columns=64)
+    v, t = _mesh(2)
+    kh, pol = synth.plane_wave_z()
+    first = srv.submit(v, t, 1.0, kh, pol)
+    time.sleep(0.02)  # the first solve is running; these queue behind it
+    rest = [srv.submit(v, t, 1.0, kh, pol) for _ in range(5)]
+    first.result(timeout=10)
+    sizes = {f.result(timeout=10).batch_columns for f in rest}
+    srv.close()
+    assert sizes == {5}
+    assert len(be.created) == 1  # the operator stayed resident
+
+
+def test_admission_respects_the_budget_and_evicts_lru():
+    be = serve.FakeBackend()
+    one = serve.op_footprint(42, 80, 1, with_factors=False)
+    budget = int(2.5 * serve.op_footprint(42, 80, 1, with_factors=True))
+    srv = serve.Server(be, hbm_budget=budget, workers=2)
+    v, t = _mesh(2)
+    kh, pol = synth.plane_wave_z()
+    futs = [srv.submit(v, t, 0.5 + i, kh, pol) for i in range(8)]  # 8 distinct wavenumbers
+    for f in futs:
+        f.result(timeout=10)
+    srv.close()
+    assert be.max_in_use <= budget
+    assert len(be.destroyed) >= 8 - budget // one
+
+
+def test_a_failing_batch_fails_only_its_requests():
+    class Flaky(serve.FakeBackend):
+        def solve(self, op, khat, pol, tol, stream):
+            if op["scene"][1] == 2.0:
+                raise RuntimeError("boom")
+            return super().solve(op, khat, pol, tol, stream)
+
+    srv = serve.Server(Flaky(), hbm_budget=0, workers=2)
+    v, t = _mesh(2)
+    kh, pol = synth.plane_wave_z()
+    good = srv.submit(v, t, 1.0, kh, pol)
+    bad = srv.submit(v, t, 2.0, kh, pol)
+    assert good.result(timeout=10).j.shape[0] == 1
+    with pytest.raises(RuntimeError):
+        bad.result(timeout=10)
+    srv.close()
+
+
+def test_poisson_workload_is_seeded():
+    a = serve.poisson_workload(50, 20.0, seed=4)
+    b = serve.poisson_workload(50, 20.0, seed=4)
+    assert a == b
+    t = np.array([x[0] for x in a])
+    assert np.all(np.diff(t) > 0)
+    assert all(1 <= x[2] <= 64 for x in a)
+    assert len({x[1] for x in a}) <= 48
