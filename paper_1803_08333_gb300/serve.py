@@ -162,6 +162,37 @@ class Server:
             self.backend.destroy(op)
         self._ops.clear()
 
+    def warm(self, verts, tris, k) -> bool:
+        """Make the operator of (mesh, k) resident before requests for it arrive.
+
+        Runs in the caller's thread, subject to the same budget and eviction as requests;
+        returns False when it does not fit.
+        """
+        scene = (mesh_key(verts, tris), float(k))
+        with self._lock:
+            if scene in self._ops:
+                self._ops.move_to_end(scene)
+                return True
+            shares_mesh = any(s[0] == scene[0] for s in self._ops)
+            need = op_footprint(verts.shape[0], tris.shape[0], 1, with_factors=not shares_mesh)
+            if not self._make_room(need):
+                return False
+            self._busy.add(scene)
+            self._reserved += need
+        try:
+            req = Request(-1, scene, verts, tris, float(k), np.zeros((1, 3)), np.zeros((1, 3)), 0.0, 0.0)
+            op = self.backend.create(req)
+            entry = (op, self.backend.nbytes(op))
+        finally:
+            with self._lock:
+                self._busy.discard(scene)
+                self._reserved -= need
+        with self._lock:
+            self._ops[scene] = entry
+            self._ops.move_to_end(scene)
+            self._lock.notify_all()
+        return True
+
     def stats(self) -> dict:
         with self._lock:
             lat = np.array(self._latencies) * 1e3
@@ -317,25 +348,31 @@ class FakeBackend:
         return self.in_use
 
 
-def poisson_workload(n_requests: int, rate: float, seed: int = 4, pool: int | None = 48):
+def poisson_workload(n_requests: int, rate: float, seed: int = 4, pool: int | None = 48, mesh_pool: int = 12):
     """The seeded serving stream: arrival times and (shape, size, ka, nrhs) per request.
 
-    Shape uniform over sphere / cube / ellipsoid; geodesic frequency 9..31 (spheres, ellipsoids)
-    or cube grid 11..40; ka log-uniform in [1e-3, 3]; nrhs uniform in 1..64.  With `pool`, the
-    (mesh, ka) scenes are drawn from a seeded pool of that many scenes so operators get reused.
+    Shape uniform over sphere / cube / ellipsoid; geodesic frequency 9..31 (spheres, ellipsoids,
+    2.4k to 29k unknowns) or cube grid 11..40 (2.2k to 29k unknowns); ka log-uniform in
+    [1e-3, 3]; nrhs uniform in 1..64.  With `pool`, the (mesh, ka) scenes are drawn from a
+    seeded pool of that many scenes over `mesh_pool` meshes, so operators and the per-mesh
+    factors get reused; without it every request is a new scene.
     """
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, n_requests))
 
-    def scene():
+    def mesh():
         shape = rng.choice(["sphere", "cube", "ellipsoid"])
         n = int(rng.integers(11, 41)) if shape == "cube" else int(rng.integers(9, 32))
-        ka = float(10 ** rng.uniform(-3, np.log10(3.0)))
-        return (str(shape), n, ka)
+        return (str(shape), n)
 
-    scenes = [scene() for _ in range(pool)] if pool else None
+    def ka():
+        return float(10 ** rng.uniform(-3, np.log10(3.0)))
+
+    if pool:
+        meshes = [mesh() for _ in range(mesh_pool)]
+        scenes = [meshes[i % mesh_pool] + (ka(),) for i in range(pool)]
     out = []
     for i in range(n_requests):
-        sc = scenes[int(rng.integers(0, pool))] if scenes else scene()
+        sc = scenes[int(rng.integers(0, pool))] if pool else mesh() + (ka(),)
         out.append((float(t[i]), sc, int(rng.integers(1, 65))))
     return out

@@ -39,5 +39,8 @@ def test_results_alone_equal_results_in_the_mix():
         alone = j.cpu().numpy()
         assert all(x <= 1e-10 for x in r.residuals)
         err = np.linalg.norm(r.j - alone) / np.linalg.norm(alone)
-        assert err <= 1e-8, err
+        # both solve the same system to relative residual 1e-10; merged columns take the
+        # multi-column (tensor-core) products and their own rounding, so they agree to about
+        # cond * 1e-10, with cond below 1e3 for these meshes
+        assert err <= 1e-7, err
         op.close()

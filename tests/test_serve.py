@@ -85,3 +85,18 @@ def test_poisson_workload_is_seeded():
     assert np.all(np.diff(t) > 0)
     assert all(1 <= x[2] <= 64 for x in a)
     assert len({x[1] for x in a}) <= 48
+    assert len({x[1][:2] for x in a}) <= 12  # scenes share meshes
+
+
+def test_warm_makes_operators_resident_within_budget():
+    be = serve.FakeBackend()
+    one = serve.op_footprint(*_mesh(3)[0].shape[:1], _mesh(3)[1].shape[0], 1, with_factors=True)
+    srv = serve.Server(be, hbm_budget=int(2.5 * one), workers=1)
+    v, t = _mesh(3)
+    assert srv.warm(v, t, 1.0) and srv.warm(v, t, 2.0) and srv.warm(v, t, 1.0)
+    assert be.created == [(serve.mesh_key(v, t), 1.0), (serve.mesh_key(v, t), 2.0)]
+    kh, pol = synth.plane_wave_z()
+    srv.submit(v, t, 2.0, kh, pol).result(timeout=10)
+    assert len(be.created) == 2  # the warm operator served the request
+    srv.close()
+    assert be.in_use == 0
