@@ -126,7 +126,7 @@ def _dist():
     return ws, rank, local
 
 
-def run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, copy_back=False):
+def run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, copy_back=False, tuning=None):
     """One pass of the hot path over the six wavenumbers; returns host bytes moved."""
     import torch
 
@@ -137,6 +137,7 @@ def run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, copy_back=False):
         t0 = time.perf_counter()
         # alpha, beta, gamma power iterations start from the previous wavenumber's iterates
         op = rf.Operator(ctx, mesh.verts, mesh.tris, ka, scaling_start=prev)
+        op.tuning = tuning
         if prev is not None:
             prev.close()
         e = op.rhs_planewave(kh, pol)
@@ -157,6 +158,22 @@ def run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, copy_back=False):
     return h2d, d2h
 
 
+def _tuning(ctx, n, args):
+    """The committed autotuner table of this device (None with --no-tuning or when absent)."""
+    import torch
+
+    from paper_1803_08333_gb300 import autotune
+
+    if args.no_tuning:
+        return None, "built-in"
+    table = autotune.Table.for_device(torch.cuda.get_device_name(torch.cuda.current_device()))
+    if table is None:
+        return None, "built-in (no table for this device)"
+    plan = table.lookup(n, 1, "mixed") or {}
+    ctx.set_plan({"far_min_blocks": plan.get("far_min_blocks", 0)})
+    return table, plan
+
+
 def bench_ours(args):
     import torch
 
@@ -175,9 +192,10 @@ def bench_ours(args):
     dirs = _cut_dirs()
     kh, pol = synth.plane_wave_z()
     ctx = rf.Context(local)
+    tuning, plan = _tuning(ctx, 3 * mesh.tris.shape[0] // 2, args)
     lat, reports = [], []
     for _ in range(args.warmup):
-        run_step(rf, ctx, mesh, dirs, kh, pol, [], [])
+        run_step(rf, ctx, mesh, dirs, kh, pol, [], [], tuning=tuning)
 
     def barrier():
         torch.cuda.synchronize()
@@ -195,7 +213,7 @@ def bench_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports)
+        run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, tuning=tuning)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -217,7 +235,7 @@ def bench_ours(args):
     t0 = time.perf_counter()
     h2d = d2h = 0
     for _ in range(args.steps):
-        a, b = run_step(rf, ctx, mesh, dirs, kh, pol, e2e_lat, [], copy_back=True)
+        a, b = run_step(rf, ctx, mesh, dirs, kh, pol, e2e_lat, [], copy_back=True, tuning=tuning)
         h2d += a
         d2h += b
     barrier()
@@ -265,6 +283,7 @@ def bench_ours(args):
             "nrhs": 1,
             "parallelism": "replicas" if ws > 1 else "single",
             "l2": "inputs larger than L2 (T_A complex64 7.5 GB, V 3.4 GB)",
+            "plan": plan,
         },
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2), "p99": round(float(np.percentile(lat, 99)), 2)},
         "iterations": iters,
@@ -418,7 +437,10 @@ def bench_serving(args):
     meshes = {}
     scenes = [(_scene_mesh(sc[0], sc[1], meshes), sc[2], nr) for _, sc, nr in work]
     budget = int(torch.cuda.mem_get_info()[1] * 0.85)
-    be = serve.GpuBackend(0, hbm_budget=0)
+    from paper_1803_08333_gb300 import autotune
+
+    table = None if args.no_tuning else autotune.Table.for_device(torch.cuda.get_device_name(0))
+    be = serve.GpuBackend(0, hbm_budget=0, tuning=table)
     srv = serve.Server(be, hbm_budget=budget, workers=args.workers)
     t0 = time.perf_counter()
     seen = set()
@@ -457,7 +479,7 @@ def bench_serving(args):
         "unit": "right-hand sides/s", "n_gpus": 1, "higher_is_better": True,
         "config": {"workload": f"poisson_serving_{args.rate:g}rps", "requests": args.requests, "scene_pool": len(seen),
                    "mesh_pool": len(meshes), "unknowns": [sizes[0], sizes[-1]], "workers": args.workers,
-                   "budget_bytes": budget, "tol": TOL},
+                   "budget_bytes": budget, "tol": TOL, "tuning": "table" if table is not None else "built-in"},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]}, "requests_per_s": st["requests_per_s"],
         "mean_batch_columns": st["mean_batch_columns"], "max_residual": max(max(r.residuals) for r in res),
         "resident_operators": st["resident_operators"], "cold_start_s": round(cold_s, 2), "wall_s": round(wall, 2),
@@ -500,6 +522,7 @@ def main():
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--workers", type=int, default=2)
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--no-tuning", action="store_true", help="ignore the autotuner table (built-in plans)")
     args = ap.parse_args()
     global MESH_N, KA, WORKLOAD
     if args.mesh_n != 32 or args.ka:

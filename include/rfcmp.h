@@ -71,7 +71,10 @@ typedef enum {
   RFCMP_APPLY_T_A = 1,   /* y = T_A x                                                 (Sec. 2) */
   RFCMP_APPLY_T_PHI = 2, /* y = Sigma V Sigma^T x                          (Sec. 3, Eq. TPhiandV) */
   RFCMP_APPLY_T_ADJ = 3, /* y = T^H x = conj(T conj(x))                    (Sec. 3.4, T^dagger) */
-  RFCMP_APPLY_A = 4      /* y = P_o^H T^H P_m T P_o x (low-frequency-stable order)   (Sec. 3, Sec. 4) */
+  RFCMP_APPLY_A = 4,     /* y = P_o^H T^H P_m T P_o x (low-frequency-stable order)   (Sec. 3, Sec. 4) */
+  RFCMP_APPLY_A_INNER = 5 /* the same operator in the inner-iteration arithmetic of a MIXED solve:
+                            FP32 products (FP32 GEMV, or the split-BF16 tensor-core GEMM from
+                            rfcmp_plan.mrhs_min columns on); what the autotuner times */
 } rfcmp_apply_which;
 
 /* which preconditioner factor rfcmp_precondition applies */
@@ -257,6 +260,34 @@ int rfcmp_gemm_bf16x3(const float* A, int64_t lda, const float* B, int64_t ldb, 
  * Errors: RFCMP_ERR_INVALID_ARG (NULL, nrhs or size beyond the limits), RFCMP_ERR_CUDA.
  */
 int rfcmp_apply_ta_noalloc(const rfcmp_op* op, const rfcmp_c128* x, rfcmp_c128* y, int64_t nrhs, void* stream);
+
+/* ----------------------------------------------------------------------------
+ * Kernel plans (the paper has no counterpart; they choose launch shapes, never
+ * arithmetic that changes a float-float result).  A zero field means the
+ * built-in choice.  The autotuner measures candidates through rfcmp_apply
+ * (RFCMP_APPLY_A_INNER) and keeps the best per (N, nrhs, precision).
+ */
+typedef struct {
+  int32_t mrhs_min;         /* inner-iteration products of at least this many columns run on the
+                               tensor cores (split-BF16 GEMM), narrower ones on the FP32 GEMV;
+                               1..65536, default 4 */
+  int32_t gemm_bn;          /* GEMM N tile: 32, 64 or 128 columns; default by column count */
+  int32_t gemv_chunk;       /* GEMV work unit width in matrix columns: a multiple of 256 in
+                               [256, 8192]; default 1024 */
+  int32_t gemv_ctas_per_sm; /* persistent GEMV CTAs per SM, 1..8; default the occupancy maximum */
+  int32_t far_min_blocks;   /* far-pair assembly CTAs per SM its registers are sized for: 1, 2, 3;
+                               default 2 (read at rfcmp_op_create) */
+  int32_t reserved[3];      /* must be zero */
+} rfcmp_plan;
+/* Fills plan with zeros (every field at its built-in choice). */
+void rfcmp_plan_default(rfcmp_plan* plan);
+/* The plan that operators created afterwards in ctx start with.
+ * Errors: RFCMP_ERR_INVALID_ARG (NULL ctx or a field out of range). */
+int rfcmp_ctx_set_plan(rfcmp_ctx* ctx, const rfcmp_plan* plan);
+/* Replaces the plan of op for its later calls (NULL: built-in choices).  Not thread-safe
+ * against calls on the same op.  Errors: RFCMP_ERR_INVALID_ARG. */
+int rfcmp_op_set_plan(rfcmp_op* op, const rfcmp_plan* plan);
+int rfcmp_op_get_plan(const rfcmp_op* op, rfcmp_plan* out);
 
 /* ----------------------------------------------------------------------------
  * Profiling counters (the paper has no counterpart; measurement support).

@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librfcmp.so")
 
-APPLY = {"T": 0, "T_A": 1, "T_PHI": 2, "T_ADJ": 3, "A": 4}
+APPLY = {"T": 0, "T_A": 1, "T_PHI": 2, "T_ADJ": 3, "A": 4, "A_INNER": 5}
 PREC = {"P_O": 0, "P_O_ADJ": 1, "P_M": 2, "P_SIGMA": 3, "P_LAMBDAH": 4}
 SCALING = {"power": 0, "k": 1, "fixed": 2}
 PRECISION = {"mixed": 0, "ff": 1}
@@ -33,7 +33,7 @@ EXPORTED_SYMBOLS = [
     "rfcmp_rhs_planewave", "rfcmp_apply", "rfcmp_precondition", "rfcmp_solve", "rfcmp_solve_host",
     "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
-    "rfcmp_gemm_bf16x3",
+    "rfcmp_gemm_bf16x3", "rfcmp_plan_default", "rfcmp_ctx_set_plan", "rfcmp_op_set_plan", "rfcmp_op_get_plan",
 ]
 
 
@@ -44,6 +44,28 @@ class OpOpts(ctypes.Structure):
         ("factor_tol", ctypes.c_double), ("power_rtol", ctypes.c_double), ("scaling_start", ctypes.c_void_p),
         ("reserved", ctypes.c_int32 * 8),
     ]
+
+
+class Plan(ctypes.Structure):
+    """Launch shapes of one operator (zero fields: the library's built-in choices)."""
+
+    _fields_ = [
+        ("mrhs_min", ctypes.c_int32), ("gemm_bn", ctypes.c_int32), ("gemv_chunk", ctypes.c_int32),
+        ("gemv_ctas_per_sm", ctypes.c_int32), ("far_min_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+    ]
+    KEYS = ("mrhs_min", "gemm_bn", "gemv_chunk", "gemv_ctas_per_sm", "far_min_blocks")
+
+    @classmethod
+    def of(cls, d: "dict | None") -> "Plan":
+        p = cls()
+        for k_, v in (d or {}).items():
+            if k_ not in cls.KEYS:
+                raise KeyError("unknown plan field %r" % k_)
+            setattr(p, k_, int(v))
+        return p
+
+    def as_dict(self) -> dict:
+        return {k_: int(getattr(self, k_)) for k_ in self.KEYS}
 
 
 class SolveOpts(ctypes.Structure):
@@ -121,6 +143,11 @@ def lib():
         L.rfcmp_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
         L.rfcmp_apply_ta_noalloc.argtypes = [vp, vp, vp, i64, vp]
         L.rfcmp_gemm_bf16x3.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, vp]
+        L.rfcmp_plan_default.argtypes = [ctypes.POINTER(Plan)]
+        L.rfcmp_plan_default.restype = None
+        L.rfcmp_ctx_set_plan.argtypes = [vp, ctypes.POINTER(Plan)]
+        L.rfcmp_op_set_plan.argtypes = [vp, ctypes.POINTER(Plan)]
+        L.rfcmp_op_get_plan.argtypes = [vp, ctypes.POINTER(Plan)]
         L.rfcmp_profile_enable.argtypes = [i32]
         L.rfcmp_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
         _LIB = L
@@ -185,6 +212,11 @@ class Context:
     def clear_cache(self):
         _check(lib().rfcmp_ctx_clear_cache(self._h))
 
+    def set_plan(self, plan: "dict | None" = None):
+        """Plan that operators created from now on start with (fields of `Plan`; None: built-in)."""
+        p = Plan.of(plan)
+        _check(lib().rfcmp_ctx_set_plan(self._h, ctypes.byref(p)))
+
     def bytes_in_use(self) -> int:
         return int(lib().rfcmp_ctx_bytes_in_use(self._h))
 
@@ -238,11 +270,23 @@ class Operator:
         self.k = float(k)
         inf = self.info()
         self.N, self.nc, self.nv = int(inf.n_edges), int(inf.n_cells), int(inf.n_vertices)
+        self.tuning = None  # an autotune.Table: solve() and apply("A_INNER") take its plans
+        self._plan_set = None
 
     def info(self) -> OpInfo:
         out = OpInfo()
         _check(lib().rfcmp_op_info_get(self._h, ctypes.byref(out)))
         return out
+
+    def plan(self) -> dict:
+        p = Plan()
+        _check(lib().rfcmp_op_get_plan(self._h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def set_plan(self, plan: "dict | None" = None):
+        """Launch shapes for this operator's later calls (fields of `Plan`; None: built-in)."""
+        p = Plan.of(plan)
+        _check(lib().rfcmp_op_set_plan(self._h, ctypes.byref(p)))
 
     @property
     def scaling(self):
@@ -287,13 +331,25 @@ class Operator:
             x = x[None]
         return x.contiguous()
 
-    def apply(self, which: str, x):
+    def apply(self, which: str, x, out=None):
         import torch
 
         x = self._vec(x)
-        y = torch.empty_like(x)
+        y = torch.empty_like(x) if out is None else out
+        if which == "A_INNER":
+            self._tuned(x.shape[0], "mixed")
         _check(lib().rfcmp_apply(self._h, APPLY[which], _ptr(x), _ptr(y), x.shape[0], _stream()))
         return y
+
+    def _tuned(self, nrhs: int, precision: str):
+        """Applies the tuning table's plan for this call's shape (if the operator carries a table)."""
+        if self.tuning is None:
+            return
+        plan = self.tuning.lookup(self.N, nrhs, precision) or {}
+        plan = {k_: v for k_, v in plan.items() if k_ != "far_min_blocks"}
+        if plan != self._plan_set:
+            self.set_plan(plan)
+            self._plan_set = plan
 
     def apply_ta_noalloc(self, x, out=None):
         """y = T_A x through the allocation-free entry point; `out` may be preallocated."""
@@ -330,6 +386,7 @@ class Operator:
         nr = e.shape[0]
         rep = (SolveReport * nr)()
         o = self._solve_opts(tol, max_iter, max_refine, inner_tol, precision)
+        self._tuned(nr, precision)
         _check(lib().rfcmp_solve(self._h, _ptr(e), _ptr(j), nr, ctypes.byref(o), rep, _stream()))
         return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]
 
@@ -341,6 +398,7 @@ class Operator:
         nr = e.shape[0]
         rep = (SolveReport * nr)()
         o = self._solve_opts(tol, max_iter, max_refine, inner_tol, precision)
+        self._tuned(nr, precision)
         _check(lib().rfcmp_solve_host(self._h, e.ctypes.data_as(ctypes.c_void_p), j.ctypes.data_as(ctypes.c_void_p),
                                       nr, ctypes.byref(o), rep, _stream(stream)))
         return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]

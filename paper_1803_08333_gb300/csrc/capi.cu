@@ -161,8 +161,10 @@ ProfScope::~ProfScope() {
 // the tensor cores from a multigrid-PCG start accurate to NS_START_TOL.
 constexpr int NS_MIN_CELLS = 256;
 // Products with at least this many right-hand sides in the FP32 inner iterations run on the tensor
-// cores (split-BF16 GEMM) instead of the HBM-bound GEMV.
-constexpr int MRHS_MIN = 16;
+// cores (split-BF16 GEMM) instead of the HBM-bound GEMV: one pass over the BF16 planes (as many
+// bytes as the complex64 matrix) serves every column, so from about 4 columns on it beats the
+// GEMV's pass per 4 columns (measured on GB300 from 2k to 31k unknowns).
+constexpr int MRHS_MIN = 4;
 constexpr double NS_START_TOL = 1e-2;
 
 struct DenseFactor {
@@ -193,6 +195,7 @@ struct rfcmp_ctx {
   std::map<uint64_t, std::shared_ptr<DenseFactor>> gll_cache;    // key: connectivity + coordinates hash
   std::mutex build_mu;  // one factor build at a time, so concurrent ops on one mesh share it
   std::atomic<int> live_ops{0};
+  rfcmp_plan plan{};    // plan of operators created from now on
 };
 
 struct Workspace {
@@ -243,6 +246,7 @@ struct rfcmp_op {
   std::unique_ptr<SolveBuffers> sb;
   double2* power_vecs = nullptr;  // N x 3: final iterates of the X, Z and Y power iterations
   CplxPlanes ta_planes, v_planes;  // BF16 planes of T_A and V, built on the first multi-RHS product
+  rfcmp_plan plan{};               // launch shapes (zero fields: built-in choices)
   ~rfcmp_op() {
     for (void* p : owned) cudaFree(p);
   }
@@ -257,8 +261,20 @@ uint64_t mix(uint64_t h, uint64_t v) {
   return z ^ (z >> 31);
 }
 
+// columns from which inner-iteration products take the tensor cores
+int plan_mrhs(const rfcmp_op* op) { return op->plan.mrhs_min > 0 ? op->plan.mrhs_min : MRHS_MIN; }
+
+void plan_to_scratch(rfcmp_op* op) {
+  op->ws->gs.chunk = op->plan.gemv_chunk;
+  op->ws->gs.ctas_per_sm = op->plan.gemv_ctas_per_sm;
+  op->ws->ms.bn = op->plan.gemm_bn;
+}
+
 int ensure_workspace(rfcmp_op* op, int cols) {
-  if (op->ws && op->ws->cols >= cols) return RFCMP_OK;
+  if (op->ws && op->ws->cols >= cols && (cols < plan_mrhs(op) || op->ws->ms.cap_cols >= cols)) {
+    plan_to_scratch(op);
+    return RFCMP_OK;
+  }
   auto ws = std::make_unique<Workspace>();
   ws->cols = cols;
   const size_t N = op->top.ne, C = op->top.nc, NV = op->top.nv;
@@ -275,17 +291,18 @@ int ensure_workspace(rfcmp_op* op, int cols) {
     RF_TRY(dalloc(&ws->gs.xh, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.xl, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.acc, (size_t)capn * 4, ws->owned));
-    if (cols >= MRHS_MIN) {
+    if (cols >= plan_mrhs(op)) {
       ws->ms.cap_cols = cols;
       ws->ms.cap_n = capn;
       ws->ms.cap_ld = padded_ld(capn);
       RF_TRY(dalloc(&ws->ms.xb, (size_t)4 * cols * ws->ms.cap_ld, ws->owned));
-      RF_TRY(dalloc(&ws->ms.D, (size_t)2 * cols * capn, ws->owned));
+      RF_TRY(dalloc(&ws->ms.D, (size_t)4 * cols * capn, ws->owned));
       RF_TRY(dalloc(&ws->ms.err, 1, ws->owned));
       RF_CUDA(cudaMemset(ws->ms.err, 0, sizeof(int)));
     }
   }
   op->ws = std::move(ws);
+  plan_to_scratch(op);
   return RFCMP_OK;
 }
 
@@ -319,7 +336,11 @@ int make_cplx_planes(rfcmp_op* op, const float2* M, int n, int ld, CplxPlanes& P
   q.n = n;
   q.ldp = ld;
   const size_t pl = (size_t)n * ld;
-  for (__nv_bfloat16** p : {&q.rh, &q.rl, &q.ih, &q.il}) RF_TRY(dalloc(p, pl, op->owned));
+  // Re and Im rows stacked in one hi and one lo buffer: the product reads them as one 2n-row operand
+  RF_TRY(dalloc(&q.rh, 2 * pl, op->owned));
+  RF_TRY(dalloc(&q.rl, 2 * pl, op->owned));
+  q.ih = q.rh + pl;
+  q.il = q.rl + pl;
   RF_K(split_c64_planes(M, n, ld, q, st));
   op->bytes += 4 * pl * sizeof(__nv_bfloat16);
   op->ctx->bytes += 4 * pl * sizeof(__nv_bfloat16);
@@ -356,7 +377,7 @@ int ensure_planes(rfcmp_op* op, cudaStream_t st) {
 // y = scale * op(M) x (+ y) for M = T_A or V: GEMV, or the tensor-core product for wide FP32 blocks
 int prod_c(rfcmp_op* op, bool ta, const double2* x, double2* y, int nr, bool conj, double2 scale, bool acc,
            GemvMode m, cudaStream_t st) {
-  if (m == GEMV_F32 && nr >= MRHS_MIN) {
+  if (m == GEMV_F32 && nr >= plan_mrhs(op)) {
     RF_TRY(ensure_planes(op, st));
     RF_K(cplx_gemm(ta ? op->ta_planes : op->v_planes, x, y, nr, conj, scale, acc, op->ws->ms, st));
     return RFCMP_OK;
@@ -369,7 +390,7 @@ int prod_c(rfcmp_op* op, bool ta, const double2* x, double2* y, int nr, bool con
 // y = scale * F x (+ y) for a dense real factor
 int prod_r(rfcmp_op* op, DenseFactor& f, const double2* x, double2* y, int nr, double scale, bool acc, GemvMode m,
            cudaStream_t st) {
-  if (m == GEMV_F32 && nr >= MRHS_MIN) {
+  if (m == GEMV_F32 && nr >= plan_mrhs(op)) {
     RF_TRY(ensure_planes(op, st));
     RF_K(real_gemm(f.planes, x, y, nr, scale, acc, op->ws->ms, st));
     return RFCMP_OK;
@@ -954,6 +975,10 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   auto op = std::make_unique<rfcmp_op>();
   op->ctx = ctx;
   op->k = k;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    op->plan = ctx->plan;
+  }
   std::string err;
   int rc = build_topology(tris, nc, nv, op->top, err);
   if (rc != RFCMP_OK) return set_error(rc, err);
@@ -1025,7 +1050,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   RF_CUDA(cudaEventRecord(e0, 0));
   RF_CUDA(cudaMemsetAsync(op->TA, 0, (size_t)op->ldN * N * sizeof(float2), 0));
   RF_CUDA(cudaMemsetAsync(op->V, 0, (size_t)op->ldC * C * sizeof(float2), 0));
-  RF_K(launch_assemble_far(op->g, (float)k, op->TA, op->V, 0));
+  RF_K(launch_assemble_far(op->g, (float)k, op->TA, op->V, op->plan.far_min_blocks, 0));
   RF_K(launch_assemble_near(op->g, k, op->TA, op->V, 0));
   RF_K(launch_mirror_upper(op->TA, N, op->ldN, 0));
   RF_CUDA(cudaEventRecord(e1, 0));
@@ -1166,9 +1191,70 @@ int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout
     }
     case RFCMP_APPLY_A:
       return apply_A(op, x, y, nr, m, st);
+    case RFCMP_APPLY_A_INNER: {
+      RF_TRY(apply_A(op, x, y, nr, GEMV_F32, st));
+      if (nr >= plan_mrhs(op) && op->ws->ms.err) {  // the tensor-core products' bounded waits
+        int h_err = 0;
+        RF_CUDA(cudaMemcpyAsync(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RF_CUDA(cudaStreamSynchronize(st));
+        if (h_err) {
+          RF_CUDA(cudaMemsetAsync(op->ws->ms.err, 0, sizeof(int), st));
+          return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a tensor-core product gave up a bounded wait (code " +
+                                                         std::to_string(h_err) + ")");
+        }
+      }
+      return RFCMP_OK;
+    }
     default:
       return set_error(RFCMP_ERR_INVALID_ARG, "unknown operator id");
   }
+}
+
+void rfcmp_plan_default(rfcmp_plan* plan) {
+  if (plan) std::memset(plan, 0, sizeof(*plan));
+}
+
+namespace {
+int check_plan(const rfcmp_plan& p) {
+  for (int i = 0; i < 3; ++i)
+    if (p.reserved[i] != 0) return set_error(RFCMP_ERR_INVALID_ARG, "plan.reserved must be zero");
+  if (p.mrhs_min < 0 || p.mrhs_min > 65536) return set_error(RFCMP_ERR_INVALID_ARG, "plan.mrhs_min out of range");
+  if (p.gemm_bn != 0 && p.gemm_bn != 32 && p.gemm_bn != 64 && p.gemm_bn != 128)
+    return set_error(RFCMP_ERR_INVALID_ARG, "plan.gemm_bn must be 0, 32, 64 or 128");
+  if (p.gemv_chunk != 0 && (p.gemv_chunk % 256 != 0 || p.gemv_chunk < 256 || p.gemv_chunk > 8192))
+    return set_error(RFCMP_ERR_INVALID_ARG, "plan.gemv_chunk must be a multiple of 256 in [256, 8192]");
+  if (p.gemv_ctas_per_sm < 0 || p.gemv_ctas_per_sm > 8)
+    return set_error(RFCMP_ERR_INVALID_ARG, "plan.gemv_ctas_per_sm out of range");
+  if (p.far_min_blocks < 0 || p.far_min_blocks > 3)
+    return set_error(RFCMP_ERR_INVALID_ARG, "plan.far_min_blocks must be 0..3");
+  return RFCMP_OK;
+}
+}  // namespace
+
+int rfcmp_ctx_set_plan(rfcmp_ctx* ctx, const rfcmp_plan* plan) {
+  if (!ctx) return set_error(RFCMP_ERR_INVALID_ARG, "NULL context");
+  rfcmp_plan p{};
+  if (plan) p = *plan;
+  RF_TRY(check_plan(p));
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->plan = p;
+  return RFCMP_OK;
+}
+
+int rfcmp_op_set_plan(rfcmp_op* op, const rfcmp_plan* plan) {
+  if (!op) return set_error(RFCMP_ERR_INVALID_ARG, "NULL op");
+  rfcmp_plan p{};
+  if (plan) p = *plan;
+  RF_TRY(check_plan(p));
+  op->plan = p;
+  if (op->ws) plan_to_scratch(op);
+  return RFCMP_OK;
+}
+
+int rfcmp_op_get_plan(const rfcmp_op* op, rfcmp_plan* out) {
+  if (!op || !out) return set_error(RFCMP_ERR_INVALID_ARG, "NULL argument");
+  *out = op->plan;
+  return RFCMP_OK;
 }
 
 int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout, int64_t nrhs, void* stream) {

@@ -72,7 +72,9 @@ __device__ void load_tile(TileCells& T, const DeviceGeometry g, int base) {
   }
 }
 
-__global__ void __launch_bounds__(FAR_THREADS, 2)
+// MINB: resident CTAs per SM that the register allocation is sized for (the plan's choice)
+template <int MINB>
+__global__ void __launch_bounds__(FAR_THREADS, MINB)
 far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float2* __restrict__ V, int nb) {
   __shared__ TileCells S, Tt;
   // linear tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
@@ -496,14 +498,28 @@ farfield_kernel(const DeviceGeometry g, double k, const double2* __restrict__ j,
 
 }  // namespace
 
-cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, float2* V, cudaStream_t s) {
+cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, float2* V, int min_blocks,
+                                cudaStream_t s) {
   const int nb = (g.nc + TILE - 1) / TILE;
   const long long tiles = (long long)nb * (nb + 1) / 2;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   // far pairs: all unordered pairs minus the near ones (n_near counts s <= t, including s == t)
   const double far = (double)g.nc * (g.nc + 1) / 2.0 - (double)g.n_near;
   ProfScope prof("assemble_far", 8.0 * (double)g.nc * g.nc + 8.0 * (double)g.ne * g.ne, far * 49.0 * 54.0, s);
-  far_pairs_kernel<<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+  switch (min_blocks) {
+    case 1:
+      far_pairs_kernel<1><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      break;
+    case 0:
+    case 2:
+      far_pairs_kernel<2><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      break;
+    case 3:
+      far_pairs_kernel<3><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -348,14 +348,39 @@ __global__ void split_x_kernel(const double2* __restrict__ X, int n, int nr, lon
   }
 }
 
-// Y[:, r] = scale * (Dr[:, r] + i Di[:, r]) (+ Y); D row-major n x ldd with the real parts in column r and
-// the imaginary parts in column r (Di) or column nr + r (stacked, Di == Dr)
-__global__ void combine_kernel(const float* __restrict__ Dr, const float* __restrict__ Di, long long ldd, int n,
-                               int nr, int im_off, double2 scale, int accumulate, double2* __restrict__ Y) {
-  const int r = blockIdx.y;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double a = Dr[(size_t)i * ldd + r], b = Di[(size_t)i * ldd + im_off + r];
-    double2 o = make_double2(scale.x * a - scale.y * b, scale.x * b + scale.y * a);
+// Y[:, r] = scale * op(T) X[:, r] (+ Y) from D = [Tr; Ti] [Xr Xi] (2n x 2nr, row stride ldd):
+// T X = (Tr Xr - Ti Xi) + i (Tr Xi + Ti Xr); conj(T) flips the sign of the Ti terms.  With real,
+// D = P [Xr Xi] (n x 2nr) of a real P and Y = scale * (D[:, r] + i D[:, nr + r]) (+ Y).
+// 32 x 32 tiles of (row i, column r) go through shared memory so that both the reads of D
+// (along r) and the writes of Y (along i) are coalesced.
+constexpr int CT = 32;
+__global__ void combine_cplx_kernel(const float* __restrict__ D, long long ldd, int n, int nr, int conj, int real,
+                                    double2 scale, int accumulate, double2* __restrict__ Y) {
+  __shared__ double2 t[CT][CT + 1];
+  const int i0 = blockIdx.x * CT, r0 = blockIdx.y * CT;
+  const double sg = conj ? -1.0 : 1.0;
+  for (int ii = threadIdx.y; ii < CT; ii += blockDim.y) {
+    const int i = i0 + ii, r = r0 + threadIdx.x;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < n && r < nr) {
+      const float* top = D + (size_t)i * ldd;
+      if (real) {
+        v.x = (double)top[r];
+        v.y = (double)top[nr + r];
+      } else {
+        const float* bot = D + (size_t)(n + i) * ldd;
+        v.x = (double)top[r] - sg * (double)bot[nr + r];
+        v.y = (double)top[nr + r] + sg * (double)bot[r];
+      }
+    }
+    t[ii][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int rr = threadIdx.y; rr < CT; rr += blockDim.y) {
+    const int r = r0 + rr, i = i0 + threadIdx.x;
+    if (i >= n || r >= nr) continue;
+    const double2 v = t[threadIdx.x][rr];
+    double2 o = make_double2(scale.x * v.x - scale.y * v.y, scale.x * v.y + scale.y * v.x);
     if (accumulate) {
       const double2 p = Y[(size_t)r * n + i];
       o.x += p.x;
@@ -379,32 +404,21 @@ cudaError_t cplx_gemm(const CplxPlanes& T, const double2* X, double2* Y, int nr,
   const int n = T.n;
   const long long ldp = T.ldp;
   if (nr > w.cap_cols || ldp > w.cap_ld || n > w.cap_n) return cudaErrorInvalidValue;
+  if (T.ih != T.rh + (size_t)n * ldp || T.il != T.rl + (size_t)n * ldp) return cudaErrorInvalidValue;
   __nv_bfloat16* xb = w.xb;
-  const size_t pl = (size_t)nr * ldp;
-  __nv_bfloat16 *xrh = xb, *xrl = xb + pl, *xih = xb + 2 * pl, *xil = xb + 3 * pl;
+  const size_t pl = (size_t)2 * nr * ldp;  // stacked Re / Im rows of X^T
+  __nv_bfloat16 *bh = xb, *bl = xb + pl;
   dim3 g1((unsigned)std::min<long long>((ldp + 255) / 256, 64), nr);
-  split_x_kernel<<<g1, 256, 0, s>>>(X, n, nr, ldp, false, xrh, xrl, xih, xil);
-  SplitOperand Tr, Ti, XR, XI;
-  Tr.hi = T.rh; Tr.lo = T.rl; Tr.rows = n; Tr.ld = ldp;
-  Ti.hi = T.ih; Ti.lo = T.il; Ti.rows = n; Ti.ld = ldp;
-  XR.hi = xrh; XR.lo = xrl; XR.rows = nr; XR.ld = ldp;
-  XI.hi = xih; XI.lo = xil; XI.rows = nr; XI.ld = ldp;
-  float* Dr = w.D;
-  float* Di = w.D + (size_t)n * nr;
+  split_x_kernel<<<g1, 256, 0, s>>>(X, n, nr, ldp, true, bh, bl, bh, bl);
+  // one pass over the matrix: D = [Tr; Ti] [Xr Xi]  (2n x 2nr)
+  SplitOperand A, B;
+  A.hi = T.rh; A.lo = T.rl; A.rows = 2 * n; A.ld = ldp;
+  B.hi = bh; B.lo = bl; B.rows = 2 * nr; B.ld = ldp;
   cudaError_t e;
-  // Re Y = Tr Xr -/+ Ti Xi      Im Y = Tr Xi +/- Ti Xr      (lower signs for conj(T))
-  {
-    SplitOperand A[2] = {Tr, Ti}, B[2] = {XR, XI};
-    int neg[2] = {0, conj ? 0 : 1};
-    if ((e = gemm_bf16x3(A, B, neg, 2, n, nr, n, Dr, nr, false, w.err, s)) != cudaSuccess) return e;
-  }
-  {
-    SplitOperand A[2] = {Tr, Ti}, B[2] = {XI, XR};
-    int neg[2] = {0, conj ? 1 : 0};
-    if ((e = gemm_bf16x3(A, B, neg, 2, n, nr, n, Di, nr, false, w.err, s)) != cudaSuccess) return e;
-  }
-  dim3 g2((unsigned)std::min((n + 255) / 256, 64), nr);
-  combine_kernel<<<g2, 256, 0, s>>>(Dr, Di, nr, n, nr, 0, scale, accumulate ? 1 : 0, Y);
+  if ((e = gemm_bf16x3(&A, &B, nullptr, 1, 2 * n, 2 * nr, n, w.D, 2 * nr, false, w.err, s, w.bn)) != cudaSuccess)
+    return e;
+  dim3 g2((n + CT - 1) / CT, (nr + CT - 1) / CT), b2(CT, 8);
+  combine_cplx_kernel<<<g2, b2, 0, s>>>(w.D, 2 * nr, n, nr, conj ? 1 : 0, 0, scale, accumulate ? 1 : 0, Y);
   return cudaGetLastError();
 }
 
@@ -422,9 +436,9 @@ cudaError_t real_gemm(const RealPlanes& P, const double2* X, double2* Y, int nr,
   A.hi = P.h; A.lo = P.l; A.rows = n; A.ld = ldp;
   B.hi = bh; B.lo = bl; B.rows = 2 * nr; B.ld = ldp;
   cudaError_t e;
-  if ((e = gemm_bf16x3(&A, &B, nullptr, 1, n, 2 * nr, n, w.D, 2 * nr, false, w.err, s)) != cudaSuccess) return e;
-  dim3 g2((unsigned)std::min((n + 255) / 256, 64), nr);
-  combine_kernel<<<g2, 256, 0, s>>>(w.D, w.D, 2 * nr, n, nr, nr, make_double2(scale, 0.0), accumulate ? 1 : 0, Y);
+  if ((e = gemm_bf16x3(&A, &B, nullptr, 1, n, 2 * nr, n, w.D, 2 * nr, false, w.err, s, w.bn)) != cudaSuccess) return e;
+  dim3 g2((n + CT - 1) / CT, (nr + CT - 1) / CT), b2(CT, 8);
+  combine_cplx_kernel<<<g2, b2, 0, s>>>(w.D, 2 * nr, n, nr, 0, 1, make_double2(scale, 0.0), accumulate ? 1 : 0, Y);
   return cudaGetLastError();
 }
 
@@ -445,11 +459,19 @@ cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int co
 }
 
 cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N,
-                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s) {
+                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s, int bn) {
   if (nseg < 1 || nseg > 2 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
-  if (N <= 32) return gemm_launch<32>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
-  if (N <= 64) return gemm_launch<64>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
-  return gemm_launch<128>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+  if (bn == 0) bn = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+  switch (bn) {
+    case 32:
+      return gemm_launch<32>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+    case 64:
+      return gemm_launch<64>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+    case 128:
+      return gemm_launch<128>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace rfcmp

@@ -108,7 +108,7 @@ __device__ __forceinline__ void flush_rows(double (&acc)[GEMV_ROWS_PER_WARP][NR]
 template <int NR, bool FF, bool CONJ>
 __global__ void __launch_bounds__(GEMV_WARPS * 32)
 gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
-                const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr) {
+                const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr, int chunk) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   double acc[GEMV_ROWS_PER_WARP][NR][2];
@@ -124,8 +124,8 @@ gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const float2* __res
       if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
       cur_rb = rb;
     }
-    const int cb = cc * GEMV_CHUNK;
-    const int npair = min(GEMV_CHUNK, ld - cb) / 2;
+    const int cb = cc * chunk;
+    const int npair = min(chunk, ld - cb) / 2;
     float fh[GEMV_ROWS_PER_WARP][NR][2], fl[GEMV_ROWS_PER_WARP][NR][2];
 #pragma unroll
     for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
@@ -196,7 +196,7 @@ template <int NR, bool FF>
 __global__ void __launch_bounds__(GEMV_WARPS * 32)
 gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, int ld, int n,
                 const float2* __restrict__ xh, const float2* __restrict__ xl, double2* __restrict__ out,
-                long long units, int upr) {
+                long long units, int upr, int chunk) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   double acc[GEMV_ROWS_PER_WARP][NR][2];
@@ -212,8 +212,8 @@ gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, in
       if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
       cur_rb = rb;
     }
-    const int cb = cc * GEMV_CHUNK;
-    const int nquad = min(GEMV_CHUNK, ld - cb) / 4;
+    const int cb = cc * chunk;
+    const int nquad = min(chunk, ld - cb) / 4;
     float fh[GEMV_ROWS_PER_WARP][NR][2], fl[GEMV_ROWS_PER_WARP][NR][2];
 #pragma unroll
     for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
@@ -311,6 +311,22 @@ int persistent_grid(K kernel) {
   return g;
 }
 
+// grid of a persistent GEMV launch: the work units, capped at SMs x CTAs per SM (the plan's
+// count, else the occupancy maximum)
+template <class K>
+long long gemv_grid(K kernel, long long units, const GemvScratch& w) {
+  long long cap = persistent_grid(kernel);
+  if (w.ctas_per_sm > 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cap = (long long)std::max(1, sms) * w.ctas_per_sm;
+  }
+  return std::max(1LL, std::min(units, cap));
+}
+
+int gemv_chunk(const GemvScratch& w) { return w.chunk > 0 ? w.chunk : GEMV_CHUNK; }
+
 cudaError_t gemv_prep(const double2* x, int n, int ld, int nr, bool ff, GemvScratch& w, cudaStream_t s) {
   dim3 grid(std::min((ld + 255) / 256, 4 * 152), nr);
   gemv_prep_kernel<<<grid, 256, 0, s>>>(x, n, ld, nr, w.xh, ff ? w.xl : nullptr, w.acc, n);
@@ -327,15 +343,16 @@ template <int NR>
 cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, bool conj, GemvMode mode, GemvScratch& w,
                               cudaStream_t s) {
   const int rowblocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
-  const int upr = (ld + GEMV_CHUNK - 1) / GEMV_CHUNK;
+  const int chunk = gemv_chunk(w);
+  const int upr = (ld + chunk - 1) / chunk;
   const long long units = (long long)rowblocks * upr;
   ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", 8.0 * n * n + 32.0 * n * NR,
                  8.0 * n * n * NR, s);
 #define RF_LAUNCH_C(FFV, CJ)                                                                      \
   {                                                                                               \
     auto k = gemv_c64_kernel<NR, FFV, CJ>;                                                        \
-    const int grid = (int)std::min<long long>(units, persistent_grid(k));                         \
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr);                  \
+    const int grid = (int)gemv_grid(k, units, w);                                                 \
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, chunk);           \
   }
   if (mode == GEMV_FF) {
     if (conj) RF_LAUNCH_C(true, true) else RF_LAUNCH_C(true, false)
@@ -350,18 +367,19 @@ template <int NR>
 cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n, GemvMode mode, GemvScratch& w,
                               cudaStream_t s) {
   const int rowblocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
-  const int upr = (ld + GEMV_CHUNK - 1) / GEMV_CHUNK;
+  const int chunk = gemv_chunk(w);
+  const int upr = (ld + chunk - 1) / chunk;
   const long long units = (long long)rowblocks * upr;
   ProfScope prof(mode == GEMV_FF ? "gemv_r32_ff" : "gemv_r32_f32",
                  (mode == GEMV_FF ? 8.0 : 4.0) * n * n + 32.0 * n * NR, 4.0 * n * n * NR, s);
   if (mode == GEMV_FF) {
     auto k = gemv_r32_kernel<NR, true>;
-    const int grid = (int)std::min<long long>(units, persistent_grid(k));
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr);
+    const int grid = (int)gemv_grid(k, units, w);
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr, chunk);
   } else {
     auto k = gemv_r32_kernel<NR, false>;
-    const int grid = (int)std::min<long long>(units, persistent_grid(k));
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr);
+    const int grid = (int)gemv_grid(k, units, w);
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr, chunk);
   }
   return cudaGetLastError();
 }
@@ -414,7 +432,7 @@ cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y,
         cudaSuccess)                                                                             \
       break;                                                                                     \
     const int grid = (int)std::min<long long>(units, (long long)sms * std::max(1, per));         \
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr);                 \
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, GEMV_CHUNK);     \
   }
 #define RF_PLAIN_NR(NRV)                                           \
   if (mode == GEMV_FF) {                                           \

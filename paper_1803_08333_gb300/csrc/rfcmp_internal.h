@@ -104,7 +104,9 @@ struct DeviceGeometry {
 
 // ---------------------------------------------------------------- kernels (k_assembly.cu)
 // T_A (ne x ne) and V (nc x nc), complex64 row-major, must be zeroed by the caller.
-cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, float2* V, cudaStream_t s);
+// min_blocks: resident CTAs per SM the register allocation is sized for (1, 2 or 3; 0 = 2)
+cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, float2* V, int min_blocks,
+                                cudaStream_t s);
 cudaError_t launch_assemble_near(const DeviceGeometry& g, double k, float2* TA, float2* V, cudaStream_t s);
 // T_A is accumulated in its upper triangle; this copies it to the lower one (bit-identical symmetry)
 cudaError_t launch_mirror_upper(float2* M, int n, int ld, cudaStream_t s);
@@ -127,13 +129,14 @@ struct SplitOperand {
 // D[M x N] = sum_g (negate[g] ? -1 : 1) A_g B_g^T (+ D), three BF16 products per K step into an
 // FP32 tensor-memory accumulator (tcgen05).  nseg 1 or 2.  err_dev receives a nonzero code if a
 // bounded device-side wait gave up.
+// bn selects the N tile (32, 64 or 128); 0 picks it from N.
 cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N,
-                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s);
+                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s, int bn = 0);
 cudaError_t split_bf16_f32(const float* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
                            __nv_bfloat16* lo, long long ld_dst, cudaStream_t s);
 
 // BF16 planes of the resident blocks for the multi-right-hand-side products.
-struct CplxPlanes {  // complex n x n: Re hi/lo, Im hi/lo, row stride ldp
+struct CplxPlanes {  // complex n x n: Re hi/lo, Im hi/lo, row stride ldp; ih = rh + n ldp, il = rl + n ldp
   __nv_bfloat16 *rh = nullptr, *rl = nullptr, *ih = nullptr, *il = nullptr;
   int n = 0;
   long long ldp = 0;
@@ -147,10 +150,11 @@ struct RealPlanes {  // real n x n: hi/lo, row stride ldp
 // products (2 x cap_n x cap_cols); err receives device-side timeout codes.
 struct MrhsScratch {
   __nv_bfloat16* xb = nullptr;
-  float* D = nullptr;
+  float* D = nullptr;  // 4 x cap_cols x cap_n
   int* err = nullptr;
   int cap_cols = 0, cap_n = 0;
   long long cap_ld = 0;
+  int bn = 0;  // GEMM N tile (32, 64, 128; 0 = by column count)
 };
 cudaError_t split_c64_planes(const float2* M, int n, long long ld, const CplxPlanes& P, cudaStream_t s);
 // Y = scale * op(T) X (+ Y) with op = conj if conj; X, Y complex128 column-major n x nr.
@@ -173,6 +177,8 @@ struct GemvScratch {
   float2* xl = nullptr;   // cap_cols x cap_ld
   double2* acc = nullptr; // cap_cols x cap_n
   int cap_n = 0, cap_ld = 0, cap_cols = 0;
+  int chunk = 0;          // columns per work unit (multiple of 256; 0 = 1024)
+  int ctas_per_sm = 0;    // persistent CTAs per SM (0 = occupancy maximum)
 };
 int padded_ld(int n);
 

@@ -39,7 +39,7 @@ def op_footprint(nv: int, nc: int, nrhs: int, with_factors: bool) -> int:
     ne = 3 * nc // 2
     pad = lambda n: (n + 63) // 64 * 64  # noqa: E731
     ops = 8 * pad(ne) * ne + 8 * pad(nc) * nc  # T_A, V complex64
-    if nrhs >= 16:
+    if nrhs >= 4:
         ops *= 2  # BF16 planes for the tensor-core products
     fac = 8 * pad(nc) * nc + 8 * pad(nv) * nv if with_factors else 0
     transient = 64 * nc * nc if with_factors else 0  # factor build work arrays
@@ -77,13 +77,14 @@ class Result:
 class GpuBackend:
     """Operators of the library; one context shared by all workers."""
 
-    def __init__(self, device: int = 0, hbm_budget: int = 0, power_steps: int = 30):
+    def __init__(self, device: int = 0, hbm_budget: int = 0, power_steps: int = 30, tuning=None):
         import paper_1803_08333_gb300 as rf
 
         self.rf = rf
         self.ctx = rf.Context(device, hbm_budget)
         self.device = device
         self.power_steps = power_steps
+        self.tuning = tuning  # autotune.Table whose plans the solves take, or None
 
     def make_stream(self):
         import torch
@@ -92,7 +93,9 @@ class GpuBackend:
         return torch.cuda.Stream(device=self.device)
 
     def create(self, req: Request):
-        return self.rf.Operator(self.ctx, req.verts, req.tris, req.k, power_steps=self.power_steps)
+        op = self.rf.Operator(self.ctx, req.verts, req.tris, req.k, power_steps=self.power_steps)
+        op.tuning = self.tuning
+        return op
 
     def nbytes(self, op) -> int:
         return int(op.info().device_bytes)

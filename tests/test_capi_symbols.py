@@ -54,6 +54,21 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(rf.SolveOpts) == 8 + 4 + 4 + 8 + 4 + 4 + 4 * 8
     assert ctypes.sizeof(rf.SolveReport) == 4 * 4 + 8
     assert ctypes.sizeof(rf.OpInfo) == 3 * 8 + 2 * 4 + 4 * 8 + 8 + 3 * 8 + 2 * 4
+    assert ctypes.sizeof(rf.Plan) == 8 * 4
+
+
+def test_plan_defaults_and_argument_checks(libpath):
+    L = rf.lib()
+    p = rf.Plan()
+    p.mrhs_min, p.gemm_bn = 7, 64
+    L.rfcmp_plan_default(ctypes.byref(p))
+    assert p.as_dict() == {k: 0 for k in rf.Plan.KEYS}
+    assert L.rfcmp_op_set_plan(None, ctypes.byref(p)) == -1
+    assert L.rfcmp_ctx_set_plan(None, ctypes.byref(p)) == -1
+    assert L.rfcmp_op_get_plan(None, ctypes.byref(p)) == -1
+    assert rf.Plan.of({"gemm_bn": 32}).gemm_bn == 32
+    with pytest.raises(KeyError):
+        rf.Plan.of({"tile": 3})
 
 
 def test_no_device_is_an_error_not_a_fallback(libpath):

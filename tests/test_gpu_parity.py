@@ -197,11 +197,16 @@ def test_multi_rhs_columns_independent(ctx, memo):
     op = rf.Operator(ctx, m.verts, m.tris, 1.2)
     kh, pol = synth.random_plane_waves(5, seed=8)
     e = op.rhs_planewave(kh, pol)
-    jb, rb = op.solve(e, tol=1e-10)
+    jb, rb = op.solve(e, tol=1e-10)  # 5 columns: inner products on the tensor cores
+    op.set_plan({"mrhs_min": 65536})
+    jg, rg = op.solve(e, tol=1e-10)  # the same batch on the FP32 GEMV, the single columns' arithmetic
+    op.set_plan(None)
     for c in (0, 3):
         j1, r1 = op.solve(e[c : c + 1], tol=1e-10)
-        assert _rel(jb[c].cpu().numpy(), j1[0].cpu().numpy()) <= 1e-8
-    assert all(r.converged for r in rb)
+        assert _rel(jg[c].cpu().numpy(), j1[0].cpu().numpy()) <= 1e-8
+        # other inner arithmetic, same system at residual 1e-10: agreement to about cond * 1e-10
+        assert _rel(jb[c].cpu().numpy(), j1[0].cpu().numpy()) <= 1e-7
+    assert all(r.converged for r in rb + rg)
 
 
 def test_solve_host_buffers(ctx, memo):
@@ -248,7 +253,10 @@ def test_scaling_warm_start_across_a_sweep(ctx, memo):
     e = warm.rhs_planewave(*synth.plane_wave_z())
     j, rep = warm.solve(e, tol=1e-10)
     jc, _ = cold.solve(e, tol=1e-10)
-    assert rep[0].converged and _rel(j.cpu().numpy(), jc.cpu().numpy()) <= 1e-8
+    # alpha, beta, gamma differ by up to 2%, so these are two preconditioned systems, each solved
+    # to residual 1e-10: their currents agree to about cond * 1e-10 (FP64 atomics make the last
+    # digits vary between runs)
+    assert rep[0].converged and _rel(j.cpu().numpy(), jc.cpu().numpy()) <= 1e-7
 
 
 @pytest.mark.parametrize("name,k", [("l3", 1.0), ("l2", 1e-4)])
