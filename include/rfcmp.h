@@ -277,7 +277,12 @@ typedef struct {
   int32_t gemv_ctas_per_sm; /* persistent GEMV CTAs per SM, 1..8; default the occupancy maximum */
   int32_t far_min_blocks;   /* far-pair assembly CTAs per SM its registers are sized for: 1, 2, 3;
                                default 2 (read at rfcmp_op_create) */
-  int32_t reserved[3];      /* must be zero */
+  int32_t exact_min;        /* float-float accurate products of at least this many columns run as
+                               exact-digit tensor-core products (each value as 6 signed 8-bit digits
+                               under a power-of-two row scale, integer level sums exact in the FP32
+                               accumulators; about 2^-48 of the row and column maxima per term),
+                               narrower ones on the float-float GEMV; 1..65536, default 8 */
+  int32_t reserved[2];      /* must be zero */
 } rfcmp_plan;
 /* Fills plan with zeros (every field at its built-in choice). */
 void rfcmp_plan_default(rfcmp_plan* plan);

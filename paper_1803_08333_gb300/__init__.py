@@ -51,9 +51,10 @@ class Plan(ctypes.Structure):
 
     _fields_ = [
         ("mrhs_min", ctypes.c_int32), ("gemm_bn", ctypes.c_int32), ("gemv_chunk", ctypes.c_int32),
-        ("gemv_ctas_per_sm", ctypes.c_int32), ("far_min_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+        ("gemv_ctas_per_sm", ctypes.c_int32), ("far_min_blocks", ctypes.c_int32), ("exact_min", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
-    KEYS = ("mrhs_min", "gemm_bn", "gemv_chunk", "gemv_ctas_per_sm", "far_min_blocks")
+    KEYS = ("mrhs_min", "gemm_bn", "gemv_chunk", "gemv_ctas_per_sm", "far_min_blocks", "exact_min")
 
     @classmethod
     def of(cls, d: "dict | None") -> "Plan":

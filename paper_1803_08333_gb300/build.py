@@ -17,7 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librfcmp.so")
-SOURCES = ["k_assembly.cu", "k_linalg.cu", "k_gemm.cu", "k_factor.cu", "capi.cu", "noalloc.cu", "topology.cpp", "amg.cpp"]
+SOURCES = [
+    "k_assembly.cu", "k_linalg.cu", "k_gemm.cu", "k_exact.cu", "k_factor.cu", "capi.cu", "noalloc.cu", "topology.cpp",
+    "amg.cpp",
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +35,8 @@ def _stale(srcs, target) -> bool:
     if not os.path.exists(target):
         return True
     t = os.path.getmtime(target)
-    deps = srcs + [os.path.join(CSRC, "rfcmp_internal.h"), os.path.join(HERE, "..", "include", "rfcmp.h"), __file__]
+    deps = srcs + [os.path.join(CSRC, h) for h in ("rfcmp_internal.h", "tc_common.cuh")]
+    deps += [os.path.join(HERE, "..", "include", "rfcmp.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

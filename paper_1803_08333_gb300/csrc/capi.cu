@@ -165,6 +165,10 @@ constexpr int NS_MIN_CELLS = 256;
 // bytes as the complex64 matrix) serves every column, so from about 4 columns on it beats the
 // GEMV's pass per 4 columns (measured on GB300 from 2k to 31k unknowns).
 constexpr int MRHS_MIN = 4;
+// Float-float accurate products (right-hand side, refinement residuals, accurate applications)
+// with at least this many columns run as exact-digit tensor-core products instead of the
+// float-float GEMV, which spends some 40 FP32 instructions per complex multiply-add.
+constexpr int EXACT_MIN = 8;
 constexpr double NS_START_TOL = 1e-2;
 
 struct DenseFactor {
@@ -172,6 +176,7 @@ struct DenseFactor {
   int ns_steps = 0;
   double ns_residual = 0.0;
   RealPlanes planes;  // BF16 hi/lo of the FP32 hi plane, built on the first multi-RHS product
+  ExactOperand digits;  // exact-digit planes of hi + lo, built on the first accurate multi-RHS product
   std::mutex planes_mu;
   float* hi = nullptr;
   float* lo = nullptr;
@@ -183,6 +188,8 @@ struct DenseFactor {
     if (lo) cudaFree(lo);
     if (planes.h) cudaFree(planes.h);
     if (planes.l) cudaFree(planes.l);
+    if (digits.d) cudaFree(digits.d);
+    if (digits.e) cudaFree(digits.e);
   }
 };
 
@@ -246,6 +253,7 @@ struct rfcmp_op {
   std::unique_ptr<SolveBuffers> sb;
   double2* power_vecs = nullptr;  // N x 3: final iterates of the X, Z and Y power iterations
   CplxPlanes ta_planes, v_planes;  // BF16 planes of T_A and V, built on the first multi-RHS product
+  ExactOperand ta_digits, v_digits;  // exact-digit planes of T_A and V, built on the first accurate one
   rfcmp_plan plan{};               // launch shapes (zero fields: built-in choices)
   ~rfcmp_op() {
     for (void* p : owned) cudaFree(p);
@@ -263,6 +271,8 @@ uint64_t mix(uint64_t h, uint64_t v) {
 
 // columns from which inner-iteration products take the tensor cores
 int plan_mrhs(const rfcmp_op* op) { return op->plan.mrhs_min > 0 ? op->plan.mrhs_min : MRHS_MIN; }
+// columns from which float-float accurate products take the exact-digit tensor-core GEMM
+int plan_exact(const rfcmp_op* op) { return op->plan.exact_min > 0 ? op->plan.exact_min : EXACT_MIN; }
 
 void plan_to_scratch(rfcmp_op* op) {
   op->ws->gs.chunk = op->plan.gemv_chunk;
@@ -271,7 +281,8 @@ void plan_to_scratch(rfcmp_op* op) {
 }
 
 int ensure_workspace(rfcmp_op* op, int cols) {
-  if (op->ws && op->ws->cols >= cols && (cols < plan_mrhs(op) || op->ws->ms.cap_cols >= cols)) {
+  if (op->ws && op->ws->cols >= cols && (cols < plan_mrhs(op) || (op->ws->ms.xb && op->ws->ms.cap_cols >= cols)) &&
+      (cols < plan_exact(op) || (op->ws->ms.xd && op->ws->ms.cap_cols >= cols))) {
     plan_to_scratch(op);
     return RFCMP_OK;
   }
@@ -291,14 +302,22 @@ int ensure_workspace(rfcmp_op* op, int cols) {
     RF_TRY(dalloc(&ws->gs.xh, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.xl, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.acc, (size_t)capn * 4, ws->owned));
-    if (cols >= plan_mrhs(op)) {
+    const bool bf = cols >= plan_mrhs(op), ex = cols >= plan_exact(op);
+    if (bf || ex) {
       ws->ms.cap_cols = cols;
       ws->ms.cap_n = capn;
       ws->ms.cap_ld = padded_ld(capn);
-      RF_TRY(dalloc(&ws->ms.xb, (size_t)4 * cols * ws->ms.cap_ld, ws->owned));
-      RF_TRY(dalloc(&ws->ms.D, (size_t)4 * cols * capn, ws->owned));
       RF_TRY(dalloc(&ws->ms.err, 1, ws->owned));
       RF_CUDA(cudaMemset(ws->ms.err, 0, sizeof(int)));
+    }
+    if (bf) {
+      RF_TRY(dalloc(&ws->ms.xb, (size_t)4 * cols * ws->ms.cap_ld, ws->owned));
+      RF_TRY(dalloc(&ws->ms.D, (size_t)4 * cols * capn, ws->owned));
+    }
+    if (ex) {
+      RF_TRY(dalloc(&ws->ms.xd, (size_t)EXACT_DIGITS * 2 * cols * ws->ms.cap_ld, ws->owned));
+      RF_TRY(dalloc(&ws->ms.xe, (size_t)2 * cols, ws->owned));
+      RF_TRY(dalloc(&ws->ms.D64, (size_t)4 * cols * capn, ws->owned));
     }
   }
   op->ws = std::move(ws);
@@ -374,9 +393,77 @@ int ensure_planes(rfcmp_op* op, cudaStream_t st) {
   return RFCMP_OK;
 }
 
+// Reads the tensor-core products' error flag (set when a bounded device-side wait gave up).
+int check_tensor_core_waits(rfcmp_op* op, cudaStream_t st) {
+  if (!op->ws || !op->ws->ms.err) return RFCMP_OK;
+  int h_err = 0;
+  RF_CUDA(cudaMemcpyAsync(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  if (h_err) {
+    RF_CUDA(cudaMemsetAsync(op->ws->ms.err, 0, sizeof(int), st));
+    return set_error(RFCMP_ERR_DEVICE_TIMEOUT,
+                     "a tensor-core product gave up a bounded wait (code " + std::to_string(h_err) + ")");
+  }
+  return RFCMP_OK;
+}
+
+int alloc_digits(ExactOperand& q, int rows, long long ldp, std::vector<void*>* owned) {
+  q.rows = rows;
+  q.ldp = ldp;
+  q.plane_stride = (long long)rows * ldp;
+  if (owned) {
+    RF_TRY(dalloc(&q.d, (size_t)EXACT_DIGITS * q.plane_stride, *owned));
+    RF_TRY(dalloc(&q.e, (size_t)rows, *owned));
+  } else {
+    RF_CUDA(cudaMalloc(&q.d, (size_t)EXACT_DIGITS * q.plane_stride * sizeof(__nv_bfloat16)));
+    RF_CUDA(cudaMalloc(&q.e, (size_t)rows * sizeof(int)));
+  }
+  return RFCMP_OK;
+}
+
+int make_cplx_digits(rfcmp_op* op, const float2* M, int n, int ld, ExactOperand& P, cudaStream_t st) {
+  if (P.d) return RFCMP_OK;
+  ExactOperand q;
+  RF_TRY(alloc_digits(q, 2 * n, ld, &op->owned));
+  RF_K(exact_digits_c64(M, n, ld, q, st));
+  const uint64_t b = (uint64_t)EXACT_DIGITS * q.plane_stride * sizeof(__nv_bfloat16) + 2ull * n * sizeof(int);
+  op->bytes += b;
+  op->ctx->bytes += b;
+  P = q;
+  return RFCMP_OK;
+}
+
+int make_real_digits(rfcmp_op* op, DenseFactor& f, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(f.planes_mu);
+  if (f.digits.d) return RFCMP_OK;
+  ExactOperand q;
+  RF_TRY(alloc_digits(q, f.n, padded_ld(f.n), nullptr));
+  RF_K(exact_digits_f32pair(f.hi, f.lo, f.n, q.ldp, q, st));
+  const uint64_t b = (uint64_t)EXACT_DIGITS * q.plane_stride * sizeof(__nv_bfloat16) + (uint64_t)f.n * sizeof(int);
+  f.bytes += b;
+  op->ctx->bytes += b;
+  f.digits = q;
+  return RFCMP_OK;
+}
+
+int ensure_digits(rfcmp_op* op, cudaStream_t st) {
+  RF_TRY(make_cplx_digits(op, op->TA, (int)op->top.ne, op->ldN, op->ta_digits, st));
+  RF_TRY(make_cplx_digits(op, op->V, (int)op->top.nc, op->ldC, op->v_digits, st));
+  RF_TRY(make_real_digits(op, *op->lplus, st));
+  RF_TRY(make_real_digits(op, *op->gll, st));
+  return RFCMP_OK;
+}
+
 // y = scale * op(M) x (+ y) for M = T_A or V: GEMV, or the tensor-core product for wide FP32 blocks
+// (split-BF16 in the inner iterations, exact digits where float-float accuracy is asked)
 int prod_c(rfcmp_op* op, bool ta, const double2* x, double2* y, int nr, bool conj, double2 scale, bool acc,
            GemvMode m, cudaStream_t st) {
+  if (m == GEMV_FF && nr >= plan_exact(op)) {
+    RF_TRY(ensure_digits(op, st));
+    RF_K(exact_cplx_gemm(ta ? op->ta_digits : op->v_digits, ta ? (int)op->top.ne : (int)op->top.nc, x, y, nr, conj,
+                         scale, acc, op->ws->ms, st));
+    return RFCMP_OK;
+  }
   if (m == GEMV_F32 && nr >= plan_mrhs(op)) {
     RF_TRY(ensure_planes(op, st));
     RF_K(cplx_gemm(ta ? op->ta_planes : op->v_planes, x, y, nr, conj, scale, acc, op->ws->ms, st));
@@ -390,6 +477,11 @@ int prod_c(rfcmp_op* op, bool ta, const double2* x, double2* y, int nr, bool con
 // y = scale * F x (+ y) for a dense real factor
 int prod_r(rfcmp_op* op, DenseFactor& f, const double2* x, double2* y, int nr, double scale, bool acc, GemvMode m,
            cudaStream_t st) {
+  if (m == GEMV_FF && nr >= plan_exact(op)) {
+    RF_TRY(ensure_digits(op, st));
+    RF_K(exact_real_gemm(f.digits, f.n, x, y, nr, scale, acc, op->ws->ms, st));
+    return RFCMP_OK;
+  }
   if (m == GEMV_F32 && nr >= plan_mrhs(op)) {
     RF_TRY(ensure_planes(op, st));
     RF_K(real_gemm(f.planes, x, y, nr, scale, acc, op->ws->ms, st));
@@ -478,9 +570,9 @@ int apply_rhs(rfcmp_op* op, const double2* e, double2* out, int nr, GemvMode m, 
   const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
   RF_TRY(star_coeff(op, e, W.s, W.zu, nr, m, st));  // ze
   RF_K(star_middle(g, W.zu, nullptr, 1.0, W.q0, nr, W.mean, st));
-  RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, op->ws->gs, st));
+  RF_TRY(prod_r(op, *op->lplus, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
   RF_K(lambda_t(g, e, W.t, nr, st));
-  RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, op->ws->gs, st));
+  RF_TRY(prod_r(op, *op->gll, W.t, W.tg, nr, 1.0, false, m, st));
   {
     EdgeCombo c;
     c.zl = W.tg;
@@ -493,9 +585,9 @@ int apply_rhs(rfcmp_op* op, const double2* e, double2* out, int nr, GemvMode m, 
     c.d = c2(1.0, 0.0);
     RF_K(edge_combo(g, c, W.y, nr, st));
   }
-  RF_K(gemv_c64(op->TA, N, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, op->ws->gs, st));
+  RF_TRY(prod_c(op, true, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
   RF_K(lap_apply(g, W.q, W.Lq, nr, st));
-  RF_K(gemv_c64(op->V, C, W.Lq, W.vp, nr, true, c2(1.0, 0.0), false, m, op->ws->gs, st));
+  RF_TRY(prod_c(op, false, W.Lq, W.vp, nr, true, c2(1.0, 0.0), false, m, st));
   {  // th = -ik up + (i/k) Sigma vp
     EdgeCombo c;
     c.x = W.up;
@@ -1163,23 +1255,23 @@ int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout
   Workspace& W = *op->ws;
   switch (which) {
     case RFCMP_APPLY_T_A:
-      RF_K(gemv_c64(op->TA, N, x, y, nr, false, c2(1, 0), false, m, op->ws->gs, st));
-      return RFCMP_OK;
+      RF_TRY(prod_c(op, true, x, y, nr, false, c2(1, 0), false, m, st));
+      return nr >= plan_exact(op) ? check_tensor_core_waits(op, st) : RFCMP_OK;
     case RFCMP_APPLY_T_PHI: {
       RF_K(sigma_t(op->g, x, W.s, nr, st));
-      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, false, c2(1, 0), false, m, op->ws->gs, st));
+      RF_TRY(prod_c(op, false, W.s, W.w, nr, false, c2(1, 0), false, m, st));
       EdgeCombo c;
       c.zs = W.w;
       c.b = c2(1, 0);
       RF_K(edge_combo(op->g, c, y, nr, st));
-      return RFCMP_OK;
+      return nr >= plan_exact(op) ? check_tensor_core_waits(op, st) : RFCMP_OK;
     }
     case RFCMP_APPLY_T:
     case RFCMP_APPLY_T_ADJ: {
       const bool adj = which == RFCMP_APPLY_T_ADJ;
       RF_K(sigma_t(op->g, x, W.s, nr, st));
-      RF_K(gemv_c64(op->V, C, W.s, W.w, nr, adj, c2(1, 0), false, m, op->ws->gs, st));
-      RF_K(gemv_c64(op->TA, N, x, W.u, nr, adj, c2(1, 0), false, m, op->ws->gs, st));
+      RF_TRY(prod_c(op, false, W.s, W.w, nr, adj, c2(1, 0), false, m, st));
+      RF_TRY(prod_c(op, true, x, W.u, nr, adj, c2(1, 0), false, m, st));
       // T x = i k T_A x - (i/k) Sigma V Sigma^T x ; T^H x = -i k conj(T_A) x + (i/k) Sigma conj(V) Sigma^T x
       EdgeCombo c;
       c.x = W.u;
@@ -1187,24 +1279,14 @@ int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout
       c.zs = W.w;
       c.b = c2(0.0, adj ? 1.0 / k : -1.0 / k);
       RF_K(edge_combo(op->g, c, y, nr, st));
-      return RFCMP_OK;
+      return nr >= plan_exact(op) ? check_tensor_core_waits(op, st) : RFCMP_OK;
     }
     case RFCMP_APPLY_A:
-      return apply_A(op, x, y, nr, m, st);
-    case RFCMP_APPLY_A_INNER: {
+      RF_TRY(apply_A(op, x, y, nr, m, st));
+      return nr >= plan_exact(op) ? check_tensor_core_waits(op, st) : RFCMP_OK;
+    case RFCMP_APPLY_A_INNER:
       RF_TRY(apply_A(op, x, y, nr, GEMV_F32, st));
-      if (nr >= plan_mrhs(op) && op->ws->ms.err) {  // the tensor-core products' bounded waits
-        int h_err = 0;
-        RF_CUDA(cudaMemcpyAsync(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        RF_CUDA(cudaStreamSynchronize(st));
-        if (h_err) {
-          RF_CUDA(cudaMemsetAsync(op->ws->ms.err, 0, sizeof(int), st));
-          return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a tensor-core product gave up a bounded wait (code " +
-                                                         std::to_string(h_err) + ")");
-        }
-      }
-      return RFCMP_OK;
-    }
+      return nr >= plan_mrhs(op) ? check_tensor_core_waits(op, st) : RFCMP_OK;
     default:
       return set_error(RFCMP_ERR_INVALID_ARG, "unknown operator id");
   }
@@ -1216,8 +1298,9 @@ void rfcmp_plan_default(rfcmp_plan* plan) {
 
 namespace {
 int check_plan(const rfcmp_plan& p) {
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (p.reserved[i] != 0) return set_error(RFCMP_ERR_INVALID_ARG, "plan.reserved must be zero");
+  if (p.exact_min < 0 || p.exact_min > 65536) return set_error(RFCMP_ERR_INVALID_ARG, "plan.exact_min out of range");
   if (p.mrhs_min < 0 || p.mrhs_min > 65536) return set_error(RFCMP_ERR_INVALID_ARG, "plan.mrhs_min out of range");
   if (p.gemm_bn != 0 && p.gemm_bn != 32 && p.gemm_bn != 64 && p.gemm_bn != 128)
     return set_error(RFCMP_ERR_INVALID_ARG, "plan.gemm_bn must be 0, 32, 64 or 128");
@@ -1291,9 +1374,9 @@ int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c12
       const int C = (int)op->top.nc, NV = (int)op->top.nv;
       RF_TRY(star_coeff(op, x, W.s, W.zu, nr, m, st));
       RF_K(star_middle(op->g, W.zu, nullptr, 1.0, W.q0, nr, W.mean, st));
-      RF_K(gemv_r32(op->lplus->hi, op->lplus->lo, C, W.q0, W.q, nr, 1.0 / (b * b), false, m, op->ws->gs, st));
+      RF_TRY(prod_r(op, *op->lplus, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
       RF_K(lambda_t(op->g, x, W.t, nr, st));
-      RF_K(gemv_r32(op->gll->hi, op->gll->lo, NV, W.t, W.tg, nr, 1.0, false, m, op->ws->gs, st));
+      RF_TRY(prod_r(op, *op->gll, W.t, W.tg, nr, 1.0, false, m, st));
       EdgeCombo c;
       c.zl = W.tg;
       c.c = c2(1.0 / (a * a), 0.0);
@@ -1304,7 +1387,7 @@ int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c12
       c.zs2 = W.q;
       c.d = c2(1.0, 0.0);
       RF_K(edge_combo(op->g, c, y, nr, st));
-      return RFCMP_OK;
+      return nr >= plan_exact(op) ? check_tensor_core_waits(op, st) : RFCMP_OK;
     }
     default:
       return set_error(RFCMP_ERR_INVALID_ARG, "unknown preconditioner id");

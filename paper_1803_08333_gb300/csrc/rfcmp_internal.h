@@ -155,7 +155,33 @@ struct MrhsScratch {
   int cap_cols = 0, cap_n = 0;
   long long cap_ld = 0;
   int bn = 0;  // GEMM N tile (32, 64, 128; 0 = by column count)
+  // exact-digit products (float-float accurate multi-column products)
+  __nv_bfloat16* xd = nullptr;  // EXACT_DIGITS planes of 2 cap_cols x cap_ld
+  int* xe = nullptr;            // 2 cap_cols row exponents
+  double* D64 = nullptr;        // 4 x cap_cols x cap_n
 };
+
+// Exact-digit operands: every row r scaled by 2^e[r] and written as EXACT_DIGITS signed 8-bit
+// digits, plane p of rows x ldp BF16 at d + p * plane_stride.
+constexpr int EXACT_DIGITS = 6;
+struct ExactOperand {
+  __nv_bfloat16* d = nullptr;
+  int* e = nullptr;
+  int rows = 0;
+  long long ldp = 0;
+  long long plane_stride = 0;
+};
+// digit planes of a complex64 matrix (n x n, row stride ld) as 2n rows [Re; Im]
+cudaError_t exact_digits_c64(const float2* M, int n, long long ld, const ExactOperand& out, cudaStream_t s);
+// digit planes of an FP64-accurate real matrix given as FP32 hi + lo planes
+cudaError_t exact_digits_f32pair(const float* hi, const float* lo, int n, long long ld, const ExactOperand& out,
+                                 cudaStream_t s);
+// Y = scale * op(T) X (+ Y) and Y = scale * P X (+ Y), float-float accurate (about 2^-48 of the
+// row and column scales per term), X, Y complex128 column-major n x nr.
+cudaError_t exact_cplx_gemm(const ExactOperand& T, int n, const double2* X, double2* Y, int nr, bool conj,
+                            double2 scale, bool accumulate, MrhsScratch& w, cudaStream_t s);
+cudaError_t exact_real_gemm(const ExactOperand& P, int n, const double2* X, double2* Y, int nr, double scale,
+                            bool accumulate, MrhsScratch& w, cudaStream_t s);
 cudaError_t split_c64_planes(const float2* M, int n, long long ld, const CplxPlanes& P, cudaStream_t s);
 // Y = scale * op(T) X (+ Y) with op = conj if conj; X, Y complex128 column-major n x nr.
 cudaError_t cplx_gemm(const CplxPlanes& T, const double2* X, double2* Y, int nr, bool conj, double2 scale,

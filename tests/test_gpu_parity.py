@@ -98,9 +98,13 @@ def test_excitation(ctx, memo, nrhs):
 
 
 @pytest.mark.parametrize("name,k", [("l2", 1.0), ("torus", 2.0), ("l2", 1e-4)])
-@pytest.mark.parametrize("nrhs", [1, 2, 5])
+@pytest.mark.parametrize("nrhs", [1, 2, 5, 12])
 def test_operator_applications_ff_accurate(ctx, memo, name, k, nrhs):
-    """T, T_A, T_Phi, T^H through the library equal FP64 products of its own stored matrices."""
+    """T, T_A, T_Phi, T^H through the library equal FP64 products of its own stored matrices.
+
+    From 8 columns on the products are exact-digit tensor-core GEMMs: 6 digits of 8 bits under
+    a power-of-two scale per row and per column, so each term carries a truncation of about
+    2^-48 of the row and column maxima; over N terms that stays below 1e-11 of the product."""
     m, D, _, _ = _oracle(memo, name, k)
     op = rf.Operator(ctx, m.verts, m.tris, k, scaling="k")
     gTA = op.export("T_A").cpu().numpy().astype(np.complex128)
@@ -111,9 +115,10 @@ def test_operator_applications_ff_accurate(ctx, memo, name, k, nrhs):
     S = D.Sigma.toarray()
     T = 1j * k * gTA + S @ gV @ S.T / (1j * k)
     refs = {"T_A": gTA @ x.T, "T_PHI": S @ gV @ S.T @ x.T, "T": T @ x.T, "T_ADJ": T.conj().T @ x.T}
+    tol = 1e-12 if nrhs < 8 else 1e-11
     for which, ref in refs.items():
         got = op.apply(which, xt).cpu().numpy().T
-        assert _rel(got, ref) <= 1e-12, which
+        assert _rel(got, ref) <= tol, (which, _rel(got, ref))
 
 
 @pytest.mark.parametrize("name,k", [("l2", 1.0), ("l2", 1e-3), ("torus", 1.5), ("cube", 0.5)])
@@ -125,9 +130,12 @@ def test_rfcmp_application_and_preconditioners(ctx, memo, name, k):
     gTA = op.export("T_A").cpu().numpy().astype(np.complex128)
     gV = op.export("V").cpu().numpy().astype(np.complex128)
     rng = np.random.default_rng(3)
-    x = rng.standard_normal((2, op.N)) + 1j * rng.standard_normal((2, op.N))
+    x = rng.standard_normal((9, op.N)) + 1j * rng.standard_normal((9, op.N))
+    wide = op.apply("A", torch.from_numpy(x)).cpu().numpy()  # 9 columns: exact-digit products
+    x = x[:2]
     got = op.apply("A", torch.from_numpy(x)).cpu().numpy()
     for c in range(2):
+        assert _rel(wide[c], got[c]) <= 1e-11, _rel(wide[c], got[c])
         # same stored matrices: the composition itself must match to float-float accuracy
         ref_same = rfcmp.apply_A(F, gTA, gV, k, sc, x[c])
         assert _rel(got[c], ref_same) <= 1e-9
