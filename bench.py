@@ -321,7 +321,8 @@ def _one_roofline(name, v, peaks, peak_kind, clk):
         return {"kernel": name, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(name),
                 "flops_per_launch": v["flops"] / v["launches"], "avg_launch_ms": round(avg_ms, 4),
-                "peak_source": "of %s bf16_tflops_sustained (issued BF16 MMA FLOPs: 3 split products)" % peak_kind}
+                "peak_source": "of %s bf16_tflops_sustained (issued BF16 MMA FLOPs: 3 split products for "
+                               "gemm_bf16x3, 21 digit-pair products for gemm_exact)" % peak_kind}
     bytes_per = v["bytes"] / max(v["launches"], 1)
     achieved = bytes_per / (avg_ms / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -486,6 +487,93 @@ def bench_serving(args):
         "clocks": clk, "data": "synthetic (seeded jittered spheres, cubes, ellipsoids; random plane waves)"}))
 
 
+def bench_batched(args):
+    """512 plane waves on the 41070-unknown ellipsoid at ka = 2: one multi-column mixed solve per step.
+
+    Beside it, the same right-hand sides one at a time in the float-float (FP64-equivalent)
+    single-column form, on a sample of columns, for the batched-vs-single comparison.
+    """
+    import torch
+
+    import paper_1803_08333_gb300 as rf
+    import synth
+    from paper_1803_08333_gb300 import autotune, build
+
+    build.build()
+    torch.cuda.set_device(0)
+    nrhs, ka = args.nrhs, 2.0
+    mesh = synth.ellipsoid(37)  # semi-axes 1.0 / 0.6 / 0.4, 27380 cells, 41070 unknowns
+    kh, pol = synth.random_plane_waves(nrhs, seed=77)
+    ctx = rf.Context(0)
+    table = None if args.no_tuning else autotune.Table.for_device(torch.cuda.get_device_name(0))
+    t0 = time.perf_counter()
+    op = rf.Operator(ctx, mesh.verts, mesh.tris, ka)  # the major semi-axis is 1 m: k = ka
+    op.tuning = table
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    e = op.rhs_planewave(kh, pol)
+    for _ in range(args.warmup):
+        op.solve(e, tol=TOL)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    rf.profile_enable(True)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = []
+    for _ in range(args.steps):
+        j, rep = op.solve(e, tol=TOL)
+        reps.append(rep)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = rf.profile_read()
+    rf.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    value = nrhs / (ms / 1e3)
+    peaks, peak_kind = _peaks()
+    roof, roof_more = roofline(prof, peaks, peak_kind, clk)
+    gpu_launches = int(sum(v["launches"] for v in prof.values()))
+    # end to end: host right-hand sides in, host currents out, through the C call with host buffers
+    eh = e.cpu().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    jh, _ = op.solve_host(eh, tol=TOL)
+    e2e_s = time.perf_counter() - t0
+    # the float-float single-column form on a sample of the columns
+    single = []
+    for c in range(args.single_sample):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, r1 = op.solve(e[c : c + 1], tol=TOL, precision="ff")
+        torch.cuda.synchronize()
+        single.append((time.perf_counter() - t0, r1[0]))
+    single_s = float(np.median([t for t, _ in single]))
+    last = reps[-1]
+    print(json.dumps({
+        "metric": "RF-CMP EFIE batched solves/s @1e-6 resid (512 plane waves, ellipsoid, ka=2)",
+        "value": round(value, 3), "unit": "right-hand sides/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32 operator; split-BF16 inner products; exact-digit residuals",
+        "data": "synthetic (seeded jittered ellipsoid, seeded plane waves)",
+        "config": {"workload": "batched_ellipsoid_n41070_rhs%d" % nrhs, "unknowns": op.N, "ka": ka, "nrhs": nrhs,
+                   "tol": TOL, "l2": "inputs larger than L2 (T_A complex64 13.5 GB)",
+                   "tuning": "table" if table is not None else "built-in"},
+        "setup_s": round(setup_s, 2),
+        "iterations": [min(r.iterations for r in last), max(r.iterations for r in last)],
+        "refinements": max(r.refinements for r in last),
+        "max_residual": max(r.residual for r in last),
+        "single_column_ff": {"solves_per_s": round(1.0 / single_s, 3), "sample_columns": args.single_sample,
+                             "iterations": [r.iterations for _, r in single],
+                             "max_residual": max(r.residual for _, r in single)},
+        "batched_over_single": round(value * single_s, 1),
+        "roofline": roof, "rooflines_next": roof_more, "gpu_launches": gpu_launches, "clocks": clk,
+        "e2e": {"value": round(nrhs / e2e_s, 3), "unit": "right-hand sides/s",
+                "h2d_bytes_per_step": int(eh.nbytes), "d2h_bytes_per_step": int(jh.nbytes)},
+    }))
+
+
 def bench_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -517,8 +605,11 @@ def main():
     ap.add_argument("--mesh-n", type=int, default=32,
                     help="geodesic frequency of the sphere (32 = the workload; smaller for profiling captures)")
     ap.add_argument("--ka", type=float, nargs="*", default=None, help="override the wavenumber sweep")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "serving"],
-                    help="sweep: the level-5 low-frequency sweep (default); serving: the Poisson request stream")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serving", "batched"],
+                    help="sweep: the level-5 low-frequency sweep (default); serving: the Poisson request stream; "
+                         "batched: 512 plane waves on the 41070-unknown ellipsoid")
+    ap.add_argument("--nrhs", type=int, default=512, help="batched: right-hand sides per solve")
+    ap.add_argument("--single-sample", type=int, default=3, help="batched: columns solved one at a time in FF")
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--workers", type=int, default=2)
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
@@ -533,6 +624,8 @@ def main():
         bench_reference(args)
     elif args.workload == "serving":
         bench_serving(args)
+    elif args.workload == "batched":
+        bench_batched(args)
     else:
         bench_ours(args)
 

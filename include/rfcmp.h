@@ -182,6 +182,12 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
                     double k, const rfcmp_op_opts* opts, rfcmp_op** out);
 int rfcmp_op_info_get(const rfcmp_op* op, rfcmp_op_info* out);
 int rfcmp_op_destroy(rfcmp_op* op);
+/* Releases what op built for wide products (the BF16 planes of the tensor-core inner products,
+ * the exact-digit planes of the accurate ones) and its solve workspace; the assembled T_A and V,
+ * the shared factors and the scaling stay.  The next wide call rebuilds them.  Synchronises the
+ * device.  (The paper has no counterpart: memory management for resident operators.)
+ * Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_CUDA. */
+int rfcmp_op_trim(rfcmp_op* op);
 
 /* Copies an internal matrix to a caller-owned DEVICE buffer of dst_bytes bytes.
  *  which 0: T_A, N x N complex64 row-major      (8 N^2 bytes)

@@ -34,6 +34,7 @@ EXPORTED_SYMBOLS = [
     "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
     "rfcmp_gemm_bf16x3", "rfcmp_plan_default", "rfcmp_ctx_set_plan", "rfcmp_op_set_plan", "rfcmp_op_get_plan",
+    "rfcmp_op_trim",
 ]
 
 
@@ -129,6 +130,7 @@ def lib():
         L.rfcmp_op_create.argtypes = [vp, vp, i64, vp, i64, dbl, ctypes.POINTER(OpOpts), ctypes.POINTER(vp)]
         L.rfcmp_op_info_get.argtypes = [vp, ctypes.POINTER(OpInfo)]
         L.rfcmp_op_destroy.argtypes = [vp]
+        L.rfcmp_op_trim.argtypes = [vp]
         L.rfcmp_op_export.argtypes = [vp, i32, vp, ctypes.c_uint64, vp]
         L.rfcmp_op_edges.argtypes = [vp, vp, vp]
         L.rfcmp_rhs_planewave.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -278,6 +280,10 @@ class Operator:
         out = OpInfo()
         _check(lib().rfcmp_op_info_get(self._h, ctypes.byref(out)))
         return out
+
+    def trim(self):
+        """Frees the planes, digits and workspace of wide products (rebuilt on the next wide call)."""
+        _check(lib().rfcmp_op_trim(self._h))
 
     def plan(self) -> dict:
         p = Plan()

@@ -35,8 +35,8 @@ GEMM_BNS = (32, 64, 128)
 FAR_MIN_BLOCKS = (1, 2, 3)
 # columns per call measured by default (the inner CG of a solve applies A to all active columns)
 NRHS_GRID = (1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 128, 256, 512)
-GEMV_ONLY = 65536  # mrhs_min that keeps every product on the GEMV
-GEMM_ALWAYS = 1    # mrhs_min that sends every multi-column product to the tensor cores
+GEMV_ONLY = 65536  # mrhs_min / exact_min that keeps every product on the GEMV
+GEMM_ALWAYS = 1    # mrhs_min / exact_min that sends every multi-column product to the tensor cores
 
 
 def device_slug(name: str) -> str:
@@ -168,6 +168,8 @@ def tune_operator(op, nrhs_list=NRHS_GRID, precision: str = "mixed", reps: int =
         knobs = [("gemv_chunk", GEMV_CHUNKS), ("gemv_ctas_per_sm", GEMV_CTAS)]
         if precision == "mixed" and nr >= 2:
             knobs = [("mrhs_min", (GEMM_ALWAYS, GEMV_ONLY))] + knobs + [("gemm_bn", GEMM_BNS)]
+        if precision == "ff" and nr >= 2:
+            knobs = [("exact_min", (GEMM_ALWAYS, GEMV_ONLY))] + knobs
         default = measure({})
         plan, ms, tried = coordinate_descent(measure, knobs)
         if precision == "mixed" and plan.get("mrhs_min", 0) == GEMV_ONLY:
@@ -218,7 +220,7 @@ def main(argv=None):
         m = synth.geodesic_sphere(n, seed=2)
         fmb, ftimes = tune_assembly(ctx, m.verts, m.tris, 1.0)
         op = Operator(ctx, m.verts, m.tris, 1.0)
-        for prec, nrl in (("mixed", args.nrhs), ("ff", [1, 4])):
+        for prec, nrl in (("mixed", args.nrhs), ("ff", [1, 2, 4, 8, 16])):
             for e in tune_operator(op, nrl, prec, args.reps):
                 e.plan["far_min_blocks"] = fmb
                 e.tried.update({"far_min_blocks=%d" % b: t for b, t in ftimes.items()})

@@ -254,9 +254,12 @@ struct rfcmp_op {
   double2* power_vecs = nullptr;  // N x 3: final iterates of the X, Z and Y power iterations
   CplxPlanes ta_planes, v_planes;  // BF16 planes of T_A and V, built on the first multi-RHS product
   ExactOperand ta_digits, v_digits;  // exact-digit planes of T_A and V, built on the first accurate one
+  std::vector<void*> lazy;           // the planes and digits above, released by rfcmp_op_trim
+  uint64_t lazy_bytes = 0;
   rfcmp_plan plan{};               // launch shapes (zero fields: built-in choices)
   ~rfcmp_op() {
     for (void* p : owned) cudaFree(p);
+    for (void* p : lazy) cudaFree(p);
   }
 };
 
@@ -356,12 +359,13 @@ int make_cplx_planes(rfcmp_op* op, const float2* M, int n, int ld, CplxPlanes& P
   q.ldp = ld;
   const size_t pl = (size_t)n * ld;
   // Re and Im rows stacked in one hi and one lo buffer: the product reads them as one 2n-row operand
-  RF_TRY(dalloc(&q.rh, 2 * pl, op->owned));
-  RF_TRY(dalloc(&q.rl, 2 * pl, op->owned));
+  RF_TRY(dalloc(&q.rh, 2 * pl, op->lazy));
+  RF_TRY(dalloc(&q.rl, 2 * pl, op->lazy));
   q.ih = q.rh + pl;
   q.il = q.rl + pl;
   RF_K(split_c64_planes(M, n, ld, q, st));
   op->bytes += 4 * pl * sizeof(__nv_bfloat16);
+  op->lazy_bytes += 4 * pl * sizeof(__nv_bfloat16);
   op->ctx->bytes += 4 * pl * sizeof(__nv_bfloat16);
   P = q;
   return RFCMP_OK;
@@ -424,10 +428,11 @@ int alloc_digits(ExactOperand& q, int rows, long long ldp, std::vector<void*>* o
 int make_cplx_digits(rfcmp_op* op, const float2* M, int n, int ld, ExactOperand& P, cudaStream_t st) {
   if (P.d) return RFCMP_OK;
   ExactOperand q;
-  RF_TRY(alloc_digits(q, 2 * n, ld, &op->owned));
+  RF_TRY(alloc_digits(q, 2 * n, ld, &op->lazy));
   RF_K(exact_digits_c64(M, n, ld, q, st));
   const uint64_t b = (uint64_t)EXACT_DIGITS * q.plane_stride * sizeof(__nv_bfloat16) + 2ull * n * sizeof(int);
   op->bytes += b;
+  op->lazy_bytes += b;
   op->ctx->bytes += b;
   P = q;
   return RFCMP_OK;
@@ -1180,6 +1185,24 @@ int rfcmp_op_info_get(const rfcmp_op* op, rfcmp_op_info* out) {
   if (op->ws) ws += (uint64_t)op->ws->cols * (5 * op->top.ne + 8 * op->top.nc + 2 * op->top.nv) * 16;
   if (op->sb) ws += (uint64_t)op->sb->cols * 8 * op->top.ne * 16;
   out->device_bytes = op->bytes + ws;
+  return RFCMP_OK;
+}
+
+int rfcmp_op_trim(rfcmp_op* op) {
+  if (!op) return set_error(RFCMP_ERR_INVALID_ARG, "NULL op");
+  RF_CUDA(cudaSetDevice(op->ctx->device));
+  RF_CUDA(cudaDeviceSynchronize());  // nothing of this op may still be reading what is freed
+  for (void* p : op->lazy) cudaFree(p);
+  op->lazy.clear();
+  op->ta_planes = CplxPlanes();
+  op->v_planes = CplxPlanes();
+  op->ta_digits = ExactOperand();
+  op->v_digits = ExactOperand();
+  op->ctx->bytes -= op->lazy_bytes;
+  op->bytes -= op->lazy_bytes;
+  op->lazy_bytes = 0;
+  op->ws.reset();
+  op->sb.reset();
   return RFCMP_OK;
 }
 

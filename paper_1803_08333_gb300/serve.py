@@ -34,17 +34,30 @@ def mesh_key(verts: np.ndarray, tris: np.ndarray) -> str:
     return h.hexdigest()[:16]
 
 
-def op_footprint(nv: int, nc: int, nrhs: int, with_factors: bool) -> int:
-    """Upper estimate of the device bytes an operator and one solve of nrhs columns need."""
+def op_footprint(nv: int, nc: int, nrhs: int, with_factors: bool, widest: int = 0) -> int:
+    """Upper estimate of the device bytes an operator and one solve of nrhs columns add.
+
+    The complex64 T_A and V come with the operator; the BF16 planes of the tensor-core inner
+    products (from 4 columns) and the exact-digit planes of the accurate products (from 8
+    columns) are built on the first solve that wide, so an operator whose widest solve so far
+    had `widest` columns only adds what that solve has not built yet.
+    """
     ne = 3 * nc // 2
     pad = lambda n: (n + 63) // 64 * 64  # noqa: E731
-    ops = 8 * pad(ne) * ne + 8 * pad(nc) * nc  # T_A, V complex64
-    if nrhs >= 4:
-        ops *= 2  # BF16 planes for the tensor-core products
-    fac = 8 * pad(nc) * nc + 8 * pad(nv) * nv if with_factors else 0
-    transient = 64 * nc * nc if with_factors else 0  # factor build work arrays
-    vectors = 16 * ne * max(nrhs, 4) * 24
-    return ops + fac + transient + vectors
+    cplx = pad(ne) * ne + pad(nc) * nc  # entries of T_A and V
+    real = pad(nc) * nc + pad(nv) * nv  # entries of (Sigma^T Sigma)^+ and G_ll^{-1}
+
+    def extra(w):
+        b = 0
+        if w >= 4:
+            b += 8 * cplx + (4 * real if with_factors else 0)  # BF16 hi/lo (Re and Im)
+        if w >= 8:
+            b += 24 * cplx + (12 * real if with_factors else 0)  # six BF16 digit planes
+        return b
+
+    base = 0 if widest else 8 * cplx + (8 * real + 64 * nc * nc if with_factors else 0)
+    vectors = 16 * ne * max(nrhs, 4) * 24 if nrhs > widest else 0
+    return base + extra(nrhs) - extra(widest) + vectors
 
 
 @dataclass
@@ -115,6 +128,12 @@ class GpuBackend:
     def bytes_in_use(self) -> int:
         return self.ctx.bytes_in_use()
 
+    def clear_cache(self):
+        self.ctx.clear_cache()
+
+    def trim(self, op):
+        op.trim()
+
 
 class Server:
     def __init__(self, backend, hbm_budget: int, workers: int = 2, max_batch_columns: int = 64):
@@ -123,7 +142,7 @@ class Server:
         self.max_cols = int(max_batch_columns)
         self._lock = threading.Condition()
         self._pending: collections.OrderedDict = collections.OrderedDict()  # scene -> deque of requests
-        self._ops: collections.OrderedDict = collections.OrderedDict()  # scene -> (op, bytes), LRU order
+        self._ops: collections.OrderedDict = collections.OrderedDict()  # scene -> (op, widest batch), LRU order
         self._busy: set = set()  # scenes being solved
         self._reserved = 0  # bytes promised to operators being created
         self._work: "collections.deque" = collections.deque()
@@ -184,8 +203,7 @@ class Server:
             self._reserved += need
         try:
             req = Request(-1, scene, verts, tris, float(k), np.zeros((1, 3)), np.zeros((1, 3)), 0.0, 0.0)
-            op = self.backend.create(req)
-            entry = (op, self.backend.nbytes(op))
+            entry = (self.backend.create(req), 1)
         finally:
             with self._lock:
                 self._busy.discard(scene)
@@ -222,18 +240,18 @@ class Server:
                 r = queue.popleft()
                 batch.append(r)
                 cols += r.nrhs
+            r0 = batch[0]
+            nv, nc = r0.verts.shape[0], r0.tris.shape[0]
             if scene in self._ops:
                 self._ops.move_to_end(scene)
-                need = 0
+                need = op_footprint(nv, nc, cols, with_factors=True, widest=self._ops[scene][1])
             else:
-                r0 = batch[0]
-                nv, nc = r0.verts.shape[0], r0.tris.shape[0]
                 shares_mesh = any(s[0] == scene[0] for s in self._ops)
                 need = op_footprint(nv, nc, cols, with_factors=not shares_mesh)
-                if not self._make_room(need):
-                    for r in reversed(batch):  # put back: wait for memory
-                        queue.appendleft(r)
-                    continue
+            if need > 0 and not self._make_room(need, keep=scene):
+                for r in reversed(batch):  # put back: wait for memory
+                    queue.appendleft(r)
+                continue
             self._busy.add(scene)
             self._reserved += need
             if not queue:
@@ -241,14 +259,33 @@ class Server:
             return scene, batch, need
         return None
 
-    def _make_room(self, need: int) -> bool:
-        """Evict idle operators (LRU first) until `need` bytes fit; False if they cannot."""
+    def _make_room(self, need: int, keep=None) -> bool:
+        """Evict idle operators (LRU first) until `need` bytes fit; False if they cannot.
+
+        When no idle operator is left, the context's factor cache (factors no resident operator
+        holds) is dropped as a last resort."""
         if self.budget <= 0:
             return True
-        while self.backend.bytes_in_use() + self._reserved + need > self.budget:
-            victim = next((s for s in self._ops if s not in self._busy), None)
+        def over():
+            return self.backend.bytes_in_use() + self._reserved + need > self.budget
+
+        # 1: idle operators drop what their wide solves built (rebuilt on their next wide solve)
+        for s in list(self._ops):
+            if not over():
+                return True
+            if s not in self._busy and s != keep and self._ops[s][1] >= 4:
+                self.backend.trim(self._ops[s][0])
+                self._ops[s] = (self._ops[s][0], 1)
+        # 2: idle operators leave, least recently used first; 3: the factor cache goes last
+        cleared = False
+        while over():
+            victim = next((s for s in self._ops if s not in self._busy and s != keep), None)
             if victim is None:
-                return False
+                if cleared:
+                    return False
+                self.backend.clear_cache()
+                cleared = True
+                continue
             op, _ = self._ops.pop(victim)
             self.backend.destroy(op)
         return True
@@ -268,8 +305,7 @@ class Server:
                 entry = self._ops.get(scene)
             try:
                 if entry is None:
-                    op = self.backend.create(batch[0])
-                    entry = (op, self.backend.nbytes(op))
+                    entry = (self.backend.create(batch[0]), 1)
                 khat = np.concatenate([r.khat for r in batch])
                 pol = np.concatenate([r.pol for r in batch])
                 tol = min(r.tol for r in batch)
@@ -284,7 +320,7 @@ class Server:
                                  t_done - r.t_submit, int(khat.shape[0]))
                     out.append((r, res))
                 with self._lock:
-                    self._ops[scene] = entry
+                    self._ops[scene] = (entry[0], max(entry[1], int(khat.shape[0])))
                     self._ops.move_to_end(scene)
                     self._busy.discard(scene)
                     self._reserved -= need
@@ -328,13 +364,22 @@ class FakeBackend:
             self.in_use += nb
             self.max_in_use = max(self.max_in_use, self.in_use)
             self.created.append(req.scene)
-        return {"scene": req.scene, "bytes": nb, "n": 3 * req.tris.shape[0] // 2}
+        return {"scene": req.scene, "bytes": nb, "n": 3 * req.tris.shape[0] // 2, "nv": req.verts.shape[0],
+                "nc": req.tris.shape[0], "widest": 1, "lazy": 0}
 
     def nbytes(self, op) -> int:
         return op["bytes"]
 
     def solve(self, op, khat, pol, tol, stream):
         time.sleep(self.solve_seconds)
+        w = int(khat.shape[0])
+        if w > op["widest"]:
+            grow = op_footprint(op["nv"], op["nc"], w, with_factors=False, widest=op["widest"])
+            with self._lock:
+                op["lazy"] += grow
+                self.in_use += grow
+                self.max_in_use = max(self.max_in_use, self.in_use)
+            op["widest"] = w
 
         class _Rep:
             residual = 0.0
@@ -344,11 +389,20 @@ class FakeBackend:
 
     def destroy(self, op):
         with self._lock:
-            self.in_use -= op["bytes"]
+            self.in_use -= op["bytes"] + op["lazy"]
             self.destroyed.append(op["scene"])
+
+    def trim(self, op):
+        with self._lock:
+            self.in_use -= op["lazy"]
+            op["lazy"], op["widest"] = 0, 1
+            self.trims = getattr(self, "trims", 0) + 1
 
     def bytes_in_use(self) -> int:
         return self.in_use
+
+    def clear_cache(self):
+        self.cache_clears = getattr(self, "cache_clears", 0) + 1
 
 
 def poisson_workload(n_requests: int, rate: float, seed: int = 4, pool: int | None = 48, mesh_pool: int = 12):

@@ -44,3 +44,21 @@ def test_results_alone_equal_results_in_the_mix():
         # cond * 1e-10, with cond below 1e3 for these meshes
         assert err <= 1e-7, err
         op.close()
+
+
+def test_trim_releases_wide_buffers_and_rebuilds_them():
+    ctx = rf.Context(0)
+    m = synth.geodesic_sphere(5, seed=2)
+    op = rf.Operator(ctx, m.verts, m.tris, 0.9)
+    kh, pol = synth.random_plane_waves(12, seed=5)
+    e = op.rhs_planewave(kh, pol)
+    j1, r1 = op.solve(e, tol=1e-9)  # 12 columns: planes and digits get built
+    wide = ctx.bytes_in_use()
+    op.trim()
+    assert ctx.bytes_in_use() < wide
+    j2, r2 = op.solve(e, tol=1e-9)
+    assert ctx.bytes_in_use() == wide
+    assert all(r.converged for r in r1 + r2)
+    assert (torch.linalg.norm(j2 - j1) / torch.linalg.norm(j1)).item() <= 1e-8
+    op.close()
+    ctx.close()

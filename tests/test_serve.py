@@ -100,3 +100,41 @@ def test_warm_makes_operators_resident_within_budget():
     assert len(be.created) == 2  # the warm operator served the request
     srv.close()
     assert be.in_use == 0
+
+
+def test_footprint_counts_what_a_wider_solve_builds():
+    nv, nc = 1922, 3840
+    cold = serve.op_footprint(nv, nc, 1, with_factors=True)
+    assert serve.op_footprint(nv, nc, 64, with_factors=True) > cold
+    # a resident operator that already solved 64 columns adds nothing for 32 more
+    assert serve.op_footprint(nv, nc, 32, with_factors=True, widest=64) == 0
+    # one that only solved single columns still has to build the planes and digits
+    grow = serve.op_footprint(nv, nc, 16, with_factors=True, widest=1)
+    assert grow >= 32 * (3 * nc // 2) ** 2
+
+
+def test_eviction_falls_back_to_dropping_the_factor_cache():
+    be = serve.FakeBackend()
+    v, t = _mesh(3)
+    one = serve.op_footprint(v.shape[0], t.shape[0], 1, with_factors=False)
+    srv = serve.Server(be, hbm_budget=int(0.5 * one), workers=1)
+    assert not srv.warm(v, t, 1.0)  # cannot fit even after dropping the cache
+    assert getattr(be, "cache_clears", 0) == 1
+    srv.close()
+
+
+def test_idle_operators_are_trimmed_before_they_are_evicted():
+    be = serve.FakeBackend()
+    v, t = _mesh(3)
+    nv, nc = v.shape[0], t.shape[0]
+    base = serve.op_footprint(nv, nc, 1, with_factors=False)
+    wide = serve.op_footprint(nv, nc, 32, with_factors=True, widest=1)
+    # room for two resident operators and one wide solve's planes, not two
+    srv = serve.Server(be, hbm_budget=2 * base + int(1.5 * wide), workers=1)
+    kh, pol = synth.random_plane_waves(32, seed=2)
+    srv.submit(v, t, 1.0, kh, pol).result(timeout=10)
+    srv.submit(v, t, 2.0, kh, pol).result(timeout=10)
+    srv.close()
+    assert getattr(be, "trims", 0) >= 1  # the first operator gave its planes back ...
+    assert be.destroyed == [(serve.mesh_key(v, t), 1.0), (serve.mesh_key(v, t), 2.0)]  # ... and stayed until close
+    assert be.in_use == 0
