@@ -502,7 +502,7 @@ def bench_batched(args):
     build.build()
     torch.cuda.set_device(0)
     nrhs, ka = args.nrhs, 2.0
-    mesh = synth.ellipsoid(37)  # semi-axes 1.0 / 0.6 / 0.4, 27380 cells, 41070 unknowns
+    mesh = synth.ellipsoid(args.ellipsoid_n)  # semi-axes 1.0 / 0.6 / 0.4; n = 37: 27380 cells, 41070 unknowns
     kh, pol = synth.random_plane_waves(nrhs, seed=77)
     ctx = rf.Context(0)
     table = None if args.no_tuning else autotune.Table.for_device(torch.cuda.get_device_name(0))
@@ -557,7 +557,7 @@ def bench_batched(args):
         "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32 operator; split-BF16 inner products; exact-digit residuals",
         "data": "synthetic (seeded jittered ellipsoid, seeded plane waves)",
-        "config": {"workload": "batched_ellipsoid_n41070_rhs%d" % nrhs, "unknowns": op.N, "ka": ka, "nrhs": nrhs,
+        "config": {"workload": "batched_ellipsoid_n%d_rhs%d" % (op.N, nrhs), "unknowns": op.N, "ka": ka, "nrhs": nrhs,
                    "tol": TOL, "l2": "inputs larger than L2 (T_A complex64 13.5 GB)",
                    "tuning": "table" if table is not None else "built-in"},
         "setup_s": round(setup_s, 2),
@@ -609,6 +609,8 @@ def main():
                     help="sweep: the level-5 low-frequency sweep (default); serving: the Poisson request stream; "
                          "batched: 512 plane waves on the 41070-unknown ellipsoid")
     ap.add_argument("--nrhs", type=int, default=512, help="batched: right-hand sides per solve")
+    ap.add_argument("--ellipsoid-n", type=int, default=37,
+                    help="batched: geodesic frequency of the ellipsoid (37 = the workload; smaller for profiling)")
     ap.add_argument("--single-sample", type=int, default=3, help="batched: columns solved one at a time in FF")
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--workers", type=int, default=2)

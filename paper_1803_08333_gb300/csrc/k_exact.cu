@@ -19,12 +19,15 @@
 // digits past S: per term a truncation of about 2^-48 of the row scale times the column scale,
 // the only error of the product.
 //
-// Kernel layout: one CTA per 128 x 16 output tile, 192 threads.  Warp 0 lane 0 issues the TMA
-// loads of a 2-stage ring (each stage: S digit planes of A, 128 x 64, and S of B, 16 x 64, BF16
-// with the 128-byte swizzle); warp 1 lane 0 issues S(S+1)/2 MMAs per 16-wide K step into one
-// accumulator per level, in two tensor-memory buffers that alternate between K-blocks, and
-// commits each K-block; warps 2..5 fold the level sums of a finished K-block (each warp its
-// 32-lane quadrant of tensor memory) while the next one accumulates, and write D.  Every wait
+// Kernel layout: one CTA per 128 x 32 output tile, 320 threads.  Warp 0 lane 0 issues the TMA
+// loads of a 3-stage ring (each stage: the S digit planes of A, 128 x 32, and the S of B, 32 x 32,
+// BF16 with the 64-byte swizzle; the B planes lie back to back, so B_0..B_t read as one operand
+// of 32 (t + 1) rows).  Warp 1 lane 0 issues, per 16-wide K step, one MMA per A plane s against
+// B_0..B_{S-1-s}: its N = 32 (S - s) output columns land on the accumulators of levels s..S-1,
+// which sit side by side in tensor memory (level L at column 32 L), so S MMAs cover all S(S+1)/2
+// digit pairs and every A plane is read from shared memory once per K step.  Two sets of level
+// accumulators alternate between K-blocks; warps 2..9 fold a finished K-block (two warps per
+// 32-lane quadrant of tensor memory, 16 columns each) while the next one accumulates, and write D.  Every wait
 // is bounded; on timeout the kernel records an error code, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -45,27 +48,32 @@ using namespace tc;
 
 constexpr int XS = EXACT_DIGITS;  // digits per value
 static_assert(XS == 6, "the integer fold below is written for 6 digits");
-constexpr int XBN = 16;           // output columns per CTA
+constexpr int XBN = 32;           // output columns per CTA
+constexpr int XBK = 32;           // K per ring step (64-byte rows)
 constexpr int XKB = 128;          // K-block between integer folds
-constexpr int XSTAGES = 2;
-constexpr int XSPK = XKB / BK;    // ring steps per K-block
-constexpr int XTILE_A = BM * BK * 2;
-constexpr int XTILE_B = XBN * BK * 2;
+constexpr int XSTAGES = 3;
+constexpr int XSPK = XKB / XBK;   // ring steps per K-block
+constexpr int XTILE_A = BM * XBK * 2;
+constexpr int XTILE_B = XBN * XBK * 2;
 constexpr int XSTAGE = XS * (XTILE_A + XTILE_B);
 constexpr int XSMEM = XSTAGES * XSTAGE + 1024 + 256;
 constexpr int XBUF = XS * XBN;  // tensor-memory columns of one set of level accumulators
 constexpr uint32_t XTMEM_COLS = 2 * XBUF <= 128 ? 128 : (2 * XBUF <= 256 ? 256 : 512);
 static_assert(2 * XBUF <= 512, "level accumulators exceed tensor memory");
+static_assert(XS * XBN <= 256, "one MMA spans the accumulators of all levels");
 static_assert((long long)XS * (128LL * 128LL) * XKB < (1LL << 24), "K-block level sums must stay exact in FP32");
 static_assert(XSMEM <= 227 * 1024, "shared memory");
-static_assert(XKB % BK == 0, "K-blocks are whole ring steps");
+static_assert(XKB % XBK == 0 && XTILE_B % 512 == 0 && XTILE_A % 1024 == 0, "tile geometry");
 
 struct ExactMaps {
   CUtensorMap a[XS];
   CUtensorMap b[XS];
 };
 
-__global__ void __launch_bounds__(192, 1)
+constexpr int XTHREADS = 320;  // producer warp, MMA warp, 8 epilogue warps
+static_assert(XBN == 32, "two epilogue warps of 16 columns per tensor-memory quadrant");
+
+__global__ void __launch_bounds__(XTHREADS, 1)
 exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, const int* __restrict__ ea,
                   const int* __restrict__ eb, double* __restrict__ D, long long ldd, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
@@ -77,7 +85,7 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * XBN, m0 = blockIdx.y * BM;  // N tiles fastest: CTAs sharing A run together
-  const int ksteps = (K + BK - 1) / BK;
+  const int ksteps = (K + XBK - 1) / XBK;
   const int nkb = (ksteps + XSPK - 1) / XSPK;
 
   if (threadIdx.x == 0) {
@@ -87,7 +95,7 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+      mbar_init(&acc_empty[b], 8);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -111,7 +119,7 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
           break;
         }
         uint8_t* st = smem + s * XSTAGE;
-        const int kx = it * BK;
+        const int kx = it * XBK;
         mbar_expect_tx(&full[s], XSTAGE);
 #pragma unroll
         for (int p = 0; p < XS; ++p) tma_load_2d(st + p * XTILE_A, &maps.a[p], &full[s], kx, m0);
@@ -121,7 +129,6 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(BM, XBN, false);
       for (int it = 0; it < ksteps; ++it) {
         const int s = it % XSTAGES, round = it / XSTAGES;
         const int kb = it / XSPK, buf = kb & 1;
@@ -139,28 +146,26 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
         const uint32_t a0 = smem_u32(smem + s * XSTAGE), b0 = a0 + XS * XTILE_A;
         const uint32_t t0 = tmem + (uint32_t)(buf * XBUF);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte swizzled row
+        for (int kk = 0; kk < XBK / 16; ++kk) {
+          const uint32_t off = kk * 32;  // 16 BF16 along K inside the 64-byte swizzled row
+          const uint64_t bd = sw64_desc(b0 + off);
 #pragma unroll
-          for (int L = 0; L < XS; ++L)
-#pragma unroll
-            for (int sa = 0; sa <= L; ++sa) {
-              const int tb = L - sa;
-              mma_bf16(t0 + (uint32_t)(L * XBN), sw128_desc(a0 + sa * XTILE_A + off),
-                       sw128_desc(b0 + tb * XTILE_B + off), idesc, (first && kk == 0 && sa == 0) ? 0u : 1u);
-            }
+          for (int sa = 0; sa < XS; ++sa)
+            mma_bf16(t0 + (uint32_t)(sa * XBN), sw64_desc(a0 + sa * XTILE_A + off), bd,
+                     idesc_bf16(BM, (XS - sa) * XBN, false), (first && kk == 0 && sa == 0) ? 0u : 1u);
         }
         mma_commit(&empty[s]);
         if ((it % XSPK) == XSPK - 1 || it == ksteps - 1) mma_commit(&acc_full[buf]);
       }
     }
   } else {
-    // epilogue warps 2..5: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31
-    const int q = warp & 3;
+    // epilogue warps 2..9: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31 and
+    // folds output columns 16 h .. 16 h + 15, h = (w - 2) / 4
+    const int q = warp & 3, h = ((warp - 2) >> 2) * 16;
     const int row = m0 + 32 * q + lane;
-    long long H[XBN], G[XBN];
+    long long H[16], G[16];
 #pragma unroll
-    for (int j = 0; j < XBN; ++j) H[j] = G[j] = 0;
+    for (int j = 0; j < 16; ++j) H[j] = G[j] = 0;
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       const int buf = kb & 1;
@@ -170,8 +175,8 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
         break;
       }
       tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * XBUF + h);
       uint32_t r[XS][16];
-      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * XBUF);
 #pragma unroll
       for (int L = 0; L < XS; ++L) tmem_ld16_async(base + (uint32_t)(L * XBN), r[L]);
       tmem_wait_ld();
@@ -179,7 +184,7 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);  // the buffer may take the next K-block
 #pragma unroll
-      for (int j = 0; j < XBN; ++j) {
+      for (int j = 0; j < 16; ++j) {
         long long p[XS];
 #pragma unroll
         for (int L = 0; L < XS; ++L) p[L] = (long long)__float2int_rn(__uint_as_float(r[L][j]));
@@ -191,8 +196,8 @@ exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, c
       const int er = ea[row];
       double* dst = D + (size_t)row * ldd;
 #pragma unroll
-      for (int j = 0; j < XBN; ++j) {
-        const int col = n0 + j;
+      for (int j = 0; j < 16; ++j) {
+        const int col = n0 + h + j;
         if (col < N) {
           const int e = er + eb[col];
           dst[col] = ldexp((double)H[j], e - 32) + ldexp((double)G[j], e - 56);
@@ -313,8 +318,8 @@ cudaError_t exact_gemm(const ExactOperand& A, const ExactOperand& B, int M, int 
   ExactMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int p = 0; p < XS; ++p)
-    if (!make_map(&maps.a[p], A.d + p * A.plane_stride, M, K, A.ldp, BM) ||
-        !make_map(&maps.b[p], B.d + p * B.plane_stride, N, K, B.ldp, XBN))
+    if (!make_map(&maps.a[p], A.d + p * A.plane_stride, M, K, A.ldp, BM, XBK) ||
+        !make_map(&maps.b[p], B.d + p * B.plane_stride, N, K, B.ldp, XBN, XBK))
       return cudaErrorInvalidValue;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
@@ -324,7 +329,7 @@ cudaError_t exact_gemm(const ExactOperand& A, const ExactOperand& B, int M, int 
   if (attr != cudaSuccess) return attr;
   const dim3 grid((N + XBN - 1) / XBN, (M + BM - 1) / BM);
   ProfScope prof("gemm_exact", 0.0, 2.0 * (XS * (XS + 1) / 2) * (double)M * N * K, s);
-  exact_gemm_kernel<<<grid, 192, XSMEM, s>>>(maps, M, N, K, A.e, B.e, D, ldd, err);
+  exact_gemm_kernel<<<grid, XTHREADS, XSMEM, s>>>(maps, M, N, K, A.e, B.e, D, ldd, err);
   return cudaGetLastError();
 }
 

@@ -65,6 +65,17 @@ static __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   return d;
 }
 
+// the same for a K-major tile with the 64-byte swizzle (32 BF16 per row), 8-row groups 512 B apart
+static __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)4 << 61;                   // layout: 64-byte swizzle
+  return d;
+}
+
 // instruction descriptor: kind::f16, BF16 A and B, FP32 accumulator, K-major A and B, M x N
 static __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n, bool neg_a) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
@@ -128,16 +139,20 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-inline bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k, long long ld, int box_rows) {
+// box_k 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte rows, 64-byte swizzle)
+inline bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int k, long long ld, int box_rows,
+                     int box_k = BK) {
   auto fn = encode_fn();
   if (!fn) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return false;
+  if (box_k != 64 && box_k != 32) return false;
   cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
