@@ -39,10 +39,13 @@ WORKLOAD = "lowfreq_sweep_sphere_f32_n30720"
 METRIC = "RF-CMP EFIE solves/s @1e-6 resid (ka sweep 1..1e-5, level-5 sphere)"
 FP32_LANES_PER_SM = 128
 N_SMS = 152
-# DRAM bytes per launch of the dominant kernel from one ncu capture (None when
-# the kernel changed after the capture); the capture command and figures are
-# in profiles/.
-NCU_TRAFFIC = {}
+# DRAM traffic of a kernel family from one ncu capture, as the ratio of the captured
+# dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic bytes of that launch:
+# gemv_c64 at N = 7680, two columns, 472.3 + 3.2 MB measured against 8 N^2 + 32 N x 2 =
+# 472.4 MB.  The bench reports traffic per launch = ratio x its own algorithmic bytes per
+# launch (traffic grows with the units, N^2); families without a capture of the current
+# kernel report None.
+NCU_TRAFFIC_RATIO = {"gemv_c64_f32": 475.6 / 472.4}
 
 
 def _peaks():
@@ -312,14 +315,14 @@ def _one_roofline(name, v, peaks, peak_kind, clk):
         peak = N_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         achieved = v["flops"] / v["launches"] / (avg_ms / 1e3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(name),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "flops_per_launch": v["flops"] / v["launches"], "avg_launch_ms": round(avg_ms, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x median SM clock"}
     if name.startswith("gemm_"):
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
         achieved = v["flops"] / v["launches"] / (avg_ms / 1e3) / 1e12
         return {"kernel": name, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(name),
+                "frac": round(achieved / peak, 4), "traffic": None,
                 "flops_per_launch": v["flops"] / v["launches"], "avg_launch_ms": round(avg_ms, 4),
                 "peak_source": "of %s bf16_tflops_sustained (issued BF16 MMA FLOPs: 3 split products for "
                                "gemm_bf16x3, 21 digit-pair products for gemm_exact)" % peak_kind}
@@ -327,7 +330,8 @@ def _one_roofline(name, v, peaks, peak_kind, clk):
     achieved = bytes_per / (avg_ms / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(name),
+            "frac": round(achieved / peak, 4),
+            "traffic": round(NCU_TRAFFIC_RATIO[name] * bytes_per) if name in NCU_TRAFFIC_RATIO else None,
             "bytes_per_launch": bytes_per, "avg_launch_ms": round(avg_ms, 4),
             "peak_source": "of %s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind}
 
