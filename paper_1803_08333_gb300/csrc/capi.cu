@@ -170,6 +170,7 @@ constexpr int MRHS_MIN = 4;
 // float-float GEMV, which spends some 40 FP32 instructions per complex multiply-add.
 constexpr int EXACT_MIN = 8;
 constexpr double NS_START_TOL = 1e-2;
+constexpr int NS_MAX_STEPS = 14;
 
 struct DenseFactor {
   int n = 0;
@@ -896,19 +897,31 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
   int iters = 0;
   cudaError_t err;
   if (multigrid && project && n >= NS_MIN_CELLS) {
-    // multigrid PCG to a loose tolerance, then Newton-Schulz steps on the tensor cores
+    // Newton-Schulz steps on the tensor cores from one V-cycle; if they do not reach the target
+    // (a V-cycle too weak to contract), from a multigrid-PCG solve to NS_START_TOL instead
+    const double target = std::min(tol, 1e-12);
     double* Xd = nullptr;
     err = cudaMalloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
-    if (err == cudaSuccess)
-      err = dense_inverse_block_cg(dptr, dcol, dval, n, project, &H, NS_START_TOL, 20000, f->hi, f->lo, &iters, 0, Xd);
     int steps = 0;
-    double res = 0.0;
-    if (err == cudaSuccess)
-      err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, Xd, padded_ld(n), 6, std::min(tol, 1e-12), f->hi, f->lo,
-                                         &steps, &res, 0);
+    double res = 1.0;
+    for (int attempt = 0; attempt < 2 && err == cudaSuccess && !(res <= target); ++attempt) {
+      int it = 0;
+      err = dense_inverse_block_cg(dptr, dcol, dval, n, project, &H, NS_START_TOL, attempt == 0 ? 0 : 20000, f->hi,
+                                   f->lo, &it, 0, Xd);
+      iters += it;
+      int st = 0;
+      if (err == cudaSuccess)
+        err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, Xd, padded_ld(n), NS_MAX_STEPS, target, f->hi, f->lo,
+                                           &st, &res, 0);
+      steps += st;
+    }
     if (Xd) cudaFree(Xd);
     f->ns_steps = steps;
     f->ns_residual = res;
+    if (err == cudaSuccess && !(res <= target)) {
+      for (void* p : tmp) cudaFree(p);
+      return set_error(RFCMP_ERR_NOT_CONVERGED, "(Sigma^T Sigma)^+ refinement stalled at residual " + std::to_string(res));
+    }
   } else {
     err = dense_inverse_block_cg(dptr, dcol, dval, n, project, multigrid ? &H : nullptr, tol, 20000, f->hi, f->lo,
                                  &iters, 0);

@@ -1,14 +1,18 @@
 // Dense (Sigma^T Sigma)^+ by Newton-Schulz refinement on the tensor cores.
 //
 // With M = Sigma^T Sigma + 1 1^T / n, the identity of Sec. 3.2 gives
-// (Sigma^T Sigma)^+ = M^{-1} - 1 1^T / n.  A multigrid-preconditioned block CG delivers
-// X0 ~ M^{-1} to a loose tolerance; then
+// (Sigma^T Sigma)^+ = M^{-1} - 1 1^T / n.  The start X0 ~ M^{-1} is one symmetric multigrid
+// V(1,1) cycle applied to the projected identity (a convergent V-cycle B has the eigenvalues of
+// M B in (0, 2), so the spectral radius of I - M X0 is below 1), or a loose multigrid-PCG solve;
+// then
 //     R_k = I - M X_k   (FP64, formed exactly along rows: (X M)_ij = sum_k X_ik M_kj, M sparse),
-//     X_{k+1} = X_k + X_k R_k   (dense product, split-BF16 tensor-core GEMM, FP64 update)
+//     X_{k+1} = X_k + X_k R_k   (dense product, split-BF16 tensor-core GEMM, FP64 update; X_k R_k
+//                                is symmetric, so only its upper tiles are computed)
 // converges quadratically: the relative error e_k of X_k obeys e_{k+1} <= e_k^2 + c e_k with
-// c ~ 2^-16 the accuracy of one split product, so three steps take e_0 = 1e-3 to rounding
-// level.  X_k stays symmetric up to rounding (X (2I - M X) is symmetric when X is), and the
-// result is symmetrised once at the end before the 1 1^T / n term is removed.
+// c ~ 2^-16 the accuracy of one split product, so a V-cycle start (e_0 ~ 0.1) reaches rounding
+// level in about five steps.  X_k stays exactly symmetric (the update mirrors the upper tiles;
+// the residual below is formed along rows, as R^T, which needs it); an iteration that stops
+// contracting ends early so that the caller can fall back to a PCG solve.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -63,16 +67,6 @@ __global__ void row_sum_kernel(const double* __restrict__ X, long long ldx, int 
   }
 }
 
-__global__ void ns_update_kernel(double* __restrict__ X, long long ldx, const float* __restrict__ D, long long ldd,
-                                 int n) {
-  const long long total = (long long)n * n;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / n), j = (int)(idx % n);
-    X[(size_t)i * ldx + j] += (double)D[(size_t)i * ldd + j];
-  }
-}
-
 // out = (X + X^T)/2 - 1/n, split into FP32 hi + lo planes (row stride ld)
 constexpr int TT = 32;
 __global__ void symmetrize_store_kernel(const double* __restrict__ X, long long ldx, int n, float* __restrict__ hi,
@@ -117,6 +111,30 @@ __global__ void symmetrize_inplace_kernel(double* __restrict__ X, long long ldx,
     const int i2 = c0 + r, j2 = r0 + threadIdx.x;
     const double w = 0.5 * (b[r][threadIdx.x] + a[threadIdx.x][r]);
     if (i2 < n && j2 < n) X[(size_t)i2 * ldx + j2] = w;
+  }
+}
+
+// X += D for a symmetric D of which only the 128 x 128 tiles on or above the diagonal were
+// computed: block (bx, by), by <= bx, adds tile (by, bx) of D to X there and its transpose to
+// tile (bx, by); a diagonal tile adds (D + D^T) / 2, so X stays exactly symmetric.
+__global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, const float* __restrict__ D, long long ldd,
+                                     int n) {
+  __shared__ float t[TT][TT + 1];
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (by > bx) return;
+  const int r0 = by * TT, c0 = bx * TT;
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    const int i = r0 + r, j = c0 + threadIdx.x;
+    t[r][threadIdx.x] = (i < n && j < n) ? D[(size_t)i * ldd + j] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < TT; r += blockDim.y) {
+    const int c = threadIdx.x;
+    const int i = r0 + r, j = c0 + c;
+    if (i < n && j < n)
+      X[(size_t)i * ldx + j] += bx == by ? 0.5 * ((double)t[r][c] + (double)t[c][r]) : (double)t[r][c];
+    const int i2 = c0 + r, j2 = r0 + c;
+    if (bx != by && i2 < n && j2 < n) X[(size_t)i2 * ldx + j2] += (double)t[c][r];
   }
 }
 
@@ -177,16 +195,19 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
     unsigned long long hb = 0;
     if ((err = cudaMemcpyAsync(&hb, maxbits, sizeof(hb), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(err);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);
+    const double prev = res;
     std::memcpy(&res, &hb, sizeof(res));
     if (!(res > tol) || k >= max_steps) break;
+    if (k >= 2 && !(res < 0.9 * prev)) break;  // not contracting: the caller falls back
     if ((err = split_bf16_f64(X, ldx, n, n, xh, xl, ldp, s)) != cudaSuccess) return fail(err);
-    // D = X R with B = R^T stored row-major (B[j][k] = R[k][j] = Rt[j][k])
-    if ((err = gemm_bf16x3(&A, &B, nullptr, 1, n, n, n, D, ldp, false, gerr, s)) != cudaSuccess) return fail(err);
+    // D = X R with B = R^T stored row-major (B[j][k] = R[k][j] = Rt[j][k]); X R = X - X M X is
+    // symmetric, so only the tiles on and above the diagonal are computed
+    if ((err = gemm_bf16x3(&A, &B, nullptr, 1, n, n, n, D, ldp, false, gerr, s, 0, true)) != cudaSuccess)
+      return fail(err);
     {
-      ProfScope prof("factor_ns_update", 16.0 * (double)n * n, 0.0, s);
-      ns_update_kernel<<<8 * 152, 256, 0, s>>>(X, ldx, D, ldp, n);
+      ProfScope prof("factor_ns_update", 12.0 * (double)n * n, 0.0, s);
+      ns_update_sym_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, D, ldp, n);
     }
-    symmetrize_inplace_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, n);
     if ((err = cudaGetLastError()) != cudaSuccess) return fail(err);
   }
   int herr = 0;

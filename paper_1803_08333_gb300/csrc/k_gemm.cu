@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -50,7 +51,9 @@ struct GemmMaps {
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
 gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask, int M, int N, int K,
-                   float* __restrict__ D, long long ldd, int accumulate, int* __restrict__ err) {
+                   float* __restrict__ D, long long ldd, int accumulate, int* __restrict__ err, int upper) {
+  // upper: only the tiles on or above the diagonal of a symmetric result (BN == BM)
+  if (upper && (int)blockIdx.x < (int)blockIdx.y) return;
   using C = TileCfg<BN>;
   constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, TILE_B = C::TILE_B;
   extern __shared__ uint8_t smem_raw[];
@@ -176,7 +179,8 @@ __global__ void split_bf16_kernel(const T* __restrict__ src, long long ld_src, i
 
 template <int BN>
 cudaError_t gemm_launch(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N, int K,
-                        float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s) {
+                        float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s, bool upper) {
+  if (upper && BN != BM) return cudaErrorInvalidValue;
   using C = TileCfg<BN>;
   GemmMaps maps;
   std::memset(&maps, 0, sizeof(maps));
@@ -196,9 +200,14 @@ cudaError_t gemm_launch(const SplitOperand* A, const SplitOperand* B, const int*
   });
   if (attr_err != cudaSuccess) return attr_err;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-  ProfScope prof("gemm_bf16x3", 0.0, 6.0 * (double)M * N * K * nseg, s);
+  double frac = 1.0;  // share of the output tiles computed
+  if (upper) {
+    const double tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+    frac = std::min(1.0, tn * (tn + 1) / 2.0 / (tm * tn));  // tiles with n-tile >= m-tile (tm >= tn)
+  }
+  ProfScope prof("gemm_bf16x3", 0.0, 6.0 * (double)M * N * K * nseg * frac, s);
   gemm_bf16x3_kernel<BN><<<grid, 128, C::SMEM_BYTES, s>>>(maps, nseg, neg_mask, M, N, K, D, ldd, accumulate ? 1 : 0,
-                                                          err_dev);
+                                                          err_dev, upper ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -350,16 +359,18 @@ cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int co
 }
 
 cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N,
-                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s, int bn) {
+                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s, int bn,
+                        bool upper) {
   if (nseg < 1 || nseg > 2 || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  if (upper) bn = 128;
   if (bn == 0) bn = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
   switch (bn) {
     case 32:
-      return gemm_launch<32>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+      return gemm_launch<32>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s, upper);
     case 64:
-      return gemm_launch<64>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+      return gemm_launch<64>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s, upper);
     case 128:
-      return gemm_launch<128>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s);
+      return gemm_launch<128>(A, B, negate, nseg, M, N, K, D, ldd, accumulate, err_dev, s, upper);
     default:
       return cudaErrorInvalidValue;
   }

@@ -1260,6 +1260,10 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
       return Z;
     };
     double* Zp = precond(R);
+    if (max_iter == 0) {
+      // no iteration: the result is one preconditioner application, X = M^-1-approximation R0
+      if ((err = cudaMemcpyAsync(X, Zp, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return fail(err);
+    }
     bcg_dot_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, R, Zp, rzr);
     if ((err = cudaMemcpyAsync(P, Zp, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return fail(err);
     int it = 0;

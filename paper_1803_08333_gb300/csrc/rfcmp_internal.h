@@ -129,9 +129,11 @@ struct SplitOperand {
 // D[M x N] = sum_g (negate[g] ? -1 : 1) A_g B_g^T (+ D), three BF16 products per K step into an
 // FP32 tensor-memory accumulator (tcgen05).  nseg 1 or 2.  err_dev receives a nonzero code if a
 // bounded device-side wait gave up.
-// bn selects the N tile (32, 64 or 128); 0 picks it from N.
+// bn selects the N tile (32, 64 or 128); 0 picks it from N.  With upper, only the 128 x 128 tiles
+// on or above the diagonal are computed (for a result known to be symmetric).
 cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int* negate, int nseg, int M, int N,
-                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s, int bn = 0);
+                        int K, float* D, long long ldd, bool accumulate, int* err_dev, cudaStream_t s, int bn = 0,
+                        bool upper = false);
 cudaError_t split_bf16_f32(const float* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
                            __nv_bfloat16* lo, long long ld_dst, cudaStream_t s);
 
