@@ -911,8 +911,8 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
       iters += it;
       int st = 0;
       if (err == cudaSuccess)
-        err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, Xd, padded_ld(n), NS_MAX_STEPS, target, f->hi, f->lo,
-                                           &st, &res, 0);
+        err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, true, Xd, padded_ld(n), NS_MAX_STEPS, target, f->hi,
+                                           f->lo, &st, &res, 0);
       steps += st;
     }
     if (Xd) cudaFree(Xd);
@@ -922,6 +922,24 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
       for (void* p : tmp) cudaFree(p);
       return set_error(RFCMP_ERR_NOT_CONVERGED, "(Sigma^T Sigma)^+ refinement stalled at residual " + std::to_string(res));
     }
+  } else if (!project && !multigrid && n >= NS_MIN_CELLS) {
+    // G_ll^{-1}: the P1 mass matrix has the eigenvalues of D^{-1} G_ll in [1/2, 2] (element by
+    // element), so X0 = 0.8 D^{-1} leaves I - G_ll X0 a spectral radius of at most 0.6 and
+    // Newton-Schulz reaches rounding level in about six steps; block CG is the fallback
+    const double target = std::min(tol, 1e-12);
+    double* Xd = nullptr;
+    err = cudaMalloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
+    int steps = 0;
+    double res = 1.0;
+    if (err == cudaSuccess) err = jacobi_start(dptr, dcol, dval, n, 0.8, Xd, padded_ld(n), 0);
+    if (err == cudaSuccess)
+      err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, false, Xd, padded_ld(n), NS_MAX_STEPS, target, f->hi,
+                                         f->lo, &steps, &res, 0);
+    if (Xd) cudaFree(Xd);
+    f->ns_steps = steps;
+    f->ns_residual = res;
+    if (err == cudaSuccess && !(res <= target))
+      err = dense_inverse_block_cg(dptr, dcol, dval, n, project, nullptr, tol, 20000, f->hi, f->lo, &iters, 0);
   } else {
     err = dense_inverse_block_cg(dptr, dcol, dval, n, project, multigrid ? &H : nullptr, tol, 20000, f->hi, f->lo,
                                  &iters, 0);

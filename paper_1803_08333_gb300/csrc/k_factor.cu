@@ -27,8 +27,9 @@ namespace rfcmp {
 
 namespace {
 
-// Rt[i][j] = delta_ij - (X M)[i][j] with M = L + 1 1^T / n (L symmetric CSR), written as BF16
-// hi/lo planes; rowsum[i] = sum_j X[i][j] is precomputed.  Also tracks max |Rt|.
+// Rt[i][j] = delta_ij - (X M)[i][j] with M = L + 1 1^T / n (L symmetric CSR; without rowsum,
+// M = L), written as BF16 hi/lo planes; rowsum[i] = sum_j X[i][j] is precomputed.  Also tracks
+// max |Rt|.
 __global__ void ns_residual_kernel(const double* __restrict__ X, long long ldx, int n, const int32_t* __restrict__ ptr,
                                    const int32_t* __restrict__ col, const double* __restrict__ val,
                                    const double* __restrict__ rowsum, __nv_bfloat16* __restrict__ hi,
@@ -36,7 +37,7 @@ __global__ void ns_residual_kernel(const double* __restrict__ X, long long ldx, 
                                    unsigned long long* __restrict__ maxbits) {
   const int i = blockIdx.y;
   const double* xr = X + (size_t)i * ldx;
-  const double rs = rowsum[i] / n;
+  const double rs = rowsum ? rowsum[i] / n : 0.0;  // the 1 1^T / n term of the projected case
   double mx = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double a = rs;
@@ -67,10 +68,10 @@ __global__ void row_sum_kernel(const double* __restrict__ X, long long ldx, int 
   }
 }
 
-// out = (X + X^T)/2 - 1/n, split into FP32 hi + lo planes (row stride ld)
+// out = (X + X^T)/2 - shift, split into FP32 hi + lo planes (row stride ld)
 constexpr int TT = 32;
-__global__ void symmetrize_store_kernel(const double* __restrict__ X, long long ldx, int n, float* __restrict__ hi,
-                                        float* __restrict__ lo, long long ld) {
+__global__ void symmetrize_store_kernel(const double* __restrict__ X, long long ldx, int n, double shift,
+                                        float* __restrict__ hi, float* __restrict__ lo, long long ld) {
   __shared__ double tile[TT][TT + 1];
   const int bi = blockIdx.y * TT, bj = blockIdx.x * TT;
   // load the transposed tile X[bj.., bi..]
@@ -82,7 +83,7 @@ __global__ void symmetrize_store_kernel(const double* __restrict__ X, long long 
   for (int r = threadIdx.y; r < TT; r += blockDim.y) {
     const int i = bi + r, j = bj + threadIdx.x;
     if (i < n && j < n) {
-      const double v = 0.5 * (X[(size_t)i * ldx + j] + tile[threadIdx.x][r]) - 1.0 / n;
+      const double v = 0.5 * (X[(size_t)i * ldx + j] + tile[threadIdx.x][r]) - shift;
       const float h = (float)v;
       hi[(size_t)i * ld + j] = h;
       lo[(size_t)i * ld + j] = (float)(v - (double)h);
@@ -138,12 +139,33 @@ __global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, cons
   }
 }
 
+// X = c D^{-1} (D the diagonal of the CSR matrix), the rest of X zero
+__global__ void jacobi_start_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                    const double* __restrict__ val, int n, double c, double* __restrict__ X,
+                                    long long ldx) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int q = ptr[i]; q < ptr[i + 1]; ++q)
+      if (col[q] == i) d = val[q];
+    X[(size_t)i * ldx + i] = d > 0.0 ? c / d : 0.0;
+  }
+}
+
 }  // namespace
 
+cudaError_t jacobi_start(const int32_t* ptr, const int32_t* col, const double* val, int n, double c, double* X,
+                         long long ldx, cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * ldx, s);
+  if (err != cudaSuccess) return err;
+  jacobi_start_kernel<<<(n + 255) / 256, 256, 0, s>>>(ptr, col, val, n, c, X, ldx);
+  return cudaGetLastError();
+}
+
 cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col, const double* val, int n,
-                                         double* X, long long ldx, int max_steps, double tol, float* Xhi, float* Xlo,
-                                         int* steps_done, double* final_residual, cudaStream_t s) {
-  // X holds an approximation of M^{-1} = L^+ + 1 1^T / n on entry (row-major, stride ldx)
+                                         bool project, double* X, long long ldx, int max_steps, double tol, float* Xhi,
+                                         float* Xlo, int* steps_done, double* final_residual, cudaStream_t s) {
+  // X holds an approximation of M^{-1} on entry (row-major, stride ldx): M = L + 1 1^T / n with
+  // project (the result is M^{-1} - 1 1^T / n = L^+), M = L without
   const long long ldp = ldx;  // plane stride (elements); ldx is a multiple of 64
   std::vector<void*> own;
   auto fail = [&](cudaError_t e) {
@@ -185,12 +207,13 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
   // the residual below is formed along rows as I - X M, which is R^T only for symmetric X
   symmetrize_inplace_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, n);
   for (;; ++k) {
-    row_sum_kernel<<<n, 256, 0, s>>>(X, ldx, n, rowsum);
+    if (project) row_sum_kernel<<<n, 256, 0, s>>>(X, ldx, n, rowsum);
     if ((err = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), s)) != cudaSuccess) return fail(err);
     {
       ProfScope prof("factor_ns_residual", 16.0 * (double)n * n, 0.0, s);
       dim3 grid((n + 255) / 256 < 8 ? (n + 255) / 256 : 8, n);
-      ns_residual_kernel<<<grid, 256, 0, s>>>(X, ldx, n, ptr, col, val, rowsum, rh, rl, ldp, maxbits);
+      ns_residual_kernel<<<grid, 256, 0, s>>>(X, ldx, n, ptr, col, val, project ? rowsum : nullptr, rh, rl, ldp,
+                                              maxbits);
     }
     unsigned long long hb = 0;
     if ((err = cudaMemcpyAsync(&hb, maxbits, sizeof(hb), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(err);
@@ -214,7 +237,7 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
   if ((err = cudaMemcpyAsync(&herr, gerr, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(err);
   {
     dim3 grid((n + TT - 1) / TT, (n + TT - 1) / TT), block(TT, 8);
-    symmetrize_store_kernel<<<grid, block, 0, s>>>(X, ldx, n, Xhi, Xlo, ldx);
+    symmetrize_store_kernel<<<grid, block, 0, s>>>(X, ldx, n, project ? 1.0 / n : 0.0, Xhi, Xlo, ldx);
   }
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);
   if (herr) return fail(cudaErrorLaunchTimeout);

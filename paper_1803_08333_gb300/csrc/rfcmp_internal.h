@@ -289,10 +289,13 @@ int build_amg(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col, 
 cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const double* val, int n, bool project,
                                    const AmgHierarchy* H, double tol, int max_iter, float* Xhi, float* Xlo,
                                    int* iters, cudaStream_t s, double* Xd = nullptr);
-// Newton-Schulz refinement of X ~ (L + 1 1^T / n)^{-1} (k_factor.cu); writes
-// (Sigma^T Sigma)^+ = sym(X) - 1 1^T / n to the FP32 hi + lo planes.
+// Newton-Schulz refinement of X ~ M^{-1} (k_factor.cu) for M = L + 1 1^T / n (project: writes
+// (Sigma^T Sigma)^+ = sym(X) - 1 1^T / n) or M = L (writes sym(X)) to the FP32 hi + lo planes.
 cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col, const double* val, int n,
-                                         double* X, long long ldx, int max_steps, double tol, float* Xhi, float* Xlo,
-                                         int* steps_done, double* final_residual, cudaStream_t s);
+                                         bool project, double* X, long long ldx, int max_steps, double tol, float* Xhi,
+                                         float* Xlo, int* steps_done, double* final_residual, cudaStream_t s);
+// X = c D^{-1} for the diagonal D of a CSR matrix (n x n, row stride ldx; the rest of X zeroed)
+cudaError_t jacobi_start(const int32_t* ptr, const int32_t* col, const double* val, int n, double c, double* X,
+                         long long ldx, cudaStream_t s);
 
 }  // namespace rfcmp
