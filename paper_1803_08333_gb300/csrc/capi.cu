@@ -306,13 +306,15 @@ int ensure_workspace(rfcmp_op* op, int cols) {
     RF_TRY(dalloc(&ws->gs.xh, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.xl, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.acc, (size_t)capn * 4, ws->owned));
+    // one error flag for every bounded device-side wait (streaming GEMV, tensor-core products)
+    RF_TRY(dalloc(&ws->ms.err, 1, ws->owned));
+    RF_CUDA(cudaMemset(ws->ms.err, 0, sizeof(int)));
+    ws->gs.err = ws->ms.err;
     const bool bf = cols >= plan_mrhs(op), ex = cols >= plan_exact(op);
     if (bf || ex) {
       ws->ms.cap_cols = cols;
       ws->ms.cap_n = capn;
       ws->ms.cap_ld = padded_ld(capn);
-      RF_TRY(dalloc(&ws->ms.err, 1, ws->owned));
-      RF_CUDA(cudaMemset(ws->ms.err, 0, sizeof(int)));
     }
     if (bf) {
       RF_TRY(dalloc(&ws->ms.xb, (size_t)4 * cols * ws->ms.cap_ld, ws->owned));
@@ -398,7 +400,7 @@ int ensure_planes(rfcmp_op* op, cudaStream_t st) {
   return RFCMP_OK;
 }
 
-// Reads the tensor-core products' error flag (set when a bounded device-side wait gave up).
+// Reads the error flag of the bounded device-side waits (tensor-core products, streaming GEMV).
 int check_tensor_core_waits(rfcmp_op* op, cudaStream_t st) {
   if (!op->ws || !op->ws->ms.err) return RFCMP_OK;
   int h_err = 0;
@@ -407,7 +409,7 @@ int check_tensor_core_waits(rfcmp_op* op, cudaStream_t st) {
   if (h_err) {
     RF_CUDA(cudaMemsetAsync(op->ws->ms.err, 0, sizeof(int), st));
     return set_error(RFCMP_ERR_DEVICE_TIMEOUT,
-                     "a tensor-core product gave up a bounded wait (code " + std::to_string(h_err) + ")");
+                     "a bounded device-side wait gave up (code " + std::to_string(h_err) + ")");
   }
   return RFCMP_OK;
 }
@@ -1588,7 +1590,7 @@ int solve_impl(rfcmp_op* op, const double2* e, double2* j, int nr, const rfcmp_s
     RF_CUDA(cudaMemcpy(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h_err) {
       RF_CUDA(cudaMemset(op->ws->ms.err, 0, sizeof(int)));
-      return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a tensor-core product gave up a bounded wait (code " +
+      return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up (code " +
                                                      std::to_string(h_err) + ")");
     }
   }

@@ -348,6 +348,8 @@ cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, bool conj, GemvMod
   const long long units = (long long)rowblocks * upr;
   ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", 8.0 * n * n + 32.0 * n * NR,
                  8.0 * n * n * NR, s);
+  if (mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err)
+    return gemv_stream_c64<NR <= 1 ? 1 : 2>(M, ld, n, conj, w, s);
 #define RF_LAUNCH_C(FFV, CJ)                                                                      \
   {                                                                                               \
     auto k = gemv_c64_kernel<NR, FFV, CJ>;                                                        \
@@ -372,6 +374,8 @@ cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n,
   const long long units = (long long)rowblocks * upr;
   ProfScope prof(mode == GEMV_FF ? "gemv_r32_ff" : "gemv_r32_f32",
                  (mode == GEMV_FF ? 8.0 : 4.0) * n * n + 32.0 * n * NR, 4.0 * n * n * NR, s);
+  if (mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err)
+    return gemv_stream_r32<NR <= 1 ? 1 : 2>(Mhi, ld, n, w, s);
   if (mode == GEMV_FF) {
     auto k = gemv_r32_kernel<NR, true>;
     const int grid = (int)gemv_grid(k, units, w);

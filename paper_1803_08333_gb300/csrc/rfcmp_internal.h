@@ -207,7 +207,14 @@ struct GemvScratch {
   int cap_n = 0, cap_ld = 0, cap_cols = 0;
   int chunk = 0;          // columns per work unit (multiple of 256; 0 = 1024)
   int ctas_per_sm = 0;    // persistent CTAs per SM (0 = occupancy maximum)
+  int* err = nullptr;     // set when a bounded device-side wait of the streaming GEMV gives up
 };
+// Streaming FP32-mode GEMV (k_gemv_stream.cu): the prepared x (w.xh) times the complex64 or FP32
+// matrix into the FP64 accumulator w.acc, rows streamed by bulk copies; NR = 1 or 2.
+template <int NR>
+cudaError_t gemv_stream_c64(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s);
+template <int NR>
+cudaError_t gemv_stream_r32(const float* M, int ld, int n, GemvScratch& w, cudaStream_t s);
 int padded_ld(int n);
 
 // y[:, r] = scale * op(M) x[:, r] (+ y[:, r] if accumulate), r < nrhs; M n x n complex64
