@@ -287,7 +287,7 @@ typedef struct {
                                exact-digit tensor-core products (each value as 6 signed 8-bit digits
                                under a power-of-two row scale, integer level sums exact in the FP32
                                accumulators; about 2^-48 of the row and column maxima per term),
-                               narrower ones on the float-float GEMV; 1..65536, default 8 */
+                               narrower ones on the float-float GEMV; 1..65536, default 4 */
   int32_t reserved[2];      /* must be zero */
 } rfcmp_plan;
 /* Fills plan with zeros (every field at its built-in choice). */

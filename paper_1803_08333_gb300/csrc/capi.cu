@@ -167,8 +167,9 @@ constexpr int NS_MIN_CELLS = 256;
 constexpr int MRHS_MIN = 4;
 // Float-float accurate products (right-hand side, refinement residuals, accurate applications)
 // with at least this many columns run as exact-digit tensor-core products instead of the
-// float-float GEMV, which spends some 40 FP32 instructions per complex multiply-add.
-constexpr int EXACT_MIN = 8;
+// float-float GEMV, which spends some 40 FP32 instructions per complex multiply-add (measured on
+// GB300: the exact-digit product wins from 4 columns at 2k unknowns, from 2 at 17k and above).
+constexpr int EXACT_MIN = 4;
 constexpr double NS_START_TOL = 1e-2;
 constexpr int NS_MAX_STEPS = 14;
 

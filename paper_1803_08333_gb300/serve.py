@@ -38,8 +38,8 @@ def op_footprint(nv: int, nc: int, nrhs: int, with_factors: bool, widest: int = 
     """Upper estimate of the device bytes an operator and one solve of nrhs columns add.
 
     The complex64 T_A and V come with the operator; the BF16 planes of the tensor-core inner
-    products (from 4 columns) and the exact-digit planes of the accurate products (from 8
-    columns) are built on the first solve that wide, so an operator whose widest solve so far
+    products and the exact-digit planes of the accurate products (both from 4 columns) are
+    built on the first solve that wide, so an operator whose widest solve so far
     had `widest` columns only adds what that solve has not built yet.
     """
     ne = 3 * nc // 2
@@ -51,7 +51,7 @@ def op_footprint(nv: int, nc: int, nrhs: int, with_factors: bool, widest: int = 
         b = 0
         if w >= 4:
             b += 8 * cplx + (4 * real if with_factors else 0)  # BF16 hi/lo (Re and Im)
-        if w >= 8:
+        if w >= 4:
             b += 24 * cplx + (12 * real if with_factors else 0)  # six BF16 digit planes
         return b
 
