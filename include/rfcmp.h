@@ -88,7 +88,7 @@ typedef enum {
 
 /* how alpha, beta, gamma are chosen */
 typedef enum {
-  RFCMP_SCALE_POWER = 0, /* norms by power iteration (Sec. 4, second display); the default */
+  RFCMP_SCALE_POWER = 0, /* norms of Sec. 4, second display, estimated iteratively (Lanczos); the default */
   RFCMP_SCALE_K = 1,     /* alpha = sqrt k, beta = 1/sqrt k, gamma = k (Sec. 4, third display) */
   RFCMP_SCALE_FIXED = 2  /* the values given in rfcmp_op_opts */
 } rfcmp_scaling;
@@ -101,15 +101,17 @@ typedef enum {
 
 typedef struct {
   int32_t scaling;      /* rfcmp_scaling; default RFCMP_SCALE_POWER */
-  int32_t power_steps;  /* maximum power-iteration steps for each norm; default 30 */
+  int32_t power_steps;  /* maximum iteration steps for each norm (a Lanczos iteration whose largest
+                           Ritz value converges to the spectral norm the power iteration of
+                           Sec. 4 estimates); default 30 */
   double alpha, beta, gamma; /* used with RFCMP_SCALE_FIXED */
   double factor_tol;    /* relative residual of the dense-inverse builds of (Sigma^T Sigma)^+
                            and G_ll^{-1}; default 1e-13 */
-  double power_rtol;    /* power iteration stops once the Rayleigh quotient changes by at most
-                           power_rtol (relative) between two steps, after at least 2 and at most
-                           power_steps steps; 0 = always power_steps; default 1e-3 */
-  const rfcmp_op* scaling_start; /* NULL, or an op on the same mesh: the power iterations start
-                           from its final iterates instead of the splitmix64 vectors (a
+  double power_rtol;    /* a norm iteration stops once its estimate changes by at most power_rtol
+                           (relative) between two steps, after at least 2 and at most power_steps
+                           steps; 0 = always power_steps; default 1e-3 */
+  const rfcmp_op* scaling_start; /* NULL, or an op on the same mesh: the norm iterations start
+                           from its final Ritz vectors instead of the splitmix64 vectors (a
                            frequency sweep converges in a few steps); default NULL */
   int32_t reserved[8];  /* must be zero */
 } rfcmp_op_opts;

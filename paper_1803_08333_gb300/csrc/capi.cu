@@ -253,7 +253,9 @@ struct rfcmp_op {
   rfcmp_op_info info{};
   std::unique_ptr<Workspace> ws;
   std::unique_ptr<SolveBuffers> sb;
-  double2* power_vecs = nullptr;  // N x 3: final iterates of the X, Z and Y power iterations
+  double2* power_vecs = nullptr;  // N x 3: Ritz vectors of the X, Z and Y norm iterations
+  double2* lanczos = nullptr;     // Lanczos basis of the norm iterations (lanczos_slots x N x 2)
+  int lanczos_slots = 0;
   CplxPlanes ta_planes, v_planes;  // BF16 planes of T_A and V, built on the first multi-RHS product
   ExactOperand ta_digits, v_digits;  // exact-digit planes of T_A and V, built on the first accurate one
   std::vector<void*> lazy;           // the planes and digits above, released by rfcmp_op_trim
@@ -262,6 +264,7 @@ struct rfcmp_op {
   ~rfcmp_op() {
     for (void* p : owned) cudaFree(p);
     for (void* p : lazy) cudaFree(p);
+    if (lanczos) cudaFree(lanczos);
   }
 };
 
@@ -707,6 +710,55 @@ void splitmix_start(std::vector<double2>& h, int64_t n, uint64_t seed) {
 // through operator c), by normalised power steps from splitmix64 start vectors (seeds[c]);
 // Rayleigh-quotient estimates.  Each column stops once its estimate changes by at most rtol
 // (relative) between steps (after at least 2 steps; rtol = 0: always `steps`).
+// Largest eigenpair of a small symmetric matrix (row-major m x m) by cyclic Jacobi rotations.
+double small_sym_max_eig(std::vector<double> A, int m, std::vector<double>& vec) {
+  std::vector<double> V((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) off += A[(size_t)p * m + q] * A[(size_t)p * m + q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[(size_t)p * m + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double th = 0.5 * (A[(size_t)q * m + q] - A[(size_t)p * m + p]) / apq;
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+          A[(size_t)k * m + p] = c * akp - sn * akq;
+          A[(size_t)k * m + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+          A[(size_t)p * m + k] = c * apk - sn * aqk;
+          A[(size_t)q * m + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+          V[(size_t)k * m + p] = c * vkp - sn * vkq;
+          V[(size_t)k * m + q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+  int best = 0;
+  for (int i = 1; i < m; ++i)
+    if (A[(size_t)i * m + i] > A[(size_t)best * m + best]) best = i;
+  vec.resize(m);
+  for (int k = 0; k < m; ++k) vec[k] = V[(size_t)k * m + best];
+  return A[(size_t)best * m + best];
+}
+
+// Largest eigenvalue of the Hermitian positive semi-definite operators X, Z (two columns at once)
+// and Y of the scaling (Sec. 4, second display), i.e. their spectral norms, by a Lanczos
+// iteration per column: the Ritz value of the tridiagonal T_j grows monotonically to the largest
+// eigenvalue and converges far faster than the power iteration's Rayleigh quotient from the same
+// start.  Stops a column once its Ritz value moves by at most rtol (relative) between two steps,
+// after at least 2 and at most `steps` steps (rtol = 0: always `steps`).  The start is the
+// splitmix64 vector of each seed or `start`; `keep` receives each column's Ritz vector (the warm
+// start of the next wavenumber of a sweep).
 template <class Op>
 int power_norms(rfcmp_op* op, Op apply, int cols, const uint64_t* seeds, int steps, double rtol, double* lam,
                 const double2* start, double2* keep, cudaStream_t st) {
@@ -714,47 +766,106 @@ int power_norms(rfcmp_op* op, Op apply, int cols, const uint64_t* seeds, int ste
   RF_TRY(ensure_solve_buffers(op, cols));
   RF_TRY(ensure_workspace(op, cols));
   SolveBuffers& B = *op->sb;
+  const size_t slot = (size_t)N * cols;
+  if (op->lanczos_slots < steps + 1) {
+    if (op->lanczos) cudaFree(op->lanczos);
+    op->lanczos = nullptr;
+    op->lanczos_slots = 0;
+    RF_CUDA(cudaMalloc(&op->lanczos, sizeof(double2) * slot * 2 * (steps + 1)));  // room for 2 columns
+    op->lanczos_slots = steps + 1;
+  }
+  double2* Vb = op->lanczos;
+  auto Vs = [&](int j) { return Vb + (size_t)j * slot; };
   if (start) {
-    RF_CUDA(cudaMemcpyAsync(B.p, start, sizeof(double2) * N * cols, cudaMemcpyDeviceToDevice, st));
+    RF_CUDA(cudaMemcpyAsync(Vs(0), start, sizeof(double2) * slot, cudaMemcpyDeviceToDevice, st));
   } else {
     std::vector<double2> h;
     for (int c = 0; c < cols; ++c) {
       splitmix_start(h, N, seeds[c]);
-      RF_CUDA(cudaMemcpyAsync(B.p + c * N, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, st));
+      RF_CUDA(cudaMemcpyAsync(Vs(0) + c * N, h.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, st));
     }
   }
-  std::vector<double2> d1(cols), d2(cols);
-  std::vector<double> coef(cols), prev(cols, 0.0);
-  std::vector<int> done(cols, 0);
-  RF_K(vec_dot(B.p, B.p, N, cols, B.dots, st));
-  RF_CUDA(cudaMemcpyAsync(d1.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
+  std::vector<double2> d(cols);
+  std::vector<double> coef(cols);
+  std::vector<std::vector<double>> al(cols), be(cols);  // T_j: diagonal al, off-diagonal be[1..]
+  std::vector<double> theta(cols, 0.0);
+  std::vector<int> done(cols, 0), size(cols, 0);
+  RF_K(vec_dot(Vs(0), Vs(0), N, cols, B.dots, st));
+  RF_CUDA(cudaMemcpyAsync(d.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
   RF_CUDA(cudaStreamSynchronize(st));
-  for (int c = 0; c < cols; ++c) coef[c] = 1.0 / std::sqrt(d1[c].x);
+  for (int c = 0; c < cols; ++c) coef[c] = d[c].x > 0.0 ? 1.0 / std::sqrt(d[c].x) : 0.0;
   RF_CUDA(cudaMemcpyAsync(B.alpha, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
-  RF_K(vec_copy_scale_cols(B.p, B.alpha, B.p, N, cols, st));
-  for (int c = 0; c < cols; ++c) lam[c] = 0.0;
-  for (int it = 0; it < steps; ++it) {
-    RF_TRY(apply(op, B.p, B.Ap, st));
-    RF_K(vec_dot(B.p, B.Ap, N, cols, B.dots, st));
-    RF_CUDA(cudaMemcpyAsync(d1.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
-    RF_K(vec_dot(B.Ap, B.Ap, N, cols, B.dots, st));
-    RF_CUDA(cudaMemcpyAsync(d2.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
+  RF_K(vec_copy_scale_cols(Vs(0), B.alpha, Vs(0), N, cols, st));
+  int j = 0;
+  for (; j < steps; ++j) {
+    double2* W = B.Ap;
+    RF_TRY(apply(op, Vs(j), W, st));
+    RF_K(vec_dot(Vs(j), W, N, cols, B.dots, st));  // alpha_j = v_j^H A v_j (real)
+    RF_CUDA(cudaMemcpyAsync(d.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
+    RF_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c < cols; ++c) coef[c] = d[c].x;
+    for (int c = 0; c < cols; ++c)
+      if (!done[c]) al[c].push_back(d[c].x);
+    RF_CUDA(cudaMemcpyAsync(B.alpha, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+    RF_K(vec_axpy_cols(B.alpha, true, Vs(j), W, N, cols, nullptr, st));  // w -= alpha_j v_j
+    if (j > 0) {
+      for (int c = 0; c < cols; ++c) coef[c] = be[c].size() > (size_t)j ? be[c][j] : 0.0;
+      RF_CUDA(cudaMemcpyAsync(B.beta, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+      RF_K(vec_axpy_cols(B.beta, true, Vs(j - 1), W, N, cols, nullptr, st));  // w -= beta_j v_{j-1}
+    }
+    RF_K(vec_dot(W, W, N, cols, B.dots, st));
+    RF_CUDA(cudaMemcpyAsync(d.data(), B.dots, sizeof(double2) * cols, cudaMemcpyDeviceToHost, st));
     RF_CUDA(cudaStreamSynchronize(st));
     bool all = true;
     for (int c = 0; c < cols; ++c) {
       if (done[c]) continue;
-      prev[c] = lam[c];
-      lam[c] = d1[c].x;
-      if (rtol > 0.0 && it >= 1 && std::fabs(lam[c] - prev[c]) <= rtol * std::fabs(lam[c])) done[c] = 1;
-      if (!(d2[c].x > 0.0)) done[c] = 1;
+      const int m = (int)al[c].size();
+      std::vector<double> T((size_t)m * m, 0.0), s;
+      for (int i = 0; i < m; ++i) {
+        T[(size_t)i * m + i] = al[c][i];
+        if (i > 0) T[(size_t)i * m + i - 1] = T[(size_t)(i - 1) * m + i] = be[c][i];
+      }
+      const double prev = theta[c];
+      theta[c] = small_sym_max_eig(T, m, s);
+      size[c] = m;
+      const double bnext = d[c].x > 0.0 ? std::sqrt(d[c].x) : 0.0;
+      if (be[c].empty()) be[c].push_back(0.0);  // be[0] unused
+      be[c].push_back(bnext);
+      if ((rtol > 0.0 && j >= 1 && std::fabs(theta[c] - prev) <= rtol * std::fabs(theta[c])) ||
+          !(bnext > 1e-14 * std::fabs(theta[c])))
+        done[c] = 1;
       all &= done[c] != 0;
-      coef[c] = d2[c].x > 0.0 ? 1.0 / std::sqrt(d2[c].x) : 0.0;
     }
-    if (all) break;
+    if (all || j + 1 == steps) {
+      ++j;
+      break;
+    }
+    for (int c = 0; c < cols; ++c) coef[c] = !done[c] && be[c].back() > 0.0 ? 1.0 / be[c].back() : 0.0;
     RF_CUDA(cudaMemcpyAsync(B.alpha, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
-    RF_K(vec_copy_scale_cols(B.Ap, B.alpha, B.p, N, cols, st));
+    RF_K(vec_copy_scale_cols(W, B.alpha, Vs(j + 1), N, cols, st));  // v_{j+1} = w / beta_{j+1}
   }
-  if (keep) RF_CUDA(cudaMemcpyAsync(keep, B.p, sizeof(double2) * N * cols, cudaMemcpyDeviceToDevice, st));
+  for (int c = 0; c < cols; ++c) lam[c] = theta[c];
+  if (keep) {
+    // Ritz vectors: keep[:, c] = sum_i s_i v_i with s the top eigenvector of column c's T
+    RF_CUDA(cudaMemsetAsync(keep, 0, sizeof(double2) * slot, st));
+    std::vector<std::vector<double>> S(cols);
+    for (int c = 0; c < cols; ++c) {
+      const int m = size[c];
+      std::vector<double> T((size_t)m * m, 0.0);
+      for (int i = 0; i < m; ++i) {
+        T[(size_t)i * m + i] = al[c][i];
+        if (i > 0) T[(size_t)i * m + i - 1] = T[(size_t)(i - 1) * m + i] = be[c][i];
+      }
+      small_sym_max_eig(T, m, S[c]);
+    }
+    int mmax = 0;
+    for (int c = 0; c < cols; ++c) mmax = std::max(mmax, size[c]);
+    for (int i = 0; i < mmax; ++i) {
+      for (int c = 0; c < cols; ++c) coef[c] = i < size[c] ? S[c][i] : 0.0;
+      RF_CUDA(cudaMemcpyAsync(B.alpha, coef.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+      RF_K(vec_axpy_cols(B.alpha, false, Vs(i), keep, N, cols, nullptr, st));
+    }
+  }
   return RFCMP_OK;
 }
 
