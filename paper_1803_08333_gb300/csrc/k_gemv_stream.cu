@@ -8,8 +8,8 @@
 // together with the matching segment of x into a 4-stage shared-memory ring, so about 180 KB per
 // SM are in flight whatever the consumers do.  Eight consumer warps each take one row of a
 // stage, read it and x from shared memory (no global-memory latency on the consumer side),
-// accumulate in FP32 within the segment and in FP64 across segments, and release the stage
-// through an mbarrier.  Work units (row block, column segment) are dealt to
+// accumulate in FP32 within the segment and in compensated FP32 across segments, and release
+// the stage through an mbarrier.  Work units (row block, column segment) are dealt to
 // the persistent CTAs in contiguous ranges of equal size; a row block split between CTAs is
 // combined by FP64 atomics.  Every wait is bounded and records an error code on timeout.
 #include <cuda_runtime.h>
@@ -105,10 +105,13 @@ gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __r
     return;
   }
 
-  // consumer warp: row `warp` of every stage
-  double acc[NR][2];
+  // consumer warp: row `warp` of every stage.  Segment sums are FP32; across segments they are
+  // added into an FP32 pair (hi, compensation) by an error-free two-sum, so the row sum keeps
+  // about twice FP32 precision without FP64 arithmetic in the loop (GB300's FP64 pipe runs at
+  // a small fraction of the FP32 rate); FP64 enters only at the per-row flush.
+  float acc[NR][2], cmp[NR][2];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = 0.0;
+  for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = cmp[r][0] = cmp[r][1] = 0.f;
   long long cur_rb = -1;
   bool ok = true;
   for (long long u = u0; u < u1 && ok; ++u) {
@@ -121,8 +124,9 @@ gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __r
         const int row = (int)cur_rb * SROWS + warp;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          const double re = warp_sum_d(acc[r][0]), im = warp_sum_d(acc[r][1]);
-          acc[r][0] = acc[r][1] = 0.0;
+          const double re = warp_sum_d((double)acc[r][0] + (double)cmp[r][0]);
+          const double im = warp_sum_d((double)acc[r][1] + (double)cmp[r][1]);
+          acc[r][0] = acc[r][1] = cmp[r][0] = cmp[r][1] = 0.f;
           if (lane == 0 && row < n) {
             double* o = reinterpret_cast<double*>(out + (size_t)r * n + row);
             atomicAdd(o, re);
@@ -185,10 +189,13 @@ gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __r
         }
       }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        acc[r][0] += (double)f[r][0];
-        acc[r][1] += (double)f[r][1];
-      }
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {  // two-sum: acc + f = t + e exactly
+          const float a = acc[r][c], b = f[r][c], t = a + b, bb = t - a;
+          cmp[r][c] += (a - (t - bb)) + (b - bb);
+          acc[r][c] = t;
+        }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -197,7 +204,8 @@ gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __r
     const int row = (int)cur_rb * SROWS + warp;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      const double re = warp_sum_d(acc[r][0]), im = warp_sum_d(acc[r][1]);
+      const double re = warp_sum_d((double)acc[r][0] + (double)cmp[r][0]);
+      const double im = warp_sum_d((double)acc[r][1] + (double)cmp[r][1]);
       if (lane == 0 && row < n) {
         double* o = reinterpret_cast<double*>(out + (size_t)r * n + row);
         atomicAdd(o, re);
