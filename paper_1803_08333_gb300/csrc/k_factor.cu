@@ -9,10 +9,14 @@
 //     X_{k+1} = X_k + X_k R_k   (dense product, split-BF16 tensor-core GEMM, FP64 update; X_k R_k
 //                                is symmetric, so only its upper tiles are computed)
 // converges quadratically: the relative error e_k of X_k obeys e_{k+1} <= e_k^2 + c e_k with
-// c ~ 2^-16 the accuracy of one split product, so a V-cycle start (e_0 ~ 0.1) reaches rounding
-// level in about five steps.  X_k stays exactly symmetric (the update mirrors the upper tiles;
-// the residual below is formed along rows, as R^T, which needs it); an iteration that stops
-// contracting ends early so that the caller can fall back to a PCG solve.
+// c ~ 2^-16 the accuracy of one split product.  A V-cycle start leaves the smallest eigenvalue a
+// of M X0 near 0.02, where plain steps only double it; so after one plain step (which puts the
+// spectrum in (0, 1]) the lower end a is estimated by a few power steps on I - M X and the next
+// steps are scaled (X <- alpha X (2 I - alpha M X), alpha = 2 / (1 + a)), which roughly
+// quadruples a per step until it nears 1; plain quadratic steps finish.  X_k stays exactly
+// symmetric (the update mirrors the upper tiles; the residual below is formed along rows, as
+// R^T, which needs it); a plain iteration that stops contracting ends early so that the caller
+// can fall back to a PCG solve.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -27,12 +31,12 @@ namespace rfcmp {
 
 namespace {
 
-// Rt[i][j] = delta_ij - (X M)[i][j] with M = L + 1 1^T / n (L symmetric CSR; without rowsum,
-// M = L), written as BF16 hi/lo planes; rowsum[i] = sum_j X[i][j] is precomputed.  Also tracks
-// max |Rt|.
+// Rt[i][j] = delta_ij - alpha (X M)[i][j] with M = L + 1 1^T / n (L symmetric CSR; without
+// rowsum, M = L), written as BF16 hi/lo planes; rowsum[i] = sum_j X[i][j] is precomputed.  Also
+// tracks max |Rt|.
 __global__ void ns_residual_kernel(const double* __restrict__ X, long long ldx, int n, const int32_t* __restrict__ ptr,
                                    const int32_t* __restrict__ col, const double* __restrict__ val,
-                                   const double* __restrict__ rowsum, __nv_bfloat16* __restrict__ hi,
+                                   const double* __restrict__ rowsum, double alpha, __nv_bfloat16* __restrict__ hi,
                                    __nv_bfloat16* __restrict__ lo, long long ldp,
                                    unsigned long long* __restrict__ maxbits) {
   const int i = blockIdx.y;
@@ -42,7 +46,7 @@ __global__ void ns_residual_kernel(const double* __restrict__ X, long long ldx, 
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double a = rs;
     for (int q = ptr[j]; q < ptr[j + 1]; ++q) a += xr[col[q]] * val[q];  // (X L)_ij, L symmetric
-    const double r = (i == j ? 1.0 : 0.0) - a;
+    const double r = (i == j ? 1.0 : 0.0) - alpha * a;
     const float rf = (float)r;
     const __nv_bfloat16 h = __float2bfloat16_rn(rf);
     hi[(size_t)i * ldp + j] = h;
@@ -115,11 +119,11 @@ __global__ void symmetrize_inplace_kernel(double* __restrict__ X, long long ldx,
   }
 }
 
-// X += D for a symmetric D of which only the 128 x 128 tiles on or above the diagonal were
-// computed: block (bx, by), by <= bx, adds tile (by, bx) of D to X there and its transpose to
-// tile (bx, by); a diagonal tile adds (D + D^T) / 2, so X stays exactly symmetric.
+// X <- alpha (X + D) for a symmetric D of which only the 128 x 128 tiles on or above the diagonal
+// were computed: block (bx, by), by <= bx, adds tile (by, bx) of D to X there and its transpose
+// to tile (bx, by); a diagonal tile adds (D + D^T) / 2, so X stays exactly symmetric.
 __global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, const float* __restrict__ D, long long ldd,
-                                     int n) {
+                                     int n, double alpha) {
   __shared__ float t[TT][TT + 1];
   const int bx = blockIdx.x, by = blockIdx.y;
   if (by > bx) return;
@@ -132,11 +136,54 @@ __global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, cons
   for (int r = threadIdx.y; r < TT; r += blockDim.y) {
     const int c = threadIdx.x;
     const int i = r0 + r, j = c0 + c;
-    if (i < n && j < n)
-      X[(size_t)i * ldx + j] += bx == by ? 0.5 * ((double)t[r][c] + (double)t[c][r]) : (double)t[r][c];
+    if (i < n && j < n) {
+      double* x = X + (size_t)i * ldx + j;
+      *x = alpha * (*x + (bx == by ? 0.5 * ((double)t[r][c] + (double)t[c][r]) : (double)t[r][c]));
+    }
     const int i2 = c0 + r, j2 = r0 + c;
-    if (bx != by && i2 < n && j2 < n) X[(size_t)i2 * ldx + j2] += (double)t[c][r];
+    if (bx != by && i2 < n && j2 < n) {
+      double* x = X + (size_t)i2 * ldx + j2;
+      *x = alpha * (*x + (double)t[c][r]);
+    }
   }
+}
+
+// u = X v (dense FP64, one warp per row); sum += sum_i u_i
+__global__ void dmatvec_kernel(const double* __restrict__ X, long long ldx, int n, const double* __restrict__ v,
+                               double* __restrict__ u, double* __restrict__ sum) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* xr = X + (size_t)warp * ldx;
+  double a = 0.0;
+  for (int j = lane; j < n; j += 32) a = fma(xr[j], v[j], a);
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  if (lane == 0) {
+    u[warp] = a;
+    atomicAdd(sum, a);
+  }
+}
+
+// w = v - (L u + (sum / n) 1 if project); norm2 += |w|^2
+__global__ void resid_vec_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, int n, int project, const double* __restrict__ v,
+                                 const double* __restrict__ u, const double* __restrict__ sum,
+                                 double* __restrict__ w, double* __restrict__ norm2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0;
+  if (i < n) {
+    double a = project ? *sum / n : 0.0;
+    for (int q = ptr[i]; q < ptr[i + 1]; ++q) a += val[q] * u[col[q]];
+    const double r = v[i] - a;
+    w[i] = r;
+    d = r * r;
+  }
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(norm2, d);
+}
+
+__global__ void scale_vec_kernel(int n, double c, const double* __restrict__ w, double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = c * w[i];
 }
 
 // X = c D^{-1} (D the diagonal of the CSR matrix), the rest of X zero
@@ -201,7 +248,40 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
   B.lo = rl;
   B.rows = n;
   B.ld = ldp;
-  double res = 1.0;
+  // vectors of the spectral-radius estimate: v, u, w (n each) and two scalars
+  double* pv;
+  if ((err = cudaMalloc(&pv, (3 * (size_t)n + 2) * sizeof(double))) != cudaSuccess) return fail(err);
+  own.push_back(pv);
+  double *pu = pv + n, *pw = pv + 2 * (size_t)n, *psc = pv + 3 * (size_t)n;
+  // rho(I - M X) by a few power steps on I - M X (matrix-free: one dense FP64 product with X and
+  // one sparse product with M per step).  A power iteration approaches rho from below, so the
+  // bound a = 1 - rho on the smallest eigenvalue of M X is optimistic; any a in (0, 1) keeps the
+  // scaled steps convergent, an overestimate only makes them less effective.
+  auto estimate_rho = [&](double& rho) -> cudaError_t {
+    std::vector<double> h(n);
+    for (int i = 0; i < n; ++i) h[i] = 1.0 + 0.5 * std::sin(0.7 * i) + 0.25 * std::cos(1.3 * i + 0.4);
+    double nrm = 0.0;
+    for (double x : h) nrm += x * x;
+    for (double& x : h) x /= std::sqrt(nrm);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(pv, h.data(), n * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    rho = 0.0;
+    for (int it = 0; it < 12; ++it) {
+      if ((e = cudaMemsetAsync(psc, 0, 2 * sizeof(double), s)) != cudaSuccess) return e;
+      dmatvec_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(X, ldx, n, pv, pu, psc);
+      resid_vec_kernel<<<(n + 255) / 256, 256, 0, s>>>(ptr, col, val, n, project ? 1 : 0, pv, pu, psc, pw, psc + 1);
+      double nw2 = 0.0;
+      if ((e = cudaMemcpyAsync(&nw2, psc + 1, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      rho = std::sqrt(nw2);
+      if (!(rho > 0.0)) break;
+      scale_vec_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, 1.0 / rho, pw, pv);
+    }
+    return cudaGetLastError();
+  };
+  double res = 1.0, prev = 1.0;
+  bool prev_plain = false;
+  double alpha = 1.0, a = -1.0;  // scaling of the next step; lower bound on the spectrum of M X
   int k = 0;
   const dim3 sgrid((n + TT - 1) / TT, (n + TT - 1) / TT), sblock(TT, 8);
   // the residual below is formed along rows as I - X M, which is R^T only for symmetric X
@@ -212,26 +292,42 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
     {
       ProfScope prof("factor_ns_residual", 16.0 * (double)n * n, 0.0, s);
       dim3 grid((n + 255) / 256 < 8 ? (n + 255) / 256 : 8, n);
-      ns_residual_kernel<<<grid, 256, 0, s>>>(X, ldx, n, ptr, col, val, project ? rowsum : nullptr, rh, rl, ldp,
-                                              maxbits);
+      ns_residual_kernel<<<grid, 256, 0, s>>>(X, ldx, n, ptr, col, val, project ? rowsum : nullptr, alpha, rh, rl,
+                                              ldp, maxbits);
     }
     unsigned long long hb = 0;
     if ((err = cudaMemcpyAsync(&hb, maxbits, sizeof(hb), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(err);
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);
-    const double prev = res;
-    std::memcpy(&res, &hb, sizeof(res));
-    if (!(res > tol) || k >= max_steps) break;
-    if (k >= 2 && !(res < 0.9 * prev)) break;  // not contracting: the caller falls back
+    const bool plain = alpha == 1.0;
+    if (plain) {  // the residual of the current iterate: stop and contraction checks
+      std::memcpy(&res, &hb, sizeof(res));
+      if (!(res > tol)) break;
+      if (prev_plain && k >= 2 && !(res < 0.9 * prev)) break;  // not contracting: the caller falls back
+      prev = res;
+    }
+    prev_plain = plain;
+    if (k >= max_steps) break;
     if ((err = split_bf16_f64(X, ldx, n, n, xh, xl, ldp, s)) != cudaSuccess) return fail(err);
-    // D = X R with B = R^T stored row-major (B[j][k] = R[k][j] = Rt[j][k]); X R = X - X M X is
-    // symmetric, so only the tiles on and above the diagonal are computed
+    // D = X R' with B = R'^T stored row-major, R' = I - alpha M X; X R' is symmetric, so only the
+    // tiles on and above the diagonal are computed; then X <- alpha (X + D)
     if ((err = gemm_bf16x3(&A, &B, nullptr, 1, n, n, n, D, ldp, false, gerr, s, 0, true)) != cudaSuccess)
       return fail(err);
     {
       ProfScope prof("factor_ns_update", 12.0 * (double)n * n, 0.0, s);
-      ns_update_sym_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, D, ldp, n);
+      ns_update_sym_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, D, ldp, n, alpha);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return fail(err);
+    // scaling of the next step (scaled Newton-Schulz): with the spectrum of M X in [a, 1], the
+    // step X <- alpha X (2 I - alpha M X), alpha = 2 / (1 + a), maps it into [a', 1] with
+    // a' = alpha a (2 - alpha a), which grows about four-fold per step while a is small
+    if (k == 0) {  // after one plain step the spectrum lies in (0, 1]: estimate its lower end
+      double rho = 1.0;
+      if ((err = estimate_rho(rho)) != cudaSuccess) return fail(err);
+      a = 1.0 - rho;
+    } else if (!plain) {
+      a = alpha * a * (2.0 - alpha * a);
+    }
+    alpha = (a > 1e-6 && a < 0.95) ? 2.0 / (1.0 + a) : 1.0;
   }
   int herr = 0;
   if ((err = cudaMemcpyAsync(&herr, gerr, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(err);

@@ -1175,8 +1175,10 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
   int W = n_pad;
   if ((size_t)W * per_col > cap) W = std::max<int>(BCG_COLS, (int)(cap / per_col) / BCG_COLS * BCG_COLS);
   const size_t bytes = (size_t)n * W * sizeof(double);
-  double *X, *R, *P, *AP, *Z = nullptr, *T0 = nullptr, *sc;
+  double *X, *R, *P = nullptr, *AP = nullptr, *Z = nullptr, *T0 = nullptr, *sc;
+  const bool iterate = !(mg && max_iter == 0);  // max_iter 0 with a hierarchy: one V-cycle, no CG
   for (double** p : {&X, &R, &P, &AP}) {
+    if (!iterate && (p == &P || p == &AP)) continue;
     if ((err = cudaMalloc(p, bytes)) != cudaSuccess) return fail(err);
     own.push_back(*p);
   }
@@ -1264,15 +1266,15 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
       return Z;
     };
     double* Zp = precond(R);
-    if (max_iter == 0) {
-      // no iteration: the result is one preconditioner application, X = M^-1-approximation R0
-      if ((err = cudaMemcpyAsync(X, Zp, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return fail(err);
+    double* Xres = X;  // the block stored below
+    if (!iterate) Xres = Zp;  // no iteration: the result is one V-cycle applied to R0
+    else {
+      bcg_dot_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, R, Zp, rzr);
+      if ((err = cudaMemcpyAsync(P, Zp, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return fail(err);
     }
-    bcg_dot_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, R, Zp, rzr);
-    if ((err = cudaMemcpyAsync(P, Zp, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return fail(err);
     int it = 0;
     bool done = false;
-    while (!done && it < max_iter) {
+    while (iterate && !done && it < max_iter) {
       double* rz = rzr + (size_t)(it % 3) * W;
       double* rz_new = rzr + (size_t)((it + 1) % 3) * W;
       double* rz_next = rzr + (size_t)((it + 2) % 3) * W;
@@ -1309,12 +1311,12 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
     worst_iters = std::max(worst_iters, it);
     if (project) {
       if ((err = cudaMemsetAsync(sums, 0, sizeof(double) * W, s)) != cudaSuccess) return fail(err);
-      bcg_colsum_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, X, sums);
+      bcg_colsum_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, Xres, sums);
     }
     if (Xd && project)
-      bcg_store_f64_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, X, sums, Xd);
+      bcg_store_f64_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, Xres, sums, Xd);
     else
-      bcg_store_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, X, sums, project, Xhi, Xlo);
+      bcg_store_kernel<<<grid, BCG_THREADS, 0, s>>>(n, w, c0, ld, Xres, sums, project, Xhi, Xlo);
     if ((err = cudaGetLastError()) != cudaSuccess) return fail(err);
   }
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return fail(err);
