@@ -195,6 +195,18 @@ struct DenseFactor {
   }
 };
 
+// Topology and device geometry of one mesh, shared by every operator on it (a frequency sweep
+// or several requests on one mesh build them once).
+struct MeshEntry {
+  Topology top;
+  std::vector<double> verts;
+  DeviceGeometry g;
+  std::vector<void*> owned;
+  ~MeshEntry() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
 struct rfcmp_ctx {
   int device = 0;
   uint64_t budget = 0;
@@ -202,6 +214,7 @@ struct rfcmp_ctx {
   std::mutex mu;
   std::map<uint64_t, std::shared_ptr<DenseFactor>> lplus_cache;  // key: connectivity hash
   std::map<uint64_t, std::shared_ptr<DenseFactor>> gll_cache;    // key: connectivity + coordinates hash
+  std::map<uint64_t, std::shared_ptr<MeshEntry>> mesh_cache;      // key: connectivity + coordinates
   std::mutex build_mu;  // one factor build at a time, so concurrent ops on one mesh share it
   std::atomic<int> live_ops{0};
   rfcmp_plan plan{};    // plan of operators created from now on
@@ -248,6 +261,7 @@ struct rfcmp_op {
   float2* V = nullptr;
   int ldN = 0, ldC = 0;
   std::shared_ptr<DenseFactor> lplus, gll;
+  std::shared_ptr<MeshEntry> mesh;  // owns the device geometry in g
   double k = 0.0, alpha = 1.0, beta = 1.0, gamma = 1.0;
   uint64_t bytes = 0;
   rfcmp_op_info info{};
@@ -908,10 +922,9 @@ int compute_scaling(rfcmp_op* op, const rfcmp_op_opts& o, cudaStream_t st) {
 }
 
 // ---- geometry upload ----
-int upload_geometry(rfcmp_op* op) {
-  const Topology& T = op->top;
+int upload_geometry(const Topology& T, const std::vector<double>& verts, DeviceGeometry& g, std::vector<void*>& own) {
   const int64_t nc = T.nc, nv = T.nv;
-  const double* X = op->verts.data();
+  const double* X = verts.data();
   static const Rule7 R;
   std::vector<double> area(nc), cen(3 * nc), qp(21 * nc);
   std::vector<float> cen_hi(3 * nc), cen_lo(3 * nc), rho(21 * nc), wq(7 * nc), aloc(9 * nc), inv_area(nc);
@@ -941,20 +954,18 @@ int upload_geometry(rfcmp_op* op) {
       for (int a = 0; a < 3; ++a) aloc[9 * c + 3 * i + a] = (float)(P[i][a] - cen[3 * c + a]);
     inv_area[c] = (float)(1.0 / area[c]);
   }
-  DeviceGeometry& g = op->g;
   g.nc = (int32_t)nc;
   g.ne = (int32_t)T.ne;
   g.nv = (int32_t)nv;
   g.ldN = padded_ld((int)T.ne);
   g.ldC = padded_ld((int)nc);
-  auto& own = op->owned;
   RF_TRY(upload(&g.cen_hi, cen_hi, own));
   RF_TRY(upload(&g.cen_lo, cen_lo, own));
   RF_TRY(upload(&g.rho, rho, own));
   RF_TRY(upload(&g.wq, wq, own));
   RF_TRY(upload(&g.aloc, aloc, own));
   RF_TRY(upload(&g.inv_area, inv_area, own));
-  RF_TRY(upload(&g.verts, op->verts, own));
+  RF_TRY(upload(&g.verts, verts, own));
   RF_TRY(upload(&g.cen64, cen, own));
   RF_TRY(upload(&g.area64, area, own));
   RF_TRY(upload(&g.qp64, qp, own));
@@ -1192,6 +1203,7 @@ int rfcmp_ctx_clear_cache(rfcmp_ctx* ctx) {
     if (kv.second.use_count() == 1) ctx->bytes -= kv.second->bytes;
   ctx->lplus_cache.clear();
   ctx->gll_cache.clear();
+  ctx->mesh_cache.clear();
   return RFCMP_OK;
 }
 
@@ -1222,11 +1234,44 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
     op->plan = ctx->plan;
   }
   std::string err;
-  int rc = build_topology(tris, nc, nv, op->top, err);
-  if (rc != RFCMP_OK) return set_error(rc, err);
-  if (op->top.ne >= (1ll << 31) / 1 || (double)op->top.ne * op->top.ne > 9e18)
-    return set_error(RFCMP_ERR_INVALID_ARG, "mesh too large");
-  op->verts.assign(verts, verts + 3 * nv);
+  int rc = RFCMP_OK;
+  // topology and device geometry: from the context's mesh cache when the same mesh (connectivity
+  // and coordinates, compared exactly) was seen before
+  uint64_t mesh_key = mix((uint64_t)nc, (uint64_t)nv);
+  for (int64_t i = 0; i < 3 * nc; ++i) mesh_key = mix(mesh_key, (uint64_t)(uint32_t)tris[i]);
+  for (int64_t i = 0; i < 3 * nv; ++i) {
+    uint64_t b;
+    std::memcpy(&b, &verts[i], 8);
+    mesh_key = mix(mesh_key, b);
+  }
+  std::shared_ptr<MeshEntry> me;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->mesh_cache.find(mesh_key);
+    if (it != ctx->mesh_cache.end() && it->second->top.nc == nc && it->second->top.nv == nv &&
+        std::equal(tris, tris + 3 * nc, it->second->top.tris.begin()) &&
+        std::equal(verts, verts + 3 * nv, it->second->verts.begin()))
+      me = it->second;
+  }
+  if (!me) {
+    auto fresh = std::make_shared<MeshEntry>();
+    rc = build_topology(tris, nc, nv, fresh->top, err);
+    if (rc != RFCMP_OK) return set_error(rc, err);
+    if (fresh->top.ne >= (1ll << 31) / 1 || (double)fresh->top.ne * fresh->top.ne > 9e18)
+      return set_error(RFCMP_ERR_INVALID_ARG, "mesh too large");
+    fresh->verts.assign(verts, verts + 3 * nv);
+    RF_TRY(upload_geometry(fresh->top, fresh->verts, fresh->g, fresh->owned));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->mesh_cache.size() >= 16)  // keep the cache small: drop entries no operator holds
+      for (auto it = ctx->mesh_cache.begin(); it != ctx->mesh_cache.end();)
+        it = it->second.use_count() == 1 ? ctx->mesh_cache.erase(it) : std::next(it);
+    ctx->mesh_cache[mesh_key] = fresh;
+    me = fresh;
+  }
+  op->mesh = me;
+  op->top = me->top;
+  op->verts = me->verts;
+  op->g = me->g;
   const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
   op->ldN = padded_ld(N);
   op->ldC = padded_ld(C);
@@ -1253,7 +1298,6 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   if (ctx->budget && ctx->bytes.load() + need > ctx->budget)
     return set_error(RFCMP_ERR_OUT_OF_BUDGET, "op needs " + std::to_string(need) + " bytes, budget has " +
                                                   std::to_string(ctx->budget - std::min(ctx->budget, ctx->bytes.load())));
-  RF_TRY(upload_geometry(op.get()));
   // topology factors
   op->info.ms_factors = 0.0;
   if (!lp) {
