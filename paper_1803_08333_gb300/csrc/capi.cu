@@ -69,7 +69,7 @@ template <class T>
 int dalloc(T** p, size_t count, std::vector<void*>& owned) {
   if (count == 0) count = 1;
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  cudaError_t e = dev_malloc(&q, count * sizeof(T));
   if (e != cudaSuccess) return set_error(RFCMP_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   owned.push_back(q);
   *p = static_cast<T*>(q);
@@ -186,12 +186,12 @@ struct DenseFactor {
   int iterations = 0;
   double ms = 0.0;
   ~DenseFactor() {
-    if (hi) cudaFree(hi);
-    if (lo) cudaFree(lo);
-    if (planes.h) cudaFree(planes.h);
-    if (planes.l) cudaFree(planes.l);
-    if (digits.d) cudaFree(digits.d);
-    if (digits.e) cudaFree(digits.e);
+    if (hi) dev_free(hi);
+    if (lo) dev_free(lo);
+    if (planes.h) dev_free(planes.h);
+    if (planes.l) dev_free(planes.l);
+    if (digits.d) dev_free(digits.d);
+    if (digits.e) dev_free(digits.e);
   }
 };
 
@@ -203,7 +203,7 @@ struct MeshEntry {
   DeviceGeometry g;
   std::vector<void*> owned;
   ~MeshEntry() {
-    for (void* p : owned) cudaFree(p);
+    for (void* p : owned) dev_free(p);
   }
 };
 
@@ -234,7 +234,7 @@ struct Workspace {
   GemvScratch gs;
   MrhsScratch ms;
   ~Workspace() {
-    for (void* p : owned) cudaFree(p);
+    for (void* p : owned) dev_free(p);
   }
 };
 
@@ -247,7 +247,7 @@ struct SolveBuffers {
   double *rho = nullptr, *alpha = nullptr, *beta = nullptr;
   int* active = nullptr;
   ~SolveBuffers() {
-    for (void* p : owned) cudaFree(p);
+    for (void* p : owned) dev_free(p);
   }
 };
 
@@ -276,9 +276,9 @@ struct rfcmp_op {
   uint64_t lazy_bytes = 0;
   rfcmp_plan plan{};               // launch shapes (zero fields: built-in choices)
   ~rfcmp_op() {
-    for (void* p : owned) cudaFree(p);
-    for (void* p : lazy) cudaFree(p);
-    if (lanczos) cudaFree(lanczos);
+    for (void* p : owned) dev_free(p);
+    for (void* p : lazy) dev_free(p);
+    if (lanczos) dev_free(lanczos);
   }
 };
 
@@ -399,8 +399,8 @@ int make_real_planes(rfcmp_op* op, DenseFactor& f, cudaStream_t st) {
   q.n = f.n;
   q.ldp = padded_ld(f.n);
   const size_t pl = (size_t)f.n * q.ldp;
-  RF_CUDA(cudaMalloc(&q.h, pl * sizeof(__nv_bfloat16)));
-  RF_CUDA(cudaMalloc(&q.l, pl * sizeof(__nv_bfloat16)));
+  RF_CUDA(dev_malloc(&q.h, pl * sizeof(__nv_bfloat16)));
+  RF_CUDA(dev_malloc(&q.l, pl * sizeof(__nv_bfloat16)));
   RF_CUDA(cudaMemsetAsync(q.h, 0, pl * sizeof(__nv_bfloat16), st));
   RF_CUDA(cudaMemsetAsync(q.l, 0, pl * sizeof(__nv_bfloat16), st));
   RF_K(split_bf16_f32(f.hi, q.ldp, f.n, f.n, q.h, q.l, q.ldp, st));
@@ -440,8 +440,8 @@ int alloc_digits(ExactOperand& q, int rows, long long ldp, std::vector<void*>* o
     RF_TRY(dalloc(&q.d, (size_t)EXACT_DIGITS * q.plane_stride, *owned));
     RF_TRY(dalloc(&q.e, (size_t)rows, *owned));
   } else {
-    RF_CUDA(cudaMalloc(&q.d, (size_t)EXACT_DIGITS * q.plane_stride * sizeof(__nv_bfloat16)));
-    RF_CUDA(cudaMalloc(&q.e, (size_t)rows * sizeof(int)));
+    RF_CUDA(dev_malloc(&q.d, (size_t)EXACT_DIGITS * q.plane_stride * sizeof(__nv_bfloat16)));
+    RF_CUDA(dev_malloc(&q.e, (size_t)rows * sizeof(int)));
   }
   return RFCMP_OK;
 }
@@ -782,10 +782,10 @@ int power_norms(rfcmp_op* op, Op apply, int cols, const uint64_t* seeds, int ste
   SolveBuffers& B = *op->sb;
   const size_t slot = (size_t)N * cols;
   if (op->lanczos_slots < steps + 1) {
-    if (op->lanczos) cudaFree(op->lanczos);
+    if (op->lanczos) dev_free(op->lanczos);
     op->lanczos = nullptr;
     op->lanczos_slots = 0;
-    RF_CUDA(cudaMalloc(&op->lanczos, sizeof(double2) * slot * 2 * (steps + 1)));  // room for 2 columns
+    RF_CUDA(dev_malloc(&op->lanczos, sizeof(double2) * slot * 2 * (steps + 1)));  // room for 2 columns
     op->lanczos_slots = steps + 1;
   }
   double2* Vb = op->lanczos;
@@ -901,7 +901,7 @@ int compute_scaling(rfcmp_op* op, const rfcmp_op_opts& o, cudaStream_t st) {
   const uint64_t sxz[2] = {1, 3}, sy = 2;
   const int64_t N = op->top.ne;
   if (!op->power_vecs) {
-    RF_CUDA(cudaMalloc(&op->power_vecs, sizeof(double2) * N * 3));
+    RF_CUDA(dev_malloc(&op->power_vecs, sizeof(double2) * N * 3));
     op->owned.push_back(op->power_vecs);
   }
   const rfcmp_op* from = o.scaling_start;
@@ -992,8 +992,8 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
   f->n = n;
   const size_t ld = (size_t)padded_ld(n);
   f->bytes = 2 * ld * (size_t)n * sizeof(float);
-  RF_CUDA(cudaMalloc(&f->hi, ld * n * sizeof(float)));
-  RF_CUDA(cudaMalloc(&f->lo, ld * n * sizeof(float)));
+  RF_CUDA(dev_malloc(&f->hi, ld * n * sizeof(float)));
+  RF_CUDA(dev_malloc(&f->lo, ld * n * sizeof(float)));
   RF_CUDA(cudaMemset(f->hi, 0, ld * n * sizeof(float)));
   RF_CUDA(cudaMemset(f->lo, 0, ld * n * sizeof(float)));
   std::vector<void*> tmp;
@@ -1003,7 +1003,7 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
   if (rc == RFCMP_OK) rc = upload(&dcol, col, tmp);
   if (rc == RFCMP_OK) rc = upload(&dval, val, tmp);
   if (rc != RFCMP_OK) {
-    for (void* p : tmp) cudaFree(p);
+    for (void* p : tmp) dev_free(p);
     return rc;
   }
   cudaEvent_t e0, e1;
@@ -1015,7 +1015,7 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
     std::string err;
     int rc2 = build_amg(ptr, col, val, n, 64, H, err);
     if (rc2 != RFCMP_OK) {
-      for (void* p : tmp) cudaFree(p);
+      for (void* p : tmp) dev_free(p);
       return set_error(rc2, err);
     }
   }
@@ -1026,7 +1026,7 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
     // (a V-cycle too weak to contract), from a multigrid-PCG solve to NS_START_TOL instead
     const double target = std::min(tol, 1e-12);
     double* Xd = nullptr;
-    err = cudaMalloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
+    err = dev_malloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
     int steps = 0;
     double res = 1.0;
     for (int attempt = 0; attempt < 2 && err == cudaSuccess && !(res <= target); ++attempt) {
@@ -1040,11 +1040,11 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
                                            f->lo, &st, &res, 0);
       steps += st;
     }
-    if (Xd) cudaFree(Xd);
+    if (Xd) dev_free(Xd);
     f->ns_steps = steps;
     f->ns_residual = res;
     if (err == cudaSuccess && !(res <= target)) {
-      for (void* p : tmp) cudaFree(p);
+      for (void* p : tmp) dev_free(p);
       return set_error(RFCMP_ERR_NOT_CONVERGED, "(Sigma^T Sigma)^+ refinement stalled at residual " + std::to_string(res));
     }
   } else if (!project && !multigrid && n >= NS_MIN_CELLS) {
@@ -1053,14 +1053,14 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
     // Newton-Schulz reaches rounding level in about six steps; block CG is the fallback
     const double target = std::min(tol, 1e-12);
     double* Xd = nullptr;
-    err = cudaMalloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
+    err = dev_malloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
     int steps = 0;
     double res = 1.0;
     if (err == cudaSuccess) err = jacobi_start(dptr, dcol, dval, n, 0.8, Xd, padded_ld(n), 0);
     if (err == cudaSuccess)
       err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, false, Xd, padded_ld(n), NS_MAX_STEPS, target, f->hi,
                                          f->lo, &steps, &res, 0);
-    if (Xd) cudaFree(Xd);
+    if (Xd) dev_free(Xd);
     f->ns_steps = steps;
     f->ns_residual = res;
     if (err == cudaSuccess && !(res <= target))
@@ -1075,7 +1075,7 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (void* p : tmp) cudaFree(p);
+  for (void* p : tmp) dev_free(p);
   if (err != cudaSuccess) return set_error(RFCMP_ERR_CUDA, std::string("dense inverse: ") + cudaGetErrorString(err));
   f->iterations = iters;
   f->ms = ms;
@@ -1178,7 +1178,7 @@ int rfcmp_ctx_create(int device, uint64_t budget, rfcmp_ctx** out) {
   *out = nullptr;
   RF_TRY(check_device(device));
   RF_CUDA(cudaSetDevice(device));
-  RF_CUDA(cudaFree(0));
+  RF_CUDA(dev_free(0));
   auto* c = new rfcmp_ctx();
   c->device = device;
   c->budget = budget;
@@ -1191,6 +1191,7 @@ int rfcmp_ctx_destroy(rfcmp_ctx* ctx) {
   if (ctx->live_ops.load() != 0) return set_error(RFCMP_ERR_INVALID_ARG, "context still has live ops");
   cudaSetDevice(ctx->device);
   delete ctx;
+  dev_pool_trim();  // hand the memory the context's buffers left in the pool back to the driver
   return RFCMP_OK;
 }
 
@@ -1323,9 +1324,9 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   op->info.factor_iterations_lplus = lp->iterations;
   op->info.factor_iterations_gll = gl->iterations;
   // assembly
-  RF_CUDA(cudaMalloc(&op->TA, (size_t)op->ldN * N * sizeof(float2)));
+  RF_CUDA(dev_malloc(&op->TA, (size_t)op->ldN * N * sizeof(float2)));
   op->owned.push_back(op->TA);
-  RF_CUDA(cudaMalloc(&op->V, (size_t)op->ldC * C * sizeof(float2)));
+  RF_CUDA(dev_malloc(&op->V, (size_t)op->ldC * C * sizeof(float2)));
   op->owned.push_back(op->V);
   op->bytes = mat_bytes;
   rfcmp_op* raw = op.get();
@@ -1381,7 +1382,7 @@ int rfcmp_op_trim(rfcmp_op* op) {
   if (!op) return set_error(RFCMP_ERR_INVALID_ARG, "NULL op");
   RF_CUDA(cudaSetDevice(op->ctx->device));
   RF_CUDA(cudaDeviceSynchronize());  // nothing of this op may still be reading what is freed
-  for (void* p : op->lazy) cudaFree(p);
+  for (void* p : op->lazy) dev_free(p);
   op->lazy.clear();
   op->ta_planes = CplxPlanes();
   op->v_planes = CplxPlanes();

@@ -216,7 +216,7 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
   const long long ldp = ldx;  // plane stride (elements); ldx is a multiple of 64
   std::vector<void*> own;
   auto fail = [&](cudaError_t e) {
-    for (void* p : own) cudaFree(p);
+    for (void* p : own) dev_free(p);
     return e;
   };
   cudaError_t err;
@@ -227,16 +227,16 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
   int* gerr;
   const size_t plane = (size_t)n * ldp;
   for (__nv_bfloat16** p : {&xh, &xl, &rh, &rl}) {
-    if ((err = cudaMalloc(p, plane * sizeof(__nv_bfloat16))) != cudaSuccess) return fail(err);
+    if ((err = dev_malloc(p, plane * sizeof(__nv_bfloat16))) != cudaSuccess) return fail(err);
     own.push_back(*p);
   }
-  if ((err = cudaMalloc(&D, plane * sizeof(float))) != cudaSuccess) return fail(err);
+  if ((err = dev_malloc(&D, plane * sizeof(float))) != cudaSuccess) return fail(err);
   own.push_back(D);
-  if ((err = cudaMalloc(&rowsum, n * sizeof(double))) != cudaSuccess) return fail(err);
+  if ((err = dev_malloc(&rowsum, n * sizeof(double))) != cudaSuccess) return fail(err);
   own.push_back(rowsum);
-  if ((err = cudaMalloc(&maxbits, sizeof(unsigned long long))) != cudaSuccess) return fail(err);
+  if ((err = dev_malloc(&maxbits, sizeof(unsigned long long))) != cudaSuccess) return fail(err);
   own.push_back(maxbits);
-  if ((err = cudaMalloc(&gerr, sizeof(int))) != cudaSuccess) return fail(err);
+  if ((err = dev_malloc(&gerr, sizeof(int))) != cudaSuccess) return fail(err);
   own.push_back(gerr);
   if ((err = cudaMemsetAsync(gerr, 0, sizeof(int), s)) != cudaSuccess) return fail(err);
   SplitOperand A, B;
@@ -250,7 +250,7 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
   B.ld = ldp;
   // vectors of the spectral-radius estimate: v, u, w (n each) and two scalars
   double* pv;
-  if ((err = cudaMalloc(&pv, (3 * (size_t)n + 2) * sizeof(double))) != cudaSuccess) return fail(err);
+  if ((err = dev_malloc(&pv, (3 * (size_t)n + 2) * sizeof(double))) != cudaSuccess) return fail(err);
   own.push_back(pv);
   double *pu = pv + n, *pw = pv + 2 * (size_t)n, *psc = pv + 3 * (size_t)n;
   // rho(I - M X) by a few power steps on I - M X (matrix-free: one dense FP64 product with X and

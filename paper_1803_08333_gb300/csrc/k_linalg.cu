@@ -14,6 +14,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "rfcmp_internal.h"
@@ -391,6 +392,46 @@ cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n,
 }  // namespace
 
 int padded_ld(int n) { return (n + 63) / 64 * 64; }
+
+namespace {
+std::mutex g_pool_mu;
+std::set<int> g_pool_ready;  // devices whose default pool keeps freed memory
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_ready.count(dev)) {
+      cudaMemPool_t pool;
+      if ((e = cudaDeviceGetDefaultMemPool(&pool, dev)) != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;
+      if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+      g_pool_ready.insert(dev);
+    }
+  }
+  if ((e = cudaMallocAsync(p, std::max<size_t>(bytes, 1), 0)) != cudaSuccess) return e;
+  return cudaStreamSynchronize(0);
+}
+
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaError_t e2 = cudaFreeAsync(p, 0);
+  cudaError_t e3 = cudaStreamSynchronize(0);
+  return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+}
+
+void dev_pool_trim() {
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+  }
+}
 
 // y = scale * op(M) x (+ y): prep (x -> FP32 hi/lo, zero accumulator), persistent GEMV, finalize.
 cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate, double2 scale,
@@ -1117,7 +1158,7 @@ struct DevLevel {
 
 template <class T>
 cudaError_t up(T** d, const std::vector<T>& h, std::vector<void*>& own) {
-  cudaError_t e = cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(T));
+  cudaError_t e = dev_malloc(d, std::max<size_t>(1, h.size()) * sizeof(T));
   if (e != cudaSuccess) return e;
   own.push_back(*d);
   if (!h.empty()) e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
@@ -1136,7 +1177,7 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
   std::vector<void*> own;
   cudaError_t err = cudaSuccess;
   auto fail = [&](cudaError_t e) {
-    for (void* p : own) cudaFree(p);
+    for (void* p : own) dev_free(p);
     return e;
   };
   // device hierarchy
@@ -1179,18 +1220,18 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
   const bool iterate = !(mg && max_iter == 0);  // max_iter 0 with a hierarchy: one V-cycle, no CG
   for (double** p : {&X, &R, &P, &AP}) {
     if (!iterate && (p == &P || p == &AP)) continue;
-    if ((err = cudaMalloc(p, bytes)) != cudaSuccess) return fail(err);
+    if ((err = dev_malloc(p, bytes)) != cudaSuccess) return fail(err);
     own.push_back(*p);
   }
   if (mg) {
     for (double** p : {&Z, &T0}) {
-      if ((err = cudaMalloc(p, bytes)) != cudaSuccess) return fail(err);
+      if ((err = dev_malloc(p, bytes)) != cudaSuccess) return fail(err);
       own.push_back(*p);
     }
     // levels 1.. hold B, X, T; the coarsest rhs / solution live in the last level's extra slots
     for (size_t l = 1; l < L.size(); ++l)
       for (double** p : {&L[l].B, &L[l].X, &L[l].T}) {
-        if ((err = cudaMalloc(p, (size_t)L[l].n * W * sizeof(double))) != cudaSuccess) return fail(err);
+        if ((err = dev_malloc(p, (size_t)L[l].n * W * sizeof(double))) != cudaSuccess) return fail(err);
         own.push_back(*p);
       }
   }
@@ -1198,12 +1239,12 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
   double *Bc = nullptr, *Xc = nullptr;
   if (mg) {
     for (double** p : {&Bc, &Xc}) {
-      if ((err = cudaMalloc(p, (size_t)m * W * sizeof(double))) != cudaSuccess) return fail(err);
+      if ((err = dev_malloc(p, (size_t)m * W * sizeof(double))) != cudaSuccess) return fail(err);
       own.push_back(*p);
     }
   }
   // scalars: rz ring (3W), rr ring (3W), pAp, bb, sums
-  if ((err = cudaMalloc(&sc, sizeof(double) * W * 9)) != cudaSuccess) return fail(err);
+  if ((err = dev_malloc(&sc, sizeof(double) * W * 9)) != cudaSuccess) return fail(err);
   own.push_back(sc);
   double* rzr = sc;
   double* rrr = sc + 3 * (size_t)W;

@@ -217,6 +217,20 @@ template <int NR>
 cudaError_t gemv_stream_r32(const float* M, int ld, int n, GemvScratch& w, cudaStream_t s);
 int padded_ld(int n);
 
+// Device memory from the device's stream-ordered pool, which keeps freed memory mapped: the
+// large buffers of operators, factor builds and solve workspaces come and go once per operator
+// or per wavenumber, and the pool turns their allocation and release into bookkeeping instead of
+// page-table work.  Both calls synchronise like cudaMalloc / cudaFree (the memory is usable on
+// any stream on return; a free waits for the device to go idle first).
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+cudaError_t dev_free(void* p);
+// Returns the pool's unused memory of the current device to the driver.
+void dev_pool_trim();
+
 // y[:, r] = scale * op(M) x[:, r] (+ y[:, r] if accumulate), r < nrhs; M n x n complex64
 // row-major with rows padded to padded_ld(n) (symmetric, so rows are columns); op = conj if
 // conjugate.  x, y complex128 column-major with leading dimension n.
