@@ -31,6 +31,33 @@ constexpr int FAR_THREADS = 256;  // 32 s-cells x 8 t-lanes
 constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI = 0.0795774715459476679;
 
+// sin and cos of x >= 0 in FP32 for the 49 kernel evaluations of a far pair.  Cody and Waite's
+// reduction (1980): q = nearest integer to x 2/pi, r = x - q pi/2 with pi/2 split into a short
+// leading part (q times it is exact for q < 2^16) and a remainder; then the Taylor series of sin
+// and cos on |r| <= pi/4 up to r^9 and r^8 (truncation below 4e-9) and the quadrant of q.
+__device__ __forceinline__ void sincos_far(float x, float* s, float* c) {
+  constexpr float TWO_OVER_PI = 0.636619772367581343f;
+  constexpr float PIO2_HI = 1.5703125f;                    // 8 significant bits
+  constexpr float PIO2_LO = 4.83826794896619231e-4f;       // pi/2 - PIO2_HI
+  const float q = rintf(x * TWO_OVER_PI);
+  const float r = fmaf(-q, PIO2_LO, fmaf(-q, PIO2_HI, x));
+  const float r2 = r * r;
+  // sin r = r (1 - r^2/6 + r^4/120 - r^6/5040 + r^8/362880)
+  float ps = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(r2, ps, 1.0f / 120.0f);
+  ps = fmaf(r2, ps, -1.0f / 6.0f);
+  const float sr = fmaf(r * r2, ps, r);
+  // cos r = 1 - r^2/2 + r^4/24 - r^6/720 + r^8/40320
+  float pc = fmaf(r2, 1.0f / 40320.0f, -1.0f / 720.0f);
+  pc = fmaf(r2, pc, 1.0f / 24.0f);
+  pc = fmaf(r2, pc, -0.5f);
+  const float cr = fmaf(r2, pc, 1.0f);
+  const int quad = ((int)q) & 3;  // x = q pi/2 + r
+  const float ss = (quad & 1) ? cr : sr, cc = (quad & 1) ? sr : cr;
+  *s = (quad & 2) ? -ss : ss;
+  *c = ((quad + 1) & 2) ? -cc : cc;
+}
+
 __device__ __forceinline__ void atomic_add_c64(float2* p, float re, float im) {
   atomicAdd(p, make_float2(re, im));
 }
@@ -141,7 +168,7 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
         const float rinv = rsqrtf(r2);
         const float R = r2 * rinv;
         float sn, cs;
-        sincosf(k * R, &sn, &cs);
+        sincos_far(k * R, &sn, &cs);
         const float gw = wt[j] * rinv;
         const float gr = gw * cs, gi = gw * sn;
         s0r += gr;
