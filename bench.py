@@ -39,13 +39,11 @@ WORKLOAD = "lowfreq_sweep_sphere_f32_n30720"
 METRIC = "RF-CMP EFIE solves/s @1e-6 resid (ka sweep 1..1e-5, level-5 sphere)"
 FP32_LANES_PER_SM = 128
 N_SMS = 152
-# DRAM traffic of a kernel family from one ncu capture, as the ratio of the captured
-# dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic bytes of that launch:
-# gemv_c64 at N = 7680, two columns, 472.3 + 3.2 MB measured against 8 N^2 + 32 N x 2 =
-# 472.4 MB.  The bench reports traffic per launch = ratio x its own algorithmic bytes per
-# launch (traffic grows with the units, N^2); families without a capture of the current
-# kernel report None.
-NCU_TRAFFIC_RATIO = {"gemv_c64_f32": 475.6 / 472.4}
+# DRAM traffic of a kernel family from one ncu capture of the current kernel, as the ratio of
+# the captured dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic bytes of that
+# launch; the bench reports traffic per launch = ratio x its own algorithmic bytes per launch
+# (traffic grows with the units, N^2).  Families without such a capture report None.
+NCU_TRAFFIC_RATIO = {}
 
 
 def _peaks():

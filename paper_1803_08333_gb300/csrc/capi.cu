@@ -328,6 +328,7 @@ int ensure_workspace(rfcmp_op* op, int cols) {
     RF_TRY(dalloc(&ws->ms.err, 1, ws->owned));
     RF_CUDA(cudaMemset(ws->ms.err, 0, sizeof(int)));
     ws->gs.err = ws->ms.err;
+    ws->gs.symmetric = true;  // T_A, V, (Sigma^T Sigma)^+ and G_ll^{-1} are all symmetric
     const bool bf = cols >= plan_mrhs(op), ex = cols >= plan_exact(op);
     if (bf || ex) {
       ws->ms.cap_cols = cols;

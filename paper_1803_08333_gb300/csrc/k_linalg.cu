@@ -347,10 +347,12 @@ cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, bool conj, GemvMod
   const int chunk = gemv_chunk(w);
   const int upr = (ld + chunk - 1) / chunk;
   const long long units = (long long)rowblocks * upr;
-  ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", 8.0 * n * n + 32.0 * n * NR,
-                 8.0 * n * n * NR, s);
-  if (mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err)
-    return gemv_stream_c64<NR <= 1 ? 1 : 2>(M, ld, n, conj, w, s);
+  const bool stream = mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err;
+  // algorithmic bytes: the matrix (its upper triangle when the symmetric kernel reads only that)
+  // plus the vectors
+  const double mbytes = stream && w.symmetric ? 4.0 * n * (n + 1.0) : 8.0 * n * n;
+  ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", mbytes + 32.0 * n * NR, 8.0 * n * n * NR, s);
+  if (stream) return gemv_stream_c64<NR <= 1 ? 1 : 2>(M, ld, n, conj, w, s);
 #define RF_LAUNCH_C(FFV, CJ)                                                                      \
   {                                                                                               \
     auto k = gemv_c64_kernel<NR, FFV, CJ>;                                                        \
@@ -373,10 +375,10 @@ cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n,
   const int chunk = gemv_chunk(w);
   const int upr = (ld + chunk - 1) / chunk;
   const long long units = (long long)rowblocks * upr;
-  ProfScope prof(mode == GEMV_FF ? "gemv_r32_ff" : "gemv_r32_f32",
-                 (mode == GEMV_FF ? 8.0 : 4.0) * n * n + 32.0 * n * NR, 4.0 * n * n * NR, s);
-  if (mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err)
-    return gemv_stream_r32<NR <= 1 ? 1 : 2>(Mhi, ld, n, w, s);
+  const bool stream = mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err;
+  const double mbytes = mode == GEMV_FF ? 8.0 * n * n : (stream && w.symmetric ? 2.0 * n * (n + 1.0) : 4.0 * n * n);
+  ProfScope prof(mode == GEMV_FF ? "gemv_r32_ff" : "gemv_r32_f32", mbytes + 32.0 * n * NR, 4.0 * n * n * NR, s);
+  if (stream) return gemv_stream_r32<NR <= 1 ? 1 : 2>(Mhi, ld, n, w, s);
   if (mode == GEMV_FF) {
     auto k = gemv_r32_kernel<NR, true>;
     const int grid = (int)gemv_grid(k, units, w);

@@ -208,6 +208,7 @@ struct GemvScratch {
   int chunk = 0;          // columns per work unit (multiple of 256; 0 = 1024)
   int ctas_per_sm = 0;    // persistent CTAs per SM (0 = occupancy maximum)
   int* err = nullptr;     // set when a bounded device-side wait of the streaming GEMV gives up
+  bool symmetric = false; // every matrix this scratch serves is symmetric: read the upper triangle
 };
 // Streaming FP32-mode GEMV (k_gemv_stream.cu): the prepared x (w.xh) times the complex64 or FP32
 // matrix into the FP64 accumulator w.acc, rows streamed by bulk copies; NR = 1 or 2.
