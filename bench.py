@@ -43,7 +43,9 @@ N_SMS = 152
 # the captured dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic bytes of that
 # launch; the bench reports traffic per launch = ratio x its own algorithmic bytes per launch
 # (traffic grows with the units, N^2).  Families without such a capture report None.
-NCU_TRAFFIC_RATIO = {}
+# gemv_c64_f32 (symmetric streaming kernel): 604.7 MB read at N = 12000, two columns, against
+# 4 N (N + 1) + 32 N x 2 = 576.8 MB (the tiles that cross the diagonal are read whole).
+NCU_TRAFFIC_RATIO = {"gemv_c64_f32": 604.7 / 576.8}
 
 
 def _peaks():
@@ -278,7 +280,8 @@ def bench_ours(args):
         "data": "synthetic (seeded jittered icosphere, plane wave)",
         "config": {
             "workload": WORKLOAD,
-            "mesh": "geodesic sphere frequency 32, 20480 cells, 30720 unknowns, jitter 3%, seed 2",
+            "mesh": "geodesic sphere frequency %d, %d cells, %d unknowns, jitter 3%%, seed 2"
+                    % (MESH_N, 20 * MESH_N * MESH_N, 30 * MESH_N * MESH_N),
             "ka": KA,
             "tol": TOL,
             "nrhs": 1,

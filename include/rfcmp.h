@@ -105,8 +105,10 @@ typedef struct {
                            Ritz value converges to the spectral norm the power iteration of
                            Sec. 4 estimates); default 30 */
   double alpha, beta, gamma; /* used with RFCMP_SCALE_FIXED */
-  double factor_tol;    /* relative residual of the dense-inverse builds of (Sigma^T Sigma)^+
-                           and G_ll^{-1}; default 1e-13 */
+  double factor_tol;    /* accuracy of the dense-inverse builds of (Sigma^T Sigma)^+ and
+                           G_ll^{-1}: relative residual per column for a block-CG build, largest
+                           entry of I - M X (at least 1e-12, the FP64 rounding level of tens of
+                           thousands of cells) for a Newton-Schulz refinement; default 1e-13 */
   double power_rtol;    /* a norm iteration stops once its estimate changes by at most power_rtol
                            (relative) between two steps, after at least 2 and at most power_steps
                            steps; 0 = always power_steps; default 1e-3 */

@@ -171,7 +171,10 @@ constexpr int MRHS_MIN = 4;
 // GB300: the exact-digit product wins from 4 columns at 2k unknowns, from 2 at 17k and above).
 constexpr int EXACT_MIN = 4;
 constexpr double NS_START_TOL = 1e-2;
-constexpr int NS_MAX_STEPS = 14;
+constexpr int NS_MAX_STEPS = 24;
+// Newton-Schulz stops at max |I - M X| <= max(factor_tol, NS_TARGET): the FP64 residual of tens
+// of thousands of cells floors near 1e-13 (measured 1.2e-13 at 27380 cells).
+constexpr double NS_TARGET = 1e-12;
 
 struct DenseFactor {
   int n = 0;
@@ -1025,7 +1028,7 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
   if (multigrid && project && n >= NS_MIN_CELLS) {
     // Newton-Schulz steps on the tensor cores from one V-cycle; if they do not reach the target
     // (a V-cycle too weak to contract), from a multigrid-PCG solve to NS_START_TOL instead
-    const double target = std::min(tol, 1e-12);
+    const double target = std::max(tol, NS_TARGET);
     double* Xd = nullptr;
     err = dev_malloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
     int steps = 0;
@@ -1046,13 +1049,16 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
     f->ns_residual = res;
     if (err == cudaSuccess && !(res <= target)) {
       for (void* p : tmp) dev_free(p);
-      return set_error(RFCMP_ERR_NOT_CONVERGED, "(Sigma^T Sigma)^+ refinement stalled at residual " + std::to_string(res));
+      char msg[128];
+      std::snprintf(msg, sizeof(msg), "(Sigma^T Sigma)^+ refinement stalled at residual %.3e after %d steps", res,
+                    steps);
+      return set_error(RFCMP_ERR_NOT_CONVERGED, msg);
     }
   } else if (!project && !multigrid && n >= NS_MIN_CELLS) {
     // G_ll^{-1}: the P1 mass matrix has the eigenvalues of D^{-1} G_ll in [1/2, 2] (element by
     // element), so X0 = 0.8 D^{-1} leaves I - G_ll X0 a spectral radius of at most 0.6 and
     // Newton-Schulz reaches rounding level in about six steps; block CG is the fallback
-    const double target = std::min(tol, 1e-12);
+    const double target = std::max(tol, NS_TARGET);
     double* Xd = nullptr;
     err = dev_malloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
     int steps = 0;
