@@ -36,9 +36,10 @@ constexpr int SSTAGES = 4;
 constexpr int SMAT = SROWS * SBYTES_ROW;    // 32 KB of matrix per stage
 constexpr int SXMAX = 2 * 8192;             // x segments per stage: up to 2 columns x 1024 complex
 constexpr int SXI = 2 * 64;                 // x of the stage's 8 rows (symmetric kernel), up to 2 columns
-constexpr int SSTAGE = SMAT + SXMAX + SXI;  // 48 KB + 128 B
+constexpr int SRED = 8 * 32 * 4;            // row partials of the 8 consumer warps (symmetric kernel)
+constexpr int SSTAGE = SMAT + SXMAX + SXI + SRED;  // 49 KB + 128 B
 constexpr int STHREADS = (SROWS + 1) * 32;  // consumers + producer warp
-constexpr int SSMEM = SSTAGES * SSTAGE + 128;
+constexpr int SSMEM = SSTAGES * SSTAGE + 256;  // + alignment slack and the mbarriers
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -221,10 +222,16 @@ gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __r
 // lie above it are read: a tile of 8 rows I x one segment J contributes y_I += M_IJ x_J (row part,
 // entries j >= i) and y_J += M_IJ^T x_I (column part, entries j > i), so half the matrix bytes
 // leave HBM.  Units run column-major over the upper triangle: segment c holds the row blocks
-// 0 .. min(RB, P (c + 1)) - 1 (P = segment width / 8 rows), so the column part of a warp stays in
-// registers across the row blocks of a segment and reaches y once per segment; the row part of a
-// unit is reduced across the warp and added at once.  Warp w takes row w for the row part and the
-// w-th eighth of the segment's columns (one float4 per lane and row) for the column part.
+// 0 .. min(RB, P (c + 1)) - 1 (P = segment width / 8 rows), so the column part stays in registers
+// across the row blocks of a segment and reaches y once per segment.
+//
+// Both parts come from one read of the tile: consumer thread t owns float4 column slot t of the
+// segment (256 slots = the 8 consumer warps x 32 lanes) in all 8 rows.  For each row it adds
+// M_ij x_j into that row's partial (x_j of its slot held in registers) and M_ij x_i into its
+// column sums (x_i a shared-memory broadcast).  The 8 x NR complex row partials of a warp are
+// reduce-scattered across its lanes (each exchange halves the values a lane holds), the 8 warps'
+// results meet in shared memory, and one warp per unit (rotating) adds them and issues the FP64
+// atomics of the row part.
 struct SymGeom {
   long long RB, P, S, cstar, base;  // row blocks, row blocks per segment step, segments, off() knee
   __host__ __device__ long long nrb(long long c) const { return c < cstar ? P * (c + 1) : RB; }
@@ -244,6 +251,77 @@ __host__ __device__ inline SymGeom sym_geom(int n, int ld, int seg) {
   return g;
 }
 
+// Reduce-scatter of V = 16 or 32 per-lane values over the warp: on return v[0] of lane l is the
+// warp sum of value l * V / 32 (for V = 16 lanes l and l ^ 1 hold the same sum).
+template <int V>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[V], int lane) {
+#pragma unroll
+  for (int step = 0; step < 5; ++step) {
+    const int off = 16 >> step;
+    const int h = V >> (step + 1);  // values kept after this exchange (0: plain reduction)
+    if (h == 0) {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+    } else {
+      const bool upper = (lane & off) != 0;
+#pragma unroll
+      for (int k = 0; k < h; ++k) {
+        const float send = upper ? v[k] : v[k + h];
+        const float keep = upper ? v[k + h] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+  }
+}
+
+// The 8 rows of one tile for column slot qc (entries j .. j + EPQ - 1): row partials v gain
+// M_ij x_j (j >= i), column partials t gain M_ij x_i (j > i).  DIAG: the tile reaches the
+// diagonal and the entries outside those ranges are dropped.
+template <int NR, bool REAL, bool CONJ, bool DIAG, int EPQ = (REAL ? 4 : 2)>
+__device__ __forceinline__ void sym_tile(const uint8_t* st, int qc, int row0, int n, int j, const float2 (&xj)[NR][EPQ],
+                                         float (&v)[SROWS * NR * 2], float (&t)[NR][EPQ][2]) {
+  const float2* sxi = reinterpret_cast<const float2*>(st + SMAT + SXMAX);
+#pragma unroll
+  for (int rr = 0; rr < SROWS; ++rr) {
+    const int row = row0 + rr;
+    const float4 m = row < n ? reinterpret_cast<const float4*>(st + rr * SBYTES_ROW)[qc] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float er[EPQ], ei[EPQ];  // entries as (re, im)
+    if constexpr (REAL) {
+      er[0] = m.x, er[1] = m.y, er[2] = m.z, er[3] = m.w;
+#pragma unroll
+      for (int e = 0; e < EPQ; ++e) ei[e] = 0.f;
+    } else {
+      er[0] = m.x, ei[0] = CONJ ? -m.y : m.y;
+      er[1] = m.z, ei[1] = CONJ ? -m.w : m.w;
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float2 xi = sxi[r * SROWS + rr];
+      float pre = v[(rr * NR + r) * 2], pim = v[(rr * NR + r) * 2 + 1];
+#pragma unroll
+      for (int e = 0; e < EPQ; ++e) {
+        float ar = er[e], ai = ei[e], br = er[e], bi = ei[e];
+        if constexpr (DIAG) {
+          if (j + e < row) ar = ai = 0.f;
+          if (j + e <= row) br = bi = 0.f;
+        }
+        if constexpr (REAL) {
+          pre = fmaf(ar, xj[r][e].x, pre);
+          pim = fmaf(ar, xj[r][e].y, pim);
+          t[r][e][0] = fmaf(br, xi.x, t[r][e][0]);
+          t[r][e][1] = fmaf(br, xi.y, t[r][e][1]);
+        } else {
+          pre = fmaf(ar, xj[r][e].x, fmaf(-ai, xj[r][e].y, pre));
+          pim = fmaf(ar, xj[r][e].y, fmaf(ai, xj[r][e].x, pim));
+          t[r][e][0] = fmaf(br, xi.x, fmaf(-bi, xi.y, t[r][e][0]));
+          t[r][e][1] = fmaf(br, xi.y, fmaf(bi, xi.x, t[r][e][1]));
+        }
+      }
+      v[(rr * NR + r) * 2] = pre;
+      v[(rr * NR + r) * 2 + 1] = pim;
+    }
+  }
+}
+
 template <int NR, bool REAL, bool CONJ>
 __global__ void __launch_bounds__(STHREADS, 1)
 gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __restrict__ xh,
@@ -252,9 +330,13 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
   uint64_t* empty = full + SSTAGES;
+  uint64_t* rfull = empty + SSTAGES;  // the 8 warps' row partials of a stage are in shared memory
   constexpr int ESZ = REAL ? 4 : 8;
   constexpr int SEG = SBYTES_ROW / ESZ;
-  constexpr int EPQ = 16 / ESZ;  // matrix entries per float4
+  constexpr int EPQ = 16 / ESZ;       // matrix entries per float4
+  constexpr int V = SROWS * NR * 2;   // row partials per lane: 8 rows x NR columns x (re, im)
+  static_assert(SBYTES_ROW / 16 == SROWS * 32, "one float4 column slot per consumer thread");
+  static_assert(V == 16 || V == 32, "reduce-scatter of 16 or 32 values");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const SymGeom G = sym_geom(n, ld, SEG);
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
@@ -262,6 +344,7 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
     for (int s = 0; s < SSTAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], SROWS);
+      mbar_init(&rfull[s], SROWS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -315,7 +398,7 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
     return;
   }
 
-  // column part: lane's float4 q = 32 warp + lane of every row, EPQ entries, NR columns
+  // column sums of slot qc (EPQ entries, NR columns) in compensated FP32
   float ca[NR][EPQ][2], cc[NR][EPQ][2];
 #pragma unroll
   for (int r = 0; r < NR; ++r)
@@ -349,125 +432,32 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
     }
     const int cb = (int)(c * SEG), row0 = (int)(rb * SROWS);
     const bool diag = row0 + SROWS > cb;  // the segment reaches the diagonal of this row block
-    const uint8_t* st = smem + s * SSTAGE;
-    const float4* sx = reinterpret_cast<const float4*>(st + SMAT);
+    uint8_t* st = smem + s * SSTAGE;
     const int nq = min(SEG, ld - cb) * ESZ / 16;
-    // row part: row `warp`, entries j >= i
-    {
-      const int row = row0 + warp;
-      float f[NR][2];
+    float v[V];  // row partials, index (rr * NR + r) * 2 + (re, im)
 #pragma unroll
-      for (int r = 0; r < NR; ++r) f[r][0] = f[r][1] = 0.f;
-      if (row < n) {
-        const float4* srow = reinterpret_cast<const float4*>(st + warp * SBYTES_ROW);
-#pragma unroll 4
-        for (int q = lane; q < nq; q += 32) {
-          float4 m = srow[q];
-          if (diag) {  // zero the entries left of the diagonal
-            const int j = cb + EPQ * q;
-            if (REAL) {
-              if (j < row) m.x = 0.f;
-              if (j + 1 < row) m.y = 0.f;
-              if (j + 2 < row) m.z = 0.f;
-              if (j + 3 < row) m.w = 0.f;
-            } else {
-              if (j < row) m.x = m.y = 0.f;
-              if (j + 1 < row) m.z = m.w = 0.f;
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            const float4* xr = sx + r * (SXMAX / 32);
-            float re = f[r][0], im = f[r][1];
-            if (REAL) {
-              const float4 x0 = xr[2 * q], x1 = xr[2 * q + 1];
-              re = fmaf(m.x, x0.x, re);
-              im = fmaf(m.x, x0.y, im);
-              re = fmaf(m.y, x0.z, re);
-              im = fmaf(m.y, x0.w, im);
-              re = fmaf(m.z, x1.x, re);
-              im = fmaf(m.z, x1.y, im);
-              re = fmaf(m.w, x1.z, re);
-              im = fmaf(m.w, x1.w, im);
-            } else {
-              const float4 x4 = xr[q];
-              const float my = CONJ ? -m.y : m.y, mw = CONJ ? -m.w : m.w;
-              re = fmaf(m.x, x4.x, re);
-              re = fmaf(-my, x4.y, re);
-              re = fmaf(m.z, x4.z, re);
-              re = fmaf(-mw, x4.w, re);
-              im = fmaf(m.x, x4.y, im);
-              im = fmaf(my, x4.x, im);
-              im = fmaf(m.z, x4.w, im);
-              im = fmaf(mw, x4.z, im);
-            }
-            f[r][0] = re;
-            f[r][1] = im;
-          }
-        }
-      }
-      // FP32 warp reduction (FP64 arithmetic in every unit would saturate GB300's FP64 pipe);
-      // the units of a row meet in the FP64 accumulator
+    for (int k = 0; k < V; ++k) v[k] = 0.f;
+    if (qc < nq) {
+      // x_j of the slot, NR columns
+      float2 xj[NR][EPQ];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        float re = f[r][0], im = f[r][1];
+        const float4* xr = reinterpret_cast<const float4*>(st + SMAT + r * (SXMAX / 2));
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          re += __shfl_xor_sync(0xffffffffu, re, off);
-          im += __shfl_xor_sync(0xffffffffu, im, off);
-        }
-        if (lane == 0 && row < n) {
-          double* o = reinterpret_cast<double*>(out + (size_t)r * n + row);
-          atomicAdd(o, (double)re);
-          atomicAdd(o + 1, (double)im);
+        for (int h = 0; h < EPQ / 2; ++h) {
+          const float4 x4 = xr[(EPQ / 2) * qc + h];
+          xj[r][2 * h] = make_float2(x4.x, x4.y);
+          xj[r][2 * h + 1] = make_float2(x4.z, x4.w);
         }
       }
-    }
-    // column part: entries j > i of the 8 rows, the lane's float4 column slot qc
-    if (qc < nq) {
+      const int j = cb + EPQ * qc;
       float t[NR][EPQ][2];
 #pragma unroll
       for (int r = 0; r < NR; ++r)
 #pragma unroll
         for (int e = 0; e < EPQ; ++e) t[r][e][0] = t[r][e][1] = 0.f;
-      const int j = cb + EPQ * qc;
-      const float2* sxi = reinterpret_cast<const float2*>(st + SMAT + SXMAX);
-#pragma unroll
-      for (int rr = 0; rr < SROWS; ++rr) {
-        const int row = row0 + rr;
-        float4 m = row < n ? reinterpret_cast<const float4*>(st + rr * SBYTES_ROW)[qc] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (diag) {  // keep only j > i
-          if (REAL) {
-            if (j <= row) m.x = 0.f;
-            if (j + 1 <= row) m.y = 0.f;
-            if (j + 2 <= row) m.z = 0.f;
-            if (j + 3 <= row) m.w = 0.f;
-          } else {
-            if (j <= row) m.x = m.y = 0.f;
-            if (j + 1 <= row) m.z = m.w = 0.f;
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const float2 xi = sxi[r * 8 + rr];
-          if (REAL) {
-            const float mv[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-            for (int e = 0; e < EPQ; ++e) {
-              t[r][e][0] = fmaf(mv[e], xi.x, t[r][e][0]);
-              t[r][e][1] = fmaf(mv[e], xi.y, t[r][e][1]);
-            }
-          } else {
-            const float ar[2] = {m.x, m.z};
-            const float ai[2] = {CONJ ? -m.y : m.y, CONJ ? -m.w : m.w};
-#pragma unroll
-            for (int e = 0; e < EPQ; ++e) {
-              t[r][e][0] = fmaf(ar[e], xi.x, fmaf(-ai[e], xi.y, t[r][e][0]));
-              t[r][e][1] = fmaf(ar[e], xi.y, fmaf(ai[e], xi.x, t[r][e][1]));
-            }
-          }
-        }
-      }
+      if (diag) sym_tile<NR, REAL, CONJ, true>(st, qc, row0, n, j, xj, v, t);
+      else sym_tile<NR, REAL, CONJ, false>(st, qc, row0, n, j, xj, v, t);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
 #pragma unroll
@@ -478,6 +468,28 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
             cc[r][e][z] += (a - (tt - bb)) + (b - bb);
             ca[r][e][z] = tt;
           }
+    }
+    // row part: reduce-scatter over the warp, then the 8 warps meet in shared memory
+    warp_reduce_scatter<V>(v, lane);
+    float* red = reinterpret_cast<float*>(st + SMAT + SXMAX + SXI);  // [SROWS warps][V]
+    if (V == 32 || (lane & 1) == 0) red[warp * V + lane * V / 32] = v[0];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&rfull[s]);
+    if (warp == (int)(i % SROWS)) {
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&rfull[s], parity));
+      if (!got) {
+        if (lane == 0) atomicExch(err, 27);
+        ok = false;
+        break;
+      }
+      if (lane < V) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w2 = 0; w2 < SROWS; ++w2) sum += red[w2 * V + lane];
+        const int rr = lane / (2 * NR), r = (lane / 2) % NR, z = lane & 1;
+        const int row = row0 + rr;
+        if (row < n) atomicAdd(reinterpret_cast<double*>(out + (size_t)r * n + row) + z, (double)sum);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
