@@ -31,27 +31,33 @@ constexpr int FAR_THREADS = 256;  // 32 s-cells x 8 t-lanes
 constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI = 0.0795774715459476679;
 
-// sin and cos of x >= 0 in FP32 for the 49 kernel evaluations of a far pair.  Cody and Waite's
-// reduction (1980): q = nearest integer to x 2/pi, r = x - q pi/2 with pi/2 split into a short
-// leading part (q times it is exact for q < 2^16) and a remainder; then the Taylor series of sin
-// and cos on |r| <= pi/4 up to r^9 and r^8 (truncation below 4e-9) and the quadrant of q.
+// sin and cos of |r| <= pi/4 in FP32: Taylor series of sin to r^9 and of cos to r^8
+// (truncation below 4e-9).
+__device__ __forceinline__ void sincos_quarter(float r, float* s, float* c) {
+  const float r2 = r * r;
+  // sin r = r (1 - r^2/6 + r^4/120 - r^6/5040 + r^8/362880)
+  float ps = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(r2, ps, 1.0f / 120.0f);
+  ps = fmaf(r2, ps, -1.0f / 6.0f);
+  *s = fmaf(r * r2, ps, r);
+  // cos r = 1 - r^2/2 + r^4/24 - r^6/720 + r^8/40320
+  float pc = fmaf(r2, 1.0f / 40320.0f, -1.0f / 720.0f);
+  pc = fmaf(r2, pc, 1.0f / 24.0f);
+  pc = fmaf(r2, pc, -0.5f);
+  *c = fmaf(r2, pc, 1.0f);
+}
+
+// sin and cos of x >= 0 in FP32.  Cody and Waite's reduction (1980): q = nearest integer to
+// x 2/pi, r = x - q pi/2 with pi/2 split into a short leading part (q times it is exact for
+// q < 2^16) and a remainder; then the series above on |r| <= pi/4 and the quadrant of q.
 __device__ __forceinline__ void sincos_far(float x, float* s, float* c) {
   constexpr float TWO_OVER_PI = 0.636619772367581343f;
   constexpr float PIO2_HI = 1.5703125f;                    // 8 significant bits
   constexpr float PIO2_LO = 4.83826794896619231e-4f;       // pi/2 - PIO2_HI
   const float q = rintf(x * TWO_OVER_PI);
   const float r = fmaf(-q, PIO2_LO, fmaf(-q, PIO2_HI, x));
-  const float r2 = r * r;
-  // sin r = r (1 - r^2/6 + r^4/120 - r^6/5040 + r^8/362880)
-  float ps = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-  ps = fmaf(r2, ps, 1.0f / 120.0f);
-  ps = fmaf(r2, ps, -1.0f / 6.0f);
-  const float sr = fmaf(r * r2, ps, r);
-  // cos r = 1 - r^2/2 + r^4/24 - r^6/720 + r^8/40320
-  float pc = fmaf(r2, 1.0f / 40320.0f, -1.0f / 720.0f);
-  pc = fmaf(r2, pc, 1.0f / 24.0f);
-  pc = fmaf(r2, pc, -0.5f);
-  const float cr = fmaf(r2, pc, 1.0f);
+  float sr, cr;
+  sincos_quarter(r, &sr, &cr);
   const int quad = ((int)q) & 3;  // x = q pi/2 + r
   const float ss = (quad & 1) ? cr : sr, cc = (quad & 1) ? sr : cr;
   *s = (quad & 2) ? -ss : ss;
@@ -71,6 +77,7 @@ struct TileCells {
   float cen_lo[TILE][3];
   float aloc[TILE][9];
   float inv_area[TILE];
+  float rq[TILE];       // largest distance of a quadrature point from the centroid
   int32_t vid[TILE][3];
   int32_t edge[TILE][3];
   float sign[TILE][3];
@@ -81,7 +88,16 @@ __device__ void load_tile(TileCells& T, const DeviceGeometry g, int base) {
     int c = base + q;
     bool ok = c < g.nc;
     int cc = ok ? c : 0;
-    for (int e = 0; e < 21; ++e) T.rho[q][e] = g.rho[21 * cc + e];
+    float rq2 = 0.f;
+    for (int e = 0; e < 21; ++e) {
+      const float v = g.rho[21 * cc + e];
+      T.rho[q][e] = v;
+      if (e % 3 == 2) {
+        const float a = g.rho[21 * cc + e - 2], b = g.rho[21 * cc + e - 1];
+        rq2 = fmaxf(rq2, a * a + b * b + v * v);
+      }
+    }
+    T.rq[q] = sqrtf(rq2) * 1.0001f;  // rounding margin
     for (int e = 0; e < 7; ++e) {
       float w = g.wq[7 * cc + e];
       T.wq[q][e] = w;
@@ -96,6 +112,79 @@ __device__ void load_tile(TileCells& T, const DeviceGeometry g, int base) {
     }
     for (int e = 0; e < 9; ++e) T.aloc[q][e] = g.aloc[9 * cc + e];
     T.inv_area[q] = g.inv_area[cc];
+  }
+}
+
+// the four moments of a far pair (Sec. 2; I0, Ir, Irp, Irr with G = e^{ik(R - phase0/k)} / (4 pi R))
+struct FarMoments {
+  float I0r = 0.f, I0i = 0.f, Irr_r = 0.f, Irr_i = 0.f;
+  float Ir_r[3] = {0.f, 0.f, 0.f}, Ir_i[3] = {0.f, 0.f, 0.f};
+  float Ip_r[3] = {0.f, 0.f, 0.f}, Ip_i[3] = {0.f, 0.f, 0.f};
+  // multiply every moment by e^{i phi}
+  __device__ __forceinline__ void rotate(float phi) {
+    float sn, cs;
+    sincos_far(phi, &sn, &cs);
+    auto rot = [&](float& re, float& im) {
+      const float a = re, b = im;
+      re = fmaf(a, cs, -b * sn);
+      im = fmaf(a, sn, b * cs);
+    };
+    rot(I0r, I0i);
+    rot(Irr_r, Irr_i);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      rot(Ir_r[e], Ir_i[e]);
+      rot(Ip_r[e], Ip_i[e]);
+    }
+  }
+};
+
+// 7 x 7 product rule over the pair; SHIFTED: the phase of each evaluation is k R - kref with
+// |k R - kref| <= pi/4 (no range reduction), else k R
+template <bool SHIFTED>
+__device__ __forceinline__ void far_moments(const float (&rs)[21], const float (&ws)[7], const float (&rt)[21],
+                                            const float (&wt)[7], const float (&d)[3], float k, float kref,
+                                            FarMoments& M) {
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const float dx = d[0] + rs[3 * i], dy = d[1] + rs[3 * i + 1], dz = d[2] + rs[3 * i + 2];
+    float s0r = 0.f, s0i = 0.f;
+    float s1r[3] = {0.f, 0.f, 0.f}, s1i[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const float ex = dx - rt[3 * j], ey = dy - rt[3 * j + 1], ez = dz - rt[3 * j + 2];
+      const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      const float rinv = rsqrtf(r2);
+      const float R = r2 * rinv;
+      float sn, cs;
+      if (SHIFTED) sincos_quarter(fmaf(k, R, -kref), &sn, &cs);
+      else sincos_far(k * R, &sn, &cs);
+      const float gw = wt[j] * rinv;
+      const float gr = gw * cs, gi = gw * sn;
+      s0r += gr;
+      s0i += gi;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        s1r[e] = fmaf(gr, rt[3 * j + e], s1r[e]);
+        s1i[e] = fmaf(gi, rt[3 * j + e], s1i[e]);
+      }
+    }
+    const float w = ws[i];
+    M.I0r = fmaf(w, s0r, M.I0r);
+    M.I0i = fmaf(w, s0i, M.I0i);
+    float dr = 0.f, di = 0.f;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const float wr = w * rs[3 * i + e];
+      M.Ir_r[e] = fmaf(wr, s0r, M.Ir_r[e]);
+      M.Ir_i[e] = fmaf(wr, s0i, M.Ir_i[e]);
+      M.Ip_r[e] = fmaf(w, s1r[e], M.Ip_r[e]);
+      M.Ip_i[e] = fmaf(w, s1i[e], M.Ip_i[e]);
+      dr = fmaf(wr, s1r[e], dr);
+      di = fmaf(wr, s1i[e], di);
+    }
+    M.Irr_r += dr;
+    M.Irr_i += di;
   }
 }
 
@@ -153,49 +242,22 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
 #pragma unroll
     for (int e = 0; e < 3; ++e) d[e] = (S.cen_hi[sl][e] - Tt.cen_hi[tl][e]) + (S.cen_lo[sl][e] - Tt.cen_lo[tl][e]);
 
-    float I0r = 0.f, I0i = 0.f, Irr_r = 0.f, Irr_i = 0.f;
-    float Ir_r[3] = {0.f, 0.f, 0.f}, Ir_i[3] = {0.f, 0.f, 0.f};
-    float Ip_r[3] = {0.f, 0.f, 0.f}, Ip_i[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i < 7; ++i) {
-      const float dx = d[0] + rs[3 * i], dy = d[1] + rs[3 * i + 1], dz = d[2] + rs[3 * i + 2];
-      float s0r = 0.f, s0i = 0.f;
-      float s1r[3] = {0.f, 0.f, 0.f}, s1i[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < 7; ++j) {
-        const float ex = dx - rt[3 * j], ey = dy - rt[3 * j + 1], ez = dz - rt[3 * j + 2];
-        const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-        const float rinv = rsqrtf(r2);
-        const float R = r2 * rinv;
-        float sn, cs;
-        sincos_far(k * R, &sn, &cs);
-        const float gw = wt[j] * rinv;
-        const float gr = gw * cs, gi = gw * sn;
-        s0r += gr;
-        s0i += gi;
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          s1r[e] = fmaf(gr, rt[3 * j + e], s1r[e]);
-          s1i[e] = fmaf(gi, rt[3 * j + e], s1i[e]);
-        }
-      }
-      const float w = ws[i];
-      I0r = fmaf(w, s0r, I0r);
-      I0i = fmaf(w, s0i, I0i);
-      float dr = 0.f, di = 0.f;
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        const float wr = w * rs[3 * i + e];
-        Ir_r[e] = fmaf(wr, s0r, Ir_r[e]);
-        Ir_i[e] = fmaf(wr, s0i, Ir_i[e]);
-        Ip_r[e] = fmaf(w, s1r[e], Ip_r[e]);
-        Ip_i[e] = fmaf(w, s1i[e], Ip_i[e]);
-        dr = fmaf(wr, s1r[e], dr);
-        di = fmaf(wr, s1i[e], di);
-      }
-      Irr_r += dr;
-      Irr_i += di;
-    }
+    // e^{ikR} = e^{ik Rc} e^{ik (R - Rc)} with Rc the centroid distance: |R - Rc| is at most the
+    // sum of the two quadrature radii, so where k times that is within pi/4 the 49 evaluations
+    // take sin and cos of k (R - Rc) without a range reduction and the common factor
+    // e^{ik Rc} multiplies the eight moments once
+    const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+    const float kRc = k * (dd * rsqrtf(dd));
+    const bool shifted = k * (S.rq[sl] + Tt.rq[tl]) <= 0.78f;
+    FarMoments Mo;
+    if (shifted) far_moments<true>(rs, ws, rt, wt, d, k, kRc, Mo);
+    else far_moments<false>(rs, ws, rt, wt, d, k, 0.f, Mo);
+    if (shifted) Mo.rotate(kRc);
+    const float I0r = Mo.I0r, I0i = Mo.I0i, Irr_r = Mo.Irr_r, Irr_i = Mo.Irr_i;
+    const float* Ir_r = Mo.Ir_r;
+    const float* Ir_i = Mo.Ir_i;
+    const float* Ip_r = Mo.Ip_r;
+    const float* Ip_i = Mo.Ip_i;
     const float inv_aa = S.inv_area[sl] * Tt.inv_area[tl];
     V[(size_t)s * ldC + t] = make_float2(I0r * inv_aa, I0i * inv_aa);
     V[(size_t)t * ldC + s] = make_float2(I0r * inv_aa, I0i * inv_aa);

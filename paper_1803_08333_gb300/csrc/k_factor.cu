@@ -33,16 +33,21 @@ namespace {
 
 // Rt[i][j] = delta_ij - alpha (X M)[i][j] with M = L + 1 1^T / n (L symmetric CSR; without
 // rowsum, M = L), written as BF16 hi/lo planes; rowsum[i] = sum_j X[i][j] is precomputed.  Also
-// tracks max |Rt|.
-__global__ void ns_residual_kernel(const double* __restrict__ X, long long ldx, int n, const int32_t* __restrict__ ptr,
-                                   const int32_t* __restrict__ col, const double* __restrict__ val,
-                                   const double* __restrict__ rowsum, double alpha, __nv_bfloat16* __restrict__ hi,
-                                   __nv_bfloat16* __restrict__ lo, long long ldp,
-                                   unsigned long long* __restrict__ maxbits) {
+// tracks max |Rt|.  The FP64 sums bound this kernel (GB300's FP64 pipe runs at a small
+// fraction of the FP32 rate), so everything else stays off that pipe: the maximum is taken on
+// the FP32 value and reduced per CTA before its single atomic.  A CTA sweeps part of one row i,
+// whose gathers X[i][col] the CTA's L1 keeps.
+constexpr int NSR_THREADS = 256;
+constexpr int NSR_SPLIT = 8;  // CTAs per row
+__global__ void __launch_bounds__(NSR_THREADS)
+ns_residual_kernel(const double* __restrict__ X, long long ldx, int n, const int32_t* __restrict__ ptr,
+                   const int32_t* __restrict__ col, const double* __restrict__ val,
+                   const double* __restrict__ rowsum, double alpha, __nv_bfloat16* __restrict__ hi,
+                   __nv_bfloat16* __restrict__ lo, long long ldp, unsigned long long* __restrict__ maxbits) {
   const int i = blockIdx.y;
   const double* xr = X + (size_t)i * ldx;
   const double rs = rowsum ? rowsum[i] / n : 0.0;  // the 1 1^T / n term of the projected case
-  double mx = 0.0;
+  float mx = 0.f;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double a = rs;
     for (int q = ptr[j]; q < ptr[j + 1]; ++q) a += xr[col[q]] * val[q];  // (X L)_ij, L symmetric
@@ -51,10 +56,17 @@ __global__ void ns_residual_kernel(const double* __restrict__ X, long long ldx, 
     const __nv_bfloat16 h = __float2bfloat16_rn(rf);
     hi[(size_t)i * ldp + j] = h;
     lo[(size_t)i * ldp + j] = __float2bfloat16_rn(rf - __bfloat162float(h));
-    mx = fmax(mx, fabs(r));
+    mx = fmaxf(mx, fabsf(rf));
   }
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if ((threadIdx.x & 31) == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  __shared__ float wmax[NSR_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < NSR_THREADS / 32; ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(maxbits, (unsigned long long)__double_as_longlong((double)m));
+  }
 }
 
 __global__ void row_sum_kernel(const double* __restrict__ X, long long ldx, int n, double* __restrict__ out) {
@@ -121,7 +133,9 @@ __global__ void symmetrize_inplace_kernel(double* __restrict__ X, long long ldx,
 
 // X <- alpha (X + D) for a symmetric D of which only the 128 x 128 tiles on or above the diagonal
 // were computed: block (bx, by), by <= bx, adds tile (by, bx) of D to X there and its transpose
-// to tile (bx, by); a diagonal tile adds (D + D^T) / 2, so X stays exactly symmetric.
+// to tile (bx, by); a diagonal tile adds (D + D^T) / 2, so X stays exactly symmetric.  !SCALED:
+// alpha = 1 (a plain step), one FP64 operation fewer per entry.
+template <bool SCALED>
 __global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, const float* __restrict__ D, long long ldd,
                                      int n, double alpha) {
   __shared__ float t[TT][TT + 1];
@@ -138,12 +152,14 @@ __global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, cons
     const int i = r0 + r, j = c0 + c;
     if (i < n && j < n) {
       double* x = X + (size_t)i * ldx + j;
-      *x = alpha * (*x + (bx == by ? 0.5 * ((double)t[r][c] + (double)t[c][r]) : (double)t[r][c]));
+      const double v = *x + (bx == by ? 0.5 * ((double)t[r][c] + (double)t[c][r]) : (double)t[r][c]);
+      *x = SCALED ? alpha * v : v;
     }
     const int i2 = c0 + r, j2 = r0 + c;
     if (bx != by && i2 < n && j2 < n) {
       double* x = X + (size_t)i2 * ldx + j2;
-      *x = alpha * (*x + (double)t[c][r]);
+      const double v = *x + (double)t[c][r];
+      *x = SCALED ? alpha * v : v;
     }
   }
 }
@@ -290,8 +306,8 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
     if ((err = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), s)) != cudaSuccess) return fail(err);
     {
       ProfScope prof("factor_ns_residual", 16.0 * (double)n * n, 0.0, s);
-      dim3 grid((n + 255) / 256 < 8 ? (n + 255) / 256 : 8, n);
-      ns_residual_kernel<<<grid, 256, 0, s>>>(X, ldx, n, ptr, col, val, project ? rowsum : nullptr, alpha, rh, rl,
+      dim3 grid(std::min((n + NSR_THREADS - 1) / NSR_THREADS, NSR_SPLIT), n);
+      ns_residual_kernel<<<grid, NSR_THREADS, 0, s>>>(X, ldx, n, ptr, col, val, project ? rowsum : nullptr, alpha, rh, rl,
                                               ldp, maxbits);
     }
     unsigned long long hb = 0;
@@ -313,7 +329,8 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
       return fail(err);
     {
       ProfScope prof("factor_ns_update", 12.0 * (double)n * n, 0.0, s);
-      ns_update_sym_kernel<<<sgrid, sblock, 0, s>>>(X, ldx, D, ldp, n, alpha);
+      if (alpha == 1.0) ns_update_sym_kernel<false><<<sgrid, sblock, 0, s>>>(X, ldx, D, ldp, n, alpha);
+      else ns_update_sym_kernel<true><<<sgrid, sblock, 0, s>>>(X, ldx, D, ldp, n, alpha);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return fail(err);
     // scaling of the next step (scaled Newton-Schulz): with the spectrum of M X in [a, 1], the

@@ -52,8 +52,18 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1)
 gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask, int M, int N, int K,
                    float* __restrict__ D, long long ldd, int accumulate, int* __restrict__ err, int upper) {
+  // Tile order: groups of GROUP_M row tiles, the row tile fastest within a group.  The CTAs
+  // resident at one time then cover a block of about GROUP_M x (SMs / GROUP_M) tiles and share
+  // its A and B panels in L2; in plain N-fastest order a wide result (N of many tiles, as in the
+  // Newton-Schulz products) has every resident CTA stream its own B panel from HBM.
+  constexpr int GROUP_M = 8;
+  const int tn = (int)gridDim.x, tm = (int)gridDim.y;
+  const int lin = (int)blockIdx.y * tn + (int)blockIdx.x;
+  const int grp = lin / (GROUP_M * tn), first = grp * GROUP_M, gs = min(tm - first, GROUP_M);
+  const int local = lin - grp * GROUP_M * tn;
+  const int tile_m = first + local % gs, tile_n = local / gs;
   // upper: only the tiles on or above the diagonal of a symmetric result (BN == BM)
-  if (upper && (int)blockIdx.x < (int)blockIdx.y) return;
+  if (upper && tile_n < tile_m) return;
   using C = TileCfg<BN>;
   constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, TILE_B = C::TILE_B;
   extern __shared__ uint8_t smem_raw[];
@@ -63,7 +73,7 @@ gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;  // N tiles fastest: CTAs sharing an A tile run together
+  const int m0 = tile_m * BM, n0 = tile_n * BN;
   const int kblocks = (K + BK - 1) / BK;
   const int total = nseg * kblocks;
 
@@ -162,18 +172,20 @@ gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
-// FP32 (or FP64) -> BF16 hi/lo planes
+// FP32 (or FP64) -> BF16 hi/lo planes; CTAs take whole rows (no per-element index division)
 template <class T>
 __global__ void split_bf16_kernel(const T* __restrict__ src, long long ld_src, int rows, int cols,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ld_dst) {
-  const long long total = (long long)rows * cols;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / cols), c = (int)(idx % cols);
-    const float v = (float)src[(size_t)r * ld_src + c];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[(size_t)r * ld_dst + c] = h;
-    lo[(size_t)r * ld_dst + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const T* sr = src + (size_t)r * ld_src;
+    __nv_bfloat16* hr = hi + (size_t)r * ld_dst;
+    __nv_bfloat16* lr = lo + (size_t)r * ld_dst;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+      const float v = (float)sr[c];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hr[c] = h;
+      lr[c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
 }
 
@@ -211,21 +223,23 @@ cudaError_t gemm_launch(const SplitOperand* A, const SplitOperand* B, const int*
   return cudaGetLastError();
 }
 
-// complex64 matrix (row stride ld) -> BF16 planes Re hi/lo, Im hi/lo (row stride ldp)
+// complex64 matrix (row stride ld) -> BF16 planes Re hi/lo, Im hi/lo (row stride ldp); CTAs take
+// whole rows
 __global__ void split_c64_kernel(const float2* __restrict__ M, int n, long long ld, __nv_bfloat16* __restrict__ rh,
                                  __nv_bfloat16* __restrict__ rl, __nv_bfloat16* __restrict__ ih,
                                  __nv_bfloat16* __restrict__ il, long long ldp) {
-  const long long total = (long long)n * n;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / n), c = (int)(idx % n);
-    const float2 v = M[(size_t)r * ld + c];
-    const __nv_bfloat16 a = __float2bfloat16_rn(v.x), b = __float2bfloat16_rn(v.y);
-    const size_t o = (size_t)r * ldp + c;
-    rh[o] = a;
-    rl[o] = __float2bfloat16_rn(v.x - __bfloat162float(a));
-    ih[o] = b;
-    il[o] = __float2bfloat16_rn(v.y - __bfloat162float(b));
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const float2* mr = M + (size_t)r * ld;
+    const size_t o0 = (size_t)r * ldp;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const float2 v = mr[c];
+      const __nv_bfloat16 a = __float2bfloat16_rn(v.x), b = __float2bfloat16_rn(v.y);
+      const size_t o = o0 + c;
+      rh[o] = a;
+      rl[o] = __float2bfloat16_rn(v.x - __bfloat162float(a));
+      ih[o] = b;
+      il[o] = __float2bfloat16_rn(v.y - __bfloat162float(b));
+    }
   }
 }
 
@@ -293,8 +307,7 @@ __global__ void combine_cplx_kernel(const float* __restrict__ D, long long ldd, 
 }  // namespace
 
 cudaError_t split_c64_planes(const float2* M, int n, long long ld, const CplxPlanes& P, cudaStream_t s) {
-  const long long total = (long long)n * n;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 8 * 152);
+  const int blocks = std::max(1, std::min(n, 8 * 152));
   split_c64_kernel<<<blocks, 256, 0, s>>>(M, n, ld, P.rh, P.rl, P.ih, P.il, P.ldp);
   return cudaGetLastError();
 }
@@ -344,16 +357,14 @@ cudaError_t real_gemm(const RealPlanes& P, const double2* X, double2* Y, int nr,
 
 cudaError_t split_bf16_f32(const float* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
                            __nv_bfloat16* lo, long long ld_dst, cudaStream_t s) {
-  const long long total = (long long)rows * cols;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 8 * 152);
+  const int blocks = std::max(1, std::min(rows, 8 * 152));
   split_bf16_kernel<float><<<blocks, 256, 0, s>>>(src, ld_src, rows, cols, hi, lo, ld_dst);
   return cudaGetLastError();
 }
 
 cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int cols, __nv_bfloat16* hi,
                            __nv_bfloat16* lo, long long ld_dst, cudaStream_t s) {
-  const long long total = (long long)rows * cols;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 8 * 152);
+  const int blocks = std::max(1, std::min(rows, 8 * 152));
   split_bf16_kernel<double><<<blocks, 256, 0, s>>>(src, ld_src, rows, cols, hi, lo, ld_dst);
   return cudaGetLastError();
 }
