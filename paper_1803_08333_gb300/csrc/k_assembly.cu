@@ -535,53 +535,131 @@ __global__ void rhs_kernel(const DeviceGeometry g, double k, const double* __res
 }
 
 // ---------------------------------------------------------------- radiation vector (FP64)
+// F(u) = sum_cells sum_q w_q e^{-ik u.r_q} J_c(r_q) over the 7-point rule, with the cell current
+// J_c(r) = sum_i s_i j_i (r - P_i) / 2 (the RWG functions of Eq. RWGdef times the cell area of
+// the product rule) = (r S - T) / 2, S = sum_i s_i j_i, T = sum_i s_i j_i P_i.  Hence
+//   F_c = (S B1 - T B0) / 2,  B0 = sum_q w_q e^{-ik u.r_q},  B1 = sum_q w_q e^{-ik u.r_q} r_q,
+// where B0 and B1 depend on the direction and the cell only (one set for RB right-hand sides),
+// and e^{-ik u.r_q} = e^{-ik u.c} e^{-ik u.(r_q - c)} (c the centroid) takes one sincos per cell
+// and, per point, the Taylor series of a small angle.  Everything stays FP64: at low frequency
+// the radiated field is a small remainder of the cell contributions.
 constexpr int FF_THREADS = 256;
 
+// cos and sin of |x| <= 1/2 by their Taylor series (to x^12 and x^13: truncation below 1e-15)
+__device__ __forceinline__ void sincos_small64(double x, double* s, double* c) {
+  const double x2 = x * x;
+  double pc = fma(x2, 1.0 / 479001600.0, -1.0 / 3628800.0);
+  pc = fma(x2, pc, 1.0 / 40320.0);
+  pc = fma(x2, pc, -1.0 / 720.0);
+  pc = fma(x2, pc, 1.0 / 24.0);
+  pc = fma(x2, pc, -0.5);
+  *c = fma(x2, pc, 1.0);
+  double ps = fma(x2, 1.0 / 6227020800.0, -1.0 / 39916800.0);
+  ps = fma(x2, ps, 1.0 / 362880.0);
+  ps = fma(x2, ps, -1.0 / 5040.0);
+  ps = fma(x2, ps, 1.0 / 120.0);
+  ps = fma(x2, ps, -1.0 / 6.0);
+  *s = fma(x * x2, ps, x);
+}
+
+template <int RB>
 __global__ void __launch_bounds__(FF_THREADS)
-farfield_kernel(const DeviceGeometry g, double k, const double2* __restrict__ j, const double* __restrict__ dirs,
+farfield_kernel(const DeviceGeometry g, double k, const double2* __restrict__ j, int nrhs, const double* dirs,
                 int ndir, double2* __restrict__ out) {
   const int d = blockIdx.x;
-  const int r = blockIdx.y;
+  const int r0 = blockIdx.y * RB;
   const double ux = dirs[3 * d], uy = dirs[3 * d + 1], uz = dirs[3 * d + 2];
-  const double2* jr = j + (size_t)r * g.ne;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  // 7-point rule weights (sum 1) times 1/2
+  const double wa = 0.5 * (9.0 / 40.0), wb = 0.5 * (155.0 - 3.872983346207416885) / 1200.0,
+               wc = 0.5 * (155.0 + 3.872983346207416885) / 1200.0;
+  double acc[RB][6];
+#pragma unroll
+  for (int b = 0; b < RB; ++b)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) acc[b][e] = 0.0;
   for (int c = threadIdx.x; c < g.nc; c += blockDim.x) {
-    double jl_r[3], jl_i[3];
-    for (int i = 0; i < 3; ++i) {
-      const double2 v = jr[g.cell_edges[3 * c + i]];
-      const double sg = (double)g.cell_sign[3 * c + i];
-      jl_r[i] = sg * v.x;
-      jl_i[i] = sg * v.y;
-    }
+    const double cx = g.cen64[3 * c], cy = g.cen64[3 * c + 1], cz = g.cen64[3 * c + 2];
+    double b0r = 0.0, b0i = 0.0, b1r[3] = {0.0, 0.0, 0.0}, b1i[3] = {0.0, 0.0, 0.0};
+#pragma unroll
     for (int q = 0; q < 7; ++q) {
       const double* rq = g.qp64 + 21 * c + 3 * q;
-      const double w = 0.5 * (q == 0 ? 9.0 / 40.0 : (q < 4 ? (155.0 - sqrt(15.0)) / 1200.0 : (155.0 + sqrt(15.0)) / 1200.0));
+      const double x = -k * (ux * (rq[0] - cx) + uy * (rq[1] - cy) + uz * (rq[2] - cz));
       double sn, cs;
-      sincos(-k * (ux * rq[0] + uy * rq[1] + uz * rq[2]), &sn, &cs);
-      for (int x = 0; x < 3; ++x) {
-        double cr = 0.0, ci = 0.0;
-        for (int i = 0; i < 3; ++i) {
-          const double rel = rq[x] - g.verts[3 * g.tris[3 * c + i] + x];
-          cr += jl_r[i] * rel;
-          ci += jl_i[i] * rel;
+      if (fabs(x) <= 0.5) sincos_small64(x, &sn, &cs);
+      else sincos(x, &sn, &cs);
+      const double w = q == 0 ? wa : (q < 4 ? wb : wc);
+      const double er = w * cs, ei = w * sn;
+      b0r += er;
+      b0i += ei;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        b1r[e] = fma(er, rq[e], b1r[e]);
+        b1i[e] = fma(ei, rq[e], b1i[e]);
+      }
+    }
+    {  // times e^{-ik u.c}
+      double sn, cs;
+      sincos(-k * (ux * cx + uy * cy + uz * cz), &sn, &cs);
+      double t = b0r;
+      b0r = t * cs - b0i * sn;
+      b0i = t * sn + b0i * cs;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        t = b1r[e];
+        b1r[e] = t * cs - b1i[e] * sn;
+        b1i[e] = t * sn + b1i[e] * cs;
+      }
+    }
+    int ed[3];
+    double sg[3];
+    const double* P[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      ed[i] = g.cell_edges[3 * c + i];
+      sg[i] = (double)g.cell_sign[3 * c + i];
+      P[i] = g.verts + 3 * g.tris[3 * c + i];
+    }
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      if (r0 + b >= nrhs) break;
+      const double2* jr = j + (size_t)(r0 + b) * g.ne;
+      double sr = 0.0, si = 0.0, tr[3] = {0.0, 0.0, 0.0}, ti[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double2 v = jr[ed[i]];
+        const double vr = sg[i] * v.x, vi = sg[i] * v.y;
+        sr += vr;
+        si += vi;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          tr[e] = fma(vr, P[i][e], tr[e]);
+          ti[e] = fma(vi, P[i][e], ti[e]);
         }
-        acc[2 * x] += w * (cr * cs - ci * sn);
-        acc[2 * x + 1] += w * (cr * sn + ci * cs);
+      }
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {  // S B1 - T B0
+        acc[b][2 * e] += (sr * b1r[e] - si * b1i[e]) - (tr[e] * b0r - ti[e] * b0i);
+        acc[b][2 * e + 1] += (sr * b1i[e] + si * b1r[e]) - (tr[e] * b0i + ti[e] * b0r);
       }
     }
   }
   __shared__ double red[FF_THREADS / 32][6];
-  for (int e = 0; e < 6; ++e) {
-    double v = acc[e];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][e] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    double v = 0.0;
-    for (int w = 0; w < FF_THREADS / 32; ++w) v += red[w][threadIdx.x];
-    double* o = reinterpret_cast<double*>(out + ((size_t)r * ndir + d) * 3);
-    o[threadIdx.x] = v;
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    if (r0 + b >= nrhs) break;
+    for (int e = 0; e < 6; ++e) {
+      double v = acc[b][e];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][e] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      double v = 0.0;
+      for (int w = 0; w < FF_THREADS / 32; ++w) v += red[w][threadIdx.x];
+      double* o = reinterpret_cast<double*>(out + ((size_t)(r0 + b) * ndir + d) * 3);
+      o[threadIdx.x] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -637,8 +715,12 @@ cudaError_t launch_rhs_planewave(const DeviceGeometry& g, double k, const double
 
 cudaError_t launch_farfield(const DeviceGeometry& g, double k, const double2* j, int nrhs, const double* dirs,
                             int ndir, double2* out, cudaStream_t s) {
-  dim3 grid(ndir, nrhs);
-  farfield_kernel<<<grid, FF_THREADS, 0, s>>>(g, k, j, dirs, ndir, out);
+  ProfScope prof("farfield", 0.0, 0.0, s);
+  if (nrhs == 1) {
+    farfield_kernel<1><<<dim3(ndir, 1), FF_THREADS, 0, s>>>(g, k, j, nrhs, dirs, ndir, out);
+  } else {
+    farfield_kernel<4><<<dim3(ndir, (nrhs + 3) / 4), FF_THREADS, 0, s>>>(g, k, j, nrhs, dirs, ndir, out);
+  }
   return cudaGetLastError();
 }
 

@@ -208,6 +208,28 @@ def test_rcs_matches_oracle(ctx, memo):
         assert np.abs(got[keep] - 10 * np.log10(ref[keep])).max() <= 1e-3
 
 
+@pytest.mark.parametrize("ka", [1e-5, 2.5])
+def test_farfield_kernel_matches_oracle(ctx, memo, ka):
+    """The radiation-vector kernel alone: the GPU's own currents, five columns (a block of four and a
+    ragged one), through the oracle's radiation integral.  At ka = 1e-5 the field is a remainder of
+    about 1e-5 of the cell contributions, so the FP64 sums are tested where they cancel."""
+    m, D, _, _ = _oracle(memo, "l2", 1.0)
+    op = rf.Operator(ctx, m.verts, m.tris, ka)
+    kh, pol = synth.random_plane_waves(5, seed=3)
+    j, rep = op.solve(op.rhs_planewave(kh, pol), tol=1e-8)
+    assert all(r.converged for r in rep)
+    jn = j.cpu().numpy()
+    dirs = farfield.cut_directions(np.linspace(0.0, np.pi, 61), 0.3)
+    got = op.farfield(j, dirs)
+    assert got.shape == (5, 61)
+    for r in range(5):
+        ref = farfield.bistatic_rcs(D, jn[r], ka, dirs)
+        keep = ref > ref.max() * 1e-4
+        assert np.abs(got[r][keep] - 10 * np.log10(ref[keep])).max() <= 1e-6
+    one = op.farfield(j[2:3], dirs)  # the single-column kernel on one of the block's columns
+    assert np.abs(one[0] - got[2]).max() <= 1e-9
+
+
 def test_multi_rhs_columns_independent(ctx, memo):
     """Each column of a batched solve equals its single-column solve."""
     m, D, _, _ = _oracle(memo, "l2", 1.2)
