@@ -379,34 +379,50 @@ near_pairs_kernel(const DeviceGeometry g, double k, float2* __restrict__ TA, flo
       J1r[a] = (pt.V[a] + (pt.p[a] - g.cen64[3 * si + a]) * pt.S) * INV_4PI;
       J1i[a] = 0.0;
     }
-    // smooth part (e^{ikR} - 1)/(4 pi R) on the inner 7-point rule; value i k / 4pi at R = 0
-    const double Ai = g.area64[si];
-    for (int j = 0; j < 7; ++j) {
-      double rr[3], rhoi[3], R2 = 0.0;
+    // smooth part (e^{ikR} - 1)/(4 pi R) on the inner 7-point rule, value i k / 4pi at R = 0.  It
+    // is bounded and smooth (real part -2 sin^2(kR/2) / (4 pi R), imaginary sin(kR) / (4 pi R)),
+    // so it runs in FP32 from the centroid-local quadrature offsets (GB300's FP64 pipe is slow),
+    // added to the FP64 singular part once per point
+    {
+      const float kf = (float)k;
+      float dc[3], ro[3];
       for (int a = 0; a < 3; ++a) {
-        rr[a] = g.qp64[21 * si + 3 * j + a];
-        rhoi[a] = rr[a] - g.cen64[3 * si + a];
-        double dd = r[a] - rr[a];
-        R2 += dd * dd;
+        dc[a] = (g.cen_hi[3 * so + a] - g.cen_hi[3 * si + a]) + (g.cen_lo[3 * so + a] - g.cen_lo[3 * si + a]);
+        ro[a] = g.rho[21 * so + 3 * i + a];
       }
-      const double w = (j == 0 ? 9.0 / 40.0 : (j < 4 ? (155.0 - sqrt(15.0)) / 1200.0 : (155.0 + sqrt(15.0)) / 1200.0)) * Ai;
-      double gr, gi;
-      if (R2 > 0.0) {
-        const double R = sqrt(R2);
-        double sh, ch, sn, cs;
-        sincos(0.5 * k * R, &sh, &ch);
-        sincos(k * R, &sn, &cs);
-        gr = -2.0 * sh * sh * INV_4PI / R;
-        gi = sn * INV_4PI / R;
-      } else {
-        gr = 0.0;
-        gi = k * INV_4PI;
+      float s0r = 0.f, s0i = 0.f, s1r[3] = {0.f, 0.f, 0.f}, s1i[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        float ri[3], R2 = 0.f;
+        for (int a = 0; a < 3; ++a) {
+          ri[a] = g.rho[21 * si + 3 * j + a];
+          const float dd = dc[a] + (ro[a] - ri[a]);
+          R2 = fmaf(dd, dd, R2);
+        }
+        float gr, gi;
+        if (so == si && j == i) {  // the same point (R = 0 exactly)
+          gr = 0.f;
+          gi = kf * INV_4PI_F;
+        } else {
+          const float rinv = rsqrtf(R2);
+          float sh, ch;
+          sincos_far(0.5f * kf * (R2 * rinv), &sh, &ch);
+          gr = -2.f * sh * sh * INV_4PI_F * rinv;
+          gi = 2.f * sh * ch * INV_4PI_F * rinv;
+        }
+        const float w = g.wq[7 * si + j];
+        s0r = fmaf(w, gr, s0r);
+        s0i = fmaf(w, gi, s0i);
+        for (int a = 0; a < 3; ++a) {
+          s1r[a] = fmaf(w * gr, ri[a], s1r[a]);
+          s1i[a] = fmaf(w * gi, ri[a], s1i[a]);
+        }
       }
-      J0r += w * gr;
-      J0i += w * gi;
+      J0r += (double)s0r;
+      J0i += (double)s0i;
       for (int a = 0; a < 3; ++a) {
-        J1r[a] += w * gr * rhoi[a];
-        J1i[a] += w * gi * rhoi[a];
+        J1r[a] += (double)s1r[a];
+        J1i[a] += (double)s1i[a];
       }
     }
     const double wo = (i == 0 ? 9.0 / 40.0 : (i < 4 ? (155.0 - sqrt(15.0)) / 1200.0 : (155.0 + sqrt(15.0)) / 1200.0)) *

@@ -1,17 +1,19 @@
-// Streaming GEMV: y = op(M) x for one or two FP32-mode columns with the matrix moved by the
-// bulk-copy engine.
+// Streaming GEMV: y = op(M) x for one or two columns with the matrix moved by the bulk-copy
+// engine.
 //
 // The operator products of a single-right-hand-side solve are HBM bound: each application
 // streams T_A, V and the factors once.  A register-pipelined GEMV keeps only as many bytes in
 // flight as its unrolled loads allow; here one producer thread per CTA issues cp.async.bulk
 // copies of whole row segments (8 rows x 512 complex64 or 1024 FP32 values, 32 KB per stage)
 // together with the matching segment of x into a 4-stage shared-memory ring, so about 180 KB per
-// SM are in flight whatever the consumers do.  Eight consumer warps each take one row of a
-// stage, read it and x from shared memory (no global-memory latency on the consumer side),
-// accumulate in FP32 within the segment and in compensated FP32 across segments, and release
-// the stage through an mbarrier.  Work units (row block, column segment) are dealt to
-// the persistent CTAs in contiguous ranges of equal size; a row block split between CTAs is
-// combined by FP64 atomics.  Every wait is bounded and records an error code on timeout.
+// SM are in flight whatever the consumers do; consumers read the matrix and x from shared memory
+// only and release a stage through an mbarrier.  Three kernels:
+//   * gemv_sym_kernel (FP32 mode, symmetric M: T_A, V and the factors): reads only the tiles on
+//     and above the diagonal and forms both the row and the mirrored column product;
+//   * gemv_stream_kernel (FP32 mode, any M): one consumer warp per row of a stage;
+//   * gemv_stream_ff_kernel (float-float, one column of a complex64 M): the accurate products.
+// Work units are dealt to persistent CTAs in contiguous ranges of equal size; partial sums meet
+// in FP64 atomics.  Every wait is bounded and records an error code on timeout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -215,6 +217,126 @@ gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __r
       }
     }
   }
+}
+
+// ---------------------------------------------------------------- float-float, one column
+// The accurate products (right-hand side, refinement residuals) of a complex64 matrix in the
+// streaming layout: x is split into FP32 hi + lo, every product m * x_hi is exact as (p, e) by an
+// FMA residual, p enters a float-float (hi, lo) accumulator by an error-free two-sum and
+// e + m * x_lo its low word (about 1e-14 of sum |terms|).
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float a, float bh, float bl) {
+  const float p = a * bh;
+  const float e = fmaf(a, bh, -p);
+  const float c = fmaf(a, bl, e);
+  const float s = hi + p;
+  const float bb = s - hi;
+  lo += ((hi - (s - bb)) + (p - bb)) + c;
+  hi = s;
+}
+
+template <bool CONJ>
+__global__ void __launch_bounds__(STHREADS, 1)
+gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
+                      const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr,
+                      int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
+  uint64_t* empty = full + SSTAGES;
+  constexpr int SEG = SBYTES_ROW / 8;  // 512 complex entries per row segment
+  static_assert(SEG * 8 <= SXMAX / 2, "x hi and lo segments fit the stage");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], SROWS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == SROWS) {
+    if (lane == 0) {
+      for (long long u = u0; u < u1; ++u) {
+        const long long i = u - u0;
+        const int s = (int)(i % SSTAGES);
+        const long long round = i / SSTAGES;
+        if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1))) {
+          atomicExch(err, 31);
+          break;
+        }
+        const int rb = (int)(u / upr), cb = (int)(u % upr) * SEG;
+        const int row0 = rb * SROWS, rows = min(SROWS, n - row0);
+        const int cols = min(SEG, ld - cb);
+        const uint32_t bytes = (uint32_t)cols * 8;
+        mbar_expect_tx(&full[s], bytes * rows + 2 * bytes);
+        uint8_t* st = smem + s * SSTAGE;
+        for (int r = 0; r < rows; ++r)
+          bulk_load(st + r * SBYTES_ROW, M + (size_t)(row0 + r) * ld + cb, bytes, &full[s]);
+        bulk_load(st + SMAT, xh + cb, bytes, &full[s]);
+        bulk_load(st + SMAT + SXMAX / 2, xl + cb, bytes, &full[s]);
+      }
+      const long long cnt = u1 - u0;
+      for (long long i = cnt > SSTAGES ? cnt - SSTAGES : 0; i < cnt; ++i)
+        if (!mbar_wait(&full[i % SSTAGES], (uint32_t)((i / SSTAGES) & 1))) atomicExch(err, 33);
+    }
+    return;
+  }
+
+  float fh[2] = {0.f, 0.f}, fl[2] = {0.f, 0.f};  // (re, im) float-float sums of row `warp`
+  auto flush = [&](long long rb) {
+    const int row = (int)rb * SROWS + warp;
+    const double re = warp_sum_d((double)fh[0] + (double)fl[0]);
+    const double im = warp_sum_d((double)fh[1] + (double)fl[1]);
+    fh[0] = fh[1] = fl[0] = fl[1] = 0.f;
+    if (lane == 0 && row < n) {
+      double* o = reinterpret_cast<double*>(out + row);
+      atomicAdd(o, re);
+      atomicAdd(o + 1, im);
+    }
+  };
+  long long cur_rb = -1;
+  bool ok = true;
+  for (long long u = u0; u < u1 && ok; ++u) {
+    const long long i = u - u0;
+    const int s = (int)(i % SSTAGES);
+    const uint32_t parity = (uint32_t)((i / SSTAGES) & 1);
+    const int rb = (int)(u / upr), cb = (int)(u % upr) * SEG;
+    if (rb != cur_rb) {
+      if (cur_rb >= 0) flush(cur_rb);
+      cur_rb = rb;
+    }
+    ok = __all_sync(0xffffffffu, mbar_wait(&full[s], parity));
+    if (!ok) {
+      if (lane == 0) atomicExch(err, 32);
+      break;
+    }
+    const int row = rb * SROWS + warp;
+    if (row < n) {
+      const uint8_t* st = smem + s * SSTAGE;
+      const float4* sxh = reinterpret_cast<const float4*>(st + SMAT);
+      const float4* sxl = reinterpret_cast<const float4*>(st + SMAT + SXMAX / 2);
+      const float4* srow = reinterpret_cast<const float4*>(st + warp * SBYTES_ROW);
+      const int nq = min(SEG, ld - cb) / 2;  // two complex entries per float4
+#pragma unroll 2
+      for (int q = lane; q < nq; q += 32) {
+        const float4 m = srow[q], x4 = sxh[q], l4 = sxl[q];
+        const float my = CONJ ? -m.y : m.y, mw = CONJ ? -m.w : m.w;
+        ff_acc(fh[0], fl[0], m.x, x4.x, l4.x);
+        ff_acc(fh[0], fl[0], -my, x4.y, l4.y);
+        ff_acc(fh[0], fl[0], m.z, x4.z, l4.z);
+        ff_acc(fh[0], fl[0], -mw, x4.w, l4.w);
+        ff_acc(fh[1], fl[1], m.x, x4.y, l4.y);
+        ff_acc(fh[1], fl[1], my, x4.x, l4.x);
+        ff_acc(fh[1], fl[1], m.z, x4.w, l4.w);
+        ff_acc(fh[1], fl[1], mw, x4.z, l4.z);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  if (ok && cur_rb >= 0) flush(cur_rb);
 }
 
 // ---------------------------------------------------------------- symmetric matrices
@@ -546,6 +668,28 @@ cudaError_t launch_stream(const void* M, int ld, int n, GemvScratch& w, cudaStre
   return cudaGetLastError();
 }
 
+template <bool CONJ>
+cudaError_t launch_stream_ff(const float2* M, int ld, int n, GemvScratch& w, cudaStream_t s) {
+  constexpr int SEG = SBYTES_ROW / 8;
+  auto k = gemv_stream_ff_kernel<CONJ>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  static int sms = 0;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SSMEM);
+    int dev = 0;
+    if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
+    if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  if (attr != cudaSuccess) return attr;
+  if (!w.err || !w.xl) return cudaErrorInvalidValue;
+  const int upr = (ld + SEG - 1) / SEG;
+  const long long units = (long long)((n + SROWS - 1) / SROWS) * upr;
+  const int grid = (int)std::max(1LL, std::min<long long>(units, sms));
+  k<<<grid, STHREADS, SSMEM, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, w.err);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 template <int NR>
@@ -558,6 +702,9 @@ template <int NR>
 cudaError_t gemv_stream_r32(const float* M, int ld, int n, GemvScratch& w, cudaStream_t s) {
   if (w.symmetric) return launch_sym<NR, true, false>(M, ld, n, w, s);
   return launch_stream<NR, true, false>(M, ld, n, w, s);
+}
+cudaError_t gemv_stream_c64_ff(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s) {
+  return conj ? launch_stream_ff<true>(M, ld, n, w, s) : launch_stream_ff<false>(M, ld, n, w, s);
 }
 template cudaError_t gemv_stream_c64<1>(const float2*, int, int, bool, GemvScratch&, cudaStream_t);
 template cudaError_t gemv_stream_c64<2>(const float2*, int, int, bool, GemvScratch&, cudaStream_t);

@@ -353,6 +353,7 @@ cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, bool conj, GemvMod
   const double mbytes = stream && w.symmetric ? 4.0 * n * (n + 1.0) : 8.0 * n * n;
   ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", mbytes + 32.0 * n * NR, 8.0 * n * n * NR, s);
   if (stream) return gemv_stream_c64<NR <= 1 ? 1 : 2>(M, ld, n, conj, w, s);
+  if (NR == 1 && mode == GEMV_FF && w.chunk == 0 && w.ctas_per_sm == 0 && w.err) return gemv_stream_c64_ff(M, ld, n, conj, w, s);
 #define RF_LAUNCH_C(FFV, CJ)                                                                      \
   {                                                                                               \
     auto k = gemv_c64_kernel<NR, FFV, CJ>;                                                        \

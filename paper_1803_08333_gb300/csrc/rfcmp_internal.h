@@ -216,6 +216,8 @@ template <int NR>
 cudaError_t gemv_stream_c64(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s);
 template <int NR>
 cudaError_t gemv_stream_r32(const float* M, int ld, int n, GemvScratch& w, cudaStream_t s);
+// Float-float streaming GEMV of one column of a complex64 M (x split in w.xh + w.xl).
+cudaError_t gemv_stream_c64_ff(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s);
 int padded_ld(int n);
 
 // Device memory from the device's stream-ordered pool, which keeps freed memory mapped: the
