@@ -211,6 +211,7 @@ def bench_ours(args):
     clocks = Clocks(local)
     rf.profile_enable(True)
     barrier()
+    launches0 = rf.launch_count()
     clocks.start()
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -220,6 +221,7 @@ def bench_ours(args):
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
+    gpu_launches = rf.launch_count() - launches0
     prof = rf.profile_read()
     rf.profile_enable(False)
     ms = ev0.elapsed_time(ev1)
@@ -262,7 +264,6 @@ def bench_ours(args):
     kernels = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3),
                    "share_of_instrumented": round(v["total_ms"] / max(total_kernel_ms, 1e-9), 4)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])}
-    gpu_launches = int(sum(v["launches"] for v in prof.values()))
     iters = {("%g" % ka): r.iterations for ka, r, _ in reports[: len(KA)]}
     resid = max(r.residual for _, r, _ in reports)
     out = {
@@ -286,7 +287,8 @@ def bench_ours(args):
             "tol": TOL,
             "nrhs": 1,
             "parallelism": "replicas" if ws > 1 else "single",
-            "l2": "inputs larger than L2 (T_A complex64 7.5 GB, V 3.4 GB)",
+            "l2": "inputs larger than L2 (T_A complex64 %.2f GB, V %.2f GB)"
+                  % (8e-9 * (30 * MESH_N ** 2) ** 2, 8e-9 * (20 * MESH_N ** 2) ** 2),
             "plan": plan,
         },
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2), "p99": round(float(np.percentile(lat, 99)), 2)},
@@ -468,7 +470,10 @@ def bench_serving(args):
             kh, pol = synth.random_plane_waves(nr, seed=1000 + i)
             futs[i] = srv.submit(m.verts, m.tris, ka, kh, pol, tol=TOL)
 
+    import paper_1803_08333_gb300 as rf
+
     clocks = Clocks(0)
+    launches0 = rf.launch_count()
     clocks.start()
     th = threading.Thread(target=driver)
     t0 = time.perf_counter()
@@ -477,6 +482,7 @@ def bench_serving(args):
     res = [f.result() for f in futs]
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    gpu_launches = rf.launch_count() - launches0
     st = srv.stats()
     srv.close()
     sizes = sorted({3 * m.tris.shape[0] // 2 for m, _, _ in scenes})
@@ -489,7 +495,7 @@ def bench_serving(args):
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]}, "requests_per_s": st["requests_per_s"],
         "mean_batch_columns": st["mean_batch_columns"], "max_residual": max(max(r.residuals) for r in res),
         "resident_operators": st["resident_operators"], "cold_start_s": round(cold_s, 2), "wall_s": round(wall, 2),
-        "clocks": clk, "data": "synthetic (seeded jittered spheres, cubes, ellipsoids; random plane waves)"}))
+        "gpu_launches": gpu_launches, "clocks": clk, "data": "synthetic (seeded jittered spheres, cubes, ellipsoids; random plane waves)"}))
 
 
 def bench_batched(args):
@@ -522,6 +528,7 @@ def bench_batched(args):
     torch.cuda.synchronize()
     clocks = Clocks(0)
     rf.profile_enable(True)
+    launches0 = rf.launch_count()
     clocks.start()
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -533,13 +540,13 @@ def bench_batched(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    gpu_launches = rf.launch_count() - launches0
     prof = rf.profile_read()
     rf.profile_enable(False)
     ms = ev0.elapsed_time(ev1) / args.steps
     value = nrhs / (ms / 1e3)
     peaks, peak_kind = _peaks()
     roof, roof_more = roofline(prof, peaks, peak_kind, clk)
-    gpu_launches = int(sum(v["launches"] for v in prof.values()))
     # end to end: host right-hand sides in, host currents out, through the C call with host buffers
     eh = e.cpu().numpy()
     torch.cuda.synchronize()

@@ -325,6 +325,11 @@ int rfcmp_profile_enable(int enable);
 /* Copies up to max_entries families into out (host) and their number into *n_entries. */
 int rfcmp_profile_read(rfcmp_profile_entry* out, int max_entries, int* n_entries);
 
+/* Kernel launches of this library since it was loaded, over all devices of the process:
+ * every kernel adds one to a device counter from its first block and thread.  Synchronises
+ * the current device.  Errors: RFCMP_ERR_INVALID_ARG (out is NULL). */
+int rfcmp_launch_count(uint64_t* out);
+
 const char* rfcmp_strerror(int status);
 const char* rfcmp_last_error(void);
 

@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
     "rfcmp_gemm_bf16x3", "rfcmp_plan_default", "rfcmp_ctx_set_plan", "rfcmp_op_set_plan", "rfcmp_op_get_plan",
-    "rfcmp_op_trim",
+    "rfcmp_op_trim", "rfcmp_launch_count",
 ]
 
 
@@ -153,6 +153,7 @@ def lib():
         L.rfcmp_op_get_plan.argtypes = [vp, ctypes.POINTER(Plan)]
         L.rfcmp_profile_enable.argtypes = [i32]
         L.rfcmp_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
+        L.rfcmp_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         _LIB = L
     return _LIB
 
@@ -188,6 +189,13 @@ def profile_read() -> dict:
         e = buf[i]
         out[e.name.decode()] = {"launches": e.launches, "total_ms": e.total_ms, "bytes": e.bytes, "flops": e.flops}
     return out
+
+
+def launch_count() -> int:
+    """Kernel launches of the library so far (device counters; synchronises the device)."""
+    v = ctypes.c_uint64()
+    _check(lib().rfcmp_launch_count(ctypes.byref(v)))
+    return int(v.value)
 
 
 def gemm_bf16x3(A, B, D=None, accumulate=False):

@@ -1118,6 +1118,13 @@ bool op_ta_view(const rfcmp_op* op, OpTaView* out) {
 // ============================================================================ C ABI
 extern "C" {
 
+int rfcmp_launch_count(uint64_t* out) {
+  if (!out) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  *out = launches_assembly() + launches_exact() + launches_factor() + launches_gemm() + launches_gemv_stream() +
+         launches_linalg();
+  return RFCMP_OK;
+}
+
 const char* rfcmp_strerror(int st) {
   switch (st) {
     case RFCMP_OK: return "ok";

@@ -192,6 +192,7 @@ __device__ __forceinline__ void far_moments(const float (&rs)[21], const float (
 template <int MINB>
 __global__ void __launch_bounds__(FAR_THREADS, MINB)
 far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float2* __restrict__ V, int nb) {
+  RF_COUNT_LAUNCH();
   __shared__ TileCells S, Tt;
   // linear tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
   long long tix = blockIdx.x;
@@ -352,6 +353,7 @@ constexpr int NEAR_THREADS = NEAR_PAIRS_PER_BLOCK * 16;
 // 16 slots per pair: slot = order * 7 + outer point, slots 14, 15 idle
 __global__ void __launch_bounds__(NEAR_THREADS)
 near_pairs_kernel(const DeviceGeometry g, double k, float2* __restrict__ TA, float2* __restrict__ V) {
+  RF_COUNT_LAUNCH();
   __shared__ double mom[NEAR_PAIRS_PER_BLOCK][16][16];  // per slot: I0(2) Iouter(6) Iinner(6) Irr(2)
   const int lp = threadIdx.x >> 4;
   const int slot = threadIdx.x & 15;
@@ -507,6 +509,7 @@ near_pairs_kernel(const DeviceGeometry g, double k, float2* __restrict__ TA, flo
 constexpr int MT = 32;
 
 __global__ void mirror_upper_kernel(float2* __restrict__ M, int n, size_t ld) {
+  RF_COUNT_LAUNCH();
   // block (bx, by) with by <= bx copies tile (by, bx) of the upper triangle into tile (bx, by)
   __shared__ float2 tile[MT][MT + 1];
   const int bx = blockIdx.x, by = blockIdx.y;
@@ -526,6 +529,7 @@ __global__ void mirror_upper_kernel(float2* __restrict__ M, int n, size_t ld) {
 // ---------------------------------------------------------------- excitation (FP64)
 __global__ void rhs_kernel(const DeviceGeometry g, double k, const double* __restrict__ khat,
                            const double* __restrict__ pol, int nrhs, double2* __restrict__ e) {
+  RF_COUNT_LAUNCH();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (n >= g.ne || r >= nrhs) return;
@@ -582,6 +586,7 @@ template <int RB>
 __global__ void __launch_bounds__(FF_THREADS)
 farfield_kernel(const DeviceGeometry g, double k, const double2* __restrict__ j, int nrhs, const double* dirs,
                 int ndir, double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   const int d = blockIdx.x;
   const int r0 = blockIdx.y * RB;
   const double ux = dirs[3 * d], uy = dirs[3 * d + 1], uz = dirs[3 * d + 2];
@@ -739,5 +744,7 @@ cudaError_t launch_farfield(const DeviceGeometry& g, double k, const double2* j,
   }
   return cudaGetLastError();
 }
+
+RF_LAUNCH_READER(launches_assembly)
 
 }  // namespace rfcmp

@@ -76,6 +76,7 @@ static_assert(XBN == 32, "two epilogue warps of 16 columns per tensor-memory qua
 __global__ void __launch_bounds__(XTHREADS, 1)
 exact_gemm_kernel(const __grid_constant__ ExactMaps maps, int M, int N, int K, const int* __restrict__ ea,
                   const int* __restrict__ eb, double* __restrict__ D, long long ldd, int* __restrict__ err) {
+  RF_COUNT_LAUNCH();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + XSTAGES * XSTAGE);
@@ -244,6 +245,7 @@ constexpr int DT = 256;
 template <class Src>
 __global__ void __launch_bounds__(DT) digits_kernel(Src src, int K, long long ldp, __nv_bfloat16* __restrict__ planes,
                                                     long long plane_stride, int* __restrict__ e_out) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.x;
   double m = 0.0;
   for (int k = threadIdx.x; k < K; k += DT) m = fmax(m, fabs(src(r, k)));
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(DT) digits_kernel(Src src, int K, long long ld
 constexpr int CT = 32;
 __global__ void combine_f64_kernel(const double* __restrict__ D, long long ldd, int n, int nr, int conj, int real,
                                    double2 scale, int accumulate, double2* __restrict__ Y) {
+  RF_COUNT_LAUNCH();
   __shared__ double2 t[CT][CT + 1];
   const int i0 = blockIdx.x * CT, r0 = blockIdx.y * CT;
   const double sg = conj ? -1.0 : 1.0;
@@ -385,5 +388,7 @@ cudaError_t exact_real_gemm(const ExactOperand& P, int n, const double2* X, doub
   combine_f64_kernel<<<g, b, 0, s>>>(w.D64, 2 * nr, n, nr, 0, 1, make_double2(scale, 0.0), accumulate ? 1 : 0, Y);
   return cudaGetLastError();
 }
+
+RF_LAUNCH_READER(launches_exact)
 
 }  // namespace rfcmp

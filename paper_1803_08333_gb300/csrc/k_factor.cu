@@ -44,6 +44,7 @@ ns_residual_kernel(const double* __restrict__ X, long long ldx, int n, const int
                    const int32_t* __restrict__ col, const double* __restrict__ val,
                    const double* __restrict__ rowsum, double alpha, __nv_bfloat16* __restrict__ hi,
                    __nv_bfloat16* __restrict__ lo, long long ldp, unsigned long long* __restrict__ maxbits) {
+  RF_COUNT_LAUNCH();
   const int i = blockIdx.y;
   const double* xr = X + (size_t)i * ldx;
   const double rs = rowsum ? rowsum[i] / n : 0.0;  // the 1 1^T / n term of the projected case
@@ -70,6 +71,7 @@ ns_residual_kernel(const double* __restrict__ X, long long ldx, int n, const int
 }
 
 __global__ void row_sum_kernel(const double* __restrict__ X, long long ldx, int n, double* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   const int i = blockIdx.x;
   double s = 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) s += X[(size_t)i * ldx + j];
@@ -88,6 +90,7 @@ __global__ void row_sum_kernel(const double* __restrict__ X, long long ldx, int 
 constexpr int TT = 32;
 __global__ void symmetrize_store_kernel(const double* __restrict__ X, long long ldx, int n, double shift,
                                         float* __restrict__ hi, float* __restrict__ lo, long long ld) {
+  RF_COUNT_LAUNCH();
   __shared__ double tile[TT][TT + 1];
   const int bi = blockIdx.y * TT, bj = blockIdx.x * TT;
   // load the transposed tile X[bj.., bi..]
@@ -110,6 +113,7 @@ __global__ void symmetrize_store_kernel(const double* __restrict__ X, long long 
 // X <- (X + X^T) / 2 in place: block (bx, by), by <= bx, averages tile (by, bx) with the
 // transpose of tile (bx, by) and writes both
 __global__ void symmetrize_inplace_kernel(double* __restrict__ X, long long ldx, int n) {
+  RF_COUNT_LAUNCH();
   __shared__ double a[TT][TT + 1], b[TT][TT + 1];
   const int bx = blockIdx.x, by = blockIdx.y;
   if (by > bx) return;
@@ -138,6 +142,7 @@ __global__ void symmetrize_inplace_kernel(double* __restrict__ X, long long ldx,
 template <bool SCALED>
 __global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, const float* __restrict__ D, long long ldd,
                                      int n, double alpha) {
+  RF_COUNT_LAUNCH();
   __shared__ float t[TT][TT + 1];
   const int bx = blockIdx.x, by = blockIdx.y;
   if (by > bx) return;
@@ -167,6 +172,7 @@ __global__ void ns_update_sym_kernel(double* __restrict__ X, long long ldx, cons
 // u = X v (dense FP64, one warp per row); sum += sum_i u_i
 __global__ void dmatvec_kernel(const double* __restrict__ X, long long ldx, int n, const double* __restrict__ v,
                                double* __restrict__ u, double* __restrict__ sum) {
+  RF_COUNT_LAUNCH();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const double* xr = X + (size_t)warp * ldx;
@@ -184,6 +190,7 @@ __global__ void resid_vec_kernel(const int32_t* __restrict__ ptr, const int32_t*
                                  const double* __restrict__ val, int n, int project, const double* __restrict__ v,
                                  const double* __restrict__ u, const double* __restrict__ sum,
                                  double* __restrict__ w, double* __restrict__ norm2) {
+  RF_COUNT_LAUNCH();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double d = 0.0;
   if (i < n) {
@@ -198,6 +205,7 @@ __global__ void resid_vec_kernel(const int32_t* __restrict__ ptr, const int32_t*
 }
 
 __global__ void scale_vec_kernel(int n, double c, const double* __restrict__ w, double* __restrict__ v) {
+  RF_COUNT_LAUNCH();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = c * w[i];
 }
@@ -206,6 +214,7 @@ __global__ void scale_vec_kernel(int n, double c, const double* __restrict__ w, 
 __global__ void jacobi_start_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                     const double* __restrict__ val, int n, double c, double* __restrict__ X,
                                     long long ldx) {
+  RF_COUNT_LAUNCH();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double d = 0.0;
     for (int q = ptr[i]; q < ptr[i + 1]; ++q)
@@ -360,5 +369,7 @@ cudaError_t newton_schulz_pseudo_inverse(const int32_t* ptr, const int32_t* col,
   *final_residual = res;
   return fail(cudaSuccess);
 }
+
+RF_LAUNCH_READER(launches_factor)
 
 }  // namespace rfcmp

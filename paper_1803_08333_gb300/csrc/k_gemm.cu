@@ -52,6 +52,7 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1)
 gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask, int M, int N, int K,
                    float* __restrict__ D, long long ldd, int accumulate, int* __restrict__ err, int upper) {
+  RF_COUNT_LAUNCH();
   // Tile order: groups of GROUP_M row tiles, the row tile fastest within a group.  The CTAs
   // resident at one time then cover a block of about GROUP_M x (SMs / GROUP_M) tiles and share
   // its A and B panels in L2; in plain N-fastest order a wide result (N of many tiles, as in the
@@ -176,6 +177,7 @@ gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask
 template <class T>
 __global__ void split_bf16_kernel(const T* __restrict__ src, long long ld_src, int rows, int cols,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ld_dst) {
+  RF_COUNT_LAUNCH();
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {
     const T* sr = src + (size_t)r * ld_src;
     __nv_bfloat16* hr = hi + (size_t)r * ld_dst;
@@ -228,6 +230,7 @@ cudaError_t gemm_launch(const SplitOperand* A, const SplitOperand* B, const int*
 __global__ void split_c64_kernel(const float2* __restrict__ M, int n, long long ld, __nv_bfloat16* __restrict__ rh,
                                  __nv_bfloat16* __restrict__ rl, __nv_bfloat16* __restrict__ ih,
                                  __nv_bfloat16* __restrict__ il, long long ldp) {
+  RF_COUNT_LAUNCH();
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
     const float2* mr = M + (size_t)r * ld;
     const size_t o0 = (size_t)r * ldp;
@@ -248,6 +251,7 @@ __global__ void split_c64_kernel(const float2* __restrict__ M, int n, long long 
 __global__ void split_x_kernel(const double2* __restrict__ X, int n, int nr, long long ldp, bool stacked,
                                __nv_bfloat16* __restrict__ rh, __nv_bfloat16* __restrict__ rl,
                                __nv_bfloat16* __restrict__ ih, __nv_bfloat16* __restrict__ il) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.y;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < ldp; k += (long long)gridDim.x * blockDim.x) {
     const double2 v = k < n ? X[(size_t)r * n + k] : make_double2(0.0, 0.0);
@@ -270,6 +274,7 @@ __global__ void split_x_kernel(const double2* __restrict__ X, int n, int nr, lon
 constexpr int CT = 32;
 __global__ void combine_cplx_kernel(const float* __restrict__ D, long long ldd, int n, int nr, int conj, int real,
                                     double2 scale, int accumulate, double2* __restrict__ Y) {
+  RF_COUNT_LAUNCH();
   __shared__ double2 t[CT][CT + 1];
   const int i0 = blockIdx.x * CT, r0 = blockIdx.y * CT;
   const double sg = conj ? -1.0 : 1.0;
@@ -386,5 +391,7 @@ cudaError_t gemm_bf16x3(const SplitOperand* A, const SplitOperand* B, const int*
       return cudaErrorInvalidValue;
   }
 }
+
+RF_LAUNCH_READER(launches_gemm)
 
 }  // namespace rfcmp

@@ -61,6 +61,7 @@ template <int NR, bool REAL, bool CONJ>
 __global__ void __launch_bounds__(STHREADS, 1)
 gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __restrict__ xh,
                    double2* __restrict__ out, long long units, int upr, int* __restrict__ err) {
+  RF_COUNT_LAUNCH();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
@@ -239,6 +240,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
 gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
                       const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr,
                       int* __restrict__ err) {
+  RF_COUNT_LAUNCH();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
@@ -448,6 +450,7 @@ template <int NR, bool REAL, bool CONJ>
 __global__ void __launch_bounds__(STHREADS, 1)
 gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __restrict__ xh,
                 double2* __restrict__ out, long long units, int* __restrict__ err) {
+  RF_COUNT_LAUNCH();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
@@ -710,5 +713,7 @@ template cudaError_t gemv_stream_c64<1>(const float2*, int, int, bool, GemvScrat
 template cudaError_t gemv_stream_c64<2>(const float2*, int, int, bool, GemvScratch&, cudaStream_t);
 template cudaError_t gemv_stream_r32<1>(const float*, int, int, GemvScratch&, cudaStream_t);
 template cudaError_t gemv_stream_r32<2>(const float*, int, int, GemvScratch&, cudaStream_t);
+
+RF_LAUNCH_READER(launches_gemv_stream)
 
 }  // namespace rfcmp

@@ -58,6 +58,7 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
 // x (complex128, n x nr) -> FP32 hi (and lo) copies padded to ld, and zero the accumulator
 __global__ void gemv_prep_kernel(const double2* __restrict__ x, int n, int ld, int nr, float2* __restrict__ xh,
                                  float2* __restrict__ xl, double2* __restrict__ acc, int acc_n) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x) {
     const double2 v = i < n ? x[(size_t)r * n + i] : make_double2(0.0, 0.0);
@@ -71,6 +72,7 @@ __global__ void gemv_prep_kernel(const double2* __restrict__ x, int n, int ld, i
 // y = scale * acc (+ y)
 __global__ void gemv_finalize_kernel(const double2* __restrict__ acc, int n, int nr, double2 scale, int accumulate,
                                      double2* __restrict__ y) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double2 a = acc[(size_t)r * n + i];
@@ -110,6 +112,7 @@ template <int NR, bool FF, bool CONJ>
 __global__ void __launch_bounds__(GEMV_WARPS * 32)
 gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
                 const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr, int chunk) {
+  RF_COUNT_LAUNCH();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   double acc[GEMV_ROWS_PER_WARP][NR][2];
@@ -198,6 +201,7 @@ __global__ void __launch_bounds__(GEMV_WARPS * 32)
 gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, int ld, int n,
                 const float2* __restrict__ xh, const float2* __restrict__ xl, double2* __restrict__ out,
                 long long units, int upr, int chunk) {
+  RF_COUNT_LAUNCH();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   double acc[GEMV_ROWS_PER_WARP][NR][2];
@@ -532,6 +536,7 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 
 __global__ void sigma_t_kernel(const int32_t* __restrict__ cell_edges, const int8_t* __restrict__ cell_sign, int nc,
                                int ne, const double2* __restrict__ x, double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (c >= nc) return;
@@ -550,6 +555,7 @@ __global__ void sigma_t_kernel(const int32_t* __restrict__ cell_edges, const int
 __global__ void lambda_t_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ edge,
                                 const int8_t* __restrict__ sign, int nv, int ne, const double2* __restrict__ x,
                                 double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (v >= nv) return;
@@ -566,6 +572,7 @@ __global__ void lambda_t_kernel(const int32_t* __restrict__ ptr, const int32_t* 
 
 __global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, int nc,
                            const double2* __restrict__ z, double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   // Sigma^T Sigma z: 3 z_c - sum over edge-neighbours (values are +-1 and 3 by construction)
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
@@ -583,6 +590,7 @@ __global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __res
 
 __global__ void edge_combo_kernel(const int32_t* __restrict__ edge_cells, const int32_t* __restrict__ edge_verts,
                                   int ne, int nc, int nv, EdgeCombo cb, double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (n >= ne) return;
@@ -622,6 +630,7 @@ __global__ void edge_combo_kernel(const int32_t* __restrict__ edge_cells, const 
 }
 
 __global__ void column_sum_kernel(const double2* __restrict__ w, int n, double* __restrict__ sums) {
+  RF_COUNT_LAUNCH();
   // sums[2r], sums[2r+1] += column r of w (block per (chunk, column))
   const int r = blockIdx.y;
   double sx = 0.0, sy = 0.0;
@@ -640,6 +649,7 @@ __global__ void column_sum_kernel(const double2* __restrict__ w, int n, double* 
 __global__ void star_middle_kernel(const double* __restrict__ area, int nc, const double2* __restrict__ z,
                                    const double2* __restrict__ w, const double* __restrict__ sums, double scale,
                                    double2* __restrict__ q) {
+  RF_COUNT_LAUNCH();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (c >= nc) return;
@@ -696,6 +706,7 @@ cudaError_t star_middle(const DeviceGeometry& g, const double2* z, const double2
 namespace {
 __global__ void area_center_kernel(const double* __restrict__ area, int nc, const double2* __restrict__ w,
                                    const double* __restrict__ sums, double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (c >= nc) return;
@@ -704,6 +715,7 @@ __global__ void area_center_kernel(const double* __restrict__ area, int nc, cons
   out[o] = make_double2(area[c] * (w[o].x - mx), area[c] * (w[o].y - my));
 }
 __global__ void center_kernel(int nc, const double* __restrict__ sums, double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (c >= nc) return;
@@ -733,6 +745,7 @@ constexpr int DOT_THREADS = 256;
 
 __global__ void dot_kernel(const double2* __restrict__ a, const double2* __restrict__ b, int64_t n,
                            double2* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   // out[r] += a_r^H b_r (block per (chunk, column); out zeroed by the caller)
   const int r = blockIdx.y;
   double sx = 0.0, sy = 0.0;
@@ -762,6 +775,7 @@ __global__ void dot_kernel(const double2* __restrict__ a, const double2* __restr
 
 __global__ void axpy_cols_kernel(const double* __restrict__ coef, double sgn, const double2* __restrict__ x,
                                  double2* __restrict__ y, int64_t n, const int* __restrict__ active) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const double a = sgn * coef[r];
@@ -776,6 +790,7 @@ __global__ void axpy_cols_kernel(const double* __restrict__ coef, double sgn, co
 
 __global__ void xpby_cols_kernel(const double2* __restrict__ x, const double* __restrict__ coef,
                                  double2* __restrict__ y, int64_t n, const int* __restrict__ active) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const double b = coef[r];
@@ -789,12 +804,14 @@ __global__ void xpby_cols_kernel(const double2* __restrict__ x, const double* __
 }
 
 __global__ void copy_kernel(const double2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+  RF_COUNT_LAUNCH();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = x[i];
 }
 
 __global__ void copy_scale_cols_kernel(const double2* __restrict__ x, const double* __restrict__ coef,
                                        double2* __restrict__ y, int64_t n) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.y;
   const double a = coef[r];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -804,6 +821,7 @@ __global__ void copy_scale_cols_kernel(const double2* __restrict__ x, const doub
 }
 
 __global__ void scale_kernel(double2* __restrict__ y, double2 a, int64_t n) {
+  RF_COUNT_LAUNCH();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = y[i];
     y[i] = make_double2(a.x * v.x - a.y * v.y, a.x * v.y + a.y * v.x);
@@ -812,6 +830,7 @@ __global__ void scale_kernel(double2* __restrict__ y, double2 a, int64_t n) {
 
 __global__ void cg_alpha_kernel(const double* __restrict__ rr, const double2* __restrict__ pAp,
                                 double* __restrict__ alpha, const int* __restrict__ active, int nrhs) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   const double d = pAp[r].x;
@@ -820,6 +839,7 @@ __global__ void cg_alpha_kernel(const double* __restrict__ rr, const double2* __
 
 __global__ void cg_beta_kernel(const double2* __restrict__ rr_new2, double* __restrict__ rr, double* __restrict__ beta,
                                const int* __restrict__ active, int nrhs) {
+  RF_COUNT_LAUNCH();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   if (active && !active[r]) {
@@ -921,6 +941,7 @@ __device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<do
 // columns c0 + c >= n (padding of the last block) get b = 0: they are frozen from the start
 __global__ void bcg_init_kernel(int n, int W, int c0, bool project, double* __restrict__ X, double* __restrict__ R,
                                 double* __restrict__ rr0) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   const double off = project ? 1.0 / n : 0.0;
   const bool v0 = c0 + it.c < n, v1 = c0 + it.c + 1 < n;
@@ -943,6 +964,7 @@ __global__ void __launch_bounds__(BCG_THREADS)
 bcg_spmm_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const double* __restrict__ val,
                 int n, int W, const double* __restrict__ in, double* __restrict__ out, int accumulate,
                 double* __restrict__ dotp) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   double d0 = 0.0, d1 = 0.0;
 #pragma unroll 4
@@ -977,6 +999,7 @@ bcg_spmm_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col
 __global__ void __launch_bounds__(BCG_THREADS)
 mg_smooth0_kernel(int n, int W, double w, const double* __restrict__ diag, const double* __restrict__ B,
                   double* __restrict__ X) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
 #pragma unroll 4
   for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
@@ -992,6 +1015,7 @@ __global__ void __launch_bounds__(BCG_THREADS)
 mg_resid_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const double* __restrict__ val,
                 const double* __restrict__ diag, int n, int W, double w, int mode, const double* __restrict__ B,
                 const double* __restrict__ X, double* __restrict__ T) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
 #pragma unroll 4
   for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
@@ -1017,6 +1041,7 @@ mg_resid_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col
 // Xc = Cinv Bc (dense m x m times m x W)
 __global__ void mg_coarse_kernel(int m, int W, const double* __restrict__ Cinv, const double* __restrict__ Bc,
                                  double* __restrict__ Xc) {
+  RF_COUNT_LAUNCH();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (c >= W || i >= m) return;
@@ -1035,6 +1060,7 @@ bcg_update_kernel(int n, int W, const double* __restrict__ rz, const double* __r
                   const double* __restrict__ pAp, const double* __restrict__ bb, double tol2, double* __restrict__ X,
                   double* __restrict__ R, const double* __restrict__ P, const double* __restrict__ AP,
                   double* __restrict__ rr_new) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   const bool f0 = frozen(rr, bb, tol2, it.c), f1 = frozen(rr, bb, tol2, it.c + 1);
   if (it.first()) {
@@ -1066,6 +1092,7 @@ bcg_update_kernel(int n, int W, const double* __restrict__ rz, const double* __r
 // out += R.Z (per column)
 __global__ void __launch_bounds__(BCG_THREADS)
 bcg_dot_kernel(int n, int W, const double* __restrict__ R, const double* __restrict__ Z, double* __restrict__ out) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   double d0 = 0.0, d1 = 0.0;
 #pragma unroll 4
@@ -1085,6 +1112,7 @@ bcg_direction_kernel(int n, int W, const double* __restrict__ rz, const double* 
                      const double* __restrict__ rr_new, const double* __restrict__ bb, double tol2,
                      const double* __restrict__ Z, double* __restrict__ P, double* __restrict__ pAp,
                      double* __restrict__ zero_a, double* __restrict__ zero_b) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   if (it.first()) {
     for (int k = 0; k < 2; ++k) {
@@ -1109,6 +1137,7 @@ bcg_direction_kernel(int n, int W, const double* __restrict__ rz, const double* 
 }
 
 __global__ void bcg_colsum_kernel(int n, int W, const double* __restrict__ X, double* __restrict__ sums) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   double s0 = 0.0, s1 = 0.0;
   for (int i = it.r0; i < it.r1; i += BCG_RLANES) {
@@ -1124,6 +1153,7 @@ __global__ void bcg_colsum_kernel(int n, int W, const double* __restrict__ X, do
 __global__ void bcg_store_kernel(int n, int W, int c0, int ld, const double* __restrict__ X,
                                  const double* __restrict__ sums, bool project, float* __restrict__ Xhi,
                                  float* __restrict__ Xlo) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   for (int k = 0; k < 2; ++k) {
     const int cc = it.c + k;
@@ -1141,6 +1171,7 @@ __global__ void bcg_store_kernel(int n, int W, int c0, int ld, const double* __r
 // Xd[i, c0 + c] = X[i, c] - mean_c + 1/n  (an approximation of (L + 1 1^T / n)^{-1}, FP64)
 __global__ void bcg_store_f64_kernel(int n, int W, int c0, long long ld, const double* __restrict__ X,
                                      const double* __restrict__ sums, double* __restrict__ Xd) {
+  RF_COUNT_LAUNCH();
   RowIter it(n);
   for (int k = 0; k < 2; ++k) {
     const int cc = it.c + k;
@@ -1367,5 +1398,7 @@ cudaError_t dense_inverse_block_cg(const int32_t* ptr, const int32_t* col, const
   *iters = worst_iters;
   return fail(cudaSuccess);
 }
+
+RF_LAUNCH_READER(launches_linalg)
 
 }  // namespace rfcmp

@@ -14,6 +14,31 @@
 
 namespace rfcmp {
 
+// Launch accounting: every kernel of the library adds one to its translation unit's device
+// counter from block 0, thread 0 as its first statement, so the count covers every launch
+// whatever the kernel does next.  Each .cu file defines a reader (RF_LAUNCH_READER); the C ABI
+// sums them (rfcmp_launch_count).
+#ifdef __CUDACC__
+static __device__ unsigned long long g_rf_launches;
+#define RF_COUNT_LAUNCH()                                                                      \
+  do {                                                                                         \
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0) \
+      atomicAdd(&::rfcmp::g_rf_launches, 1ULL);                                                \
+  } while (0)
+#define RF_LAUNCH_READER(fn)                                                              \
+  unsigned long long fn() {                                                                \
+    unsigned long long v = 0;                                                              \
+    if (cudaMemcpyFromSymbol(&v, ::rfcmp::g_rf_launches, sizeof(v)) != cudaSuccess) v = 0; \
+    return v;                                                                              \
+  }
+#endif
+unsigned long long launches_assembly();
+unsigned long long launches_exact();
+unsigned long long launches_factor();
+unsigned long long launches_gemm();
+unsigned long long launches_gemv_stream();
+unsigned long long launches_linalg();
+
 // ---------------------------------------------------------------- op accessors
 // Read-only view of an operator's T_A for translation units outside capi.cu.
 struct OpTaView {

@@ -320,3 +320,22 @@ def test_multi_rhs_tensor_core_path(ctx, memo, name, k):
     # each column equals its single-column (GEMV) solve
     j1, _ = op.solve(e[7:8], tol=1e-10)
     assert _rel(jg[7], j1.cpu().numpy()[0]) <= 1e-8
+
+
+def test_launch_counter_counts_every_kernel(ctx, memo):
+    """The device launch counter sees each kernel of an application: the split of x, the
+    streaming GEMV and the scaling of the accumulator, at least."""
+    import torch
+
+    m, _, _, _ = _oracle(memo, "l2", 1.0)
+    op = rf.Operator(ctx, m.verts, m.tris, 1.0)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    x = torch.complex(torch.randn(1, op.N, generator=g, dtype=torch.float64),
+                      torch.randn(1, op.N, generator=g, dtype=torch.float64)).cuda()
+    n0 = rf.launch_count()
+    op.apply("T_A", x)
+    n1 = rf.launch_count()
+    op.apply("T_A", x)
+    n2 = rf.launch_count()
+    assert n1 - n0 >= 3
+    assert n2 - n1 == n1 - n0  # the same call launches the same kernels
