@@ -47,6 +47,14 @@ __device__ __forceinline__ void sincos_quarter(float r, float* s, float* c) {
   *c = fmaf(r2, pc, 1.0f);
 }
 
+// sin and cos of |r| <= 1/20 in FP32: sin to r^3 (truncation r^4/120 <= 6e-8 relative, the FP32
+// rounding) and cos to r^4 (below 3e-11)
+__device__ __forceinline__ void sincos_twentieth(float r, float* s, float* c) {
+  const float r2 = r * r;
+  *s = fmaf(r * r2, -1.0f / 6.0f, r);
+  *c = fmaf(r2, fmaf(r2, 1.0f / 24.0f, -0.5f), 1.0f);
+}
+
 // sin and cos of x >= 0 in FP32.  Cody and Waite's reduction (1980): q = nearest integer to
 // x 2/pi, r = x - q pi/2 with pi/2 split into a short leading part (q times it is exact for
 // q < 2^16) and a remainder; then the series above on |r| <= pi/4 and the quadrant of q.
@@ -139,9 +147,9 @@ struct FarMoments {
   }
 };
 
-// 7 x 7 product rule over the pair; SHIFTED: the phase of each evaluation is k R - kref with
-// |k R - kref| <= pi/4 (no range reduction), else k R
-template <bool SHIFTED>
+// 7 x 7 product rule over the pair; SHIFTED > 0: the phase of each evaluation is k R - kref with
+// |k R - kref| <= pi/4 (SHIFTED 1) or <= 1/20 (SHIFTED 2), no range reduction; 0: k R
+template <int SHIFTED>
 __device__ __forceinline__ void far_moments(const float (&rs)[21], const float (&ws)[7], const float (&rt)[21],
                                             const float (&wt)[7], const float (&d)[3], float k, float kref,
                                             FarMoments& M) {
@@ -157,7 +165,8 @@ __device__ __forceinline__ void far_moments(const float (&rs)[21], const float (
       const float rinv = rsqrtf(r2);
       const float R = r2 * rinv;
       float sn, cs;
-      if (SHIFTED) sincos_quarter(fmaf(k, R, -kref), &sn, &cs);
+      if (SHIFTED == 2) sincos_twentieth(fmaf(k, R, -kref), &sn, &cs);
+      else if (SHIFTED == 1) sincos_quarter(fmaf(k, R, -kref), &sn, &cs);
       else sincos_far(k * R, &sn, &cs);
       const float gw = wt[j] * rinv;
       const float gr = gw * cs, gi = gw * sn;
@@ -245,15 +254,16 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
 
     // e^{ikR} = e^{ik Rc} e^{ik (R - Rc)} with Rc the centroid distance: |R - Rc| is at most the
     // sum of the two quadrature radii, so where k times that is within pi/4 the 49 evaluations
-    // take sin and cos of k (R - Rc) without a range reduction and the common factor
-    // e^{ik Rc} multiplies the eight moments once
+    // take sin and cos of k (R - Rc) without a range reduction (a shorter series within 1/20,
+    // the common case at low frequency) and the factor e^{ik Rc} multiplies the eight moments once
     const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
     const float kRc = k * (dd * rsqrtf(dd));
-    const bool shifted = k * (S.rq[sl] + Tt.rq[tl]) <= 0.78f;
+    const float span = k * (S.rq[sl] + Tt.rq[tl]);  // bound on |k (R - Rc)|
     FarMoments Mo;
-    if (shifted) far_moments<true>(rs, ws, rt, wt, d, k, kRc, Mo);
-    else far_moments<false>(rs, ws, rt, wt, d, k, 0.f, Mo);
-    if (shifted) Mo.rotate(kRc);
+    if (span <= 0.05f) far_moments<2>(rs, ws, rt, wt, d, k, kRc, Mo);
+    else if (span <= 0.78f) far_moments<1>(rs, ws, rt, wt, d, k, kRc, Mo);
+    else far_moments<0>(rs, ws, rt, wt, d, k, 0.f, Mo);
+    if (span <= 0.78f) Mo.rotate(kRc);
     const float I0r = Mo.I0r, I0i = Mo.I0i, Irr_r = Mo.Irr_r, Irr_i = Mo.Irr_i;
     const float* Ir_r = Mo.Ir_r;
     const float* Ir_i = Mo.Ir_i;
@@ -565,6 +575,13 @@ __global__ void rhs_kernel(const DeviceGeometry g, double k, const double* __res
 // the radiated field is a small remainder of the cell contributions.
 constexpr int FF_THREADS = 256;
 
+// cos and sin of |x| <= 1/20 by their Taylor series (to x^6 and x^7: truncation below 1e-15)
+__device__ __forceinline__ void sincos_tiny64(double x, double* s, double* c) {
+  const double x2 = x * x;
+  *c = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  *s = fma(x * x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), x);
+}
+
 // cos and sin of |x| <= 1/2 by their Taylor series (to x^12 and x^13: truncation below 1e-15)
 __device__ __forceinline__ void sincos_small64(double x, double* s, double* c) {
   const double x2 = x * x;
@@ -606,7 +623,9 @@ farfield_kernel(const DeviceGeometry g, double k, const double2* __restrict__ j,
       const double* rq = g.qp64 + 21 * c + 3 * q;
       const double x = -k * (ux * (rq[0] - cx) + uy * (rq[1] - cy) + uz * (rq[2] - cz));
       double sn, cs;
-      if (fabs(x) <= 0.5) sincos_small64(x, &sn, &cs);
+      const double ax = fabs(x);
+      if (ax <= 0.05) sincos_tiny64(x, &sn, &cs);
+      else if (ax <= 0.5) sincos_small64(x, &sn, &cs);
       else sincos(x, &sn, &cs);
       const double w = q == 0 ? wa : (q < 4 ? wb : wc);
       const double er = w * cs, ei = w * sn;
