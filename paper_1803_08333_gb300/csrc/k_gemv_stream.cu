@@ -5,9 +5,10 @@
 // streams T_A, V and the factors once.  A register-pipelined GEMV keeps only as many bytes in
 // flight as its unrolled loads allow; here one producer thread per CTA issues cp.async.bulk
 // copies of whole row segments (8 rows x 512 complex64 or 1024 FP32 values, 32 KB per stage)
-// together with the matching segment of x into a 4-stage shared-memory ring, so about 180 KB per
-// SM are in flight whatever the consumers do; consumers read the matrix and x from shared memory
-// only and release a stage through an mbarrier.  Three kernels:
+// together with the matching segment of x into a shared-memory ring of four stages per SM (one
+// CTA with four stages, or two CTAs with two where the registers allow twice the warps), so about
+// 180 KB per SM are in flight whatever the consumers do; consumers read the matrix and x from
+// shared memory only and release a stage through an mbarrier.  Three kernels:
 //   * gemv_sym_kernel (FP32 mode, symmetric M: T_A, V and the factors): reads only the tiles on
 //     and above the diagonal and forms both the row and the mirrored column product;
 //   * gemv_stream_kernel (FP32 mode, any M): one consumer warp per row of a stage;
@@ -225,6 +226,10 @@ gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __r
 // streaming layout: x is split into FP32 hi + lo, every product m * x_hi is exact as (p, e) by an
 // FMA residual, p enters a float-float (hi, lo) accumulator by an error-free two-sum and
 // e + m * x_lo its low word (about 1e-14 of sum |terms|).
+// two CTAs per SM, two stages each: twice the consumer warps to hide the two-sum chains
+constexpr int FF_NCTA = 2;
+constexpr int FF_NST = 2;
+
 __device__ __forceinline__ void ff_acc(float& hi, float& lo, float a, float bh, float bl) {
   const float p = a * bh;
   const float e = fmaf(a, bh, -p);
@@ -236,21 +241,21 @@ __device__ __forceinline__ void ff_acc(float& hi, float& lo, float a, float bh, 
 }
 
 template <bool CONJ>
-__global__ void __launch_bounds__(STHREADS, 1)
+__global__ void __launch_bounds__(STHREADS, FF_NCTA)
 gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
                       const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr,
                       int* __restrict__ err) {
   RF_COUNT_LAUNCH();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
-  uint64_t* empty = full + SSTAGES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + FF_NST * SSTAGE);
+  uint64_t* empty = full + FF_NST;
   constexpr int SEG = SBYTES_ROW / 8;  // 512 complex entries per row segment
   static_assert(SEG * 8 <= SXMAX / 2, "x hi and lo segments fit the stage");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < SSTAGES; ++s) {
+    for (int s = 0; s < FF_NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], SROWS);
     }
@@ -262,8 +267,8 @@ gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2*
     if (lane == 0) {
       for (long long u = u0; u < u1; ++u) {
         const long long i = u - u0;
-        const int s = (int)(i % SSTAGES);
-        const long long round = i / SSTAGES;
+        const int s = (int)(i % FF_NST);
+        const long long round = i / FF_NST;
         if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1))) {
           atomicExch(err, 31);
           break;
@@ -280,8 +285,8 @@ gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2*
         bulk_load(st + SMAT + SXMAX / 2, xl + cb, bytes, &full[s]);
       }
       const long long cnt = u1 - u0;
-      for (long long i = cnt > SSTAGES ? cnt - SSTAGES : 0; i < cnt; ++i)
-        if (!mbar_wait(&full[i % SSTAGES], (uint32_t)((i / SSTAGES) & 1))) atomicExch(err, 33);
+      for (long long i = cnt > FF_NST ? cnt - FF_NST : 0; i < cnt; ++i)
+        if (!mbar_wait(&full[i % FF_NST], (uint32_t)((i / FF_NST) & 1))) atomicExch(err, 33);
     }
     return;
   }
@@ -302,8 +307,8 @@ gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2*
   bool ok = true;
   for (long long u = u0; u < u1 && ok; ++u) {
     const long long i = u - u0;
-    const int s = (int)(i % SSTAGES);
-    const uint32_t parity = (uint32_t)((i / SSTAGES) & 1);
+    const int s = (int)(i % FF_NST);
+    const uint32_t parity = (uint32_t)((i / FF_NST) & 1);
     const int rb = (int)(u / upr), cb = (int)(u % upr) * SEG;
     if (rb != cur_rb) {
       if (cur_rb >= 0) flush(cur_rb);
@@ -446,16 +451,17 @@ __device__ __forceinline__ void sym_tile(const uint8_t* st, int qc, int row0, in
   }
 }
 
-template <int NR, bool REAL, bool CONJ>
-__global__ void __launch_bounds__(STHREADS, 1)
+template <int NR, bool REAL, bool CONJ, int NCTA>
+__global__ void __launch_bounds__(STHREADS, NCTA)
 gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __restrict__ xh,
                 double2* __restrict__ out, long long units, int* __restrict__ err) {
   RF_COUNT_LAUNCH();
+  constexpr int NST = NCTA == 2 ? 2 : SSTAGES;  // ring depth per CTA (the SM holds NCTA rings)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
-  uint64_t* empty = full + SSTAGES;
-  uint64_t* rfull = empty + SSTAGES;  // the 8 warps' row partials of a stage are in shared memory
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * SSTAGE);
+  uint64_t* empty = full + NST;
+  uint64_t* rfull = empty + NST;  // the 8 warps' row partials of a stage are in shared memory
   constexpr int ESZ = REAL ? 4 : 8;
   constexpr int SEG = SBYTES_ROW / ESZ;
   constexpr int EPQ = 16 / ESZ;       // matrix entries per float4
@@ -466,7 +472,7 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
   const SymGeom G = sym_geom(n, ld, SEG);
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < SSTAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], SROWS);
       mbar_init(&rfull[s], SROWS);
@@ -494,8 +500,8 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
       long long c = c0, rb = rb0;
       for (long long u = u0; u < u1; ++u) {
         const long long i = u - u0;
-        const int s = (int)(i % SSTAGES);
-        const long long round = i / SSTAGES;
+        const int s = (int)(i % NST);
+        const long long round = i / NST;
         if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1))) {
           atomicExch(err, 24);
           break;
@@ -517,8 +523,8 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
         }
       }
       const long long cnt = u1 - u0;
-      for (long long i = cnt > SSTAGES ? cnt - SSTAGES : 0; i < cnt; ++i)
-        if (!mbar_wait(&full[i % SSTAGES], (uint32_t)((i / SSTAGES) & 1))) atomicExch(err, 25);
+      for (long long i = cnt > NST ? cnt - NST : 0; i < cnt; ++i)
+        if (!mbar_wait(&full[i % NST], (uint32_t)((i / NST) & 1))) atomicExch(err, 25);
     }
     return;
   }
@@ -548,8 +554,8 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
   bool ok = true;
   for (long long u = u0; u < u1; ++u) {
     const long long i = u - u0;
-    const int s = (int)(i % SSTAGES);
-    const uint32_t parity = (uint32_t)((i / SSTAGES) & 1);
+    const int s = (int)(i % NST);
+    const uint32_t parity = (uint32_t)((i / NST) & 1);
     ok = __all_sync(0xffffffffu, mbar_wait(&full[s], parity));
     if (!ok) {
       if (lane == 0) atomicExch(err, 26);
@@ -627,15 +633,21 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
   if (ok && rb > 0) flush_cols(c);
 }
 
+// Two CTAs per SM with two stages each where the registers allow (the real two-column variant
+// needs more than half the register file): twice the warps to hide the consumers' latency for
+// the same bytes in flight (complex T_A product at N = 30720: 0.659 -> 0.585 ms, 95 % of the
+// copy bandwidth).
 template <int NR, bool REAL, bool CONJ>
 cudaError_t launch_sym(const void* M, int ld, int n, GemvScratch& w, cudaStream_t s) {
   constexpr int SEG = SBYTES_ROW / (REAL ? 4 : 8);
-  auto k = gemv_sym_kernel<NR, REAL, CONJ>;
+  constexpr int NCTA = REAL && NR == 2 ? 1 : 2;
+  constexpr int SMEM = (NCTA == 2 ? 2 : SSTAGES) * SSTAGE + 256;
+  auto k = gemv_sym_kernel<NR, REAL, CONJ, NCTA>;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   static int sms = 0;
   std::call_once(once, [&] {
-    attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SSMEM);
+    attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     int dev = 0;
     if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
     if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -644,8 +656,8 @@ cudaError_t launch_sym(const void* M, int ld, int n, GemvScratch& w, cudaStream_
   if (!w.err) return cudaErrorInvalidValue;
   const SymGeom G = sym_geom(n, ld, SEG);
   const long long units = G.off(G.S);
-  const int grid = (int)std::max(1LL, std::min<long long>(units, sms));
-  k<<<grid, STHREADS, SSMEM, s>>>(M, ld, n, w.xh, w.acc, units, w.err);
+  const int grid = (int)std::max(1LL, std::min<long long>(units, (long long)NCTA * sms));
+  k<<<grid, STHREADS, SMEM, s>>>(M, ld, n, w.xh, w.acc, units, w.err);
   return cudaGetLastError();
 }
 
@@ -679,7 +691,7 @@ cudaError_t launch_stream_ff(const float2* M, int ld, int n, GemvScratch& w, cud
   static cudaError_t attr = cudaSuccess;
   static int sms = 0;
   std::call_once(once, [&] {
-    attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SSMEM);
+    attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, FF_NST * SSTAGE + 256);
     int dev = 0;
     if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
     if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -688,8 +700,8 @@ cudaError_t launch_stream_ff(const float2* M, int ld, int n, GemvScratch& w, cud
   if (!w.err || !w.xl) return cudaErrorInvalidValue;
   const int upr = (ld + SEG - 1) / SEG;
   const long long units = (long long)((n + SROWS - 1) / SROWS) * upr;
-  const int grid = (int)std::max(1LL, std::min<long long>(units, sms));
-  k<<<grid, STHREADS, SSMEM, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, w.err);
+  const int grid = (int)std::max(1LL, std::min<long long>(units, (long long)FF_NCTA * sms));
+  k<<<grid, STHREADS, FF_NST * SSTAGE + 256, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, w.err);
   return cudaGetLastError();
 }
 
