@@ -131,6 +131,27 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """x reduced by MAX over the ranks of the default process group (x itself without one).
+
+    Every rank runs its own replica of the workload (the path has no data exchange), so the job
+    takes as long as its slowest rank.
+    """
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world_size: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world_size / (ms_max / 1e3)
+
+
 def run_step(rf, ctx, mesh, dirs, kh, pol, lat, reports, copy_back=False, tuning=None):
     """One pass of the hot path over the six wavenumbers; returns host bytes moved."""
     import torch
@@ -226,15 +247,9 @@ def bench_ours(args):
     gpu_launches = rf.launch_count() - launches0
     prof = rf.profile_read()
     rf.profile_enable(False)
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), "cuda")
     solves = args.steps * len(KA) * ws
-    value = solves / (ms / 1e3)
+    value = job_rate(args.steps * len(KA), ws, ms)
 
     # end to end through the C ABI: host mesh and plane wave in, host currents and RCS out
     e2e_lat = []
@@ -246,13 +261,7 @@ def bench_ours(args):
         h2d += a
         d2h += b
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, "cuda")
 
     if rank != 0:
         if ws > 1:
