@@ -8,11 +8,11 @@
 // together with the matching segment of x into a shared-memory ring of four stages per SM (one
 // CTA with four stages, or two CTAs with two where the registers allow twice the warps), so about
 // 180 KB per SM are in flight whatever the consumers do; consumers read the matrix and x from
-// shared memory only and release a stage through an mbarrier.  Three kernels:
+// shared memory only and release a stage through an mbarrier.  Two kernels:
 //   * gemv_sym_kernel (FP32 mode, symmetric M: T_A, V and the factors): reads only the tiles on
 //     and above the diagonal and forms both the row and the mirrored column product;
-//   * gemv_stream_kernel (FP32 mode, any M): one consumer warp per row of a stage;
-//   * gemv_stream_ff_kernel (float-float, one column of a complex64 M): the accurate products.
+//   * gemv_stream_ff_kernel (float-float, one column of a complex64 M): the accurate products,
+//     one consumer warp per row of a stage.
 // Work units are dealt to persistent CTAs in contiguous ranges of equal size; partial sums meet
 // in FP64 atomics.  Every wait is bounded and records an error code on timeout.
 #include <cuda_runtime.h>
@@ -42,7 +42,6 @@ constexpr int SXI = 2 * 64;                 // x of the stage's 8 rows (symmetri
 constexpr int SRED = 8 * 32 * 4;            // row partials of the 8 consumer warps (symmetric kernel)
 constexpr int SSTAGE = SMAT + SXMAX + SXI + SRED;  // 49 KB + 128 B
 constexpr int STHREADS = (SROWS + 1) * 32;  // consumers + producer warp
-constexpr int SSMEM = SSTAGES * SSTAGE + 256;  // + alignment slack and the mbarriers
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -55,170 +54,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
-}
-
-// REAL: M is FP32 (n x ld), else complex64; CONJ: conj(M) (complex only)
-template <int NR, bool REAL, bool CONJ>
-__global__ void __launch_bounds__(STHREADS, 1)
-gemv_stream_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __restrict__ xh,
-                   double2* __restrict__ out, long long units, int upr, int* __restrict__ err) {
-  RF_COUNT_LAUNCH();
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SSTAGES * SSTAGE);
-  uint64_t* empty = full + SSTAGES;
-  constexpr int ESZ = REAL ? 4 : 8;          // bytes per matrix element
-  constexpr int SEG = SBYTES_ROW / ESZ;      // elements per row segment
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < SSTAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], SROWS);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  const char* M = reinterpret_cast<const char*>(Mv);
-
-  if (warp == SROWS) {
-    if (lane == 0) {
-      for (long long u = u0; u < u1; ++u) {
-        const long long i = u - u0;
-        const int s = (int)(i % SSTAGES);
-        const long long round = i / SSTAGES;
-        if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1))) {
-          atomicExch(err, 21);
-          break;
-        }
-        const int rb = (int)(u / upr), cb = (int)(u % upr) * SEG;
-        const int row0 = rb * SROWS, rows = min(SROWS, n - row0);
-        const int cols = min(SEG, ld - cb);
-        const uint32_t bytes = (uint32_t)cols * ESZ, xbytes = (uint32_t)cols * 8;
-        mbar_expect_tx(&full[s], bytes * rows + xbytes * NR);
-        uint8_t* st = smem + s * SSTAGE;
-        for (int r = 0; r < rows; ++r)
-          bulk_load(st + r * SBYTES_ROW, M + ((size_t)(row0 + r) * ld + cb) * ESZ, bytes, &full[s]);
-        for (int r = 0; r < NR; ++r)
-          bulk_load(st + SMAT + r * (SXMAX / 2), xh + (size_t)r * ld + cb, xbytes, &full[s]);
-      }
-      // the CTA must not end with copies into its shared memory in flight: wait (bounded) for
-      // the last stages issued
-      const long long cnt = u1 - u0;
-      for (long long i = cnt > SSTAGES ? cnt - SSTAGES : 0; i < cnt; ++i)
-        if (!mbar_wait(&full[i % SSTAGES], (uint32_t)((i / SSTAGES) & 1))) atomicExch(err, 23);
-    }
-    return;
-  }
-
-  // consumer warp: row `warp` of every stage.  Segment sums are FP32; across segments they are
-  // added into an FP32 pair (hi, compensation) by an error-free two-sum, so the row sum keeps
-  // about twice FP32 precision without FP64 arithmetic in the loop (GB300's FP64 pipe runs at
-  // a small fraction of the FP32 rate); FP64 enters only at the per-row flush.
-  float acc[NR][2], cmp[NR][2];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = cmp[r][0] = cmp[r][1] = 0.f;
-  long long cur_rb = -1;
-  bool ok = true;
-  for (long long u = u0; u < u1 && ok; ++u) {
-    const long long i = u - u0;
-    const int s = (int)(i % SSTAGES);
-    const uint32_t parity = (uint32_t)((i / SSTAGES) & 1);
-    const int rb = (int)(u / upr), cb = (int)(u % upr) * SEG;
-    if (rb != cur_rb) {
-      if (cur_rb >= 0) {
-        const int row = (int)cur_rb * SROWS + warp;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const double re = warp_sum_d((double)acc[r][0] + (double)cmp[r][0]);
-          const double im = warp_sum_d((double)acc[r][1] + (double)cmp[r][1]);
-          acc[r][0] = acc[r][1] = cmp[r][0] = cmp[r][1] = 0.f;
-          if (lane == 0 && row < n) {
-            double* o = reinterpret_cast<double*>(out + (size_t)r * n + row);
-            atomicAdd(o, re);
-            atomicAdd(o + 1, im);
-          }
-        }
-      }
-      cur_rb = rb;
-    }
-    ok = __all_sync(0xffffffffu, mbar_wait(&full[s], parity));
-    if (!ok) {
-      if (lane == 0) atomicExch(err, 22);
-      break;
-    }
-    const int row = rb * SROWS + warp;
-    if (row < n) {
-      const float4* srow = reinterpret_cast<const float4*>(smem + s * SSTAGE + warp * SBYTES_ROW);
-      const float4* sx = reinterpret_cast<const float4*>(smem + s * SSTAGE + SMAT);
-      const int nq = min(SEG, ld - cb) * ESZ / 16;  // float4 per segment row
-      float f[NR][2];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) f[r][0] = f[r][1] = 0.f;
-#pragma unroll 4
-      for (int q = lane; q < nq; q += 32) {
-        const float4 m = srow[q];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const float4* xr = sx + r * (SXMAX / 32);
-          if (REAL) {
-            // four real entries times four complex x values
-            const float4 x0 = xr[2 * q];
-            const float4 x1 = xr[2 * q + 1];
-            float re = f[r][0], im = f[r][1];
-            re = fmaf(m.x, x0.x, re);
-            im = fmaf(m.x, x0.y, im);
-            re = fmaf(m.y, x0.z, re);
-            im = fmaf(m.y, x0.w, im);
-            re = fmaf(m.z, x1.x, re);
-            im = fmaf(m.z, x1.y, im);
-            re = fmaf(m.w, x1.z, re);
-            im = fmaf(m.w, x1.w, im);
-            f[r][0] = re;
-            f[r][1] = im;
-          } else {
-            // two complex entries (m.x + i m.y, m.z + i m.w) times two complex x values
-            const float4 x4 = xr[q];
-            const float my = CONJ ? -m.y : m.y, mw = CONJ ? -m.w : m.w;
-            float re = f[r][0], im = f[r][1];
-            re = fmaf(m.x, x4.x, re);
-            re = fmaf(-my, x4.y, re);
-            re = fmaf(m.z, x4.z, re);
-            re = fmaf(-mw, x4.w, re);
-            im = fmaf(m.x, x4.y, im);
-            im = fmaf(my, x4.x, im);
-            im = fmaf(m.z, x4.w, im);
-            im = fmaf(mw, x4.z, im);
-            f[r][0] = re;
-            f[r][1] = im;
-          }
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {  // two-sum: acc + f = t + e exactly
-          const float a = acc[r][c], b = f[r][c], t = a + b, bb = t - a;
-          cmp[r][c] += (a - (t - bb)) + (b - bb);
-          acc[r][c] = t;
-        }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
-  }
-  if (ok && cur_rb >= 0) {
-    const int row = (int)cur_rb * SROWS + warp;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const double re = warp_sum_d((double)acc[r][0] + (double)cmp[r][0]);
-      const double im = warp_sum_d((double)acc[r][1] + (double)cmp[r][1]);
-      if (lane == 0 && row < n) {
-        double* o = reinterpret_cast<double*>(out + (size_t)r * n + row);
-        atomicAdd(o, re);
-        atomicAdd(o + 1, im);
-      }
-    }
-  }
 }
 
 // ---------------------------------------------------------------- float-float, one column
@@ -661,28 +496,6 @@ cudaError_t launch_sym(const void* M, int ld, int n, GemvScratch& w, cudaStream_
   return cudaGetLastError();
 }
 
-template <int NR, bool REAL, bool CONJ>
-cudaError_t launch_stream(const void* M, int ld, int n, GemvScratch& w, cudaStream_t s) {
-  constexpr int SEG = SBYTES_ROW / (REAL ? 4 : 8);
-  auto k = gemv_stream_kernel<NR, REAL, CONJ>;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  static int sms = 0;
-  std::call_once(once, [&] {
-    attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SSMEM);
-    int dev = 0;
-    if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
-    if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  });
-  if (attr != cudaSuccess) return attr;
-  if (!w.err) return cudaErrorInvalidValue;
-  const int upr = (ld + SEG - 1) / SEG;
-  const long long units = (long long)((n + SROWS - 1) / SROWS) * upr;
-  const int grid = (int)std::max(1LL, std::min<long long>(units, sms));
-  k<<<grid, STHREADS, SSMEM, s>>>(M, ld, n, w.xh, w.acc, units, upr, w.err);
-  return cudaGetLastError();
-}
-
 template <bool CONJ>
 cudaError_t launch_stream_ff(const float2* M, int ld, int n, GemvScratch& w, cudaStream_t s) {
   constexpr int SEG = SBYTES_ROW / 8;
@@ -709,14 +522,13 @@ cudaError_t launch_stream_ff(const float2* M, int ld, int n, GemvScratch& w, cud
 
 template <int NR>
 cudaError_t gemv_stream_c64(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s) {
-  if (w.symmetric)
-    return conj ? launch_sym<NR, false, true>(M, ld, n, w, s) : launch_sym<NR, false, false>(M, ld, n, w, s);
-  return conj ? launch_stream<NR, false, true>(M, ld, n, w, s) : launch_stream<NR, false, false>(M, ld, n, w, s);
+  if (!w.symmetric) return cudaErrorInvalidValue;
+  return conj ? launch_sym<NR, false, true>(M, ld, n, w, s) : launch_sym<NR, false, false>(M, ld, n, w, s);
 }
 template <int NR>
 cudaError_t gemv_stream_r32(const float* M, int ld, int n, GemvScratch& w, cudaStream_t s) {
-  if (w.symmetric) return launch_sym<NR, true, false>(M, ld, n, w, s);
-  return launch_stream<NR, true, false>(M, ld, n, w, s);
+  if (!w.symmetric) return cudaErrorInvalidValue;
+  return launch_sym<NR, true, false>(M, ld, n, w, s);
 }
 cudaError_t gemv_stream_c64_ff(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s) {
   return conj ? launch_stream_ff<true>(M, ld, n, w, s) : launch_stream_ff<false>(M, ld, n, w, s);

@@ -351,10 +351,10 @@ cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, bool conj, GemvMod
   const int chunk = gemv_chunk(w);
   const int upr = (ld + chunk - 1) / chunk;
   const long long units = (long long)rowblocks * upr;
-  const bool stream = mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err;
-  // algorithmic bytes: the matrix (its upper triangle when the symmetric kernel reads only that)
+  const bool stream = mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err && w.symmetric;
+  // algorithmic bytes: the matrix (its upper triangle where the symmetric kernel reads only that)
   // plus the vectors
-  const double mbytes = stream && w.symmetric ? 4.0 * n * (n + 1.0) : 8.0 * n * n;
+  const double mbytes = stream ? 4.0 * n * (n + 1.0) : 8.0 * n * n;
   ProfScope prof(mode == GEMV_FF ? "gemv_c64_ff" : "gemv_c64_f32", mbytes + 32.0 * n * NR, 8.0 * n * n * NR, s);
   if (stream) return gemv_stream_c64<NR <= 1 ? 1 : 2>(M, ld, n, conj, w, s);
   if (NR == 1 && mode == GEMV_FF && w.chunk == 0 && w.ctas_per_sm == 0 && w.err) return gemv_stream_c64_ff(M, ld, n, conj, w, s);
@@ -380,8 +380,8 @@ cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n,
   const int chunk = gemv_chunk(w);
   const int upr = (ld + chunk - 1) / chunk;
   const long long units = (long long)rowblocks * upr;
-  const bool stream = mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err;
-  const double mbytes = mode == GEMV_FF ? 8.0 * n * n : (stream && w.symmetric ? 2.0 * n * (n + 1.0) : 4.0 * n * n);
+  const bool stream = mode == GEMV_F32 && NR <= 2 && w.chunk == 0 && w.ctas_per_sm == 0 && w.err && w.symmetric;
+  const double mbytes = mode == GEMV_FF ? 8.0 * n * n : (stream ? 2.0 * n * (n + 1.0) : 4.0 * n * n);
   ProfScope prof(mode == GEMV_FF ? "gemv_r32_ff" : "gemv_r32_f32", mbytes + 32.0 * n * NR, 4.0 * n * n * NR, s);
   if (stream) return gemv_stream_r32<NR <= 1 ? 1 : 2>(Mhi, ld, n, w, s);
   if (mode == GEMV_FF) {

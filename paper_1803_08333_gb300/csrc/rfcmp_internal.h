@@ -235,8 +235,9 @@ struct GemvScratch {
   int* err = nullptr;     // set when a bounded device-side wait of the streaming GEMV gives up
   bool symmetric = false; // every matrix this scratch serves is symmetric: read the upper triangle
 };
-// Streaming FP32-mode GEMV (k_gemv_stream.cu): the prepared x (w.xh) times the complex64 or FP32
-// matrix into the FP64 accumulator w.acc, rows streamed by bulk copies; NR = 1 or 2.
+// Streaming FP32-mode GEMV of a symmetric matrix (k_gemv_stream.cu; w.symmetric must be set): the
+// prepared x (w.xh) times the complex64 or FP32 matrix into the FP64 accumulator w.acc, the
+// upper triangle streamed by bulk copies; NR = 1 or 2.
 template <int NR>
 cudaError_t gemv_stream_c64(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s);
 template <int NR>
