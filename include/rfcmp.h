@@ -282,8 +282,11 @@ typedef struct {
                                tensor cores (split-BF16 GEMM), narrower ones on the FP32 GEMV;
                                1..65536, default 4 */
   int32_t gemm_bn;          /* GEMM N tile: 32, 64 or 128 columns; default by column count */
-  int32_t gemv_chunk;       /* GEMV work unit width in matrix columns: a multiple of 256 in
-                               [256, 8192]; default 1024 */
+  int32_t gemv_chunk;       /* register-pipelined GEMV work unit width in matrix columns: a multiple
+                               of 256 in [256, 8192]; default 1024.  Nonzero (like gemv_ctas_per_sm)
+                               selects that kernel also where the default is the streaming one (one
+                               or two FP32 columns of the symmetric blocks, one float-float column
+                               of T_A or V), whose shape is fixed */
   int32_t gemv_ctas_per_sm; /* persistent GEMV CTAs per SM, 1..8; default the occupancy maximum */
   int32_t far_min_blocks;   /* far-pair assembly CTAs per SM its registers are sized for: 1, 2, 3;
                                default 2 (read at rfcmp_op_create) */
