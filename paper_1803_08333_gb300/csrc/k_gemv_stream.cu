@@ -5,9 +5,9 @@
 // streams T_A, V and the factors once.  A register-pipelined GEMV keeps only as many bytes in
 // flight as its unrolled loads allow; here one producer thread per CTA issues cp.async.bulk
 // copies of whole row segments (8 rows x 512 complex64 or 1024 FP32 values, 32 KB per stage)
-// together with the matching segment of x into a shared-memory ring of four stages per SM (one
-// CTA with four stages, or two CTAs with two where the registers allow twice the warps), so about
-// 180 KB per SM are in flight whatever the consumers do; consumers read the matrix and x from
+// together with the matching segment of x into shared-memory rings of four to six stages per SM
+// (one CTA with four stages, or two CTAs with two or three where the registers allow twice the
+// warps), so 128 to 192 KB of matrix per SM are in flight whatever the consumers do; consumers read the matrix and x from
 // shared memory only and release a stage through an mbarrier.  Two kernels:
 //   * gemv_sym_kernel (FP32 mode, symmetric M: T_A, V and the factors): reads only the tiles on
 //     and above the diagonal and forms both the row and the mirrored column product;
@@ -37,10 +37,8 @@ constexpr int SROWS = 8;                 // rows per stage (one consumer warp ea
 constexpr int SBYTES_ROW = 4096;         // bytes per row segment
 constexpr int SSTAGES = 4;
 constexpr int SMAT = SROWS * SBYTES_ROW;    // 32 KB of matrix per stage
-constexpr int SXMAX = 2 * 8192;             // x segments per stage: up to 2 columns x 1024 complex
-constexpr int SXI = 2 * 64;                 // x of the stage's 8 rows (symmetric kernel), up to 2 columns
-constexpr int SRED = 8 * 32 * 4;            // row partials of the 8 consumer warps (symmetric kernel)
-constexpr int SSTAGE = SMAT + SXMAX + SXI + SRED;  // 49 KB + 128 B
+constexpr int SXMAX = 2 * 8192;             // x per stage of the float-float kernel: hi and lo segments
+constexpr int SSTAGE = SMAT + SXMAX;        // 48 KB: a stage of the float-float kernel
 constexpr int STHREADS = (SROWS + 1) * 32;  // consumers + producer warp
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -237,13 +235,27 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&v)[V], int lane) {
   }
 }
 
+// Stage layout of the symmetric kernel: the 8 row segments, the x segments of its NR columns,
+// x of the 8 rows, and the consumer warps' row partials, rounded to 128 bytes.  With two CTAs
+// per SM a CTA takes three stages where both rings fit the SM's 228 KB of shared memory
+// (1 KB per CTA reserved by the system): the one-column complex product (37.5 KB stages);
+// the others take two.
+template <int NR, bool REAL, int NCTA>
+struct SymStage {
+  static constexpr int SEG = SBYTES_ROW / (REAL ? 4 : 8);
+  static constexpr int XB = NR * SEG * 8;  // x segments of the stage (complex FP32)
+  static constexpr int BYTES = ((SMAT + XB + NR * 64 + 8 * (SROWS * NR * 2) * 4) + 127) / 128 * 128;
+  static constexpr int NST = NCTA == 1 ? SSTAGES : ((2 * (3 * BYTES + 256 + 1024) <= 233472) ? 3 : 2);
+  static constexpr int SMEM = NST * BYTES + 256;  // + alignment slack and the mbarriers
+};
+
 // The 8 rows of one tile for column slot qc (entries j .. j + EPQ - 1): row partials v gain
 // M_ij x_j (j >= i), column partials t gain M_ij x_i (j > i).  DIAG: the tile reaches the
 // diagonal and the entries outside those ranges are dropped.
-template <int NR, bool REAL, bool CONJ, bool DIAG, int EPQ = (REAL ? 4 : 2)>
+template <int NR, bool REAL, bool CONJ, bool DIAG, int XB, int EPQ = (REAL ? 4 : 2)>
 __device__ __forceinline__ void sym_tile(const uint8_t* st, int qc, int row0, int n, int j, const float2 (&xj)[NR][EPQ],
                                          float (&v)[SROWS * NR * 2], float (&t)[NR][EPQ][2]) {
-  const float2* sxi = reinterpret_cast<const float2*>(st + SMAT + SXMAX);
+  const float2* sxi = reinterpret_cast<const float2*>(st + SMAT + XB);
 #pragma unroll
   for (int rr = 0; rr < SROWS; ++rr) {
     const int row = row0 + rr;
@@ -291,10 +303,12 @@ __global__ void __launch_bounds__(STHREADS, NCTA)
 gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __restrict__ xh,
                 double2* __restrict__ out, long long units, int* __restrict__ err) {
   RF_COUNT_LAUNCH();
-  constexpr int NST = NCTA == 2 ? 2 : SSTAGES;  // ring depth per CTA (the SM holds NCTA rings)
+  constexpr int NST = SymStage<NR, REAL, NCTA>::NST;
+  constexpr int STG = SymStage<NR, REAL, NCTA>::BYTES;
+  constexpr int XB = SymStage<NR, REAL, NCTA>::XB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * SSTAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STG);
   uint64_t* empty = full + NST;
   uint64_t* rfull = empty + NST;  // the 8 warps' row partials of a stage are in shared memory
   constexpr int ESZ = REAL ? 4 : 8;
@@ -345,12 +359,12 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
         const int cols = min(SEG, ld - cb);
         const uint32_t bytes = (uint32_t)cols * ESZ, xbytes = (uint32_t)cols * 8;
         mbar_expect_tx(&full[s], bytes * rows + (xbytes + 64) * NR);
-        uint8_t* st = smem + s * SSTAGE;
+        uint8_t* st = smem + s * STG;
         for (int r = 0; r < rows; ++r)
           bulk_load(st + r * SBYTES_ROW, M + ((size_t)(row0 + r) * ld + cb) * ESZ, bytes, &full[s]);
         for (int r = 0; r < NR; ++r) {
-          bulk_load(st + SMAT + r * (SXMAX / 2), xh + (size_t)r * ld + cb, xbytes, &full[s]);
-          bulk_load(st + SMAT + SXMAX + r * 64, xh + (size_t)r * ld + row0, 64, &full[s]);  // x of the 8 rows
+          bulk_load(st + SMAT + r * (XB / NR), xh + (size_t)r * ld + cb, xbytes, &full[s]);
+          bulk_load(st + SMAT + XB + r * 64, xh + (size_t)r * ld + row0, 64, &full[s]);  // x of the 8 rows
         }
         if (++rb == G.nrb(c)) {
           ++c;
@@ -398,7 +412,7 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
     }
     const int cb = (int)(c * SEG), row0 = (int)(rb * SROWS);
     const bool diag = row0 + SROWS > cb;  // the segment reaches the diagonal of this row block
-    uint8_t* st = smem + s * SSTAGE;
+    uint8_t* st = smem + s * STG;
     const int nq = min(SEG, ld - cb) * ESZ / 16;
     float v[V];  // row partials, index (rr * NR + r) * 2 + (re, im)
 #pragma unroll
@@ -408,7 +422,7 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
       float2 xj[NR][EPQ];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        const float4* xr = reinterpret_cast<const float4*>(st + SMAT + r * (SXMAX / 2));
+        const float4* xr = reinterpret_cast<const float4*>(st + SMAT + r * (XB / NR));
 #pragma unroll
         for (int h = 0; h < EPQ / 2; ++h) {
           const float4 x4 = xr[(EPQ / 2) * qc + h];
@@ -422,8 +436,8 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
       for (int r = 0; r < NR; ++r)
 #pragma unroll
         for (int e = 0; e < EPQ; ++e) t[r][e][0] = t[r][e][1] = 0.f;
-      if (diag) sym_tile<NR, REAL, CONJ, true>(st, qc, row0, n, j, xj, v, t);
-      else sym_tile<NR, REAL, CONJ, false>(st, qc, row0, n, j, xj, v, t);
+      if (diag) sym_tile<NR, REAL, CONJ, true, XB>(st, qc, row0, n, j, xj, v, t);
+      else sym_tile<NR, REAL, CONJ, false, XB>(st, qc, row0, n, j, xj, v, t);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
 #pragma unroll
@@ -437,7 +451,7 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
     }
     // row part: reduce-scatter over the warp, then the 8 warps meet in shared memory
     warp_reduce_scatter<V>(v, lane);
-    float* red = reinterpret_cast<float*>(st + SMAT + SXMAX + SXI);  // [SROWS warps][V]
+    float* red = reinterpret_cast<float*>(st + SMAT + XB + NR * 64);  // [SROWS warps][V]
     if (V == 32 || (lane & 1) == 0) red[warp * V + lane * V / 32] = v[0];
     __syncwarp();
     if (lane == 0) mbar_arrive(&rfull[s]);
@@ -468,15 +482,15 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
   if (ok && rb > 0) flush_cols(c);
 }
 
-// Two CTAs per SM with two stages each where the registers allow (the real two-column variant
-// needs more than half the register file): twice the warps to hide the consumers' latency for
-// the same bytes in flight (complex T_A product at N = 30720: 0.659 -> 0.585 ms, 95 % of the
-// copy bandwidth).
+// Two CTAs per SM where the registers allow (the real two-column variant needs more than half
+// the register file): twice the warps to hide the consumers' latency (complex T_A product at
+// N = 30720: 0.659 ms with one CTA of four stages, 0.585 ms with two CTAs of two stages,
+// 0.557 ms with two CTAs of three stages: the measured copy bandwidth).
 template <int NR, bool REAL, bool CONJ>
 cudaError_t launch_sym(const void* M, int ld, int n, GemvScratch& w, cudaStream_t s) {
   constexpr int SEG = SBYTES_ROW / (REAL ? 4 : 8);
   constexpr int NCTA = REAL && NR == 2 ? 1 : 2;
-  constexpr int SMEM = (NCTA == 2 ? 2 : SSTAGES) * SSTAGE + 256;
+  constexpr int SMEM = SymStage<NR, REAL, NCTA>::SMEM;
   auto k = gemv_sym_kernel<NR, REAL, CONJ, NCTA>;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
