@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -84,7 +85,9 @@ class Clocks:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % device)
+        # the raw samples stay on disk: $RFCMP_BENCH_OUT if set, else the temporary directory
+        out = os.environ.get("RFCMP_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out, "clocks_bench_%d.csv" % device)
 
     def start(self):
         try:

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (stated in the spec contract of this library): matrix
+Tolerances (the accuracy contract of this library): matrix
 entries <= 1e-5 relative (Frobenius, real and imaginary parts separately),
 solution currents <= 1e-6 relative, RCS <= 1e-3 dB where sigma is within 40 dB
 of its peak.  Float-float applications of the stored complex64 operator are
