@@ -62,6 +62,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // two CTAs per SM, two stages each: twice the consumer warps to hide the two-sum chains
 constexpr int FF_NCTA = 2;
 constexpr int FF_NST = 2;
+static_assert(FF_NCTA * (FF_NST * SSTAGE + 256 + 1024) <= 233472, "the SM holds FF_NCTA float-float CTAs");
 
 __device__ __forceinline__ void ff_acc(float& hi, float& lo, float a, float bh, float bl) {
   const float p = a * bh;
@@ -247,6 +248,9 @@ struct SymStage {
   static constexpr int BYTES = ((SMAT + XB + NR * 64 + 8 * (SROWS * NR * 2) * 4) + 127) / 128 * 128;
   static constexpr int NST = NCTA == 1 ? SSTAGES : ((2 * (3 * BYTES + 256 + 1024) <= 233472) ? 3 : 2);
   static constexpr int SMEM = NST * BYTES + 256;  // + alignment slack and the mbarriers
+  static_assert(SMEM <= 232448, "dynamic shared memory of one CTA");
+  static_assert(NCTA * (SMEM + 1024) <= 233472, "the SM holds NCTA such CTAs");
+  static_assert(BYTES % 128 == 0 && (SMAT + XB) % 16 == 0, "bulk-copy destinations stay 16-byte aligned");
 };
 
 // The 8 rows of one tile for column slot qc (entries j .. j + EPQ - 1): row partials v gain
