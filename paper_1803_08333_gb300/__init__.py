@@ -406,10 +406,18 @@ class Operator:
         return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]
 
     def solve_host(self, e: np.ndarray, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 8,
-                   inner_tol: float = 1e-4, precision: str = "mixed", stream=None):
-        """Same solve with host arrays (nrhs, N) complex128; copies happen inside the C call."""
+                   inner_tol: float = 1e-4, precision: str = "mixed", stream=None, out: "np.ndarray | None" = None):
+        """Same solve with host arrays (nrhs, N) complex128; copies happen inside the C call.
+
+        `out` (optional, C-contiguous complex128 of e's shape, e.g. a view of pinned memory)
+        receives j; otherwise a new array is returned."""
         e = np.ascontiguousarray(np.atleast_2d(e), dtype=np.complex128)
-        j = np.empty_like(e)
+        if out is not None:
+            if out.shape != e.shape or out.dtype != np.complex128 or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous complex128 array of shape %s" % (e.shape,))
+            j = out
+        else:
+            j = np.empty_like(e)
         nr = e.shape[0]
         rep = (SolveReport * nr)()
         o = self._solve_opts(tol, max_iter, max_refine, inner_tol, precision)

@@ -100,6 +100,7 @@ std::mutex g_prof_mu;
 std::atomic<bool> g_prof_on{false};
 std::vector<ProfFamily> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
+uint64_t g_prof_generation = 0;  // bumped when rfcmp_profile_enable clears the families
 
 cudaEvent_t pool_event() {
   if (!g_event_pool.empty()) {
@@ -112,18 +113,28 @@ cudaEvent_t pool_event() {
   return e;
 }
 
-void prof_resolve_locked() {
-  for (auto& f : g_prof) {
-    for (auto& pr : f.pending) {
-      cudaEventSynchronize(pr.second);
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) f.ms += ms;
-      g_event_pool.push_back(pr.first);
-      g_event_pool.push_back(pr.second);
-    }
-    f.pending.clear();
+// Pending pairs hold only scopes whose end event has been recorded (the destructor pushes them),
+// so resolving never waits on an event that is not on a stream.  A failed elapsed-time query
+// (an event of a stream that was destroyed, say) drops that pair and clears the runtime's
+// last error, so it cannot surface later as the failure of an unrelated launch check.
+void prof_resolve_family_locked(ProfFamily& f) {
+  for (auto& pr : f.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(pr.second) == cudaSuccess && cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+      f.ms += ms;
+    else
+      (void)cudaGetLastError();
+    g_event_pool.push_back(pr.first);
+    g_event_pool.push_back(pr.second);
   }
+  f.pending.clear();
 }
+
+void prof_resolve_locked() {
+  for (auto& f : g_prof) prof_resolve_family_locked(f);
+}
+
+constexpr size_t PROF_MAX_PENDING = 4096;
 }  // namespace
 
 namespace rfcmp {
@@ -142,17 +153,31 @@ ProfScope::ProfScope(const char* family, double bytes, double flops, cudaStream_
   f.launches++;
   f.bytes += bytes;
   f.flops += flops;
-  cudaEvent_t a = pool_event(), b = pool_event();
-  cudaEventRecord(a, s);
-  f.pending.push_back({a, b});
+  a_ = pool_event();
+  b_ = pool_event();
+  if (!a_ || !b_ || cudaEventRecord(a_, s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (a_) g_event_pool.push_back(a_);
+    if (b_) g_event_pool.push_back(b_);
+    a_ = b_ = nullptr;
+    return;
+  }
   slot_ = idx;
-  if (f.pending.size() > 4096) prof_resolve_locked();
+  gen_ = g_prof_generation;
 }
 ProfScope::~ProfScope() {
   if (slot_ < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  if (slot_ < (int)g_prof.size() && !g_prof[slot_].pending.empty())
-    cudaEventRecord(g_prof[slot_].pending.back().second, s_);
+  // rfcmp_profile_enable may have cleared the families since the constructor ran
+  if (gen_ != g_prof_generation || slot_ >= (int)g_prof.size() || cudaEventRecord(b_, s_) != cudaSuccess) {
+    (void)cudaGetLastError();
+    g_event_pool.push_back(a_);
+    g_event_pool.push_back(b_);
+    return;
+  }
+  ProfFamily& f = g_prof[slot_];
+  f.pending.push_back({a_, b_});
+  if (f.pending.size() >= PROF_MAX_PENDING) prof_resolve_family_locked(f);
 }
 }  // namespace rfcmp
 
@@ -1146,6 +1171,7 @@ int rfcmp_profile_enable(int enable) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   prof_resolve_locked();
   g_prof.clear();
+  ++g_prof_generation;
   g_prof_on.store(enable != 0);
   return RFCMP_OK;
 }

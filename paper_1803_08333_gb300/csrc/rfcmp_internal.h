@@ -62,6 +62,8 @@ class ProfScope {
  private:
   int slot_ = -1;
   cudaStream_t s_ = nullptr;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;  // this launch's own start / end events
+  uint64_t gen_ = 0;                        // profiling generation the slot belongs to
 };
 
 // ---------------------------------------------------------------- host topology

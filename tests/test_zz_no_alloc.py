@@ -52,3 +52,28 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(op):
     with pytest.raises(rf.RfcmpError) as ei:
         op.apply_ta_noalloc(x)
     assert ei.value.status == -1
+
+
+def test_noalloc_rejects_columns_beyond_its_capacity():
+    # nrhs = 4 passes the column check, but a padded row of 34 688 entries x 4 columns exceeds the
+    # 131 072 complex entries of the scratch; the call must refuse it and leave y untouched
+    ctx = rf.Context(0)
+    m = synth.geodesic_sphere(34, seed=2)  # 23 120 cells, N = 34 680
+    big = rf.Operator(ctx, m.verts, m.tris, 1.0, scaling="k")
+    try:
+        assert big.N == 34680
+        x = torch.ones((4, big.N), dtype=torch.complex128, device="cuda")
+        y = torch.full((4, big.N), 7.0 + 0j, dtype=torch.complex128, device="cuda")
+        with pytest.raises(rf.RfcmpError) as ei:
+            big.apply_ta_noalloc(x, out=y)
+        assert ei.value.status == -1
+        assert "131072" in str(ei.value)
+        torch.cuda.synchronize()
+        assert bool((y == 7.0).all())
+        # one column fits: it matches the regular entry point
+        got = big.apply_ta_noalloc(x[:1]).cpu().numpy()
+        ref = big.apply("T_A", x[:1]).cpu().numpy()
+        assert _rel(got, ref) <= 1e-12
+    finally:
+        big.close()
+        ctx.close()
