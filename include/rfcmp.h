@@ -120,8 +120,8 @@ typedef struct {
 
 typedef struct {
   double tol;           /* stop when ||b - A i|| / ||b|| <= tol on the preconditioned system; default 1e-6 */
-  int32_t max_iter;     /* total CG iterations per right-hand side; default 2000 */
-  int32_t max_refine;   /* refinement sweeps (MIXED); default 8 */
+  int32_t max_iter;     /* total CG iterations per right-hand side, 1..1000000; default 2000 */
+  int32_t max_refine;   /* refinement sweeps (MIXED), 0..1000; default 8 */
   double inner_tol;     /* relative reduction asked of each inner CG (MIXED); default 1e-4 */
   int32_t precision;    /* rfcmp_precision; default RFCMP_PREC_MIXED */
   int32_t fail_on_nonconvergence; /* nonzero: return RFCMP_ERR_NOT_CONVERGED if any column fails */
@@ -332,6 +332,17 @@ int rfcmp_profile_read(rfcmp_profile_entry* out, int max_entries, int* n_entries
  * every kernel adds one to a device counter from its first block and thread.  Synchronises
  * the current device.  Errors: RFCMP_ERR_INVALID_ARG (out is NULL). */
 int rfcmp_launch_count(uint64_t* out);
+
+/* How rfcmp_solve runs its loop (the paper has no counterpart; the arithmetic is the same
+ * either way, so the results are identical).  Nonzero (the default, unless the environment
+ * variable RFCMP_SOLVE_GRAPHS is "0" when the first solve starts): refinement sweeps and CG
+ * iterations run as one CUDA graph per op with nested WHILE conditional nodes, whose conditions
+ * the solve's own kernels set on the device (convergence test, active-column mask, inner
+ * tolerance); the host launches it and synchronises once per solve.  The graph is captured on
+ * the op's first solve of a shape and reused while the shape, the op's buffers, its plan and the
+ * profiling state stay the same.  Zero: the same kernels launched one by one, the host reading
+ * the device's decision after every iteration.  Process-wide; returns the previous setting. */
+int rfcmp_set_solve_graphs(int enable);
 
 const char* rfcmp_strerror(int status);
 const char* rfcmp_last_error(void);

@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
     "rfcmp_gemm_bf16x3", "rfcmp_plan_default", "rfcmp_ctx_set_plan", "rfcmp_op_set_plan", "rfcmp_op_get_plan",
-    "rfcmp_op_trim", "rfcmp_launch_count",
+    "rfcmp_op_trim", "rfcmp_launch_count", "rfcmp_set_solve_graphs",
 ]
 
 
@@ -154,6 +154,7 @@ def lib():
         L.rfcmp_profile_enable.argtypes = [i32]
         L.rfcmp_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
         L.rfcmp_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.rfcmp_set_solve_graphs.argtypes = [i32]
         _LIB = L
     return _LIB
 
@@ -189,6 +190,12 @@ def profile_read() -> dict:
         e = buf[i]
         out[e.name.decode()] = {"launches": e.launches, "total_ms": e.total_ms, "bytes": e.bytes, "flops": e.flops}
     return out
+
+
+def set_solve_graphs(enable: bool) -> bool:
+    """Solve loops as one CUDA graph per op (True, the default) or launched kernel by kernel;
+    returns the previous setting.  The arithmetic, and so every result, is the same."""
+    return bool(lib().rfcmp_set_solve_graphs(1 if enable else 0))
 
 
 def launch_count() -> int:

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librfcmp.so")
 SOURCES = [
-    "k_assembly.cu", "k_linalg.cu", "k_gemv_stream.cu", "k_gemm.cu", "k_exact.cu", "k_factor.cu", "capi.cu",
+    "k_assembly.cu", "k_linalg.cu", "k_gemv_stream.cu", "k_gemm.cu", "k_exact.cu", "k_factor.cu", "k_krylov.cu",
+    "capi.cu",
     "noalloc.cu", "topology.cpp", "amg.cpp",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

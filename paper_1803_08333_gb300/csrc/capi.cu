@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -102,6 +103,41 @@ std::vector<ProfFamily> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 uint64_t g_prof_generation = 0;  // bumped when rfcmp_profile_enable clears the families
 
+// Launches captured into a CUDA graph (the solve loop) cannot carry CUDA events: a conditional
+// body holds kernel, memset and memcpy nodes only, and one capture runs many times.  A captured
+// scope is bracketed by two one-thread kernels instead, which read the device's global
+// nanosecond timer before and after the launch and add the difference, one launch and the
+// launch's algorithmic bytes and FLOPs to the family's device accumulators.
+constexpr int PROF_DEV_FAMILIES = 64;
+constexpr int PROF_DEV_SCOPES = 4096;
+struct DevProfFamily {
+  unsigned long long ns, launches;
+  double bytes, flops;
+};
+__device__ DevProfFamily g_prof_dev[PROF_DEV_FAMILIES];
+__device__ unsigned long long g_prof_t0[PROF_DEV_SCOPES];
+int g_next_scope = 0;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__global__ void prof_begin_kernel(int scope) { g_prof_t0[scope] = global_ns(); }
+__global__ void prof_end_kernel(int scope, int fam, double bytes, double flops) {
+  const unsigned long long t = global_ns();
+  DevProfFamily& f = g_prof_dev[fam];
+  atomicAdd(&f.ns, t - g_prof_t0[scope]);
+  atomicAdd(&f.launches, 1ULL);
+  atomicAdd(&f.bytes, bytes);
+  atomicAdd(&f.flops, flops);
+}
+
+void prof_dev_clear() {
+  static const DevProfFamily zero[PROF_DEV_FAMILIES] = {};
+  if (cudaMemcpyToSymbol(g_prof_dev, zero, sizeof(zero)) != cudaSuccess) (void)cudaGetLastError();
+}
+
 cudaEvent_t pool_event() {
   if (!g_event_pool.empty()) {
     cudaEvent_t e = g_event_pool.back();
@@ -137,9 +173,34 @@ void prof_resolve_locked() {
 constexpr size_t PROF_MAX_PENDING = 4096;
 }  // namespace
 
+namespace {
+std::atomic<int> g_solve_graphs{-1};  // -1: not yet read from the environment
+
+bool solve_graphs_enabled() {
+  int v = g_solve_graphs.load();
+  if (v < 0) {
+    const char* e = std::getenv("RFCMP_SOLVE_GRAPHS");
+    v = (e && e[0] == '0') ? 0 : 1;
+    g_solve_graphs.store(v);
+  }
+  return v != 0;
+}
+
+}  // namespace
+
+uint64_t prof_capture_key() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_prof_on.load() ? (g_prof_generation << 1) | 1u : 0u;
+}
+
 namespace rfcmp {
 ProfScope::ProfScope(const char* family, double bytes, double flops, cudaStream_t s) : s_(s) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   int idx = -1;
   for (size_t i = 0; i < g_prof.size(); ++i)
@@ -148,6 +209,19 @@ ProfScope::ProfScope(const char* family, double bytes, double flops, cudaStream_
     g_prof.push_back(ProfFamily());
     g_prof.back().name = family;
     idx = (int)g_prof.size() - 1;
+  }
+  if (cap == cudaStreamCaptureStatusActive) {
+    if (idx >= PROF_DEV_FAMILIES) return;
+    scope_ = g_next_scope;
+    g_next_scope = (g_next_scope + 1) % PROF_DEV_SCOPES;
+    prof_begin_kernel<<<1, 1, 0, s>>>(scope_);
+    if (cudaGetLastError() != cudaSuccess) return;
+    captured_ = true;
+    bytes_ = bytes;
+    flops_ = flops;
+    slot_ = idx;
+    gen_ = g_prof_generation;
+    return;
   }
   ProfFamily& f = g_prof[idx];
   f.launches++;
@@ -167,6 +241,11 @@ ProfScope::ProfScope(const char* family, double bytes, double flops, cudaStream_
 }
 ProfScope::~ProfScope() {
   if (slot_ < 0) return;
+  if (captured_) {
+    prof_end_kernel<<<1, 1, 0, s_>>>(scope_, slot_, bytes_, flops_);
+    (void)cudaGetLastError();
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   // rfcmp_profile_enable may have cleared the families since the constructor ran
   if (gen_ != g_prof_generation || slot_ >= (int)g_prof.size() || cudaEventRecord(b_, s_) != cudaSuccess) {
@@ -274,8 +353,31 @@ struct SolveBuffers {
   double2* dots = nullptr;  // cols
   double *rho = nullptr, *alpha = nullptr, *beta = nullptr;
   int* active = nullptr;
+  // device-resident CG state (k_krylov.cu)
+  KrylovCtl* ctl = nullptr;
+  double *bb = nullptr, *rr = nullptr, *r0 = nullptr, *res = nullptr;
+  int *conv = nullptr, *iters = nullptr, *sweeps = nullptr;
+  double2* part = nullptr;
+  unsigned int* ticket = nullptr;
   ~SolveBuffers() {
     for (void* p : owned) dev_free(p);
+  }
+};
+
+// The solve loop of one op as an executable CUDA graph (refinement sweeps and CG iterations as
+// nested WHILE nodes), with what it was captured for: a different shape, buffer set, plan or
+// profiling state means a new capture.
+struct SolveGraph {
+  cudaGraphExec_t exec = nullptr;
+  int nr = 0, mode = 0, max_sweeps = 0;
+  const void* ws = nullptr;
+  const void* sb = nullptr;
+  int ws_cols = 0, sb_cols = 0;
+  const void* lazy[8] = {};
+  rfcmp_plan plan{};
+  uint64_t prof_key = 0;
+  ~SolveGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
   }
 };
 
@@ -303,7 +405,13 @@ struct rfcmp_op {
   std::vector<void*> lazy;           // the planes and digits above, released by rfcmp_op_trim
   uint64_t lazy_bytes = 0;
   rfcmp_plan plan{};               // launch shapes (zero fields: built-in choices)
+  std::unique_ptr<SolveGraph> solve_graph;  // the captured solve loop (rebuilt when stale)
+  cudaStream_t capture[3] = {};    // streams the solve loop is captured on (never run work)
+  bool graphs_failed = false;      // a capture failed once: this op solves eagerly
   ~rfcmp_op() {
+    solve_graph.reset();
+    for (cudaStream_t c : capture)
+      if (c) cudaStreamDestroy(c);
     for (void* p : owned) dev_free(p);
     for (void* p : lazy) dev_free(p);
     if (lanczos) dev_free(lanczos);
@@ -390,6 +498,13 @@ int ensure_solve_buffers(rfcmp_op* op, int cols) {
   RF_TRY(dalloc(&sb->alpha, cols, sb->owned));
   RF_TRY(dalloc(&sb->beta, cols, sb->owned));
   RF_TRY(dalloc(&sb->active, cols, sb->owned));
+  RF_TRY(dalloc(&sb->ctl, 1, sb->owned));
+  for (double** p : {&sb->bb, &sb->rr, &sb->r0, &sb->res}) RF_TRY(dalloc(p, cols, sb->owned));
+  for (int** p : {&sb->conv, &sb->iters, &sb->sweeps}) RF_TRY(dalloc(p, cols, sb->owned));
+  RF_TRY(dalloc(&sb->part, (size_t)cols * KRYLOV_MAX_G, sb->owned));
+  RF_TRY(dalloc(&sb->ticket, cols, sb->owned));
+  RF_CUDA(cudaMemset(sb->ticket, 0, sizeof(unsigned int) * cols));
+  RF_CUDA(cudaMemset(sb->ctl, 0, sizeof(KrylovCtl)));
   op->sb = std::move(sb);
   return RFCMP_OK;
 }
@@ -1146,8 +1261,14 @@ extern "C" {
 int rfcmp_launch_count(uint64_t* out) {
   if (!out) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
   *out = launches_assembly() + launches_exact() + launches_factor() + launches_gemm() + launches_gemv_stream() +
-         launches_linalg();
+         launches_linalg() + launches_krylov();
   return RFCMP_OK;
+}
+
+int rfcmp_set_solve_graphs(int enable) {
+  const int prev = solve_graphs_enabled() ? 1 : 0;
+  g_solve_graphs.store(enable ? 1 : 0);
+  return prev;
 }
 
 const char* rfcmp_strerror(int st) {
@@ -1172,6 +1293,7 @@ int rfcmp_profile_enable(int enable) {
   prof_resolve_locked();
   g_prof.clear();
   ++g_prof_generation;
+  prof_dev_clear();
   g_prof_on.store(enable != 0);
   return RFCMP_OK;
 }
@@ -1180,14 +1302,22 @@ int rfcmp_profile_read(rfcmp_profile_entry* out, int max_entries, int* n_entries
   if (!n_entries || (max_entries > 0 && !out)) return set_error(RFCMP_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(g_prof_mu);
   prof_resolve_locked();
+  // launches captured into graphs: the device accumulators (after the device has drained)
+  static DevProfFamily dev[PROF_DEV_FAMILIES];
+  std::memset(dev, 0, sizeof(dev));
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpyFromSymbol(dev, g_prof_dev, sizeof(dev)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    std::memset(dev, 0, sizeof(dev));
+  }
   *n_entries = (int)g_prof.size();
   for (int i = 0; i < max_entries && i < (int)g_prof.size(); ++i) {
     std::memset(&out[i], 0, sizeof(out[i]));
     std::strncpy(out[i].name, g_prof[i].name.c_str(), sizeof(out[i].name) - 1);
-    out[i].launches = g_prof[i].launches;
-    out[i].total_ms = g_prof[i].ms;
-    out[i].bytes = g_prof[i].bytes;
-    out[i].flops = g_prof[i].flops;
+    const DevProfFamily d = i < PROF_DEV_FAMILIES ? dev[i] : DevProfFamily{};
+    out[i].launches = g_prof[i].launches + (int64_t)d.launches;
+    out[i].total_ms = g_prof[i].ms + 1e-6 * (double)d.ns;
+    out[i].bytes = g_prof[i].bytes + d.bytes;
+    out[i].flops = g_prof[i].flops + d.flops;
   }
   return RFCMP_OK;
 }
@@ -1652,65 +1782,203 @@ int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c12
 // ---------------------------------------------------------------- the solve
 namespace {
 
-// column norms^2 (host) of a device block
-int col_norms2(rfcmp_op* op, const double2* x, int nr, std::vector<double>& out, cudaStream_t st) {
+KrylovView krylov_view(rfcmp_op* op, int nr) {
   SolveBuffers& B = *op->sb;
-  RF_K(vec_dot(x, x, op->top.ne, nr, B.dots, st));
-  std::vector<double2> h(nr);
-  RF_CUDA(cudaMemcpyAsync(h.data(), B.dots, sizeof(double2) * nr, cudaMemcpyDeviceToHost, st));
-  RF_CUDA(cudaStreamSynchronize(st));
-  out.resize(nr);
-  for (int r = 0; r < nr; ++r) out[r] = h[r].x;
+  KrylovView K;
+  K.ctl = B.ctl;
+  K.bb = B.bb;
+  K.rr = B.rr;
+  K.rho = B.rho;
+  K.r0 = B.r0;
+  K.alpha = B.alpha;
+  K.beta = B.beta;
+  K.res = B.res;
+  K.active = B.active;
+  K.conv = B.conv;
+  K.iters = B.iters;
+  K.sweeps = B.sweeps;
+  K.part = B.part;
+  K.ticket = B.ticket;
+  K.n = op->top.ne;
+  K.nr = nr;
+  K.G = krylov_blocks_per_column(op->top.ne);
+  return K;
+}
+
+// one CG iteration of the inner solve on the active columns (Sec. 4: CG on A d = r)
+int cg_iteration(rfcmp_op* op, const KrylovView& K, int nr, GemvMode m, cudaStream_t st) {
+  SolveBuffers& B = *op->sb;
+  RF_TRY(apply_A(op, B.p, B.Ap, nr, m, st));
+  RF_K(krylov_cg_pap(K, B.p, B.Ap, st));
+  RF_K(krylov_cg_update(K, B.p, B.Ap, B.d, B.rin, st));
+  RF_K(krylov_cg_direction(K, B.rin, B.p, st));
   return RFCMP_OK;
 }
 
-// CG on A d = r for the columns in `active` (host mask); d starts at 0.
-// Stops a column when ||r_inner|| <= rel_tol * ||r||.  Counts iterations per column.
-int inner_cg(rfcmp_op* op, const double2* r, double2* d, int nr, std::vector<int>& active, double rel_tol,
-             std::vector<int>& iters, int max_iter_total, GemvMode m, cudaStream_t st) {
+// the end of a sweep: i += d, r = b - A i (float-float accurate), norms and the next decision
+int refine_step(rfcmp_op* op, const KrylovView& K, int nr, cudaStream_t st) {
   SolveBuffers& B = *op->sb;
-  const int64_t N = op->top.ne;
-  RF_CUDA(cudaMemsetAsync(d, 0, sizeof(double2) * N * nr, st));
-  RF_K(vec_copy(r, B.rin, N * nr, st));
-  RF_K(vec_copy(r, B.p, N * nr, st));
-  std::vector<double> r0;
-  RF_TRY(col_norms2(op, r, nr, r0, st));
-  std::vector<double2> hd(nr);
-  std::vector<double> rho(nr);
-  for (int c = 0; c < nr; ++c) {
-    rho[c] = r0[c];
-    if (r0[c] == 0.0) active[c] = 0;
-  }
-  RF_CUDA(cudaMemcpyAsync(B.rho, rho.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
-  RF_CUDA(cudaMemcpyAsync(B.active, active.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
-  for (;;) {
-    bool any = false;
-    for (int c = 0; c < nr; ++c)
-      if (active[c] && iters[c] < max_iter_total) any = true;
-    if (!any) break;
-    RF_TRY(apply_A(op, B.p, B.Ap, nr, m, st));
-    RF_K(vec_dot(B.p, B.Ap, N, nr, B.dots, st));
-    RF_K(cg_scalars_alpha(B.rho, B.dots, B.alpha, B.active, nr, st));
-    RF_K(vec_axpy_cols(B.alpha, false, B.p, d, N, nr, B.active, st));
-    RF_K(vec_axpy_cols(B.alpha, true, B.Ap, B.rin, N, nr, B.active, st));
-    RF_K(vec_dot(B.rin, B.rin, N, nr, B.dots, st));
-    RF_K(cg_scalars_beta(B.dots, B.rho, B.beta, B.active, nr, st));
-    RF_K(vec_xpby_cols(B.rin, B.beta, B.p, N, nr, B.active, st));
-    RF_CUDA(cudaMemcpyAsync(rho.data(), B.rho, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
-    RF_CUDA(cudaStreamSynchronize(st));
-    bool changed = false;
-    for (int c = 0; c < nr; ++c) {
-      if (!active[c]) continue;
-      iters[c]++;
-      if (std::sqrt(rho[c]) <= rel_tol * std::sqrt(r0[c]) || iters[c] >= max_iter_total || !std::isfinite(rho[c])) {
-        active[c] = 0;
-        changed = true;
-      }
+  RF_K(krylov_add(K, B.d, B.i, st));
+  RF_TRY(apply_A(op, B.i, B.tmp, nr, GEMV_FF, st));
+  RF_K(krylov_refine_residual(K, B.b, B.tmp, B.r, B.i, false, st));
+  return RFCMP_OK;
+}
+
+int read_ctl(rfcmp_op* op, KrylovCtl& h, cudaStream_t st) {
+  RF_CUDA(cudaMemcpyAsync(&h, op->sb->ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  return RFCMP_OK;
+}
+
+// Eager driver: the same kernels launched one by one, the host reading the control block after
+// every decision (used where graphs are switched off or a capture failed).
+int solve_loop_eager(rfcmp_op* op, int nr, GemvMode inner, int max_sweeps, int max_iter, cudaStream_t st) {
+  SolveBuffers& B = *op->sb;
+  KrylovView K = krylov_view(op, nr);
+  RF_K(krylov_refine_residual(K, B.b, nullptr, B.r, B.i, true, st));
+  KrylovCtl h{};
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+    RF_TRY(read_ctl(op, h, st));
+    if (!h.go) break;
+    RF_K(krylov_cg_start(K, B.r, B.d, B.rin, B.p, st));
+    for (int pass = 0; pass < max_iter; ++pass) {
+      RF_TRY(cg_iteration(op, K, nr, inner, st));
+      RF_TRY(read_ctl(op, h, st));
+      if (h.live == 0 || h.passes >= h.max_passes) break;
     }
-    if (changed)
-      RF_CUDA(cudaMemcpyAsync(B.active, active.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    RF_TRY(refine_step(op, K, nr, st));
   }
   return RFCMP_OK;
+}
+
+// Ends a capture left open by an error path.  The graph it captured into is owned elsewhere (the
+// top-level graph by the capture function, a conditional body by its node), so nothing is freed.
+struct CaptureGuard {
+  cudaStream_t s;
+  bool open = true;
+  explicit CaptureGuard(cudaStream_t st) : s(st) {}
+  ~CaptureGuard() {
+    if (!open) return;
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(s, &g);
+    (void)cudaGetLastError();
+  }
+};
+
+// Adds a WHILE node on handle h after what stream s has captured so far and returns its body.
+int add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus stat;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  RF_CUDA(cudaStreamGetCaptureInfo(s, &stat, nullptr, &g, &deps, nullptr, &ndeps));
+  if (stat != cudaStreamCaptureStatusActive) return set_error(RFCMP_ERR_CUDA, "capture not active");
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  RF_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p));
+  *body = p.conditional.phGraph_out[0];
+  RF_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return RFCMP_OK;
+}
+
+bool solve_graph_current(const rfcmp_op* op, int nr, GemvMode inner, int max_sweeps) {
+  const SolveGraph* G = op->solve_graph.get();
+  if (!G || !G->exec) return false;
+  const void* lazy[8] = {op->ta_planes.rh,   op->v_planes.rh,     op->ta_digits.d,  op->v_digits.d,
+                         op->lplus->planes.h, op->lplus->digits.d, op->gll->planes.h, op->gll->digits.d};
+  return G->nr == nr && G->mode == (int)inner && G->max_sweeps == max_sweeps && G->ws == op->ws.get() &&
+         G->sb == op->sb.get() && G->ws_cols == op->ws->cols && G->sb_cols == op->sb->cols &&
+         std::memcmp(G->lazy, lazy, sizeof(lazy)) == 0 && std::memcmp(&G->plan, &op->plan, sizeof(rfcmp_plan)) == 0 &&
+         G->prof_key == prof_capture_key();
+}
+
+// Captures the solve loop of op for nr columns into one executable graph:
+//   refine_residual(init)                       sets go
+//   WHILE go:  cg_start
+//              WHILE live: apply A (inner arithmetic), cg_pap, cg_update, cg_direction
+//              i += d, r = b - A i (accurate), refine_residual  (sets go)
+int capture_solve_graph(rfcmp_op* op, int nr, GemvMode inner, int max_sweeps) {
+  SolveBuffers& B = *op->sb;
+  for (cudaStream_t& c : op->capture)
+    if (!c) RF_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+  op->solve_graph.reset();
+  cudaGraph_t g = nullptr;
+  RF_CUDA(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() {
+      if (g) cudaGraphDestroy(g);
+    }
+  } gg{g};
+  KrylovView K = krylov_view(op, nr);
+  K.graph = 1;
+  RF_CUDA(cudaGraphConditionalHandleCreate(&K.h_outer, g, 0, 0));
+  RF_CUDA(cudaGraphConditionalHandleCreate(&K.h_inner, g, 0, 0));
+  cudaStream_t s0 = op->capture[0], s1 = op->capture[1], s2 = op->capture[2];
+  RF_CUDA(cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  CaptureGuard c0(s0);
+  RF_K(krylov_refine_residual(K, B.b, nullptr, B.r, B.i, true, s0));
+  cudaGraph_t outer = nullptr;
+  RF_TRY(add_while(s0, K.h_outer, &outer));
+  {
+    RF_CUDA(cudaStreamBeginCaptureToGraph(s1, outer, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    CaptureGuard c1(s1);
+    RF_K(krylov_cg_start(K, B.r, B.d, B.rin, B.p, s1));
+    cudaGraph_t body = nullptr;
+    RF_TRY(add_while(s1, K.h_inner, &body));
+    {
+      RF_CUDA(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      CaptureGuard c2(s2);
+      RF_TRY(cg_iteration(op, K, nr, inner, s2));
+      c2.open = false;
+      RF_CUDA(cudaStreamEndCapture(s2, &body));
+    }
+    RF_TRY(refine_step(op, K, nr, s1));
+    c1.open = false;
+    RF_CUDA(cudaStreamEndCapture(s1, &outer));
+  }
+  c0.open = false;
+  RF_CUDA(cudaStreamEndCapture(s0, &g));
+  auto G = std::make_unique<SolveGraph>();
+  RF_CUDA(cudaGraphInstantiate(&G->exec, g, 0));
+  G->nr = nr;
+  G->mode = (int)inner;
+  G->max_sweeps = max_sweeps;
+  G->ws = op->ws.get();
+  G->sb = op->sb.get();
+  G->ws_cols = op->ws->cols;
+  G->sb_cols = op->sb->cols;
+  const void* lazy[8] = {op->ta_planes.rh,   op->v_planes.rh,     op->ta_digits.d,  op->v_digits.d,
+                         op->lplus->planes.h, op->lplus->digits.d, op->gll->planes.h, op->gll->digits.d};
+  std::memcpy(G->lazy, lazy, sizeof(lazy));
+  G->plan = op->plan;
+  G->prof_key = prof_capture_key();
+  op->solve_graph = std::move(G);
+  return RFCMP_OK;
+}
+
+// The refinement loop (Sec. 4 CG inside FP64-accurate residual sweeps), device-resident: one
+// graph launch where graphs are available, else the eager driver.
+int solve_loop(rfcmp_op* op, int nr, GemvMode inner, int max_sweeps, int max_iter, cudaStream_t st) {
+  if (solve_graphs_enabled() && !op->graphs_failed) {
+    if (!solve_graph_current(op, nr, inner, max_sweeps)) {
+      const int rc = capture_solve_graph(op, nr, inner, max_sweeps);
+      if (rc != RFCMP_OK) {
+        op->solve_graph.reset();
+        op->graphs_failed = true;
+        (void)cudaGetLastError();
+      }
+    }
+    if (op->solve_graph) {
+      RF_CUDA(cudaGraphLaunch(op->solve_graph->exec, st));
+      return RFCMP_OK;
+    }
+  }
+  return solve_loop_eager(op, nr, inner, max_sweeps, max_iter, st);
 }
 
 int solve_impl(rfcmp_op* op, const double2* e, double2* j, int nr, const rfcmp_solve_opts& o,
@@ -1718,78 +1986,33 @@ int solve_impl(rfcmp_op* op, const double2* e, double2* j, int nr, const rfcmp_s
   RF_TRY(ensure_workspace(op, nr));
   RF_TRY(ensure_solve_buffers(op, nr));
   SolveBuffers& B = *op->sb;
-  const int64_t N = op->top.ne;
-  // b = -P_o^H T^H P_m e (float-float accurate)
-  RF_TRY(apply_rhs(op, e, B.b, nr, GEMV_FF, st));
-  std::vector<double> bb, rr;
-  RF_TRY(col_norms2(op, B.b, nr, bb, st));
-  RF_CUDA(cudaMemsetAsync(B.i, 0, sizeof(double2) * N * nr, st));
-  RF_K(vec_copy(B.b, B.r, N * nr, st));
-  std::vector<int> iters(nr, 0), sweeps(nr, 0), conv(nr, 0);
-  std::vector<double> res(nr, 1.0);
   const bool mixed = o.precision == RFCMP_PREC_MIXED;
   const GemvMode inner_mode = mixed ? GEMV_F32 : GEMV_FF;
   const int max_sweeps = mixed ? o.max_refine : 1;
-  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-    if (sweep > 0) {
-      // r = b - A i, float-float accurate
-      RF_TRY(apply_A(op, B.i, B.tmp, nr, GEMV_FF, st));
-      RF_K(vec_copy(B.b, B.r, N * nr, st));
-      std::vector<double> ones(nr, 1.0);
-      RF_CUDA(cudaMemcpyAsync(B.alpha, ones.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
-      RF_K(vec_axpy_cols(B.alpha, true, B.tmp, B.r, N, nr, nullptr, st));
-      for (int c = 0; c < nr; ++c) sweeps[c]++;
-    }
-    RF_TRY(col_norms2(op, B.r, nr, rr, st));
-    std::vector<int> active(nr, 0);
-    bool any = false;
-    for (int c = 0; c < nr; ++c) {
-      res[c] = bb[c] > 0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
-      conv[c] = res[c] <= o.tol;
-      active[c] = !conv[c] && iters[c] < o.max_iter;
-      any |= active[c] != 0;
-    }
-    if (!any || sweep == max_sweeps) break;
-    // inner tolerance: mixed asks inner_tol per sweep (never below what reaches tol); ff solves to tol
-    std::vector<double> dummy;
-    double rel = mixed ? o.inner_tol : o.tol * 0.5;
-    if (mixed) {
-      double worst = 0.0;
-      for (int c = 0; c < nr; ++c)
-        if (active[c]) worst = std::max(worst, res[c]);
-      rel = std::max(o.inner_tol, 0.5 * o.tol / std::max(worst, 1e-300));
-      rel = std::min(rel, 0.5);
-    }
-    RF_TRY(inner_cg(op, B.r, B.d, nr, active, rel, iters, o.max_iter, inner_mode, st));
-    // i += d
-    std::vector<double> ones(nr, 1.0);
-    RF_CUDA(cudaMemcpyAsync(B.alpha, ones.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
-    RF_K(vec_axpy_cols(B.alpha, false, B.d, B.i, N, nr, nullptr, st));
-    if (!mixed) {
-      // FF: one accurate residual to report
-      RF_TRY(apply_A(op, B.i, B.tmp, nr, GEMV_FF, st));
-      RF_K(vec_copy(B.b, B.r, N * nr, st));
-      RF_K(vec_axpy_cols(B.alpha, true, B.tmp, B.r, N, nr, nullptr, st));
-      RF_TRY(col_norms2(op, B.r, nr, rr, st));
-      for (int c = 0; c < nr; ++c) {
-        res[c] = bb[c] > 0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
-        conv[c] = res[c] <= o.tol;
-        sweeps[c] = 1;
-      }
-      break;
-    }
-  }
+  // operands built on first use must exist before the loop is captured
+  if (inner_mode == GEMV_F32 && nr >= plan_mrhs(op)) RF_TRY(ensure_planes(op, st));
+  if (nr >= plan_exact(op)) RF_TRY(ensure_digits(op, st));
+  // b = -P_o^H T^H P_m e (float-float accurate)
+  RF_TRY(apply_rhs(op, e, B.b, nr, GEMV_FF, st));
+  const KrylovView K = krylov_view(op, nr);
+  RF_K(krylov_params(K, o.tol, o.inner_tol, o.max_iter, max_sweeps, mixed, st));
+  RF_TRY(solve_loop(op, nr, inner_mode, max_sweeps, o.max_iter, st));
   // j = P_o i
   RF_TRY(apply_Po(op, B.i, j, nr, false, GEMV_FF, st));
+  // the per-column report and the wait-error flag, read once the stream has drained
+  std::vector<int> iters(nr), sweeps(nr), conv(nr);
+  std::vector<double> res(nr);
+  int h_err = 0;
+  RF_CUDA(cudaMemcpyAsync(iters.data(), B.iters, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(sweeps.data(), B.sweeps, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(conv.data(), B.conv, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(res.data(), B.res, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+  if (op->ws->ms.err) RF_CUDA(cudaMemcpyAsync(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   RF_CUDA(cudaStreamSynchronize(st));
-  if (op->ws->ms.err) {
-    int h_err = 0;
-    RF_CUDA(cudaMemcpy(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h_err) {
-      RF_CUDA(cudaMemset(op->ws->ms.err, 0, sizeof(int)));
-      return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up (code " +
-                                                     std::to_string(h_err) + ")");
-    }
+  if (h_err) {
+    RF_CUDA(cudaMemset(op->ws->ms.err, 0, sizeof(int)));
+    return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up (code " +
+                                                   std::to_string(h_err) + ")");
   }
   bool all = true;
   for (int c = 0; c < nr; ++c) {
@@ -1811,7 +2034,8 @@ int check_solve_opts(const rfcmp_solve_opts* in, rfcmp_solve_opts& o) {
   if (in) o = *in;
   for (int i = 0; i < 8; ++i)
     if (o.reserved[i] != 0) return set_error(RFCMP_ERR_INVALID_ARG, "opts.reserved must be zero");
-  if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_refine < 0 || !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 ||
+  if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_iter > 1000000 || o.max_refine < 0 || o.max_refine > 1000 ||
+      !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 ||
       (o.precision != RFCMP_PREC_MIXED && o.precision != RFCMP_PREC_FF))
     return set_error(RFCMP_ERR_INVALID_ARG, "invalid solve options");
   return RFCMP_OK;

@@ -38,6 +38,7 @@ unsigned long long launches_factor();
 unsigned long long launches_gemm();
 unsigned long long launches_gemv_stream();
 unsigned long long launches_linalg();
+unsigned long long launches_krylov();
 
 // ---------------------------------------------------------------- op accessors
 // Read-only view of an operator's T_A for translation units outside capi.cu.
@@ -64,6 +65,10 @@ class ProfScope {
   cudaStream_t s_ = nullptr;
   cudaEvent_t a_ = nullptr, b_ = nullptr;  // this launch's own start / end events
   uint64_t gen_ = 0;                        // profiling generation the slot belongs to
+  // launches captured into a graph: device timestamps instead of events
+  bool captured_ = false;
+  int scope_ = 0;
+  double bytes_ = 0.0, flops_ = 0.0;
 };
 
 // ---------------------------------------------------------------- host topology
@@ -314,6 +319,47 @@ cudaError_t cg_scalars_alpha(const double* rr, const double2* pAp, double* alpha
                              cudaStream_t s);
 cudaError_t cg_scalars_beta(const double2* rr_new2, double* rr, double* beta, const int* active, int nrhs,
                             cudaStream_t s);
+
+// ---------------------------------------------------------------- device-resident CG (k_krylov.cu)
+// Control block of one solve (device).  Written by the solve's kernels; the host reads it only
+// in the eager (non-graph) driver and never in the middle of a captured solve.
+struct KrylovCtl {
+  double tol, inner_tol, tol2;  // outer tolerance, inner reduction asked per sweep, (inner rel tol)^2
+  int max_iter, max_sweeps, mixed;
+  int sweep;                    // refinement sweeps done
+  int passes, max_passes;       // inner iterations of this sweep and their bound
+  int live;                     // active columns after the last decision
+  int go;                       // 1 while another sweep is due
+  unsigned int gticket;         // columns finished in the current launch
+};
+constexpr int KRYLOV_MAX_G = 32;  // blocks per column of the column kernels
+// Device pointers of one solve's per-column state (passed by value to the kernels).  With graph
+// set, the kernels set the WHILE conditions h_outer (refinement sweeps) and h_inner (CG iterations).
+struct KrylovView {
+  KrylovCtl* ctl = nullptr;
+  double *bb = nullptr, *rr = nullptr, *rho = nullptr, *r0 = nullptr, *alpha = nullptr, *beta = nullptr,
+         *res = nullptr;
+  int *active = nullptr, *conv = nullptr, *iters = nullptr, *sweeps = nullptr;
+  double2* part = nullptr;       // nr x G partial sums
+  unsigned int* ticket = nullptr;  // nr per-column tickets
+  int64_t n = 0;                 // rows (edges)
+  int nr = 0, G = 1;
+  int graph = 0;
+  cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
+};
+int krylov_blocks_per_column(int64_t n);
+cudaError_t krylov_params(const KrylovView& K, double tol, double inner_tol, int max_iter, int max_sweeps, bool mixed,
+                          cudaStream_t s);
+// r = b - t and the sweep decision (init: r = b, i = 0, bb = ||b||^2, no t)
+cudaError_t krylov_refine_residual(const KrylovView& K, const double2* b, const double2* t, double2* r, double2* i,
+                                   bool init, cudaStream_t s);
+cudaError_t krylov_cg_start(const KrylovView& K, const double2* r, double2* d, double2* rin, double2* p,
+                            cudaStream_t s);
+cudaError_t krylov_cg_pap(const KrylovView& K, const double2* p, const double2* Ap, cudaStream_t s);
+cudaError_t krylov_cg_update(const KrylovView& K, const double2* p, const double2* Ap, double2* d, double2* rin,
+                             cudaStream_t s);
+cudaError_t krylov_cg_direction(const KrylovView& K, const double2* rin, double2* p, cudaStream_t s);
+cudaError_t krylov_add(const KrylovView& K, const double2* d, double2* i, cudaStream_t s);
 
 // Smoothed-aggregation multigrid hierarchy (host side, amg.cpp).
 struct AmgLevelHost {
