@@ -288,8 +288,8 @@ typedef struct {
                                or two FP32 columns of the symmetric blocks, one float-float column
                                of T_A or V), whose shape is fixed */
   int32_t gemv_ctas_per_sm; /* persistent GEMV CTAs per SM, 1..8; default the occupancy maximum */
-  int32_t far_min_blocks;   /* far-pair assembly CTAs per SM its registers are sized for: 1, 2, 3;
-                               default 2 (read at rfcmp_op_create) */
+  int32_t far_min_blocks;   /* far-pair assembly CTAs per SM its registers are sized for: 1 to 4;
+                               default 3 (read at rfcmp_op_create) */
   int32_t exact_min;        /* float-float accurate products of at least this many columns run as
                                exact-digit tensor-core products (each value as 6 signed 8-bit digits
                                under a power-of-two row scale, integer level sums exact in the FP32

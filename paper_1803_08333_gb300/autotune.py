@@ -32,7 +32,7 @@ TUNING_DIR = os.path.join(HERE, "tuning")
 GEMV_CHUNKS = (256, 512, 1024, 2048, 4096)
 GEMV_CTAS = (0, 1, 2, 4)
 GEMM_BNS = (32, 64, 128)
-FAR_MIN_BLOCKS = (1, 2, 3)
+FAR_MIN_BLOCKS = (1, 2, 3, 4)
 # columns per call measured by default (the inner CG of a solve applies A to all active columns)
 NRHS_GRID = (1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 128, 256, 512)
 GEMV_ONLY = 65536  # mrhs_min / exact_min that keeps every product on the GEMV
@@ -103,10 +103,15 @@ class Table:
         return t if t.device == name else None
 
 
-def coordinate_descent(measure, knobs: "list[tuple[str, tuple]]", start: "dict | None" = None):
+MIN_GAIN = 0.01  # a knob moves off its current value only for a gain above timing noise
+
+
+def coordinate_descent(measure, knobs: "list[tuple[str, tuple]]", start: "dict | None" = None,
+                       min_gain: float = MIN_GAIN):
     """Minimise measure(plan) over one knob at a time, in the given order.
 
-    measure(plan dict) -> milliseconds (inf for an invalid candidate).  Returns
+    measure(plan dict) -> milliseconds (inf for an invalid candidate).  A candidate replaces the
+    current plan only when it is faster by more than the fraction min_gain.  Returns
     (best plan, its ms, {"knob=value": ms} of every candidate tried).
     """
     plan = dict(start or {})
@@ -120,7 +125,7 @@ def coordinate_descent(measure, knobs: "list[tuple[str, tuple]]", start: "dict |
             cand[name] = v
             t = measure(cand)
             tried["%s=%d" % (name, v)] = t
-            if t < best:
+            if t < best * (1.0 - min_gain):
                 best, plan = t, cand
     return plan, best, tried
 
@@ -174,6 +179,11 @@ def tune_operator(op, nrhs_list=NRHS_GRID, precision: str = "mixed", reps: int =
         plan, ms, tried = coordinate_descent(measure, knobs)
         if precision == "mixed" and plan.get("mrhs_min", 0) == GEMV_ONLY:
             plan.pop("gemm_bn", None)
+        if plan:
+            # the winner against the built-in plan once more, back to back: it must stay ahead
+            ms, default = measure(plan), measure({})
+            if ms >= default:
+                plan, ms = {}, default
         out.append(Entry(op.N, nr, precision, plan, ms, default, tried))
         del x, y
     op.set_plan(None)

@@ -1691,8 +1691,8 @@ int check_plan(const rfcmp_plan& p) {
     return set_error(RFCMP_ERR_INVALID_ARG, "plan.gemv_chunk must be a multiple of 256 in [256, 8192]");
   if (p.gemv_ctas_per_sm < 0 || p.gemv_ctas_per_sm > 8)
     return set_error(RFCMP_ERR_INVALID_ARG, "plan.gemv_ctas_per_sm out of range");
-  if (p.far_min_blocks < 0 || p.far_min_blocks > 3)
-    return set_error(RFCMP_ERR_INVALID_ARG, "plan.far_min_blocks must be 0..3");
+  if (p.far_min_blocks < 0 || p.far_min_blocks > 4)
+    return set_error(RFCMP_ERR_INVALID_ARG, "plan.far_min_blocks must be 0..4");
   return RFCMP_OK;
 }
 }  // namespace

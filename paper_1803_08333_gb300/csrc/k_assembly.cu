@@ -79,7 +79,6 @@ __device__ __forceinline__ void atomic_add_c64(float2* p, float re, float im) {
 // shared-memory image of one tile of cells
 struct TileCells {
   float rho[TILE][21];
-  float wq4[TILE][7];   // weight x area / (4 pi)
   float wq[TILE][7];    // weight x area
   float cen_hi[TILE][3];
   float cen_lo[TILE][3];
@@ -91,36 +90,54 @@ struct TileCells {
   float sign[TILE][3];
 };
 
-__device__ void load_tile(TileCells& T, const DeviceGeometry g, int base) {
-  for (int q = threadIdx.x; q < TILE; q += blockDim.x) {
-    int c = base + q;
-    bool ok = c < g.nc;
-    int cc = ok ? c : 0;
-    float rq2 = 0.f;
-    for (int e = 0; e < 21; ++e) {
-      const float v = g.rho[21 * cc + e];
-      T.rho[q][e] = v;
-      if (e % 3 == 2) {
-        const float a = g.rho[21 * cc + e - 2], b = g.rho[21 * cc + e - 1];
-        rq2 = fmaxf(rq2, a * a + b * b + v * v);
-      }
+// Source-side quadrature data of the t tile as the evaluation loop reads it: per cell and point j
+// (-2 rho'_j, |rho'_j|^2) in one 16-byte word, and the weight x area / (4 pi).  A warp reads eight
+// cells at once; row strides of 28 and 7 words put them on distinct banks.
+struct SourceTile {
+  float4 qn[TILE][7];
+  float w[TILE][7];
+};
+
+// Both tiles of a block and the source data, loaded by all threads: first coalesced copies of the
+// per-cell arrays (cells past the end read cell 0 and get vertex ids that match nothing), then the
+// derived quantities.  Ends with the block synchronised.
+__device__ void load_tiles(TileCells& S, TileCells& T, SourceTile& Q, const DeviceGeometry& g, int bs, int bt) {
+  const int nt = blockDim.x;
+  for (int side = 0; side < 2; ++side) {
+    TileCells& X = side ? T : S;
+    const int base = side ? bt : bs;
+    auto cell = [&](int q) { return base + q < g.nc ? base + q : 0; };
+    for (int it = threadIdx.x; it < TILE * 21; it += nt) X.rho[it / 21][it % 21] = g.rho[21 * cell(it / 21) + it % 21];
+    for (int it = threadIdx.x; it < TILE * 9; it += nt) X.aloc[it / 9][it % 9] = g.aloc[9 * cell(it / 9) + it % 9];
+    for (int it = threadIdx.x; it < TILE * 7; it += nt) X.wq[it / 7][it % 7] = g.wq[7 * cell(it / 7) + it % 7];
+    for (int it = threadIdx.x; it < TILE * 3; it += nt) {
+      const int q = it / 3, e = it % 3, c = cell(q);
+      X.cen_hi[q][e] = g.cen_hi[3 * c + e];
+      X.cen_lo[q][e] = g.cen_lo[3 * c + e];
+      X.vid[q][e] = base + q < g.nc ? g.tris[3 * c + e] : -1 - q;
+      X.edge[q][e] = g.cell_edges[3 * c + e];
+      X.sign[q][e] = (float)g.cell_sign[3 * c + e];
     }
-    T.rq[q] = sqrtf(rq2) * 1.0001f;  // rounding margin
-    for (int e = 0; e < 7; ++e) {
-      float w = g.wq[7 * cc + e];
-      T.wq[q][e] = w;
-      T.wq4[q][e] = w * INV_4PI_F;
-    }
-    for (int e = 0; e < 3; ++e) {
-      T.cen_hi[q][e] = g.cen_hi[3 * cc + e];
-      T.cen_lo[q][e] = g.cen_lo[3 * cc + e];
-      T.vid[q][e] = ok ? g.tris[3 * cc + e] : -1 - q;
-      T.edge[q][e] = g.cell_edges[3 * cc + e];
-      T.sign[q][e] = (float)g.cell_sign[3 * cc + e];
-    }
-    for (int e = 0; e < 9; ++e) T.aloc[q][e] = g.aloc[9 * cc + e];
-    T.inv_area[q] = g.inv_area[cc];
+    for (int q = threadIdx.x; q < TILE; q += nt) X.inv_area[q] = g.inv_area[cell(q)];
   }
+  __syncthreads();
+  for (int it = threadIdx.x; it < 2 * TILE; it += nt) {
+    TileCells& X = it < TILE ? S : T;
+    const int q = it % TILE;
+    float rq2 = 0.f;
+    for (int j = 0; j < 7; ++j) {
+      const float a = X.rho[q][3 * j], b = X.rho[q][3 * j + 1], c = X.rho[q][3 * j + 2];
+      rq2 = fmaxf(rq2, fmaf(a, a, fmaf(b, b, c * c)));
+    }
+    X.rq[q] = sqrtf(rq2) * 1.0001f;  // rounding margin
+  }
+  for (int it = threadIdx.x; it < TILE * 7; it += nt) {
+    const int q = it / 7, j = it % 7;
+    const float x = T.rho[q][3 * j], y = T.rho[q][3 * j + 1], z = T.rho[q][3 * j + 2];
+    Q.qn[q][j] = make_float4(-2.f * x, -2.f * y, -2.f * z, fmaf(x, x, fmaf(y, y, z * z)));
+    Q.w[q][j] = T.wq[q][j] * INV_4PI_F;
+  }
+  __syncthreads();
 }
 
 // the four moments of a far pair (Sec. 2; I0, Ir, Irp, Irr with G = e^{ik(R - phase0/k)} / (4 pi R))
@@ -147,62 +164,122 @@ struct FarMoments {
   }
 };
 
-// 7 x 7 product rule over the pair; SHIFTED > 0: the phase of each evaluation is k R - kref with
-// |k R - kref| <= pi/4 (SHIFTED 1) or <= 1/20 (SHIFTED 2), no range reduction; 0: k R
-template <int SHIFTED>
-__device__ __forceinline__ void far_moments(const float (&rs)[21], const float (&ws)[7], const float (&rt)[21],
-                                            const float (&wt)[7], const float (&d)[3], float k, float kref,
-                                            FarMoments& M) {
-#pragma unroll
+// 7 x 7 product rule over the pair (s outer, t source).  For outer point i, D = c_s + rho_i - c_t
+// and R^2 = |D|^2 + |rho'_j|^2 + D.(-2 rho'_j): four operations per evaluation for R^2, the
+// source data read from shared memory where they are used.  SHIFTED > 0: the phase of each
+// evaluation is k R - k Rc with |k R - k Rc| <= pi/4 (SHIFTED 1, series to r^9 / r^8) or <= 1/20
+// (SHIFTED 2: sin to r^3, cos to r^2, truncation below 3e-7), no range reduction; 0: sin and cos
+// of k R with the reduction.  The rho' moments come out of the loop against -2 rho' and are
+// scaled back at the end.
+// 7 x 7 product rule over the pair (s outer, t source).  For outer point i, D = c_s + rho_i - c_t
+// and R^2 = |D|^2 + |rho'_j|^2 + D.(-2 rho'_j): four operations per evaluation for R^2, the
+// source data read from shared memory where they are used.  SHIFTED > 0: the phase of each
+// evaluation is k R - k Rc with |k R - k Rc| <= pi/4 (SHIFTED 1, series to r^9 / r^8) or <= 1/20
+// (SHIFTED 2: sin to r^3, cos to r^2, truncation below 3e-7), no range reduction; 0: sin and cos
+// of k R with the reduction.  The rho' moments come out of the loop against -2 rho' and are
+// scaled back at the end.
+template <int SHIFTED, int UNROLL>
+__device__ __forceinline__ void far_moments(const TileCells& S, int sl, const SourceTile& Q, int tl, const float (&d)[3],
+                                            float k, float kref, FarMoments& M) {
+#pragma unroll 1
   for (int i = 0; i < 7; ++i) {
-    const float dx = d[0] + rs[3 * i], dy = d[1] + rs[3 * i + 1], dz = d[2] + rs[3 * i + 2];
+    const float rsx = S.rho[sl][3 * i], rsy = S.rho[sl][3 * i + 1], rsz = S.rho[sl][3 * i + 2], wsi = S.wq[sl][i];
+    const float Dx = d[0] + rsx, Dy = d[1] + rsy, Dz = d[2] + rsz;
+    const float A = fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz));
     float s0r = 0.f, s0i = 0.f;
     float s1r[3] = {0.f, 0.f, 0.f}, s1i[3] = {0.f, 0.f, 0.f};
-#pragma unroll
+#pragma unroll UNROLL
     for (int j = 0; j < 7; ++j) {
-      const float ex = dx - rt[3 * j], ey = dy - rt[3 * j + 1], ez = dz - rt[3 * j + 2];
-      const float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      const float4 q = Q.qn[tl][j];
+      const float r2 = fmaf(Dx, q.x, fmaf(Dy, q.y, fmaf(Dz, q.z, A + q.w)));
       const float rinv = rsqrtf(r2);
       const float R = r2 * rinv;
       float sn, cs;
-      if (SHIFTED == 2) sincos_twentieth(fmaf(k, R, -kref), &sn, &cs);
-      else if (SHIFTED == 1) sincos_quarter(fmaf(k, R, -kref), &sn, &cs);
-      else sincos_far(k * R, &sn, &cs);
-      const float gw = wt[j] * rinv;
+      if (SHIFTED == 2) {
+        const float x = fmaf(k, R, -kref), xx = x * x;
+        cs = fmaf(xx, -0.5f, 1.f);
+        sn = fmaf(x * xx, -1.0f / 6.0f, x);
+      } else if (SHIFTED == 1) {
+        sincos_quarter(fmaf(k, R, -kref), &sn, &cs);
+      } else {
+        sincos_far(k * R, &sn, &cs);
+      }
+      const float gw = Q.w[tl][j] * rinv;
       const float gr = gw * cs, gi = gw * sn;
       s0r += gr;
       s0i += gi;
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        s1r[e] = fmaf(gr, rt[3 * j + e], s1r[e]);
-        s1i[e] = fmaf(gi, rt[3 * j + e], s1i[e]);
-      }
+      s1r[0] = fmaf(gr, q.x, s1r[0]);
+      s1r[1] = fmaf(gr, q.y, s1r[1]);
+      s1r[2] = fmaf(gr, q.z, s1r[2]);
+      s1i[0] = fmaf(gi, q.x, s1i[0]);
+      s1i[1] = fmaf(gi, q.y, s1i[1]);
+      s1i[2] = fmaf(gi, q.z, s1i[2]);
     }
-    const float w = ws[i];
-    M.I0r = fmaf(w, s0r, M.I0r);
-    M.I0i = fmaf(w, s0i, M.I0i);
+    M.I0r = fmaf(wsi, s0r, M.I0r);
+    M.I0i = fmaf(wsi, s0i, M.I0i);
+    const float rsi[3] = {rsx, rsy, rsz};
     float dr = 0.f, di = 0.f;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      const float wr = w * rs[3 * i + e];
+      const float wr = wsi * rsi[e];
       M.Ir_r[e] = fmaf(wr, s0r, M.Ir_r[e]);
       M.Ir_i[e] = fmaf(wr, s0i, M.Ir_i[e]);
-      M.Ip_r[e] = fmaf(w, s1r[e], M.Ip_r[e]);
-      M.Ip_i[e] = fmaf(w, s1i[e], M.Ip_i[e]);
+      M.Ip_r[e] = fmaf(wsi, s1r[e], M.Ip_r[e]);
+      M.Ip_i[e] = fmaf(wsi, s1i[e], M.Ip_i[e]);
       dr = fmaf(wr, s1r[e], dr);
       di = fmaf(wr, s1i[e], di);
     }
     M.Irr_r += dr;
     M.Irr_i += di;
   }
+  M.Irr_r *= -0.5f;
+  M.Irr_i *= -0.5f;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    M.Ip_r[e] *= -0.5f;
+    M.Ip_i[e] *= -0.5f;
+  }
 }
 
-// MINB: resident CTAs per SM that the register allocation is sized for (the plan's choice)
+// V and the T_A contributions of one far pair (s outer cell sl of S, t cell tl of Tt)
+__device__ __forceinline__ void far_store(const TileCells& S, const TileCells& Tt, int sl, int tl, int s, int t,
+                                          const FarMoments& Mo, size_t ldN, size_t ldC, float2* __restrict__ TA,
+                                          float2* __restrict__ V) {
+  const float inv_aa = S.inv_area[sl] * Tt.inv_area[tl];
+  V[(size_t)s * ldC + t] = make_float2(Mo.I0r * inv_aa, Mo.I0i * inv_aa);
+  V[(size_t)t * ldC + s] = make_float2(Mo.I0r * inv_aa, Mo.I0i * inv_aa);
+  const float quarter = 0.25f * inv_aa;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float ax = S.aloc[sl][3 * a], ay = S.aloc[sl][3 * a + 1], az = S.aloc[sl][3 * a + 2];
+    // Irr - a.Irp (shared by the three j)
+    const float pa_r = Mo.Irr_r - (ax * Mo.Ip_r[0] + ay * Mo.Ip_r[1] + az * Mo.Ip_r[2]);
+    const float pa_i = Mo.Irr_i - (ax * Mo.Ip_i[0] + ay * Mo.Ip_i[1] + az * Mo.Ip_i[2]);
+    const int m = S.edge[sl][a];
+    const float sa = S.sign[sl][a] * quarter;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float bx = Tt.aloc[tl][3 * b], by = Tt.aloc[tl][3 * b + 1], bz = Tt.aloc[tl][3 * b + 2];
+      const float ab = ax * bx + ay * by + az * bz;
+      const float vr = pa_r - (bx * Mo.Ir_r[0] + by * Mo.Ir_r[1] + bz * Mo.Ir_r[2]) + ab * Mo.I0r;
+      const float vi = pa_i - (bx * Mo.Ir_i[0] + by * Mo.Ir_i[1] + bz * Mo.Ir_i[2]) + ab * Mo.I0i;
+      const float f = sa * Tt.sign[tl][b];
+      const int n = Tt.edge[tl][b];
+      // T_A is complex symmetric: only the upper triangle is accumulated (m != n on far pairs),
+      // the lower one is mirrored afterwards so that both are bit-identical
+      atomic_add_c64(&TA[(size_t)min(m, n) * ldN + max(m, n)], f * vr, f * vi);
+    }
+  }
+}
+
+// MINB: resident CTAs per SM that the register allocation is sized for (the plan's choice).
+// Thread (sl, l) of a 32 x 32 tile pair takes s-cell sl against t-cells l, l + 8, l + 16, l + 24.
 template <int MINB>
 __global__ void __launch_bounds__(FAR_THREADS, MINB)
 far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float2* __restrict__ V, int nb) {
   RF_COUNT_LAUNCH();
   __shared__ TileCells S, Tt;
+  __shared__ SourceTile Q;
   // linear tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
   long long tix = blockIdx.x;
   int bi = 0;
@@ -215,20 +292,15 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
     tix = rem;
   }
   const int bj = bi + (int)tix;
-  load_tile(S, g, bi * TILE);
-  load_tile(Tt, g, bj * TILE);
-  __syncthreads();
+  load_tiles(S, Tt, Q, g, bi * TILE, bj * TILE);
 
   const int sl = threadIdx.x >> 3;
   const int s = bi * TILE + sl;
   if (s >= g.nc) return;
-  float rs[21], ws[7];
-#pragma unroll
-  for (int e = 0; e < 21; ++e) rs[e] = S.rho[sl][e];
-#pragma unroll
-  for (int e = 0; e < 7; ++e) ws[e] = S.wq[sl][e];
   const size_t ldN = g.ldN, ldC = g.ldC;
   const int NC = g.nc;
+  // a fully unrolled source loop hoists its shared-memory reads into registers
+  constexpr int UNR = MINB >= 4 ? 2 : 7;
 
   for (int q = 0; q < 4; ++q) {
     const int tl = (threadIdx.x & 7) + 8 * q;
@@ -242,12 +314,6 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
 #pragma unroll
       for (int b = 0; b < 3; ++b) near |= (S.vid[sl][a] == Tt.vid[tl][b]);
     if (near) continue;
-
-    float rt[21], wt[7];
-#pragma unroll
-    for (int e = 0; e < 21; ++e) rt[e] = Tt.rho[tl][e];
-#pragma unroll
-    for (int e = 0; e < 7; ++e) wt[e] = Tt.wq4[tl][e];
     float d[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) d[e] = (S.cen_hi[sl][e] - Tt.cen_hi[tl][e]) + (S.cen_lo[sl][e] - Tt.cen_lo[tl][e]);
@@ -260,40 +326,11 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
     const float kRc = k * (dd * rsqrtf(dd));
     const float span = k * (S.rq[sl] + Tt.rq[tl]);  // bound on |k (R - Rc)|
     FarMoments Mo;
-    if (span <= 0.05f) far_moments<2>(rs, ws, rt, wt, d, k, kRc, Mo);
-    else if (span <= 0.78f) far_moments<1>(rs, ws, rt, wt, d, k, kRc, Mo);
-    else far_moments<0>(rs, ws, rt, wt, d, k, 0.f, Mo);
+    if (span <= 0.05f) far_moments<2, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
+    else if (span <= 0.78f) far_moments<1, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
+    else far_moments<0, UNR>(S, sl, Q, tl, d, k, 0.f, Mo);
     if (span <= 0.78f) Mo.rotate(kRc);
-    const float I0r = Mo.I0r, I0i = Mo.I0i, Irr_r = Mo.Irr_r, Irr_i = Mo.Irr_i;
-    const float* Ir_r = Mo.Ir_r;
-    const float* Ir_i = Mo.Ir_i;
-    const float* Ip_r = Mo.Ip_r;
-    const float* Ip_i = Mo.Ip_i;
-    const float inv_aa = S.inv_area[sl] * Tt.inv_area[tl];
-    V[(size_t)s * ldC + t] = make_float2(I0r * inv_aa, I0i * inv_aa);
-    V[(size_t)t * ldC + s] = make_float2(I0r * inv_aa, I0i * inv_aa);
-    const float quarter = 0.25f * inv_aa;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float ax = S.aloc[sl][3 * a], ay = S.aloc[sl][3 * a + 1], az = S.aloc[sl][3 * a + 2];
-      // Irr - a.Irp (shared by the three j)
-      const float pa_r = Irr_r - (ax * Ip_r[0] + ay * Ip_r[1] + az * Ip_r[2]);
-      const float pa_i = Irr_i - (ax * Ip_i[0] + ay * Ip_i[1] + az * Ip_i[2]);
-      const int m = S.edge[sl][a];
-      const float sa = S.sign[sl][a] * quarter;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float bx = Tt.aloc[tl][3 * b], by = Tt.aloc[tl][3 * b + 1], bz = Tt.aloc[tl][3 * b + 2];
-        const float ab = ax * bx + ay * by + az * bz;
-        const float vr = pa_r - (bx * Ir_r[0] + by * Ir_r[1] + bz * Ir_r[2]) + ab * I0r;
-        const float vi = pa_i - (bx * Ir_i[0] + by * Ir_i[1] + bz * Ir_i[2]) + ab * I0i;
-        const float f = sa * Tt.sign[tl][b];
-        const int n = Tt.edge[tl][b];
-        // T_A is complex symmetric: only the upper triangle is accumulated (m != n on far pairs),
-        // the lower one is mirrored afterwards so that both are bit-identical
-        atomic_add_c64(&TA[(size_t)min(m, n) * ldN + max(m, n)], f * vr, f * vi);
-      }
-    }
+    far_store(S, Tt, sl, tl, s, t, Mo, ldN, ldC, TA, V);
   }
 }
 
@@ -717,12 +754,15 @@ cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, fl
     case 1:
       far_pairs_kernel<1><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
       break;
-    case 0:
     case 2:
       far_pairs_kernel<2><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
       break;
+    case 0:
     case 3:
       far_pairs_kernel<3><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      break;
+    case 4:
+      far_pairs_kernel<4><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
       break;
     default:
       return cudaErrorInvalidValue;

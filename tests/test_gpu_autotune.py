@@ -64,7 +64,7 @@ def test_inner_products_agree_on_gemv_and_tensor_cores(op, nr):
 
 
 def test_invalid_plans_are_rejected(op):
-    for bad in ({"gemm_bn": 48}, {"gemv_chunk": 300}, {"gemv_ctas_per_sm": 9}, {"far_min_blocks": 4}):
+    for bad in ({"gemm_bn": 48}, {"gemv_chunk": 300}, {"gemv_ctas_per_sm": 9}, {"far_min_blocks": 5}):
         with pytest.raises(rf.RfcmpError):
             op.set_plan(bad)
     assert op.plan() == {k: 0 for k in rf.Plan.KEYS}
@@ -93,7 +93,7 @@ def test_far_pair_register_budgets_assemble_the_same_matrix():
     ctx = rf.Context(0)
     m = synth.geodesic_sphere(5, seed=4)
     mats = []
-    for b in (1, 2, 3):
+    for b in (1, 2, 3, 4):
         ctx.set_plan({"far_min_blocks": b})
         o = rf.Operator(ctx, m.verts, m.tris, 1.3, scaling="k")
         mats.append(o.export("T_A").cpu().numpy())
@@ -102,5 +102,5 @@ def test_far_pair_register_budgets_assemble_the_same_matrix():
     for M in mats[1:]:
         assert np.linalg.norm(M - mats[0]) <= 1e-6 * np.linalg.norm(mats[0])
     best, times = at.tune_assembly(ctx, m.verts, m.tris, 1.3, reps=1)
-    assert best in (1, 2, 3) and all(t > 0 for t in times.values())
+    assert best in (1, 2, 3, 4) and all(t > 0 for t in times.values())
     ctx.close()
