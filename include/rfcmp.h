@@ -37,8 +37,13 @@
  *    that return host results synchronise that stream.
  *  - An rfcmp_op is not thread-safe; different ops may be used from
  *    different threads.  rfcmp_ctx create/destroy are thread-safe.
- *  - Device memory of an op is allocated by the library (cudaMalloc) on the
- *    context's device and counted against the context's HBM budget.
+ *  - Device memory of an op is allocated by the library on the context's
+ *    device and counted against the context's HBM budget.  Allocations and
+ *    frees are queued on the legacy default stream (a stream-ordered pool that
+ *    keeps freed memory mapped), never with a host synchronisation: blocking
+ *    streams are ordered with that stream by CUDA's rules; for a non-blocking
+ *    stream an entry point makes it wait for the library's allocations, and
+ *    memory an op frees waits for every non-blocking stream the op was used on.
  */
 #ifndef RFCMP_H
 #define RFCMP_H
@@ -188,8 +193,9 @@ int rfcmp_op_info_get(const rfcmp_op* op, rfcmp_op_info* out);
 int rfcmp_op_destroy(rfcmp_op* op);
 /* Releases what op built for wide products (the BF16 planes of the tensor-core inner products,
  * the exact-digit planes of the accurate ones) and its solve workspace; the assembled T_A and V,
- * the shared factors and the scaling stay.  The next wide call rebuilds them.  Synchronises the
- * device.  (The paper has no counterpart: memory management for resident operators.)
+ * the shared factors and the scaling stay.  The next wide call rebuilds them.  The memory returns
+ * to the pool behind the work already queued with op; the host does not wait.  (The paper has no
+ * counterpart: memory management for resident operators.)
  * Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_CUDA. */
 int rfcmp_op_trim(rfcmp_op* op);
 

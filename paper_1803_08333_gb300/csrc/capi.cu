@@ -405,10 +405,13 @@ struct rfcmp_op {
   std::vector<void*> lazy;           // the planes and digits above, released by rfcmp_op_trim
   uint64_t lazy_bytes = 0;
   rfcmp_plan plan{};               // launch shapes (zero fields: built-in choices)
+  std::vector<cudaStream_t> nb_streams;  // non-blocking streams this op's work was queued on
+  cudaEvent_t order_ev = nullptr;        // orders streams against the legacy stream (no timing)
   std::unique_ptr<SolveGraph> solve_graph;  // the captured solve loop (rebuilt when stale)
   cudaStream_t capture[3] = {};    // streams the solve loop is captured on (never run work)
   bool graphs_failed = false;      // a capture failed once: this op solves eagerly
   ~rfcmp_op() {
+    if (order_ev) cudaEventDestroy(order_ev);
     solve_graph.reset();
     for (cudaStream_t c : capture)
       if (c) cudaStreamDestroy(c);
@@ -438,12 +441,40 @@ void plan_to_scratch(rfcmp_op* op) {
   op->ws->ms.bn = op->plan.gemm_bn;
 }
 
+// Device memory is allocated and freed in the order of the legacy default stream, which the
+// blocking streams are ordered with.  A non-blocking caller stream is not, so an entry point
+// that queues work on one makes it wait for the legacy stream (the allocations made so far), and
+// the op remembers it so that its memory is freed only after that stream's work.
+int order_stream(rfcmp_op* op, cudaStream_t st) {
+  if (!st) return RFCMP_OK;
+  unsigned int flags = 0;
+  RF_CUDA(cudaStreamGetFlags(st, &flags));
+  if (!(flags & cudaStreamNonBlocking)) return RFCMP_OK;
+  if (std::find(op->nb_streams.begin(), op->nb_streams.end(), st) == op->nb_streams.end())
+    op->nb_streams.push_back(st);
+  if (!op->order_ev) RF_CUDA(cudaEventCreateWithFlags(&op->order_ev, cudaEventDisableTiming));
+  RF_CUDA(cudaEventRecord(op->order_ev, 0));
+  RF_CUDA(cudaStreamWaitEvent(st, op->order_ev, 0));
+  return RFCMP_OK;
+}
+
+// The legacy stream (where frees are queued) waits for the non-blocking streams op was used on.
+int drain_streams(rfcmp_op* op) {
+  for (cudaStream_t s : op->nb_streams) {
+    if (!op->order_ev) RF_CUDA(cudaEventCreateWithFlags(&op->order_ev, cudaEventDisableTiming));
+    RF_CUDA(cudaEventRecord(op->order_ev, s));
+    RF_CUDA(cudaStreamWaitEvent(0, op->order_ev, 0));
+  }
+  return RFCMP_OK;
+}
+
 int ensure_workspace(rfcmp_op* op, int cols) {
   if (op->ws && op->ws->cols >= cols && (cols < plan_mrhs(op) || (op->ws->ms.xb && op->ws->ms.cap_cols >= cols)) &&
       (cols < plan_exact(op) || (op->ws->ms.xd && op->ws->ms.cap_cols >= cols))) {
     plan_to_scratch(op);
     return RFCMP_OK;
   }
+  RF_TRY(drain_streams(op));  // the old workspace, if any, is freed below
   auto ws = std::make_unique<Workspace>();
   ws->cols = cols;
   const size_t N = op->top.ne, C = op->top.nc, NV = op->top.nv;
@@ -488,6 +519,7 @@ int ensure_workspace(rfcmp_op* op, int cols) {
 
 int ensure_solve_buffers(rfcmp_op* op, int cols) {
   if (op->sb && op->sb->cols >= cols) return RFCMP_OK;
+  RF_TRY(drain_streams(op));
   auto sb = std::make_unique<SolveBuffers>();
   sb->cols = cols;
   const size_t N = op->top.ne;
@@ -1551,7 +1583,7 @@ int rfcmp_op_info_get(const rfcmp_op* op, rfcmp_op_info* out) {
 int rfcmp_op_trim(rfcmp_op* op) {
   if (!op) return set_error(RFCMP_ERR_INVALID_ARG, "NULL op");
   RF_CUDA(cudaSetDevice(op->ctx->device));
-  RF_CUDA(cudaDeviceSynchronize());  // nothing of this op may still be reading what is freed
+  RF_TRY(drain_streams(op));  // frees are queued behind every stream op was used on
   for (void* p : op->lazy) dev_free(p);
   op->lazy.clear();
   op->ta_planes = CplxPlanes();
@@ -1570,6 +1602,7 @@ int rfcmp_op_destroy(rfcmp_op* op) {
   if (!op) return RFCMP_OK;
   rfcmp_ctx* ctx = op->ctx;
   cudaSetDevice(ctx->device);
+  drain_streams(op);  // frees are queued behind every stream op was used on
   ctx->bytes -= op->bytes;
   ctx->live_ops--;
   delete op;
@@ -1635,6 +1668,9 @@ int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout
   const double k = op->k;
   const GemvMode m = GEMV_FF;
   RF_TRY(ensure_workspace(op, nr));
+  if (which == RFCMP_APPLY_A_INNER && nr >= plan_mrhs(op)) RF_TRY(ensure_planes(op, 0));
+  if (which != RFCMP_APPLY_A_INNER && nr >= plan_exact(op)) RF_TRY(ensure_digits(op, 0));
+  RF_TRY(order_stream(op, st));
   Workspace& W = *op->ws;
   switch (which) {
     case RFCMP_APPLY_T_A:
@@ -1731,6 +1767,8 @@ int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c12
   const int nr = (int)nrhs;
   const GemvMode m = GEMV_FF;
   RF_TRY(ensure_workspace(op, nr));
+  if (nr >= plan_exact(op)) RF_TRY(ensure_digits(op, 0));
+  RF_TRY(order_stream(op, st));
   Workspace& W = *op->ws;
   const double a = op->alpha, b = op->beta, gm = op->gamma;
   switch (which) {
@@ -1990,8 +2028,9 @@ int solve_impl(rfcmp_op* op, const double2* e, double2* j, int nr, const rfcmp_s
   const GemvMode inner_mode = mixed ? GEMV_F32 : GEMV_FF;
   const int max_sweeps = mixed ? o.max_refine : 1;
   // operands built on first use must exist before the loop is captured
-  if (inner_mode == GEMV_F32 && nr >= plan_mrhs(op)) RF_TRY(ensure_planes(op, st));
-  if (nr >= plan_exact(op)) RF_TRY(ensure_digits(op, st));
+  if (inner_mode == GEMV_F32 && nr >= plan_mrhs(op)) RF_TRY(ensure_planes(op, 0));
+  if (nr >= plan_exact(op)) RF_TRY(ensure_digits(op, 0));
+  RF_TRY(order_stream(op, st));
   // b = -P_o^H T^H P_m e (float-float accurate)
   RF_TRY(apply_rhs(op, e, B.b, nr, GEMV_FF, st));
   const KrylovView K = krylov_view(op, nr);

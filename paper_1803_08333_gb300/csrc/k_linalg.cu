@@ -419,16 +419,18 @@ cudaError_t dev_malloc(void** p, size_t bytes) {
       g_pool_ready.insert(dev);
     }
   }
-  if ((e = cudaMallocAsync(p, std::max<size_t>(bytes, 1), 0)) != cudaSuccess) return e;
-  return cudaStreamSynchronize(0);
+  // On the legacy default stream: the allocation is ordered after all earlier work of the blocking
+  // streams and before all their later work, so no host synchronisation is needed (non-blocking
+  // caller streams are ordered explicitly by the C ABI's entry points).
+  return cudaMallocAsync(p, std::max<size_t>(bytes, 1), 0);
 }
 
 cudaError_t dev_free(void* p) {
   if (!p) return cudaSuccess;
-  cudaError_t e = cudaDeviceSynchronize();
-  cudaError_t e2 = cudaFreeAsync(p, 0);
-  cudaError_t e3 = cudaStreamSynchronize(0);
-  return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+  // Freed in the order of the legacy default stream: after every kernel already queued on the
+  // blocking streams (those that may still read p); the entry points make the legacy stream wait
+  // for the non-blocking streams an operator was used on before they free its memory.
+  return cudaFreeAsync(p, 0);
 }
 
 void dev_pool_trim() {

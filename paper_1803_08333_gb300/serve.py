@@ -88,12 +88,21 @@ class Result:
 
 
 class GpuBackend:
-    """Operators of the library; one context shared by all workers."""
+    """Operators of the library; one context shared by all workers.
 
-    def __init__(self, device: int = 0, hbm_budget: int = 0, power_steps: int = 30, tuning=None):
+    solve_graphs: run each solve's loop as one CUDA graph (rfcmp_set_solve_graphs, process-wide)
+    or launch its kernels one by one.  Off by default here: with two workers solving at once the
+    eager loop measured shorter latencies on GB300 (Poisson stream, 600 requests: p50 398 ms, p99
+    1461 ms, 623 RHS/s, against 1051 / 2740 ms and 598 RHS/s with graphs), although a solve alone
+    is faster as a graph.
+    """
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, power_steps: int = 30, tuning=None,
+                 solve_graphs: bool = False):
         import paper_1803_08333_gb300 as rf
 
         self.rf = rf
+        rf.set_solve_graphs(solve_graphs)
         self.ctx = rf.Context(device, hbm_budget)
         self.device = device
         self.power_steps = power_steps
