@@ -26,6 +26,13 @@ estimated by power iteration (Sec. 4) from a start vector given by the caller
 the estimate changes by at most 1e-3 (relative) between steps (the paper states
 neither; the solution does not depend on these choices).
 
+Theory variant of the outer preconditioner (Sec. 3, Eq. NewFormulation and Eq. Pgs):
+  P_o = P_LH / alpha + i P_gS / beta,  P_gS = Sigma (Sigma^T Sigma)^+ G_l~p^{-1} Sigma^T,
+with G_l~p the mixed Gram matrix of the dual piecewise linear functions and the primal pulses
+(``gram.g_lambda_tilde_p``); P_m is unchanged.  With alpha = sqrt k, beta = 1/sqrt k,
+gamma = k this is the formulation of Sec. 3 exactly.  P_gS is not a projector (nor Hermitian);
+the solution j = P_o i is the same, -T^{-1} e.  ``outer="gsigma"`` selects it below.
+
 Low-frequency-stable application (reading of Eq. LastProofBigUmformung with
 the separate storage of T_A and V, Sec. 4): the products that vanish exactly,
 Sigma^T P_LH = 0, Lambda^T Sigma = 0, P_LH Sigma = 0 and
@@ -73,6 +80,8 @@ class Factors:
     Gpp_inv: np.ndarray  # diag(A)
     P_S: np.ndarray
     P_LH: np.ndarray
+    Gtp_inv: np.ndarray  # G_l~p^{-1} (dual piecewise linear x primal pulse, Sec. 3)
+    P_gS: np.ndarray  # Sigma (Sigma^T Sigma)^+ G_l~p^{-1} Sigma^T (Eq. Pgs)
 
 
 def factors(D) -> Factors:
@@ -84,7 +93,9 @@ def factors(D) -> Factors:
     Gll_inv = np.linalg.inv(gram.g_ll(D).toarray())
     Gpp_inv = np.diag(D.area)
     P_S = S @ Lplus @ S.T
-    return Factors(S, L, Lplus, Gll_inv, Gpp_inv, P_S, np.eye(D.N) - P_S)
+    Gtp_inv = np.linalg.inv(gram.g_lambda_tilde_p(D).toarray())
+    P_gS = S @ Lplus @ Gtp_inv @ S.T
+    return Factors(S, L, Lplus, Gll_inv, Gpp_inv, P_S, np.eye(D.N) - P_S, Gtp_inv, P_gS)
 
 
 @dataclass
@@ -145,20 +156,63 @@ def power_scaling(F: Factors, TA, V, k: float, steps: int = 30, exact: bool = Fa
     return Scaling(alpha, beta, gamma)
 
 
-def preconditioners(F: Factors, sc: Scaling):
-    """Dense P_o and P_m of the numerical variant (Sec. 4)."""
+def preconditioners(F: Factors, sc: Scaling, outer: str = "sigma"):
+    """Dense P_o and P_m of the numerical variant (Sec. 4); outer="gsigma": P_gS in P_o (Sec. 3)."""
     S = F.Sigma
-    Po = F.P_LH / sc.alpha + 1j * F.P_S / sc.beta
+    Po = F.P_LH / sc.alpha + 1j * (F.P_gS if outer == "gsigma" else F.P_S) / sc.beta
     PmL = F.Lambda @ F.Gll_inv @ F.Lambda.T / sc.alpha**2 + F.P_LH / sc.gamma
     PmS = S @ F.Lplus @ F.Gpp_inv @ F.Lplus @ S.T / sc.beta**2
     return Po, PmL + PmS
 
 
-def dense_system(F: Factors, T: np.ndarray, sc: Scaling):
+def dense_system(F: Factors, T: np.ndarray, sc: Scaling, outer: str = "sigma"):
     """A = P_o^H T^H P_m T P_o and the map b = -P_o^H T^H P_m e (Sec. 3, Eq. NewFormulation)."""
-    Po, Pm = preconditioners(F, sc)
+    Po, Pm = preconditioners(F, sc, outer)
     left = Po.conj().T @ T.conj().T @ Pm
     return left @ T @ Po, -left, Po
+
+
+def apply_A_gsigma(F: Factors, TA, V, k: float, sc: Scaling, x: np.ndarray) -> np.ndarray:
+    """A x with P_o = P_LH / alpha + i P_gS / beta, in the low-frequency-stable order.
+
+    With z = L^+ Sigma^T x (x_L = x - Sigma z) and z' = L^+ G^{-1} Sigma^T x (G = G_l~p):
+      T P_o x = u + Sigma w,  u = T_A (i k x_L / alpha - k Sigma z' / beta),
+                               w = V Pi G^{-1} Sigma^T x / (k beta),  Pi = I - 1 1^T / N_C
+    (Sigma^T x_L = 0 and Sigma^T Sigma L^+ = Pi); y = P_m T P_o x as in ``apply_A``; and
+      A x = -(i k / alpha) P_LH u' - (k / beta) Sigma G^{-1} L^+ Sigma^T u'
+            + Sigma G^{-1} Pi conj(V) L q / (k beta),  u' = conj(T_A) y,  L = Sigma^T Sigma,
+    from P_gS^H = Sigma G^{-1} L^+ Sigma^T and Sigma^T y = L q.
+    """
+    S, Lp, Gi = F.Sigma, F.Lplus, F.Gtp_inv
+    a, b, g = sc.alpha, sc.beta, sc.gamma
+    s = S.T @ x
+    x_L = x - S @ (Lp @ s)
+    t = Gi @ s
+    u = TA @ (1j * k * x_L / a - k * (S @ (Lp @ t)) / b)
+    w = V @ (t - t.mean()) / (k * b)
+    zu = Lp @ (S.T @ u)
+    uL = u - S @ zu
+    q = Lp @ (F.Gpp_inv @ (zu + w - w.mean())) / b**2
+    y = F.Lambda @ (F.Gll_inv @ (F.Lambda.T @ u)) / a**2 + uL / g + S @ q
+    up = TA.conj() @ y
+    zp = Lp @ (S.T @ up)
+    vp = V.conj() @ (S.T @ (S @ q)) / (k * b)
+    return -(1j * k / a) * (up - S @ zp) + S @ (Gi @ (-(k / b) * zp + vp - vp.mean()))
+
+
+def apply_rhs_gsigma(F: Factors, TA, V, k: float, sc: Scaling, e: np.ndarray) -> np.ndarray:
+    """b = -P_o^H T^H P_m e with P_gS in P_o; P_m e and T^H as in ``apply_rhs``."""
+    S, Lp, Gi = F.Sigma, F.Lplus, F.Gtp_inv
+    a, b, g = sc.alpha, sc.beta, sc.gamma
+    ze = Lp @ (S.T @ e)
+    eL = e - S @ ze
+    q = Lp @ (F.Gpp_inv @ ze) / b**2
+    y = F.Lambda @ (F.Gll_inv @ (F.Lambda.T @ e)) / a**2 + eL / g + S @ q
+    up = TA.conj() @ y
+    tv = S @ (V.conj() @ (S.T @ (S @ q)))
+    th = -1j * k * up + (1j / k) * tv
+    zt = Lp @ (S.T @ th)
+    return -((th - S @ zt) / a - 1j * (S @ (Gi @ zt)) / b)
 
 
 def apply_A(F: Factors, TA, V, k: float, sc: Scaling, x: np.ndarray) -> np.ndarray:
@@ -208,19 +262,24 @@ def apply_rhs(F: Factors, TA, V, k: float, sc: Scaling, e: np.ndarray) -> np.nda
     return -(th_L / a - 1j * th_S / b)
 
 
-def solve(F: Factors, TA, V, k: float, sc: Scaling, e: np.ndarray, tol: float, maxiter: int = 5000):
+def solve(F: Factors, TA, V, k: float, sc: Scaling, e: np.ndarray, tol: float, maxiter: int = 5000,
+          outer: str = "sigma"):
     """RF-CMP solve with CG (Sec. 4): returns j = P_o i, iterations, CG residual."""
     from .krylov import cg
 
-    bvec = apply_rhs(F, TA, V, k, sc, e)
-    i, it, res = cg(lambda v: apply_A(F, TA, V, k, sc, v), bvec, tol, maxiter)
-    x_S = F.Sigma @ (F.Lplus @ (F.Sigma.T @ i))
-    j = (i - x_S) / sc.alpha + 1j * x_S / sc.beta
+    gs = outer == "gsigma"
+    bvec = (apply_rhs_gsigma if gs else apply_rhs)(F, TA, V, k, sc, e)
+    Aop = apply_A_gsigma if gs else apply_A
+    i, it, res = cg(lambda v: Aop(F, TA, V, k, sc, v), bvec, tol, maxiter)
+    s = F.Sigma.T @ i
+    x_L = i - F.Sigma @ (F.Lplus @ s)
+    x_S = F.Sigma @ (F.Lplus @ (F.Gtp_inv @ s if gs else s))
+    j = x_L / sc.alpha + 1j * x_S / sc.beta
     return j, it, res
 
 
-def condition_number(F: Factors, T, sc: Scaling) -> float:
-    A, _, _ = dense_system(F, T, sc)
+def condition_number(F: Factors, T, sc: Scaling, outer: str = "sigma") -> float:
+    A, _, _ = dense_system(F, T, sc, outer)
     ev = np.linalg.eigvalsh(0.5 * (A + A.conj().T))
     return ev[-1] / ev[0]
 
