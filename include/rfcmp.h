@@ -88,8 +88,20 @@ typedef enum {
   RFCMP_PREC_P_O_ADJ = 1, /* P_o^H */
   RFCMP_PREC_P_M = 2,     /* P_m = P_mL + P_mS   (Sec. 4, first display) */
   RFCMP_PREC_P_SIGMA = 3, /* P_S = Sigma (Sigma^T Sigma)^+ Sigma^T   (Sec. 2) */
-  RFCMP_PREC_P_LAMBDAH = 4 /* P_LH = I - P_S                          (Sec. 2) */
+  RFCMP_PREC_P_LAMBDAH = 4, /* P_LH = I - P_S                         (Sec. 2) */
+  RFCMP_PREC_P_GSIGMA = 5   /* P_gS = Sigma (Sigma^T Sigma)^+ G_l~p^{-1} Sigma^T (Sec. 3, Eq. Pgs);
+                               only for an op created with outer = RFCMP_OUTER_GSIGMA */
 } rfcmp_prec_which;
+
+/* the star part of the outer preconditioner P_o */
+typedef enum {
+  RFCMP_OUTER_SIGMA = 0,  /* P_o = P_LH / alpha + i P_S / beta (numerical variant, Sec. 4); the default */
+  RFCMP_OUTER_GSIGMA = 1  /* P_o = P_LH / alpha + i P_gS / beta with P_gS of Eq. Pgs (Sec. 3) and the
+                             mixed Gram matrix G_l~p of the dual piecewise linear functions and the
+                             primal pulses (the case formula of Sec. 3); with RFCMP_SCALE_K this is
+                             the formulation of Sec. 3, P_o = P_LH / sqrt k + i P_gS sqrt k.  The
+                             current j = P_o i is the same; the conditioning differs */
+} rfcmp_outer;
 
 /* how alpha, beta, gamma are chosen */
 typedef enum {
@@ -120,7 +132,10 @@ typedef struct {
   const rfcmp_op* scaling_start; /* NULL, or an op on the same mesh: the norm iterations start
                            from its final Ritz vectors instead of the splitmix64 vectors (a
                            frequency sweep converges in a few steps); default NULL */
-  int32_t reserved[8];  /* must be zero */
+  int32_t outer;        /* rfcmp_outer; default RFCMP_OUTER_SIGMA.  RFCMP_OUTER_GSIGMA builds the
+                           dense G_l~p^{-1} (N_C x N_C, FP32 hi + lo planes, cached per connectivity
+                           in the context) at rfcmp_op_create */
+  int32_t reserved[7];  /* must be zero */
 } rfcmp_op_opts;
 
 typedef struct {
@@ -204,6 +219,7 @@ int rfcmp_op_trim(rfcmp_op* op);
  *        1: V, N_C x N_C complex64 row-major    (8 N_C^2 bytes)
  *        2: (Sigma^T Sigma)^+, N_C x N_C float64 (hi + lo)  (8 N_C^2 bytes)
  *        3: G_ll^{-1}, N_V x N_V float64 (hi + lo)         (8 N_V^2 bytes)
+ *        4: G_l~p^{-1}, N_C x N_C float64 (hi + lo)        (8 N_C^2 bytes; RFCMP_OUTER_GSIGMA ops)
  * Errors: RFCMP_ERR_INVALID_ARG (unknown which, dst_bytes too small), RFCMP_ERR_CUDA. */
 int rfcmp_op_export(const rfcmp_op* op, int which, void* dst, uint64_t dst_bytes, void* stream);
 

@@ -21,10 +21,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librfcmp.so")
 
 APPLY = {"T": 0, "T_A": 1, "T_PHI": 2, "T_ADJ": 3, "A": 4, "A_INNER": 5}
-PREC = {"P_O": 0, "P_O_ADJ": 1, "P_M": 2, "P_SIGMA": 3, "P_LAMBDAH": 4}
+PREC = {"P_O": 0, "P_O_ADJ": 1, "P_M": 2, "P_SIGMA": 3, "P_LAMBDAH": 4, "P_GSIGMA": 5}
+OUTER = {"sigma": 0, "gsigma": 1}
 SCALING = {"power": 0, "k": 1, "fixed": 2}
 PRECISION = {"mixed": 0, "ff": 1}
-EXPORT = {"T_A": 0, "V": 1, "LPLUS": 2, "GLL_INV": 3}
+EXPORT = {"T_A": 0, "V": 1, "LPLUS": 2, "GLL_INV": 3, "GTP_INV": 4}
 
 # every symbol include/rfcmp.h declares
 EXPORTED_SYMBOLS = [
@@ -43,7 +44,7 @@ class OpOpts(ctypes.Structure):
         ("scaling", ctypes.c_int32), ("power_steps", ctypes.c_int32),
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
         ("factor_tol", ctypes.c_double), ("power_rtol", ctypes.c_double), ("scaling_start", ctypes.c_void_p),
-        ("reserved", ctypes.c_int32 * 8),
+        ("outer", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -264,7 +265,8 @@ class Operator:
 
     def __init__(self, ctx: Context, verts, tris, k: float, scaling: str = "power", power_steps: int = 30,
                  alpha: float = 1.0, beta: float = 1.0, gamma: float = 1.0, factor_tol: float = 1e-13,
-                 power_rtol: float = 1e-3, scaling_start: "Operator | None" = None):
+                 power_rtol: float = 1e-3, scaling_start: "Operator | None" = None, outer: str = "sigma"):
+        """outer: "sigma" (P_o with P_S, the numerical variant of Sec. 4) or "gsigma" (P_gS of Sec. 3)."""
         self.ctx = ctx
         self.verts = np.ascontiguousarray(verts, dtype=np.float64)
         self.tris = np.ascontiguousarray(tris, dtype=np.int32)
@@ -275,6 +277,7 @@ class Operator:
         o.alpha, o.beta, o.gamma = float(alpha), float(beta), float(gamma)
         o.factor_tol = float(factor_tol)
         o.power_rtol = float(power_rtol)
+        o.outer = OUTER[outer]
         if scaling_start is not None:
             o.scaling_start = scaling_start._h
         self._h = ctypes.c_void_p()
@@ -316,10 +319,10 @@ class Operator:
         return i.alpha, i.beta, i.gamma
 
     def export(self, which: str):
-        """T_A, V (complex64 n x n) or LPLUS, GLL_INV (float64 n x n from the hi + lo planes) as CUDA tensors."""
+        """T_A, V (complex64 n x n) or LPLUS, GLL_INV, GTP_INV (float64 n x n from the hi + lo planes) as CUDA tensors."""
         import torch
 
-        n = {"T_A": self.N, "V": self.nc, "LPLUS": self.nc, "GLL_INV": self.nv}[which]
+        n = {"T_A": self.N, "V": self.nc, "LPLUS": self.nc, "GLL_INV": self.nv, "GTP_INV": self.nc}[which]
         if which in ("T_A", "V"):
             t = torch.empty((n, n), dtype=torch.complex64, device="cuda")
             _check(lib().rfcmp_op_export(self._h, EXPORT[which], _ptr(t), n * n * 8, _stream()))

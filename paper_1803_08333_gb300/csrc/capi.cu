@@ -321,6 +321,7 @@ struct rfcmp_ctx {
   std::mutex mu;
   std::map<uint64_t, std::shared_ptr<DenseFactor>> lplus_cache;  // key: connectivity hash
   std::map<uint64_t, std::shared_ptr<DenseFactor>> gll_cache;    // key: connectivity + coordinates hash
+  std::map<uint64_t, std::shared_ptr<DenseFactor>> gtp_cache;    // key: connectivity hash (G_l~p^{-1})
   std::map<uint64_t, std::shared_ptr<MeshEntry>> mesh_cache;      // key: connectivity + coordinates
   std::mutex build_mu;  // one factor build at a time, so concurrent ops on one mesh share it
   std::atomic<int> live_ops{0};
@@ -334,7 +335,7 @@ struct Workspace {
   double2 *v = nullptr, *u = nullptr, *y = nullptr, *up = nullptr, *tmpN = nullptr;
   // cell space (N_C)
   double2 *s = nullptr, *z = nullptr, *w = nullptr, *zu = nullptr, *q0 = nullptr, *q = nullptr, *Lq = nullptr,
-          *vp = nullptr;
+          *vp = nullptr, *g1 = nullptr, *g2 = nullptr;
   // vertex space (N_V)
   double2 *t = nullptr, *tg = nullptr;
   double* mean = nullptr;  // 4 x cols
@@ -373,7 +374,7 @@ struct SolveGraph {
   const void* ws = nullptr;
   const void* sb = nullptr;
   int ws_cols = 0, sb_cols = 0;
-  const void* lazy[8] = {};
+  const void* lazy[10] = {};
   rfcmp_plan plan{};
   uint64_t prof_key = 0;
   ~SolveGraph() {
@@ -391,6 +392,8 @@ struct rfcmp_op {
   float2* V = nullptr;
   int ldN = 0, ldC = 0;
   std::shared_ptr<DenseFactor> lplus, gll;
+  std::shared_ptr<DenseFactor> gtp;  // G_l~p^{-1} (outer = RFCMP_OUTER_GSIGMA only)
+  int outer = RFCMP_OUTER_SIGMA;
   std::shared_ptr<MeshEntry> mesh;  // owns the device geometry in g
   double k = 0.0, alpha = 1.0, beta = 1.0, gamma = 1.0;
   uint64_t bytes = 0;
@@ -481,6 +484,8 @@ int ensure_workspace(rfcmp_op* op, int cols) {
   for (double2** p : {&ws->v, &ws->u, &ws->y, &ws->up, &ws->tmpN}) RF_TRY(dalloc(p, N * cols, ws->owned));
   for (double2** p : {&ws->s, &ws->z, &ws->w, &ws->zu, &ws->q0, &ws->q, &ws->Lq, &ws->vp})
     RF_TRY(dalloc(p, C * cols, ws->owned));
+  if (op->gtp)
+    for (double2** p : {&ws->g1, &ws->g2}) RF_TRY(dalloc(p, C * cols, ws->owned));
   for (double2** p : {&ws->t, &ws->tg}) RF_TRY(dalloc(p, NV * cols, ws->owned));
   RF_TRY(dalloc(&ws->mean, 4 * (size_t)cols, ws->owned));  // pgp_apply uses 4 per column
   {
@@ -591,6 +596,7 @@ int ensure_planes(rfcmp_op* op, cudaStream_t st) {
   RF_TRY(make_cplx_planes(op, op->V, (int)op->top.nc, op->ldC, op->v_planes, st));
   RF_TRY(make_real_planes(op, *op->lplus, st));
   RF_TRY(make_real_planes(op, *op->gll, st));
+  if (op->gtp) RF_TRY(make_real_planes(op, *op->gtp, st));
   return RFCMP_OK;
 }
 
@@ -653,6 +659,7 @@ int ensure_digits(rfcmp_op* op, cudaStream_t st) {
   RF_TRY(make_cplx_digits(op, op->V, (int)op->top.nc, op->ldC, op->v_digits, st));
   RF_TRY(make_real_digits(op, *op->lplus, st));
   RF_TRY(make_real_digits(op, *op->gll, st));
+  if (op->gtp) RF_TRY(make_real_digits(op, *op->gtp, st));
   return RFCMP_OK;
 }
 
@@ -703,7 +710,10 @@ int star_coeff(rfcmp_op* op, const double2* x, double2* s, double2* z, int nr, G
 
 // out = A x (Sec. 3 Eq. NewFormulation, numerical variant of Sec. 4) in the
 // low-frequency-stable order: analytically vanishing products are not formed.
+int apply_A_gsigma(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cudaStream_t st);
+
 int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cudaStream_t st) {
+  if (op->outer == RFCMP_OUTER_GSIGMA) return apply_A_gsigma(op, x, out, nr, m, st);
   RF_TRY(ensure_workspace(op, nr));
   Workspace& W = *op->ws;
   const DeviceGeometry& g = op->g;
@@ -763,6 +773,79 @@ int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cu
   return RFCMP_OK;
 }
 
+// y = P_m T P_o x from u (= T_A v) and w (= V ... / (k b)), the middle of both forms of A:
+//   y = Lambda G_ll^{-1} Lambda^T u / a^2 + (u - Sigma zu) / gamma + Sigma q,
+//   zu = L^+ Sigma^T u,  q = L^+ G_pp^{-1} (zu + w - mean(w)) / b^2  (W.zu, W.q, W.y)
+int apply_middle(rfcmp_op* op, GemvMode m, int nr, cudaStream_t st) {
+  Workspace& W = *op->ws;
+  const DeviceGeometry& g = op->g;
+  const double a = op->alpha, b = op->beta, gm = op->gamma;
+  RF_TRY(star_coeff(op, W.u, W.s, W.zu, nr, m, st));
+  RF_K(lambda_t(g, W.u, W.t, nr, st));
+  RF_TRY(prod_r(op, *op->gll, W.t, W.tg, nr, 1.0, false, m, st));
+  RF_K(star_middle(g, W.zu, W.w, 1.0, W.q0, nr, W.mean, st));
+  RF_TRY(prod_r(op, *op->lplus, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+  EdgeCombo c;
+  c.zl = W.tg;
+  c.c = c2(1.0 / (a * a), 0.0);
+  c.x = W.u;
+  c.a = c2(1.0 / gm, 0.0);
+  c.zs = W.zu;
+  c.b = c2(-1.0 / gm, 0.0);
+  c.zs2 = W.q;
+  c.d = c2(1.0, 0.0);
+  RF_K(edge_combo(g, c, W.y, nr, st));
+  return RFCMP_OK;
+}
+
+// out = A x with P_o = P_LH / a + i P_gS / b, P_gS = Sigma L^+ G^{-1} Sigma^T (Sec. 3, Eq. Pgs;
+// G = G_l~p, L = Sigma^T Sigma), in the low-frequency-stable order.  With s = Sigma^T x,
+// z = L^+ s (x_L = x - Sigma z), t = G^{-1} s, z' = L^+ t:
+//   T P_o x = u + Sigma w,  u = T_A ((ik/a) x_L - (k/b) Sigma z'),  w = V Pi t / (k b),
+// (Sigma^T x_L = 0, Sigma^T Sigma L^+ = Pi = I - 1 1^T / N_C); y = P_m T P_o x as in apply_A;
+//   A x = -(ik/a) P_LH u' + Sigma G^{-1} (-(k/b) zp + Pi vp),
+// u' = conj(T_A) y, zp = L^+ Sigma^T u', vp = conj(V) L q / (k b), from P_gS^H = Sigma G^{-1} L^+
+// Sigma^T and Sigma^T y = L q.
+int apply_A_gsigma(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cudaStream_t st) {
+  RF_TRY(ensure_workspace(op, nr));
+  Workspace& W = *op->ws;
+  const DeviceGeometry& g = op->g;
+  const double k = op->k, a = op->alpha, b = op->beta;
+  RF_K(sigma_t(g, x, W.s, nr, st));
+  RF_TRY(prod_r(op, *op->lplus, W.s, W.z, nr, 1.0, false, m, st));
+  RF_TRY(prod_r(op, *op->gtp, W.s, W.g1, nr, 1.0, false, m, st));
+  RF_TRY(prod_r(op, *op->lplus, W.g1, W.g2, nr, 1.0, false, m, st));
+  {  // v = (ik/a) x - (ik/a) Sigma z - (k/b) Sigma z'
+    EdgeCombo c;
+    c.x = x;
+    c.a = c2(0.0, k / a);
+    c.zs = W.z;
+    c.b = c2(0.0, -k / a);
+    c.zs2 = W.g2;
+    c.d = c2(-k / b, 0.0);
+    RF_K(edge_combo(g, c, W.v, nr, st));
+  }
+  RF_TRY(prod_c(op, true, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, st));
+  RF_K(cell_combo(g, nullptr, c2(0, 0), W.g1, c2(1.0, 0.0), W.q0, nr, W.mean, st));  // Pi t
+  RF_TRY(prod_c(op, false, W.q0, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, st));
+  RF_TRY(apply_middle(op, m, nr, st));
+  RF_TRY(prod_c(op, true, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
+  RF_K(lap_apply(g, W.q, W.Lq, nr, st));
+  RF_TRY(prod_c(op, false, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, st));
+  RF_TRY(star_coeff(op, W.up, W.s, W.z, nr, m, st));  // zp
+  RF_K(cell_combo(g, W.z, c2(-k / b, 0.0), W.vp, c2(1.0, 0.0), W.g1, nr, W.mean, st));
+  RF_TRY(prod_r(op, *op->gtp, W.g1, W.g2, nr, 1.0, false, m, st));
+  EdgeCombo c;  // out = -(ik/a) up + (ik/a) Sigma zp + Sigma G^{-1}(...)
+  c.x = W.up;
+  c.a = c2(0.0, -k / a);
+  c.zs = W.z;
+  c.b = c2(0.0, k / a);
+  c.zs2 = W.g2;
+  c.d = c2(1.0, 0.0);
+  RF_K(edge_combo(g, c, out, nr, st));
+  return RFCMP_OK;
+}
+
 // b = -P_o^H T^H P_m e in the same order
 int apply_rhs(rfcmp_op* op, const double2* e, double2* out, int nr, GemvMode m, cudaStream_t st) {
   RF_TRY(ensure_workspace(op, nr));
@@ -799,6 +882,18 @@ int apply_rhs(rfcmp_op* op, const double2* e, double2* out, int nr, GemvMode m, 
     RF_K(edge_combo(g, c, W.tmpN, nr, st));
   }
   RF_TRY(star_coeff(op, W.tmpN, W.s, W.z, nr, m, st));
+  if (op->outer == RFCMP_OUTER_GSIGMA) {  // out = -th / a + Sigma zt / a + (i/b) Sigma G^{-1} zt
+    RF_TRY(prod_r(op, *op->gtp, W.z, W.g1, nr, 1.0, false, m, st));
+    EdgeCombo c;
+    c.x = W.tmpN;
+    c.a = c2(-1.0 / a, 0.0);
+    c.zs = W.z;
+    c.b = c2(1.0 / a, 0.0);
+    c.zs2 = W.g1;
+    c.d = c2(0.0, 1.0 / b);
+    RF_K(edge_combo(g, c, out, nr, st));
+    return RFCMP_OK;
+  }
   {  // out = -th / a + Sigma zt (1/a + i/b)
     EdgeCombo c;
     c.x = W.tmpN;
@@ -815,6 +910,24 @@ int apply_Po(rfcmp_op* op, const double2* x, double2* out, int nr, bool adj, Gem
   RF_TRY(ensure_workspace(op, nr));
   Workspace& W = *op->ws;
   RF_TRY(star_coeff(op, x, W.s, W.z, nr, m, st));
+  if (op->outer == RFCMP_OUTER_GSIGMA) {
+    // P_o x = x_L / a + (i/b) Sigma L^+ G^{-1} Sigma^T x;  P_o^H x = x_L / a - (i/b) Sigma G^{-1} L^+ Sigma^T x
+    if (adj) {
+      RF_TRY(prod_r(op, *op->gtp, W.z, W.g2, nr, 1.0, false, m, st));
+    } else {
+      RF_TRY(prod_r(op, *op->gtp, W.s, W.g1, nr, 1.0, false, m, st));
+      RF_TRY(prod_r(op, *op->lplus, W.g1, W.g2, nr, 1.0, false, m, st));
+    }
+    EdgeCombo c;
+    c.x = x;
+    c.a = c2(1.0 / op->alpha, 0.0);
+    c.zs = W.z;
+    c.b = c2(-1.0 / op->alpha, 0.0);
+    c.zs2 = W.g2;
+    c.d = c2(0.0, adj ? -1.0 / op->beta : 1.0 / op->beta);
+    RF_K(edge_combo(op->g, c, out, nr, st));
+    return RFCMP_OK;
+  }
   EdgeCombo c;
   c.x = x;
   c.a = c2(1.0 / op->alpha, 0.0);
@@ -1163,7 +1276,8 @@ int upload_geometry(const Topology& T, const std::vector<double>& verts, DeviceG
 
 // dense inverse of a sparse SPD matrix (CSR on the host), FP32 hi + lo planes
 int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col, const std::vector<double>& val,
-                 int n, bool project, bool multigrid, double tol, std::shared_ptr<DenseFactor>& out) {
+                 int n, bool project, bool multigrid, double tol, std::shared_ptr<DenseFactor>& out,
+                 double jacobi_c = 0.8) {
   auto f = std::make_shared<DenseFactor>();
   f->n = n;
   const size_t ld = (size_t)padded_ld(n);
@@ -1229,13 +1343,15 @@ int build_factor(const std::vector<int32_t>& ptr, const std::vector<int32_t>& co
   } else if (!project && !multigrid && n >= NS_MIN_CELLS) {
     // G_ll^{-1}: the P1 mass matrix has the eigenvalues of D^{-1} G_ll in [1/2, 2] (element by
     // element), so X0 = 0.8 D^{-1} leaves I - G_ll X0 a spectral radius of at most 0.6 and
-    // Newton-Schulz reaches rounding level in about six steps; block CG is the fallback
+    // Newton-Schulz reaches rounding level in about six steps.  G_l~p^{-1}: G_l~p is strictly
+    // diagonally dominant with the off-diagonal row sums below 0.8 of the diagonal, so
+    // X0 = D^{-1} (jacobi_c = 1) leaves a spectral radius below 0.8.  Block CG is the fallback
     const double target = std::max(tol, NS_TARGET);
     double* Xd = nullptr;
     err = dev_malloc(&Xd, sizeof(double) * (size_t)n * padded_ld(n));
     int steps = 0;
     double res = 1.0;
-    if (err == cudaSuccess) err = jacobi_start(dptr, dcol, dval, n, 0.8, Xd, padded_ld(n), 0);
+    if (err == cudaSuccess) err = jacobi_start(dptr, dcol, dval, n, jacobi_c, Xd, padded_ld(n), 0);
     if (err == cudaSuccess)
       err = newton_schulz_pseudo_inverse(dptr, dcol, dval, n, false, Xd, padded_ld(n), NS_MAX_STEPS, target, f->hi,
                                          f->lo, &steps, &res, 0);
@@ -1404,8 +1520,11 @@ int rfcmp_ctx_clear_cache(rfcmp_ctx* ctx) {
     if (kv.second.use_count() == 1) ctx->bytes -= kv.second->bytes;
   for (auto& kv : ctx->gll_cache)
     if (kv.second.use_count() == 1) ctx->bytes -= kv.second->bytes;
+  for (auto& kv : ctx->gtp_cache)
+    if (kv.second.use_count() == 1) ctx->bytes -= kv.second->bytes;
   ctx->lplus_cache.clear();
   ctx->gll_cache.clear();
+  ctx->gtp_cache.clear();
   ctx->mesh_cache.clear();
   return RFCMP_OK;
 }
@@ -1420,8 +1539,10 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   rfcmp_op_opts o;
   rfcmp_op_opts_default(&o);
   if (opts_in) o = *opts_in;
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 7; ++i)
     if (o.reserved[i] != 0) return set_error(RFCMP_ERR_INVALID_ARG, "opts.reserved must be zero");
+  if (o.outer != RFCMP_OUTER_SIGMA && o.outer != RFCMP_OUTER_GSIGMA)
+    return set_error(RFCMP_ERR_INVALID_ARG, "opts.outer must be RFCMP_OUTER_SIGMA or RFCMP_OUTER_GSIGMA");
   if (o.scaling < 0 || o.scaling > 2 || o.power_steps < 1 || !(o.factor_tol > 0.0) || !(o.power_rtol >= 0.0))
     return set_error(RFCMP_ERR_INVALID_ARG, "invalid op options");
   if (o.scaling == RFCMP_SCALE_FIXED && !(o.alpha > 0 && o.beta > 0 && o.gamma > 0))
@@ -1486,7 +1607,9 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
     std::memcpy(&b, &verts[i], 8);
     geo_hash = mix(geo_hash, b);
   }
-  std::shared_ptr<DenseFactor> lp, gl;
+  std::shared_ptr<DenseFactor> lp, gl, gt;
+  const bool gsigma = o.outer == RFCMP_OUTER_GSIGMA;
+  op->outer = o.outer;
   std::unique_lock<std::mutex> build_lock(ctx->build_mu);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1494,10 +1617,13 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
     if (a != ctx->lplus_cache.end()) lp = a->second;
     auto b = ctx->gll_cache.find(geo_hash);
     if (b != ctx->gll_cache.end()) gl = b->second;
+    auto c = ctx->gtp_cache.find(op->top.hash);
+    if (gsigma && c != ctx->gtp_cache.end()) gt = c->second;
   }
   uint64_t need = mat_bytes;
   if (!lp) need += 2ull * padded_ld(C) * C * 4;
   if (!gl) need += 2ull * padded_ld(NV) * NV * 4;
+  if (gsigma && !gt) need += 2ull * padded_ld(C) * C * 4;
   if (ctx->budget && ctx->bytes.load() + need > ctx->budget)
     return set_error(RFCMP_ERR_OUT_OF_BUDGET, "op needs " + std::to_string(need) + " bytes, budget has " +
                                                   std::to_string(ctx->budget - std::min(ctx->budget, ctx->bytes.load())));
@@ -1520,8 +1646,19 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
     ctx->gll_cache[geo_hash] = gl;
     ctx->bytes += gl->bytes;
   }
+  if (gsigma && !gt) {
+    std::vector<int32_t> gp, gc;
+    std::vector<double> gv;
+    gtp_matrix_csr(op->top, gp, gc, gv);
+    RF_TRY(build_factor(gp, gc, gv, C, false, false, o.factor_tol, gt, 1.0));
+    op->info.ms_factors += gt->ms;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->gtp_cache[op->top.hash] = gt;
+    ctx->bytes += gt->bytes;
+  }
   op->lplus = lp;
   op->gll = gl;
+  op->gtp = gt;
   build_lock.unlock();
   op->info.factor_iterations_lplus = lp->iterations;
   op->info.factor_iterations_gll = gl->iterations;
@@ -1621,9 +1758,10 @@ int rfcmp_op_export(const rfcmp_op* op, int which, void* dst, uint64_t dst_bytes
     RF_CUDA(cudaMemcpy2DAsync(dst, (size_t)n * 8, M, (size_t)ld * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice, st));
     return RFCMP_OK;
   }
-  if (which == 2 || which == 3) {
-    const DenseFactor& f = which == 2 ? *op->lplus : *op->gll;
-    const int n = which == 2 ? C : NV;
+  if (which == 4 && !op->gtp) return set_error(RFCMP_ERR_INVALID_ARG, "op has no G_l~p factor");
+  if (which == 2 || which == 3 || which == 4) {
+    const DenseFactor& f = which == 2 ? *op->lplus : (which == 3 ? *op->gll : *op->gtp);
+    const int n = which == 3 ? NV : C;
     if (dst_bytes < (uint64_t)n * n * 8) return set_error(RFCMP_ERR_INVALID_ARG, "destination too small");
     // hi and lo planes side by side: first n*n floats hi, then n*n floats lo
     float* d = static_cast<float*>(dst);
@@ -1791,6 +1929,17 @@ int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c12
       RF_K(edge_combo(op->g, c, y, nr, st));
       return RFCMP_OK;
     }
+    case RFCMP_PREC_P_GSIGMA: {  // Sigma L^+ G^{-1} Sigma^T x
+      if (!op->gtp) return set_error(RFCMP_ERR_INVALID_ARG, "op was created without outer = RFCMP_OUTER_GSIGMA");
+      RF_K(sigma_t(op->g, x, W.s, nr, st));
+      RF_TRY(prod_r(op, *op->gtp, W.s, W.g1, nr, 1.0, false, m, st));
+      RF_TRY(prod_r(op, *op->lplus, W.g1, W.g2, nr, 1.0, false, m, st));
+      EdgeCombo c;
+      c.zs = W.g2;
+      c.b = c2(1, 0);
+      RF_K(edge_combo(op->g, c, y, nr, st));
+      return nr >= plan_exact(op) ? check_tensor_core_waits(op, st) : RFCMP_OK;
+    }
     case RFCMP_PREC_P_M: {
       const int C = (int)op->top.nc, NV = (int)op->top.nv;
       RF_TRY(star_coeff(op, x, W.s, W.zu, nr, m, st));
@@ -1926,8 +2075,9 @@ int add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
 bool solve_graph_current(const rfcmp_op* op, int nr, GemvMode inner, int max_sweeps) {
   const SolveGraph* G = op->solve_graph.get();
   if (!G || !G->exec) return false;
-  const void* lazy[8] = {op->ta_planes.rh,   op->v_planes.rh,     op->ta_digits.d,  op->v_digits.d,
-                         op->lplus->planes.h, op->lplus->digits.d, op->gll->planes.h, op->gll->digits.d};
+  const void* lazy[10] = {op->ta_planes.rh,   op->v_planes.rh,     op->ta_digits.d,  op->v_digits.d,
+                          op->lplus->planes.h, op->lplus->digits.d, op->gll->planes.h, op->gll->digits.d,
+                          op->gtp ? op->gtp->planes.h : nullptr, op->gtp ? op->gtp->digits.d : nullptr};
   return G->nr == nr && G->mode == (int)inner && G->max_sweeps == max_sweeps && G->ws == op->ws.get() &&
          G->sb == op->sb.get() && G->ws_cols == op->ws->cols && G->sb_cols == op->sb->cols &&
          std::memcmp(G->lazy, lazy, sizeof(lazy)) == 0 && std::memcmp(&G->plan, &op->plan, sizeof(rfcmp_plan)) == 0 &&
@@ -1990,8 +2140,9 @@ int capture_solve_graph(rfcmp_op* op, int nr, GemvMode inner, int max_sweeps) {
   G->sb = op->sb.get();
   G->ws_cols = op->ws->cols;
   G->sb_cols = op->sb->cols;
-  const void* lazy[8] = {op->ta_planes.rh,   op->v_planes.rh,     op->ta_digits.d,  op->v_digits.d,
-                         op->lplus->planes.h, op->lplus->digits.d, op->gll->planes.h, op->gll->digits.d};
+  const void* lazy[10] = {op->ta_planes.rh,   op->v_planes.rh,     op->ta_digits.d,  op->v_digits.d,
+                          op->lplus->planes.h, op->lplus->digits.d, op->gll->planes.h, op->gll->digits.d,
+                          op->gtp ? op->gtp->planes.h : nullptr, op->gtp ? op->gtp->digits.d : nullptr};
   std::memcpy(G->lazy, lazy, sizeof(lazy));
   G->plan = op->plan;
   G->prof_key = prof_capture_key();

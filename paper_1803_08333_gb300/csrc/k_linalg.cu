@@ -666,7 +666,38 @@ __global__ void star_middle_kernel(const double* __restrict__ area, int nc, cons
   q[o] = make_double2(f * v.x, f * v.y);
 }
 
+__global__ void cell_combo_kernel(int nc, const double2* __restrict__ z, double2 a, const double2* __restrict__ w,
+                                  double2 b, const double* __restrict__ sums, double2* __restrict__ q) {
+  RF_COUNT_LAUNCH();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (c >= nc) return;
+  const size_t o = (size_t)r * nc + c;
+  double2 v = make_double2(0.0, 0.0);
+  if (z) v = cmul(a, z[o]);
+  if (w) {
+    const double2 d = make_double2(w[o].x - sums[2 * r] / nc, w[o].y - sums[2 * r + 1] / nc);
+    const double2 t = cmul(b, d);
+    v.x += t.x;
+    v.y += t.y;
+  }
+  q[o] = v;
+}
+
 }  // namespace
+
+cudaError_t cell_combo(const DeviceGeometry& g, const double2* z, double2 a, const double2* w, double2 b, double2* q,
+                       int nrhs, double* scratch_mean, cudaStream_t s) {
+  if (w) {
+    cudaError_t e = cudaMemsetAsync(scratch_mean, 0, sizeof(double) * 2 * nrhs, s);
+    if (e != cudaSuccess) return e;
+    dim3 grid(std::min(64, (g.nc + 255) / 256), nrhs);
+    column_sum_kernel<<<grid, 256, 0, s>>>(w, g.nc, scratch_mean);
+  }
+  dim3 grid((g.nc + 255) / 256, nrhs);
+  cell_combo_kernel<<<grid, 256, 0, s>>>(g.nc, z, a, w, b, scratch_mean, q);
+  return cudaGetLastError();
+}
 
 cudaError_t sigma_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s) {
   dim3 grid((g.nc + 255) / 256, nrhs);

@@ -96,6 +96,11 @@ struct Topology {
 // Builds the topology; returns RFCMP_OK or a mesh error with a message.
 int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& out, std::string& err);
 
+// G_l~p (dual piecewise linear x primal pulse, Sec. 3) as CSR over the cells, from the case
+// formula of Sec. 3 (diagonal, cells sharing an edge, cells sharing only a vertex).
+void gtp_matrix_csr(const Topology& top, std::vector<int32_t>& ptr, std::vector<int32_t>& col,
+                    std::vector<double>& val);
+
 // G_ll (P1 mass matrix) as CSR over the vertices, local block A/12 [[2,1,1],[1,2,1],[1,1,2]].
 void mass_matrix_csr(const Topology& top, const double* verts, std::vector<int32_t>& ptr,
                      std::vector<int32_t>& col, std::vector<double>& val);
@@ -299,6 +304,10 @@ cudaError_t edge_combo(const DeviceGeometry& g, const EdgeCombo& c, double2* out
 // q = scale * diag(area) (z + w - mean(w)); mean over each column of w (N_C).  w may be null.
 cudaError_t star_middle(const DeviceGeometry& g, const double2* z, const double2* w, double scale, double2* q,
                         int nrhs, double* scratch_mean, cudaStream_t s);
+
+// q = a z + b (w - mean(w)) over the cells, per column; z may be null; scratch holds 2 x nrhs doubles
+cudaError_t cell_combo(const DeviceGeometry& g, const double2* z, double2 a, const double2* w, double2 b, double2* q,
+                       int nrhs, double* scratch_mean, cudaStream_t s);
 
 // out = Pi diag(area) Pi w, Pi = I - 1 1^T / N_C (per column); scratch holds 4 x nrhs doubles
 cudaError_t pgp_apply(const DeviceGeometry& g, const double2* w, double2* out, int nrhs, double* scratch,

@@ -223,4 +223,48 @@ void mass_matrix_csr(const Topology& T, const double* verts, std::vector<int32_t
   }
 }
 
+void gtp_matrix_csr(const Topology& T, std::vector<int32_t>& ptr, std::vector<int32_t>& col,
+                    std::vector<double>& val) {
+  // (lambda~_m, p_n) by the case formula of Sec. 3:
+  //   m = n:                      2/18 (9/2 + sum over the vertices v of m of 1/NoC(v))
+  //   cells sharing edge (a, b):  2/18 (1/2 + 1/NoC(a) + 1/NoC(b))
+  //   sharing only vertex v:      2/18 (1/NoC(v))
+  // with NoC(v) the number of cells around vertex v.
+  const int64_t nv = T.nv, nc = T.nc;
+  std::vector<int32_t> noc(nv, 0);
+  for (int64_t i = 0; i < 3 * nc; ++i) noc[T.tris[i]]++;
+  std::vector<std::vector<int32_t>> v2c(nv);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int i = 0; i < 3; ++i) v2c[T.tris[3 * c + i]].push_back((int32_t)c);
+  ptr.assign(nc + 1, 0);
+  col.clear();
+  val.clear();
+  std::vector<int32_t> nb;
+  for (int64_t m = 0; m < nc; ++m) {
+    const int32_t* tm = &T.tris[3 * m];
+    nb.clear();
+    for (int i = 0; i < 3; ++i) nb.insert(nb.end(), v2c[tm[i]].begin(), v2c[tm[i]].end());
+    std::sort(nb.begin(), nb.end());
+    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    for (int32_t n : nb) {
+      const int32_t* tn = &T.tris[3 * n];
+      double s = 0.0;
+      int shared = 0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          if (tm[i] == tn[j]) {
+            ++shared;
+            s += 1.0 / noc[tm[i]];
+          }
+      double v = 0.0;
+      if (n == m) v = 2.0 / 18.0 * (4.5 + s);
+      else if (shared == 2) v = 2.0 / 18.0 * (0.5 + s);
+      else v = 2.0 / 18.0 * s;
+      col.push_back(n);
+      val.push_back(v);
+    }
+    ptr[m + 1] = (int32_t)col.size();
+  }
+}
+
 }  // namespace rfcmp
