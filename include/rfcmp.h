@@ -233,6 +233,20 @@ int rfcmp_op_edges(const rfcmp_op* op, int32_t* edge_verts, int32_t* edge_cells)
 int rfcmp_rhs_planewave(rfcmp_op* op, const double* khat, const double* pol, int64_t nrhs,
                         rfcmp_c128* e, void* stream);
 
+/* Voltage-gap (delta-gap) excitation, the second excitation of the paper's Fokker experiment
+ * (Sec. 4; the paper gives no formula).  Reading: an impressed field V delta(s) u across the
+ * closed line of mesh edges cut by the plane through `origin` with normal `normal` -- the edges
+ * whose two cells have their centroids on opposite sides -- u the in-surface normal of that line
+ * towards the side `normal` points to.  The flux of an RWG function (Eq. RWGdef, no edge-length
+ * factor) through its own edge is 1, so e_n = +V where c_n^+ lies on the negative side, -V where
+ * it lies on the positive side, 0 off the gap (e = V Sigma chi, chi the indicator of the
+ * negative side's cells).
+ *  origin, normal  HOST 3 float64 each; normal nonzero (need not be unit length).
+ *  e               DEVICE, N complex128 (one column).
+ * Errors: RFCMP_ERR_INVALID_ARG (NULL, zero or non-finite plane), RFCMP_ERR_CUDA. */
+int rfcmp_rhs_voltage_gap(rfcmp_op* op, const double* origin, const double* normal, rfcmp_c128 voltage,
+                          rfcmp_c128* e, void* stream);
+
 /* y = op(x) for nrhs columns (see rfcmp_apply_which).  Float-float accurate
  * accumulation over the stored complex64 matrices.  x and y must not alias. */
 int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* x, rfcmp_c128* y, int64_t nrhs, void* stream);

@@ -284,3 +284,46 @@ def excitation(D: Discretization, k: float, khat, pol) -> np.ndarray:
     loc = (w * dots * phase[:, None, :, :]).sum(axis=2)  # (N_C, 3, nrhs)
     loc /= (2.0 * D.area)[:, None, None]  # the sign sigma is applied by B
     return D.B.T @ loc.reshape(3 * D.nc, nrhs)
+
+
+def gap_edges(D: Discretization, origin, normal):
+    """Edges of a voltage gap cut by the plane (origin, normal): those whose two cells have their
+    centroids on opposite sides.  Returns (edge indices, s) with s = +1 where c^+ lies on the
+    negative side (the RWG direction c^+ -> c^- runs along the normal), -1 otherwise."""
+    o = np.asarray(origin, dtype=np.float64)
+    nh = np.asarray(normal, dtype=np.float64)
+    nh = nh / np.linalg.norm(nh)
+    side = (D.cent - o) @ nh > 0.0
+    cp, cm = D.top.edge_cells[:, 0], D.top.edge_cells[:, 1]
+    cut = np.flatnonzero(side[cp] != side[cm])
+    return cut, np.where(side[cp[cut]], -1.0, 1.0)
+
+
+def excitation_voltage_gap(D: Discretization, origin, normal, voltage: complex = 1.0) -> np.ndarray:
+    """e_n = int f_n . E^i for a delta-gap source E^i = V delta(s) u (Sec. 4, the Fokker model's
+    second excitation; the paper gives no formula, reading: the gap is the closed line of mesh
+    edges cut by a plane, u the unit in-surface normal of that line pointing to the plane
+    normal's side, s the distance across it).  The delta reduces the surface integral to the
+    line integral V int_edge f_n . u dl over the gap edges, evaluated here from the RWG function
+    on c^+ (Eq. RWGdef, (r - r^+) / (2 A^+)) with a 5-point Gauss rule along the edge."""
+    cut, s = gap_edges(D, origin, normal)
+    e = np.zeros(D.N, dtype=np.complex128)
+    x, w = np.polynomial.legendre.leggauss(5)
+    t, w = 0.5 * (x + 1.0), 0.5 * w
+    for n, sg in zip(cut, s):
+        v1, v2 = D.verts[D.top.edge_verts[n]]
+        cp = D.top.edge_cells[n, 0]
+        rp = D.verts[D.top.edge_free[n, 0]]
+        ev = v2 - v1
+        le = np.linalg.norm(ev)
+        # in-surface normal of the edge pointing out of c^+ (away from its free vertex)
+        nrm = D.normal[cp]
+        out = np.cross(ev, nrm)
+        out = out / np.linalg.norm(out)
+        if out @ (v1 - rp) < 0:
+            out = -out
+        pts = v1[None, :] + t[:, None] * ev[None, :]
+        f = (pts - rp[None, :]) / (2.0 * D.area[cp])
+        flux = le * np.sum(w * (f @ out))
+        e[n] = voltage * sg * flux
+    return e[:, None]

@@ -35,8 +35,12 @@ EXPORTED_SYMBOLS = [
     "rfcmp_farfield", "rfcmp_strerror", "rfcmp_last_error", "rfcmp_op_opts_default",
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
     "rfcmp_gemm_bf16x3", "rfcmp_plan_default", "rfcmp_ctx_set_plan", "rfcmp_op_set_plan", "rfcmp_op_get_plan",
-    "rfcmp_op_trim", "rfcmp_launch_count", "rfcmp_set_solve_graphs",
+    "rfcmp_op_trim", "rfcmp_launch_count", "rfcmp_set_solve_graphs", "rfcmp_rhs_voltage_gap",
 ]
+
+
+class C128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
 
 
 class OpOpts(ctypes.Structure):
@@ -135,6 +139,7 @@ def lib():
         L.rfcmp_op_export.argtypes = [vp, i32, vp, ctypes.c_uint64, vp]
         L.rfcmp_op_edges.argtypes = [vp, vp, vp]
         L.rfcmp_rhs_planewave.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.rfcmp_rhs_voltage_gap.argtypes = [vp, vp, vp, C128, vp, vp]
         L.rfcmp_apply.argtypes = [vp, i32, vp, vp, i64, vp]
         L.rfcmp_precondition.argtypes = [vp, i32, vp, vp, i64, vp]
         L.rfcmp_solve.argtypes = [vp, vp, vp, i64, ctypes.POINTER(SolveOpts), vp, vp]
@@ -346,6 +351,18 @@ class Operator:
         e = torch.empty((nr, self.N), dtype=torch.complex128, device="cuda")
         _check(lib().rfcmp_rhs_planewave(self._h, khat.ctypes.data_as(ctypes.c_void_p),
                                          pol.ctypes.data_as(ctypes.c_void_p), nr, _ptr(e), _stream()))
+        return e
+
+    def rhs_voltage_gap(self, origin, normal, voltage: complex = 1.0):
+        """Delta-gap excitation across the mesh edges cut by the plane (origin, normal): (1, N)."""
+        import torch
+
+        o = np.ascontiguousarray(origin, dtype=np.float64).reshape(3)
+        u = np.ascontiguousarray(normal, dtype=np.float64).reshape(3)
+        e = torch.empty((1, self.N), dtype=torch.complex128, device="cuda")
+        v = C128(float(np.real(voltage)), float(np.imag(voltage)))
+        _check(lib().rfcmp_rhs_voltage_gap(self._h, o.ctypes.data_as(ctypes.c_void_p), u.ctypes.data_as(ctypes.c_void_p),
+                                           v, _ptr(e), _stream()))
         return e
 
     def _vec(self, x):

@@ -1796,6 +1796,19 @@ int rfcmp_rhs_planewave(rfcmp_op* op, const double* khat, const double* pol, int
   return RFCMP_OK;
 }
 
+int rfcmp_rhs_voltage_gap(rfcmp_op* op, const double* origin, const double* normal, rfcmp_c128 voltage, rfcmp_c128* e,
+                          void* stream) {
+  if (!op || !origin || !normal || !e) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  const double nn = normal[0] * normal[0] + normal[1] * normal[1] + normal[2] * normal[2];
+  if (!(nn > 0.0) || !std::isfinite(nn) || !std::isfinite(origin[0] + origin[1] + origin[2]))
+    return set_error(RFCMP_ERR_INVALID_ARG, "the gap plane needs a finite origin and a nonzero normal");
+  cudaStream_t st = (cudaStream_t)stream;
+  RF_TRY(order_stream(op, st));
+  RF_K(launch_rhs_voltage_gap(op->g, origin, normal, make_double2(voltage.re, voltage.im),
+                              reinterpret_cast<double2*>(e), st));
+  return RFCMP_OK;
+}
+
 int rfcmp_apply(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c128* yout, int64_t nrhs, void* stream) {
   if (!op || !xin || !yout || nrhs <= 0 || nrhs > 4096) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
   cudaStream_t st = (cudaStream_t)stream;

@@ -574,6 +574,22 @@ __global__ void mirror_upper_kernel(float2* __restrict__ M, int n, size_t ld) {
 }
 
 // ---------------------------------------------------------------- excitation (FP64)
+// Delta-gap excitation: the edges whose two cells have their centroids on opposite sides of the
+// plane (o, u) carry e_n = +-V (the flux of an RWG function through its own edge is 1), + where
+// c^+ lies on the negative side; every other edge 0.
+__global__ void gap_kernel(const DeviceGeometry g, double ox, double oy, double oz, double ux, double uy, double uz,
+                           double vr, double vi, double2* __restrict__ e) {
+  RF_COUNT_LAUNCH();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.ne) return;
+  const double* cp = g.cen64 + 3 * g.edge_cells[2 * n];
+  const double* cm = g.cen64 + 3 * g.edge_cells[2 * n + 1];
+  const bool sp = (cp[0] - ox) * ux + (cp[1] - oy) * uy + (cp[2] - oz) * uz > 0.0;
+  const bool sm = (cm[0] - ox) * ux + (cm[1] - oy) * uy + (cm[2] - oz) * uz > 0.0;
+  const double s = sp == sm ? 0.0 : (sp ? -1.0 : 1.0);
+  e[n] = make_double2(s * vr, s * vi);
+}
+
 __global__ void rhs_kernel(const DeviceGeometry g, double k, const double* __restrict__ khat,
                            const double* __restrict__ pol, int nrhs, double2* __restrict__ e) {
   RF_COUNT_LAUNCH();
@@ -783,6 +799,14 @@ cudaError_t launch_mirror_upper(float2* M, int n, int ld, cudaStream_t s) {
   dim3 grid(nb, nb), block(MT, 8);
   ProfScope prof("mirror_upper", 8.0 * (double)n * n, 0.0, s);
   mirror_upper_kernel<<<grid, block, 0, s>>>(M, n, (size_t)ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_voltage_gap(const DeviceGeometry& g, const double* origin, const double* normal, double2 v,
+                                   double2* e, cudaStream_t s) {
+  const double nn = std::sqrt(normal[0] * normal[0] + normal[1] * normal[1] + normal[2] * normal[2]);
+  gap_kernel<<<(g.ne + 255) / 256, 256, 0, s>>>(g, origin[0], origin[1], origin[2], normal[0] / nn, normal[1] / nn,
+                                                normal[2] / nn, v.x, v.y, e);
   return cudaGetLastError();
 }
 

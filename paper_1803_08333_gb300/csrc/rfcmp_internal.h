@@ -148,6 +148,8 @@ cudaError_t launch_assemble_near(const DeviceGeometry& g, double k, float2* TA, 
 // T_A is accumulated in its upper triangle; this copies it to the lower one (bit-identical symmetry)
 cudaError_t launch_mirror_upper(float2* M, int n, int ld, cudaStream_t s);
 // e (ne x nrhs complex128), khat/pol device nrhs x 3
+cudaError_t launch_rhs_voltage_gap(const DeviceGeometry& g, const double* origin, const double* normal, double2 v,
+                                   double2* e, cudaStream_t s);
 cudaError_t launch_rhs_planewave(const DeviceGeometry& g, double k, const double* khat, const double* pol,
                                  int nrhs, double2* e, cudaStream_t s);
 // radiation vector N(rhat) for nrhs currents and ndir directions -> out (ndir x nrhs x 3 complex)

@@ -348,3 +348,43 @@ def test_cg_and_cgs_on_small_systems():
     G = M + 15 * np.eye(40)
     y, it2, res2 = krylov.cgs(lambda v: G @ v, b, 1e-12)
     assert np.linalg.norm(y - np.linalg.solve(G, b)) < 1e-9 * np.linalg.norm(y)
+
+
+# ---------------------------------------------------------------- voltage gap
+def test_voltage_gap_flux_and_loop():
+    # the flux of an (unnormalised) RWG function through its own edge is 1, so a delta gap of
+    # voltage V gives e_n = +-V on the gap edges; the gap edges close into a loop around the cut
+    m = synth.geodesic_sphere(4, seed=5)
+    D = efie.discretize(m.verts, m.tris)
+    origin, normal = [0.0, 0.0, 0.1], [0.2, 0.1, 1.0]
+    e = efie.excitation_voltage_gap(D, origin, normal, 2.5)[:, 0]
+    cut, s = efie.gap_edges(D, origin, normal)
+    assert cut.size > 0
+    assert np.abs(np.abs(e[cut]) - 2.5).max() <= 1e-13
+    assert np.abs(np.delete(e, cut)).max() == 0.0
+    assert np.array_equal(np.sign(e[cut].real), s)
+    # a closed line: every vertex touched by the gap edges meets two of them
+    vs, counts = np.unique(D.top.edge_verts[cut].ravel(), return_counts=True)
+    assert (counts % 2 == 0).all()
+    # the impressed field is a gradient jump across the line: e is Sigma times the indicator of one side
+    side = ((D.cent - origin) @ (np.array(normal) / np.linalg.norm(normal)) > 0).astype(float)
+    assert np.abs(e.real - 2.5 * (D.Sigma @ (1.0 - side))).max() <= 1e-13
+
+
+@pytest.mark.slow
+def test_dense_discretization_stability():
+    # Sec. 4 (Fig. SphereH): the RF-CMP condition number stays bounded as h -> 0 at fixed k,
+    # while the plain EFIE's grows like h^-2 (here N = 120 -> 480, h halves)
+    cond_A, cond_T = [], []
+    for n in (2, 4):
+        m = synth.geodesic_sphere(n, seed=1)
+        D = efie.discretize(m.verts, m.tris)
+        F = rfcmp.factors(D)
+        k = 0.5
+        TA, V = efie.assemble(D, k)
+        T = efie.efie_matrix(D, TA, V, k)
+        cond_A.append(rfcmp.condition_number(F, T, rfcmp.power_scaling(F, TA, V, k, exact=True)))
+        sv = np.linalg.svd(T, compute_uv=False)
+        cond_T.append(sv[0] / sv[-1])
+    assert max(cond_A) < 10 and cond_A[1] / cond_A[0] < 1.1
+    assert 3.5 < cond_T[1] / cond_T[0] < 5.0
