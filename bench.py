@@ -631,6 +631,85 @@ def bench_batched(args):
     }))
 
 
+def bench_large(args):
+    """The large instance: the seeded frequency-55 sphere (60500 cells, 90750 unknowns; T_A 65.9 GB
+    of complex64), ka = 10 with 1024 seeded plane waves, then ka = 1e-4 with one plane wave, each
+    solved by the mixed-precision RF-CMP CG with float-float refinement to 1e-6.
+
+    The device memory is budgeted before anything is created: the resident operator (T_A, V and
+    the two FP32 hi + lo factors), the BF16 planes the tensor-core inner products build, and the
+    solve vectors of one block of columns must fit the free memory, which fixes the block of
+    columns solved at once (512 on a GB300).  The six-digit exact planes of the accurate
+    products would take 24 bytes per matrix entry (285 GB), so the accurate products stay on the
+    float-float GEMV here (plan exact_min).
+    """
+    import torch
+
+    import paper_1803_08333_gb300 as rf
+    import synth
+    from paper_1803_08333_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    n_geo = args.large_n
+    mesh = synth.geodesic_sphere(n_geo, seed=5)
+    nc = mesh.tris.shape[0]
+    N, nv = 3 * nc // 2, nc // 2 + 2
+    pad = lambda n: (n + 63) // 64 * 64  # noqa: E731
+    op_bytes = 8 * (pad(N) * N + pad(nc) * nc) + 8 * (pad(nc) * nc + pad(nv) * nv)
+    planes = 8 * (pad(N) * N + pad(nc) * nc) + 4 * (pad(nc) * nc + pad(nv) * nv)
+    per_col = 16 * (14 * N + 10 * nc + 2 * nv) + 16 * 2 * N
+    rf.pool_trim()
+    free = torch.cuda.mem_get_info()[0]
+    margin = 6 << 30
+    cols = args.large_nrhs
+    while cols > 4 and op_bytes + planes + per_col * cols + margin > free:
+        cols //= 2
+    if op_bytes + planes + per_col * cols + margin > free:
+        raise SystemExit("large instance does not fit: %.1f GB free, %.1f GB needed"
+                         % (free / 1e9, (op_bytes + planes + per_col * cols + margin) / 1e9))
+    ctx = rf.Context(0)
+    ctx.set_plan({"exact_min": 65536})
+    rf.pool_reset_high()
+    out = {"workload": "large_sphere_f%d_n%d" % (n_geo, N), "unknowns": N, "cells": nc,
+           "budget": {"free_gb": round(free / 1e9, 1), "operator_gb": round(op_bytes / 1e9, 1),
+                      "planes_gb": round(planes / 1e9, 1), "vectors_gb": round(per_col * cols / 1e9, 1),
+                      "columns_per_solve": cols}}
+    clocks = Clocks(0)
+    clocks.start()
+    for ka, nrhs in ((10.0, args.large_nrhs), (1e-4, 1)):
+        t0 = time.perf_counter()
+        op = rf.Operator(ctx, mesh.verts, mesh.tris, ka)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        info = op.info()
+        kh, pol = synth.random_plane_waves(nrhs, seed=33) if nrhs > 1 else synth.plane_wave_z()
+        t0 = time.perf_counter()
+        reps = []
+        for c0 in range(0, nrhs, cols):
+            e = op.rhs_planewave(kh[c0 : c0 + cols], pol[c0 : c0 + cols])
+            _, rep = op.solve(e, tol=TOL)
+            reps += rep
+            del e
+        torch.cuda.synchronize()
+        solve = time.perf_counter() - t0
+        out["ka=%g" % ka] = {
+            "nrhs": nrhs, "setup_s": round(setup, 2), "assembly_ms": round(info.ms_assembly, 1),
+            "factors_ms": round(info.ms_factors, 1), "scaling_ms": round(info.ms_scaling, 1),
+            "solve_s": round(solve, 2), "rhs_per_s": round(nrhs / solve, 2),
+            "iterations": [min(r.iterations for r in reps), max(r.iterations for r in reps)],
+            "refinements": max(r.refinements for r in reps), "converged": sum(r.converged for r in reps),
+            "max_residual": max(r.residual for r in reps),
+        }
+        op.close()
+    clk = clocks.stop()
+    st = rf.pool_stats()
+    out["memory_high_water_gb"] = {"used": round(st["used_high"] / 1e9, 1),
+                                   "reserved": round(st["reserved_high"] / 1e9, 1)}
+    out["clocks"] = clk
+    print(json.dumps(out))
+
+
 def bench_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -662,13 +741,16 @@ def main():
     ap.add_argument("--mesh-n", type=int, default=32,
                     help="geodesic frequency of the sphere (32 = the workload; smaller for profiling captures)")
     ap.add_argument("--ka", type=float, nargs="*", default=None, help="override the wavenumber sweep")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "serving", "batched"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serving", "batched", "large"],
                     help="sweep: the level-5 low-frequency sweep (default); serving: the Poisson request stream; "
                          "batched: 512 plane waves on the 41070-unknown ellipsoid")
     ap.add_argument("--nrhs", type=int, default=512, help="batched: right-hand sides per solve")
     ap.add_argument("--ellipsoid-n", type=int, default=37,
                     help="batched: geodesic frequency of the ellipsoid (37 = the workload; smaller for profiling)")
     ap.add_argument("--single-sample", type=int, default=3, help="batched: columns solved one at a time in FF")
+    ap.add_argument("--large-n", type=int, default=55,
+                    help="large: geodesic frequency of the sphere (55 = 90750 unknowns)")
+    ap.add_argument("--large-nrhs", type=int, default=1024, help="large: plane waves at ka = 10")
     ap.add_argument("--requests", type=int, default=600)
     ap.add_argument("--workers", type=int, default=2)
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
@@ -685,6 +767,8 @@ def main():
         bench_serving(args)
     elif args.workload == "batched":
         bench_batched(args)
+    elif args.workload == "large":
+        bench_large(args)
     else:
         bench_ours(args)
 

@@ -369,6 +369,15 @@ int rfcmp_profile_read(rfcmp_profile_entry* out, int max_entries, int* n_entries
  * the current device.  Errors: RFCMP_ERR_INVALID_ARG (out is NULL). */
 int rfcmp_launch_count(uint64_t* out);
 
+/* Device memory of the library's stream-ordered pool on the current device (the paper has no
+ * counterpart: memory accounting for large operators): bytes in use now and at most since the
+ * last reset, bytes the pool holds mapped now and at most.  Any pointer may be NULL.
+ * rfcmp_pool_reset_high restarts both high-water marks.  Errors: RFCMP_ERR_CUDA. */
+int rfcmp_pool_stats(uint64_t* used, uint64_t* used_high, uint64_t* reserved, uint64_t* reserved_high);
+int rfcmp_pool_reset_high(void);
+/* Hands the memory the pool holds but no buffer uses back to the driver (synchronises the device). */
+int rfcmp_pool_trim(void);
+
 /* How rfcmp_solve runs its loop (the paper has no counterpart; the arithmetic is the same
  * either way, so the results are identical).  Nonzero (the default, unless the environment
  * variable RFCMP_SOLVE_GRAPHS is "0" when the first solve starts): refinement sweeps and CG

@@ -36,6 +36,7 @@ EXPORTED_SYMBOLS = [
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
     "rfcmp_gemm_bf16x3", "rfcmp_plan_default", "rfcmp_ctx_set_plan", "rfcmp_op_set_plan", "rfcmp_op_get_plan",
     "rfcmp_op_trim", "rfcmp_launch_count", "rfcmp_set_solve_graphs", "rfcmp_rhs_voltage_gap",
+    "rfcmp_pool_stats", "rfcmp_pool_reset_high", "rfcmp_pool_trim",
 ]
 
 
@@ -161,6 +162,8 @@ def lib():
         L.rfcmp_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
         L.rfcmp_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         L.rfcmp_set_solve_graphs.argtypes = [i32]
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.rfcmp_pool_stats.argtypes = [u64p, u64p, u64p, u64p]
         _LIB = L
     return _LIB
 
@@ -202,6 +205,22 @@ def set_solve_graphs(enable: bool) -> bool:
     """Solve loops as one CUDA graph per op (True, the default) or launched kernel by kernel;
     returns the previous setting.  The arithmetic, and so every result, is the same."""
     return bool(lib().rfcmp_set_solve_graphs(1 if enable else 0))
+
+
+def pool_stats() -> dict:
+    """Bytes of the library's device pool: used, used_high, reserved, reserved_high."""
+    v = [ctypes.c_uint64() for _ in range(4)]
+    _check(lib().rfcmp_pool_stats(*[ctypes.byref(x) for x in v]))
+    return dict(zip(("used", "used_high", "reserved", "reserved_high"), (int(x.value) for x in v)))
+
+
+def pool_reset_high():
+    _check(lib().rfcmp_pool_reset_high())
+
+
+def pool_trim():
+    """Returns the pool's unused device memory to the driver (synchronises the device)."""
+    _check(lib().rfcmp_pool_trim())
 
 
 def launch_count() -> int:

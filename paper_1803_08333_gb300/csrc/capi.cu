@@ -1413,6 +1413,37 @@ int rfcmp_launch_count(uint64_t* out) {
   return RFCMP_OK;
 }
 
+int rfcmp_pool_stats(uint64_t* used, uint64_t* used_high, uint64_t* reserved, uint64_t* reserved_high) {
+  int dev = 0;
+  cudaMemPool_t pool;
+  RF_CUDA(cudaGetDevice(&dev));
+  RF_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t v = 0;
+  if (used) RF_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, used));
+  if (used_high) RF_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, used_high));
+  if (reserved) RF_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, reserved));
+  if (reserved_high) RF_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemHigh, reserved_high));
+  (void)v;
+  return RFCMP_OK;
+}
+
+int rfcmp_pool_trim(void) {
+  dev_pool_trim();
+  RF_CUDA(cudaGetLastError());
+  return RFCMP_OK;
+}
+
+int rfcmp_pool_reset_high(void) {
+  int dev = 0;
+  cudaMemPool_t pool;
+  RF_CUDA(cudaGetDevice(&dev));
+  RF_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t zero = 0;
+  RF_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+  RF_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &zero));
+  return RFCMP_OK;
+}
+
 int rfcmp_set_solve_graphs(int enable) {
   const int prev = solve_graphs_enabled() ? 1 : 0;
   g_solve_graphs.store(enable ? 1 : 0);
@@ -1660,6 +1691,9 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   op->gll = gl;
   op->gtp = gt;
   build_lock.unlock();
+  // The pool keeps freed memory mapped; after a factor build of tens of GB the work arrays would
+  // stay reserved beside matrices of tens of GB more, so a large operator hands them back first.
+  if (mat_bytes > (32ull << 30)) dev_pool_trim();
   op->info.factor_iterations_lplus = lp->iterations;
   op->info.factor_iterations_gll = gl->iterations;
   // assembly
