@@ -494,7 +494,7 @@ def bench_serving(args):
 
     table = None if args.no_tuning else autotune.Table.for_device(torch.cuda.get_device_name(0))
     be = serve.GpuBackend(0, hbm_budget=0, tuning=table)
-    srv = serve.Server(be, hbm_budget=budget, workers=args.workers)
+    srv = serve.Server(be, hbm_budget=budget, workers=args.workers, continuous=args.serve_mode == "continuous")
     t0 = time.perf_counter()
     seen = set()
     for _, sc, _ in work:
@@ -536,8 +536,11 @@ def bench_serving(args):
         "unit": "right-hand sides/s", "n_gpus": 1, "higher_is_better": True,
         "config": {"workload": f"poisson_serving_{args.rate:g}rps", "requests": args.requests, "scene_pool": len(seen),
                    "mesh_pool": len(meshes), "unknowns": [sizes[0], sizes[-1]], "workers": args.workers,
-                   "budget_bytes": budget, "tol": TOL, "tuning": "table" if table is not None else "built-in"},
+                   "budget_bytes": budget, "tol": TOL, "tuning": "table" if table is not None else "built-in",
+                   "batching": args.serve_mode},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]}, "requests_per_s": st["requests_per_s"],
+        "queue_wait_ms": {"p50": st["p50_wait_ms"], "p99": st["p99_wait_ms"]}, "solves": st["solves"],
+        "joined_running_solve": st["joined_running_solve"], "arrived_during_solve": st["arrived_during_solve"],
         "mean_batch_columns": st["mean_batch_columns"], "max_residual": max(max(r.residuals) for r in res),
         "resident_operators": st["resident_operators"], "cold_start_s": round(cold_s, 2), "wall_s": round(wall, 2),
         "gpu_launches": gpu_launches, "clocks": clk, "data": "synthetic (seeded jittered spheres, cubes, ellipsoids; random plane waves)"}))
@@ -752,7 +755,9 @@ def main():
                     help="large: geodesic frequency of the sphere (55 = 90750 unknowns)")
     ap.add_argument("--large-nrhs", type=int, default=1024, help="large: plane waves at ka = 10")
     ap.add_argument("--requests", type=int, default=600)
-    ap.add_argument("--workers", type=int, default=2)
+    ap.add_argument("--workers", type=int, default=4, help="serving: solver threads, one CUDA stream each")
+    ap.add_argument("--serve-mode", default="continuous", choices=["continuous", "merged"],
+                    help="serving: columns join running solves between sweeps, or merged solves run to the end")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--no-tuning", action="store_true", help="ignore the autotuner table (built-in plans)")
     args = ap.parse_args()

@@ -266,6 +266,37 @@ int rfcmp_solve(rfcmp_op* op, const rfcmp_c128* e, rfcmp_c128* j, int64_t nrhs, 
 int rfcmp_solve_host(rfcmp_op* op, const rfcmp_c128* e_host, rfcmp_c128* j_host, int64_t nrhs,
                      const rfcmp_solve_opts* opts, rfcmp_solve_report* report, void* stream);
 
+/* ----------------------------------------------------------------------------
+ * Batch sessions: continuous batching of one operator's solves (the paper has no counterpart;
+ * the serving form of the solve above).  A session holds `capacity` column slots of one RF-CMP
+ * CG solve with refinement; excitations are admitted into free slots at any time between
+ * sweeps, every rfcmp_batch_step runs one refinement sweep (inner CG to the sweep's tolerance,
+ * then the accurate residual) over all running columns together, and finished columns are
+ * taken out one by one, freeing their slots for the next admissions.  A column's arithmetic is
+ * that of rfcmp_solve (the same kernels, its own scalars and stopping test); columns that share
+ * a sweep share the operator products.  The op must not be used by another call while a step
+ * runs; a session keeps its own solve vectors (capacity x N complex128, several copies).
+ */
+typedef struct rfcmp_batch rfcmp_batch;
+/* opts as for rfcmp_solve (NULL: defaults).  Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_CUDA. */
+int rfcmp_batch_create(rfcmp_op* op, int32_t capacity, const rfcmp_solve_opts* opts, rfcmp_batch** out);
+int rfcmp_batch_destroy(rfcmp_batch* b);
+/* Admits n excitations e (DEVICE, N x n complex128, column-major) into free slots, whose
+ * indices go to slots (HOST, n).  Errors: RFCMP_ERR_INVALID_ARG (fewer than n free slots). */
+int rfcmp_batch_admit(rfcmp_batch* b, const rfcmp_c128* e, int32_t n, int32_t* slots, void* stream);
+/* One refinement sweep over the running columns.  The slots whose column finished in this
+ * sweep (converged, or out of iterations or sweeps) go to finished (HOST, up to capacity) and
+ * their count to *n_finished.  Synchronises the stream. */
+int rfcmp_batch_step(rfcmp_batch* b, int32_t* finished, int32_t* n_finished, void* stream);
+/* Takes the columns of n finished slots (HOST list, no repeats): j = P_o i for all of them in one
+ * application (DEVICE, N x n complex128, column-major, in the order of slots) and their reports
+ * (HOST, n, may be NULL); the slots become free.  Synchronises the stream.
+ * Errors: RFCMP_ERR_INVALID_ARG (a slot out of range, repeated, or without a finished column). */
+int rfcmp_batch_take(rfcmp_batch* b, const int32_t* slots, int32_t n, rfcmp_c128* j, rfcmp_solve_report* reports,
+                     void* stream);
+/* Slots running, finished (not yet taken) and free; any pointer may be NULL. */
+int rfcmp_batch_counts(const rfcmp_batch* b, int32_t* running, int32_t* finished, int32_t* free_slots);
+
 /* Bistatic radar cross section sigma = (k^2 / 4 pi) |N - rhat (rhat . N)|^2,
  * N(rhat) = int j e^{-i k rhat . r} dS (7-point rule, FP64), in dBsm.
  *  j DEVICE N x nrhs; dirs HOST ndir x 3 unit vectors; rcs_dbsm HOST ndir x nrhs (column-major). */

@@ -36,7 +36,8 @@ EXPORTED_SYMBOLS = [
     "rfcmp_solve_opts_default", "rfcmp_profile_enable", "rfcmp_profile_read", "rfcmp_apply_ta_noalloc",
     "rfcmp_gemm_bf16x3", "rfcmp_plan_default", "rfcmp_ctx_set_plan", "rfcmp_op_set_plan", "rfcmp_op_get_plan",
     "rfcmp_op_trim", "rfcmp_launch_count", "rfcmp_set_solve_graphs", "rfcmp_rhs_voltage_gap",
-    "rfcmp_pool_stats", "rfcmp_pool_reset_high", "rfcmp_pool_trim",
+    "rfcmp_pool_stats", "rfcmp_pool_reset_high", "rfcmp_pool_trim", "rfcmp_batch_create", "rfcmp_batch_destroy",
+    "rfcmp_batch_admit", "rfcmp_batch_step", "rfcmp_batch_take", "rfcmp_batch_counts",
 ]
 
 
@@ -164,6 +165,13 @@ def lib():
         L.rfcmp_set_solve_graphs.argtypes = [i32]
         u64p = ctypes.POINTER(ctypes.c_uint64)
         L.rfcmp_pool_stats.argtypes = [u64p, u64p, u64p, u64p]
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        L.rfcmp_batch_create.argtypes = [vp, i32, ctypes.POINTER(SolveOpts), ctypes.POINTER(vp)]
+        L.rfcmp_batch_destroy.argtypes = [vp]
+        L.rfcmp_batch_admit.argtypes = [vp, vp, i32, i32p, vp]
+        L.rfcmp_batch_step.argtypes = [vp, i32p, i32p, vp]
+        L.rfcmp_batch_take.argtypes = [vp, i32p, i32, vp, ctypes.POINTER(SolveReport), vp]
+        L.rfcmp_batch_counts.argtypes = [vp, i32p, i32p, i32p]
         _LIB = L
     return _LIB
 
@@ -472,6 +480,11 @@ class Operator:
                                       nr, ctypes.byref(o), rep, _stream(stream)))
         return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]
 
+    def batch(self, capacity: int, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 8,
+              inner_tol: float = 1e-4, precision: str = "mixed") -> "Batch":
+        """A batch session on this operator (continuous batching; see Batch)."""
+        return Batch(self, capacity, self._solve_opts(tol, max_iter, max_refine, inner_tol, precision))
+
     def farfield(self, j, dirs) -> np.ndarray:
         """Bistatic RCS in dBsm, shape (nrhs, ndir)."""
         j = self._vec(j)
@@ -490,5 +503,59 @@ class Operator:
         try:
             if self._h:
                 lib().rfcmp_op_destroy(self._h)
+        except Exception:
+            pass
+
+
+class Batch:
+    """Continuous batching of one operator's solves (rfcmp_batch_*): excitations join free slots
+    between refinement sweeps, step() runs one sweep over all running columns, take() returns a
+    finished column's current and frees its slot."""
+
+    def __init__(self, op: Operator, capacity: int, opts: SolveOpts):
+        self.op = op
+        self.capacity = int(capacity)
+        self._h = ctypes.c_void_p()
+        _check(lib().rfcmp_batch_create(op._h, self.capacity, ctypes.byref(opts), ctypes.byref(self._h)))
+
+    def admit(self, e, stream=None) -> list:
+        e = self.op._vec(e)
+        n = e.shape[0]
+        slots = (ctypes.c_int32 * n)()
+        _check(lib().rfcmp_batch_admit(self._h, _ptr(e), n, slots, _stream(stream)))
+        return list(slots)
+
+    def step(self, stream=None) -> list:
+        fin = (ctypes.c_int32 * self.capacity)()
+        nf = ctypes.c_int32()
+        _check(lib().rfcmp_batch_step(self._h, fin, ctypes.byref(nf), _stream(stream)))
+        return list(fin[: nf.value])
+
+    def take(self, slots, stream=None):
+        """Currents (len(slots) x N) and reports of finished slots, which become free."""
+        import torch
+
+        slots = [int(s) for s in np.atleast_1d(slots)]
+        n = len(slots)
+        sl = (ctypes.c_int32 * n)(*slots)
+        j = torch.empty((n, self.op.N), dtype=torch.complex128, device="cuda")
+        r = (SolveReport * n)()
+        _check(lib().rfcmp_batch_take(self._h, sl, n, _ptr(j), r, _stream(stream)))
+        return j, [Report(bool(x.converged), x.iterations, x.refinements, x.residual) for x in r]
+
+    def counts(self) -> tuple:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rfcmp_batch_counts(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def close(self):
+        if self._h:
+            _check(lib().rfcmp_batch_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().rfcmp_batch_destroy(self._h)
         except Exception:
             pass

@@ -360,6 +360,7 @@ struct SolveBuffers {
   int *conv = nullptr, *iters = nullptr, *sweeps = nullptr;
   double2* part = nullptr;
   unsigned int* ticket = nullptr;
+  int* member = nullptr;  // batch sessions only: 1 for the columns of running requests
   ~SolveBuffers() {
     for (void* p : owned) dev_free(p);
   }
@@ -522,9 +523,15 @@ int ensure_workspace(rfcmp_op* op, int cols) {
   return RFCMP_OK;
 }
 
+int alloc_solve_buffers(rfcmp_op* op, int cols, std::unique_ptr<SolveBuffers>& out);
+
 int ensure_solve_buffers(rfcmp_op* op, int cols) {
   if (op->sb && op->sb->cols >= cols) return RFCMP_OK;
   RF_TRY(drain_streams(op));
+  return alloc_solve_buffers(op, cols, op->sb);
+}
+
+int alloc_solve_buffers(rfcmp_op* op, int cols, std::unique_ptr<SolveBuffers>& out) {
   auto sb = std::make_unique<SolveBuffers>();
   sb->cols = cols;
   const size_t N = op->top.ne;
@@ -542,7 +549,7 @@ int ensure_solve_buffers(rfcmp_op* op, int cols) {
   RF_TRY(dalloc(&sb->ticket, cols, sb->owned));
   RF_CUDA(cudaMemset(sb->ticket, 0, sizeof(unsigned int) * cols));
   RF_CUDA(cudaMemset(sb->ctl, 0, sizeof(KrylovCtl)));
-  op->sb = std::move(sb);
+  out = std::move(sb);
   return RFCMP_OK;
 }
 
@@ -2016,8 +2023,7 @@ int rfcmp_precondition(rfcmp_op* op, int which, const rfcmp_c128* xin, rfcmp_c12
 // ---------------------------------------------------------------- the solve
 namespace {
 
-KrylovView krylov_view(rfcmp_op* op, int nr) {
-  SolveBuffers& B = *op->sb;
+KrylovView krylov_view(rfcmp_op* op, SolveBuffers& B, int nr) {
   KrylovView K;
   K.ctl = B.ctl;
   K.bb = B.bb;
@@ -2033,6 +2039,7 @@ KrylovView krylov_view(rfcmp_op* op, int nr) {
   K.sweeps = B.sweeps;
   K.part = B.part;
   K.ticket = B.ticket;
+  K.member = B.member;
   K.n = op->top.ne;
   K.nr = nr;
   K.G = krylov_blocks_per_column(op->top.ne);
@@ -2040,8 +2047,7 @@ KrylovView krylov_view(rfcmp_op* op, int nr) {
 }
 
 // one CG iteration of the inner solve on the active columns (Sec. 4: CG on A d = r)
-int cg_iteration(rfcmp_op* op, const KrylovView& K, int nr, GemvMode m, cudaStream_t st) {
-  SolveBuffers& B = *op->sb;
+int cg_iteration(rfcmp_op* op, SolveBuffers& B, const KrylovView& K, int nr, GemvMode m, cudaStream_t st) {
   RF_TRY(apply_A(op, B.p, B.Ap, nr, m, st));
   RF_K(krylov_cg_pap(K, B.p, B.Ap, st));
   RF_K(krylov_cg_update(K, B.p, B.Ap, B.d, B.rin, st));
@@ -2050,37 +2056,44 @@ int cg_iteration(rfcmp_op* op, const KrylovView& K, int nr, GemvMode m, cudaStre
 }
 
 // the end of a sweep: i += d, r = b - A i (float-float accurate), norms and the next decision
-int refine_step(rfcmp_op* op, const KrylovView& K, int nr, cudaStream_t st) {
-  SolveBuffers& B = *op->sb;
+int refine_step(rfcmp_op* op, SolveBuffers& B, const KrylovView& K, int nr, cudaStream_t st) {
   RF_K(krylov_add(K, B.d, B.i, st));
   RF_TRY(apply_A(op, B.i, B.tmp, nr, GEMV_FF, st));
   RF_K(krylov_refine_residual(K, B.b, B.tmp, B.r, B.i, false, st));
   return RFCMP_OK;
 }
 
-int read_ctl(rfcmp_op* op, KrylovCtl& h, cudaStream_t st) {
-  RF_CUDA(cudaMemcpyAsync(&h, op->sb->ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
+int read_ctl(const SolveBuffers& B, KrylovCtl& h, cudaStream_t st) {
+  RF_CUDA(cudaMemcpyAsync(&h, B.ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
   RF_CUDA(cudaStreamSynchronize(st));
   return RFCMP_OK;
 }
 
 // Eager driver: the same kernels launched one by one, the host reading the control block after
 // every decision (used where graphs are switched off or a capture failed).
+// One refinement sweep of the eager driver: the inner CG on the active columns (the host reading
+// the device's decision after every iteration), then i += d and the accurate residual.
+int eager_sweep(rfcmp_op* op, SolveBuffers& B, const KrylovView& K, int nr, GemvMode inner, int max_iter,
+                cudaStream_t st) {
+  KrylovCtl h{};
+  RF_K(krylov_cg_start(K, B.r, B.d, B.rin, B.p, st));
+  for (int pass = 0; pass < max_iter; ++pass) {
+    RF_TRY(cg_iteration(op, B, K, nr, inner, st));
+    RF_TRY(read_ctl(B, h, st));
+    if (h.live == 0 || h.passes >= h.max_passes) break;
+  }
+  return refine_step(op, B, K, nr, st);
+}
+
 int solve_loop_eager(rfcmp_op* op, int nr, GemvMode inner, int max_sweeps, int max_iter, cudaStream_t st) {
   SolveBuffers& B = *op->sb;
-  KrylovView K = krylov_view(op, nr);
+  KrylovView K = krylov_view(op, B, nr);
   RF_K(krylov_refine_residual(K, B.b, nullptr, B.r, B.i, true, st));
   KrylovCtl h{};
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-    RF_TRY(read_ctl(op, h, st));
+    RF_TRY(read_ctl(B, h, st));
     if (!h.go) break;
-    RF_K(krylov_cg_start(K, B.r, B.d, B.rin, B.p, st));
-    for (int pass = 0; pass < max_iter; ++pass) {
-      RF_TRY(cg_iteration(op, K, nr, inner, st));
-      RF_TRY(read_ctl(op, h, st));
-      if (h.live == 0 || h.passes >= h.max_passes) break;
-    }
-    RF_TRY(refine_step(op, K, nr, st));
+    RF_TRY(eager_sweep(op, B, K, nr, inner, max_iter, st));
   }
   return RFCMP_OK;
 }
@@ -2149,7 +2162,7 @@ int capture_solve_graph(rfcmp_op* op, int nr, GemvMode inner, int max_sweeps) {
       if (g) cudaGraphDestroy(g);
     }
   } gg{g};
-  KrylovView K = krylov_view(op, nr);
+  KrylovView K = krylov_view(op, B, nr);
   K.graph = 1;
   RF_CUDA(cudaGraphConditionalHandleCreate(&K.h_outer, g, 0, 0));
   RF_CUDA(cudaGraphConditionalHandleCreate(&K.h_inner, g, 0, 0));
@@ -2168,11 +2181,11 @@ int capture_solve_graph(rfcmp_op* op, int nr, GemvMode inner, int max_sweeps) {
     {
       RF_CUDA(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       CaptureGuard c2(s2);
-      RF_TRY(cg_iteration(op, K, nr, inner, s2));
+      RF_TRY(cg_iteration(op, B, K, nr, inner, s2));
       c2.open = false;
       RF_CUDA(cudaStreamEndCapture(s2, &body));
     }
-    RF_TRY(refine_step(op, K, nr, s1));
+    RF_TRY(refine_step(op, B, K, nr, s1));
     c1.open = false;
     RF_CUDA(cudaStreamEndCapture(s1, &outer));
   }
@@ -2231,7 +2244,7 @@ int solve_impl(rfcmp_op* op, const double2* e, double2* j, int nr, const rfcmp_s
   RF_TRY(order_stream(op, st));
   // b = -P_o^H T^H P_m e (float-float accurate)
   RF_TRY(apply_rhs(op, e, B.b, nr, GEMV_FF, st));
-  const KrylovView K = krylov_view(op, nr);
+  const KrylovView K = krylov_view(op, B, nr);
   RF_K(krylov_params(K, o.tol, o.inner_tol, o.max_iter, max_sweeps, mixed, st));
   RF_TRY(solve_loop(op, nr, inner_mode, max_sweeps, o.max_iter, st));
   // j = P_o i
@@ -2314,6 +2327,202 @@ int rfcmp_solve_host(rfcmp_op* op, const rfcmp_c128* e_host, rfcmp_c128* j_host,
   cudaFreeAsync(de, st);
   cudaFreeAsync(dj, st);
   return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batch sessions
+// A multi-column solve whose columns are admitted and retired between refinement sweeps: the
+// serving form of continuous batching.  Slots 0..cap-1 hold columns; a sweep runs the columns
+// 0..hi-1 (hi one past the highest occupied slot), where free and finished slots are out of the
+// solve (the member mask) and only cost their share of the operator products.
+struct rfcmp_batch {
+  rfcmp_op* op = nullptr;
+  int cap = 0;
+  rfcmp_solve_opts o{};
+  GemvMode inner = GEMV_F32;
+  int max_sweeps = 0;
+  std::unique_ptr<SolveBuffers> sb;
+  std::vector<int> state;  // 0 free, 1 running, 2 finished
+  std::vector<int> h_iters, h_sweeps, h_conv;
+  std::vector<double> h_res;
+  int* dslots = nullptr;     // device copy of the slots of the current admission or release
+  double2* stage = nullptr;  // N x cap: right-hand sides b of admitted columns before they move to their slots
+  ~rfcmp_batch() {
+    if (dslots) dev_free(dslots);
+    if (stage) dev_free(stage);
+  }
+};
+
+namespace {
+int batch_hi(const rfcmp_batch* b) {
+  int hi = 0;
+  for (int c = 0; c < b->cap; ++c)
+    if (b->state[c] != 0) hi = c + 1;
+  return hi;
+}
+}  // namespace
+
+extern "C" {
+
+int rfcmp_batch_create(rfcmp_op* op, int32_t capacity, const rfcmp_solve_opts* opts, rfcmp_batch** out) {
+  if (!op || !out || capacity < 1 || capacity > 4096) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  *out = nullptr;
+  auto b = std::make_unique<rfcmp_batch>();
+  RF_TRY(check_solve_opts(opts, b->o));
+  RF_CUDA(cudaSetDevice(op->ctx->device));
+  b->op = op;
+  b->cap = capacity;
+  const bool mixed = b->o.precision == RFCMP_PREC_MIXED;
+  b->inner = mixed ? GEMV_F32 : GEMV_FF;
+  b->max_sweeps = mixed ? b->o.max_refine : 1;
+  RF_TRY(ensure_workspace(op, capacity));
+  RF_TRY(alloc_solve_buffers(op, capacity, b->sb));
+  RF_TRY(dalloc(&b->sb->member, capacity, b->sb->owned));
+  RF_CUDA(cudaMemset(b->sb->member, 0, sizeof(int) * capacity));
+  for (double2* v : {b->sb->b, b->sb->i, b->sb->r})  // free slots hold zeros, never stale values
+    RF_CUDA(cudaMemset(v, 0, sizeof(double2) * (size_t)op->top.ne * capacity));
+  RF_CUDA(dev_malloc((void**)&b->dslots, sizeof(int) * capacity));
+  RF_CUDA(dev_malloc((void**)&b->stage, sizeof(double2) * (size_t)op->top.ne * capacity));
+  b->state.assign(capacity, 0);
+  b->h_iters.assign(capacity, 0);
+  b->h_sweeps.assign(capacity, 0);
+  b->h_conv.assign(capacity, 0);
+  b->h_res.assign(capacity, 0.0);
+  KrylovView K = krylov_view(op, *b->sb, capacity);
+  RF_K(krylov_params(K, b->o.tol, b->o.inner_tol, b->o.max_iter, b->max_sweeps, mixed, 0));
+  RF_CUDA(cudaStreamSynchronize(0));
+  *out = b.release();
+  return RFCMP_OK;
+}
+
+int rfcmp_batch_destroy(rfcmp_batch* b) {
+  if (!b) return RFCMP_OK;
+  cudaSetDevice(b->op->ctx->device);
+  drain_streams(b->op);
+  delete b;
+  return RFCMP_OK;
+}
+
+int rfcmp_batch_admit(rfcmp_batch* b, const rfcmp_c128* e, int32_t n, int32_t* slots, void* stream) {
+  if (!b || !e || !slots || n < 1) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  std::vector<int> free_slots;
+  for (int c = 0; c < b->cap && (int)free_slots.size() < n; ++c)
+    if (b->state[c] == 0) free_slots.push_back(c);
+  if ((int)free_slots.size() < n) return set_error(RFCMP_ERR_INVALID_ARG, "not enough free slots in the batch");
+  rfcmp_op* op = b->op;
+  RF_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  RF_TRY(ensure_workspace(op, b->cap));
+  RF_TRY(order_stream(op, st));
+  SolveBuffers& B = *b->sb;
+  const size_t N = op->top.ne;
+  // b = -P_o^H T^H P_m e (float-float accurate) for the new columns, then into their slots
+  RF_TRY(apply_rhs(op, reinterpret_cast<const double2*>(e), b->stage, n, GEMV_FF, st));
+  RF_K(vec_dot(b->stage, b->stage, (int64_t)N, n, B.dots, st));
+  for (int q = 0; q < n; ++q) {
+    const size_t off = (size_t)free_slots[q] * N;
+    RF_CUDA(cudaMemcpyAsync(B.b + off, b->stage + (size_t)q * N, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+    RF_CUDA(cudaMemcpyAsync(B.r + off, b->stage + (size_t)q * N, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+    RF_CUDA(cudaMemsetAsync(B.i + off, 0, sizeof(double2) * N, st));
+  }
+  RF_CUDA(cudaMemcpyAsync(b->dslots, free_slots.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  KrylovView K = krylov_view(op, B, b->cap);
+  RF_K(krylov_slots(K, b->dslots, n, B.dots, st));
+  RF_CUDA(cudaStreamSynchronize(st));  // the slot list on the host is reused by the next call
+  for (int q = 0; q < n; ++q) {
+    b->state[free_slots[q]] = 1;
+    slots[q] = free_slots[q];
+  }
+  return RFCMP_OK;
+}
+
+int rfcmp_batch_step(rfcmp_batch* b, int32_t* finished, int32_t* n_finished, void* stream) {
+  if (!b || !finished || !n_finished) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  *n_finished = 0;
+  rfcmp_op* op = b->op;
+  RF_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int hi = batch_hi(b);
+  bool running = false;
+  for (int c = 0; c < hi; ++c) running |= b->state[c] == 1;
+  if (!running) return RFCMP_OK;
+  RF_TRY(ensure_workspace(op, b->cap));
+  RF_TRY(order_stream(op, st));
+  SolveBuffers& B = *b->sb;
+  KrylovView K = krylov_view(op, B, hi);
+  RF_K(krylov_decide(K, st));
+  KrylovCtl h{};
+  RF_TRY(read_ctl(B, h, st));
+  if (h.live > 0) RF_TRY(eager_sweep(op, B, K, hi, b->inner, b->o.max_iter, st));
+  RF_CUDA(cudaMemcpyAsync(b->h_iters.data(), B.iters, sizeof(int) * hi, cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(b->h_sweeps.data(), B.sweeps, sizeof(int) * hi, cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(b->h_conv.data(), B.conv, sizeof(int) * hi, cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaMemcpyAsync(b->h_res.data(), B.res, sizeof(double) * hi, cudaMemcpyDeviceToHost, st));
+  int h_err = 0;
+  if (op->ws->ms.err) RF_CUDA(cudaMemcpyAsync(&h_err, op->ws->ms.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RF_CUDA(cudaStreamSynchronize(st));
+  if (h_err) {
+    RF_CUDA(cudaMemset(op->ws->ms.err, 0, sizeof(int)));
+    return set_error(RFCMP_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(h_err) + ")");
+  }
+  for (int c = 0; c < hi; ++c) {
+    if (b->state[c] != 1) continue;
+    if (b->h_conv[c] || b->h_iters[c] >= b->o.max_iter || b->h_sweeps[c] >= b->max_sweeps) {
+      b->state[c] = 2;
+      finished[(*n_finished)++] = c;
+    }
+  }
+  return RFCMP_OK;
+}
+
+int rfcmp_batch_take(rfcmp_batch* b, const int32_t* slots, int32_t n, rfcmp_c128* j, rfcmp_solve_report* reports,
+                     void* stream) {
+  if (!b || !slots || !j || n < 1 || n > b->cap) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
+  for (int q = 0; q < n; ++q) {
+    if (slots[q] < 0 || slots[q] >= b->cap) return set_error(RFCMP_ERR_INVALID_ARG, "slot out of range");
+    if (b->state[slots[q]] != 2) return set_error(RFCMP_ERR_INVALID_ARG, "slot has no finished column");
+    for (int p = 0; p < q; ++p)
+      if (slots[p] == slots[q]) return set_error(RFCMP_ERR_INVALID_ARG, "slot listed twice");
+  }
+  rfcmp_op* op = b->op;
+  RF_CUDA(cudaSetDevice(op->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  RF_TRY(ensure_workspace(op, b->cap));
+  RF_TRY(order_stream(op, st));
+  SolveBuffers& B = *b->sb;
+  const size_t N = op->top.ne;
+  // the finished columns of i side by side, then j = P_o i for all of them in one application
+  for (int q = 0; q < n; ++q)
+    RF_CUDA(cudaMemcpyAsync(b->stage + (size_t)q * N, B.i + (size_t)slots[q] * N, sizeof(double2) * N,
+                            cudaMemcpyDeviceToDevice, st));
+  RF_TRY(apply_Po(op, b->stage, reinterpret_cast<double2*>(j), n, false, GEMV_FF, st));
+  if (reports) {
+    for (int q = 0; q < n; ++q) {
+      const int c = slots[q];
+      reports[q].converged = b->h_conv[c];
+      reports[q].iterations = b->h_iters[c];
+      reports[q].refinements = b->h_sweeps[c];
+      reports[q].reserved = 0;
+      reports[q].residual = b->h_res[c];
+    }
+  }
+  RF_CUDA(cudaMemcpyAsync(b->dslots, slots, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  KrylovView K = krylov_view(op, B, b->cap);
+  RF_K(krylov_slots(K, b->dslots, n, nullptr, st));
+  RF_CUDA(cudaStreamSynchronize(st));  // the slot list on the host may go out of scope
+  for (int q = 0; q < n; ++q) b->state[slots[q]] = 0;
+  return RFCMP_OK;
+}
+
+int rfcmp_batch_counts(const rfcmp_batch* b, int32_t* running, int32_t* finished, int32_t* free_slots) {
+  if (!b) return set_error(RFCMP_ERR_INVALID_ARG, "NULL batch");
+  int r = 0, f = 0, e = 0;
+  for (int s : b->state) (s == 1 ? r : (s == 2 ? f : e))++;
+  if (running) *running = r;
+  if (finished) *finished = f;
+  if (free_slots) *free_slots = e;
+  return RFCMP_OK;
 }
 
 int rfcmp_gemm_bf16x3(const float* A, int64_t lda, const float* B, int64_t ldb, float* D, int64_t ldd, int64_t M,

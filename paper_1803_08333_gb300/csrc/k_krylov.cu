@@ -112,7 +112,10 @@ __device__ void decide(const KrylovView& K) {
     const double res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     const int conv = res <= c->tol;
     const int it = __ldcg(&K.iters[r]);
-    const int act = !conv && it < c->max_iter;
+    const bool in = K.member == nullptr || __ldcg(&K.member[r]) != 0;
+    // a column iterates while it is in the solve, above tol, and within its iteration and sweep
+    // budgets (its own sweep count: in a batch session columns join at different sweeps)
+    const int act = in && !conv && it < c->max_iter && __ldcg(&K.sweeps[r]) < c->max_sweeps;
     K.res[r] = res;
     K.conv[r] = conv;
     K.active[r] = act;
@@ -143,7 +146,7 @@ __device__ void decide(const KrylovView& K) {
       rem = max(rem, s_rem[w]);
       worst = fmax(worst, s_worst[w]);
     }
-    const bool go = live > 0 && c->sweep < c->max_sweeps;
+    const bool go = live > 0;
     double rel = 0.5 * c->tol;
     if (c->mixed) rel = fmin(fmax(c->inner_tol, 0.5 * c->tol / fmax(worst, 1e-300)), 0.5);
     c->tol2 = rel * rel;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(KT) refine_residual_kernel(KrylovView K, const
     K.rr[r] = sum.x;
     if (init)
       K.bb[r] = sum.x;
-    else
+    else if (K.member == nullptr || K.member[r])
       K.sweeps[r] += 1;
   }
   if (!all_columns_done(K)) return;
@@ -345,6 +348,31 @@ __global__ void __launch_bounds__(KT) add_cols_kernel(KrylovView K, const double
   }
 }
 
+__global__ void __launch_bounds__(KT) decide_kernel(KrylovView K) {
+  RF_COUNT_LAUNCH();
+  decide(K);
+}
+
+__global__ void __launch_bounds__(KT) slots_kernel(KrylovView K, const int* __restrict__ slots, int n,
+                                                  const double2* __restrict__ dots) {
+  RF_COUNT_LAUNCH();
+  int* member = const_cast<int*>(K.member);
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int r = slots[q];
+    const double v = dots ? dots[q].x : 0.0;
+    K.bb[r] = v;
+    K.rr[r] = v;
+    K.rho[r] = v;
+    K.r0[r] = v;
+    K.iters[r] = 0;
+    K.sweeps[r] = 0;
+    K.conv[r] = 0;
+    K.active[r] = 0;
+    K.res[r] = dots ? 1.0 : 0.0;
+    member[r] = dots ? 1 : 0;
+  }
+}
+
 inline dim3 col_grid(const KrylovView& K) { return dim3(K.G, K.nr); }
 
 }  // namespace
@@ -380,6 +408,15 @@ cudaError_t krylov_cg_update(const KrylovView& K, const double2* p, const double
 }
 cudaError_t krylov_cg_direction(const KrylovView& K, const double2* rin, double2* p, cudaStream_t s) {
   cg_direction_kernel<<<col_grid(K), KT, 0, s>>>(K, rin, p);
+  return cudaGetLastError();
+}
+cudaError_t krylov_decide(const KrylovView& K, cudaStream_t s) {
+  decide_kernel<<<1, KT, 0, s>>>(K);
+  return cudaGetLastError();
+}
+cudaError_t krylov_slots(const KrylovView& K, const int* slots, int n, const double2* dots, cudaStream_t s) {
+  if (!K.member) return cudaErrorInvalidValue;
+  slots_kernel<<<1, KT, 0, s>>>(K, slots, n, dots);
   return cudaGetLastError();
 }
 cudaError_t krylov_add(const KrylovView& K, const double2* d, double2* i, cudaStream_t s) {

@@ -353,6 +353,7 @@ struct KrylovView {
   int *active = nullptr, *conv = nullptr, *iters = nullptr, *sweeps = nullptr;
   double2* part = nullptr;       // nr x G partial sums
   unsigned int* ticket = nullptr;  // nr per-column tickets
+  const int* member = nullptr;   // batch sessions: 1 for the columns of running requests (null: all)
   int64_t n = 0;                 // rows (edges)
   int nr = 0, G = 1;
   int graph = 0;
@@ -371,6 +372,11 @@ cudaError_t krylov_cg_update(const KrylovView& K, const double2* p, const double
                              cudaStream_t s);
 cudaError_t krylov_cg_direction(const KrylovView& K, const double2* rin, double2* p, cudaStream_t s);
 cudaError_t krylov_add(const KrylovView& K, const double2* d, double2* i, cudaStream_t s);
+// the sweep decision alone (active mask, inner tolerance) from the current rr, bb, iters, sweeps
+cudaError_t krylov_decide(const KrylovView& K, cudaStream_t s);
+// batch admission: for the n new columns at slots[q] (device), bb = rr = dots[q].x, counters 0,
+// member 1; for the n columns at slots[q] with dots == nullptr: member 0, bb = rr = 0 (a freed slot)
+cudaError_t krylov_slots(const KrylovView& K, const int* slots, int n, const double2* dots, cudaStream_t s);
 
 // Smoothed-aggregation multigrid hierarchy (host side, amg.cpp).
 struct AmgLevelHost {

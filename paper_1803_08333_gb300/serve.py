@@ -2,14 +2,18 @@
 
 Requests (a mesh, a wavenumber, one or more plane waves) arrive at any time.
 The scheduler keeps assembled operators resident (their (Sigma^T Sigma)^+ and
-G_ll^{-1} factors are shared through the context's topology cache), admits a
-request when the HBM footprint of what it still needs fits the budget
-(evicting idle operators least recently used first), merges waiting requests
-for the same operator into one multi-column solve as soon as a worker is free,
-and runs several workers, each on its own CUDA stream, so that solves on
-different operators overlap on the device.  Every request records its latency
-from submission to result; ``Server.stats()`` reports p50 / p99 latency and
-solves (right-hand sides) per second.
+G_ll^{-1} factors are shared through the context's topology cache) and admits a
+request when the HBM footprint of what it still needs fits the budget (evicting
+idle operators least recently used first).  A worker that takes an operator
+opens a batch session on it (rfcmp_batch_*: one multi-column RF-CMP solve whose
+columns come and go between refinement sweeps), admits the waiting requests of
+that operator, and then runs sweep after sweep: after each sweep the finished
+columns are taken out (a request completes when its last column does) and the
+requests that arrived meanwhile for the same operator join the running solve in
+the freed slots.  Several workers, each on its own CUDA stream, serve different
+operators at once, so their work overlaps on the device.  Every request records
+its latency from submission to result; ``Server.stats()`` reports p50 / p99
+latency and solves (right-hand sides) per second.
 
 The scheduling logic only talks to a backend (``GpuBackend`` for the library,
 ``FakeBackend`` for host-side tests), so it is exercised without a GPU.
@@ -72,6 +76,7 @@ class Request:
     tol: float
     t_submit: float
     future: cf.Future = field(default_factory=cf.Future)
+    t_start: float = 0.0  # when its columns entered a solve
 
     @property
     def nrhs(self) -> int:
@@ -131,6 +136,33 @@ class GpuBackend:
             jh = j.cpu().numpy()
         return jh, rep
 
+    # batch sessions (continuous batching of one operator's solves)
+    def open_batch(self, op, capacity: int, tol: float, stream):
+        return op.batch(capacity, tol=tol)
+
+    def admit(self, session, khat, pol, stream) -> list:
+        import torch
+
+        with torch.cuda.stream(stream):
+            e = session.op.rhs_planewave(khat, pol)
+            return session.admit(e)
+
+    def step(self, session, stream) -> list:
+        import torch
+
+        with torch.cuda.stream(stream):
+            return session.step()
+
+    def take(self, session, slots: list, stream):
+        import torch
+
+        with torch.cuda.stream(stream):
+            j, rep = session.take(slots)
+            return j.cpu().numpy(), rep
+
+    def close_batch(self, session):
+        session.close()
+
     def destroy(self, op):
         op.close()
 
@@ -145,10 +177,16 @@ class GpuBackend:
 
 
 class Server:
-    def __init__(self, backend, hbm_budget: int, workers: int = 2, max_batch_columns: int = 64):
+    """continuous: serve an operator through a batch session whose columns join and leave
+    between refinement sweeps (True), or solve each merged group of waiting requests to the end
+    before the next group of that operator starts (False)."""
+
+    def __init__(self, backend, hbm_budget: int, workers: int = 2, max_batch_columns: int = 64,
+                 continuous: bool = True):
         self.backend = backend
         self.budget = int(hbm_budget)
         self.max_cols = int(max_batch_columns)
+        self.continuous = bool(continuous)
         self._lock = threading.Condition()
         self._pending: collections.OrderedDict = collections.OrderedDict()  # scene -> deque of requests
         self._ops: collections.OrderedDict = collections.OrderedDict()  # scene -> (op, widest batch), LRU order
@@ -158,6 +196,10 @@ class Server:
         self._next_id = 0
         self._closed = False
         self._latencies = []
+        self._waits = []  # submission to the start of its solve
+        self._joined = 0  # requests that joined a running solve
+        self._during = 0  # requests that arrived while their operator was solving
+        self._sessions = 0
         self._columns = 0
         self._batches = []
         self._t0 = None
@@ -179,6 +221,7 @@ class Server:
             if self._t0 is None:
                 self._t0 = req.t_submit
             self._pending.setdefault(scene, collections.deque()).append(req)
+            self._during += scene in self._busy
             self._lock.notify_all()
         return req.future
 
@@ -226,6 +269,7 @@ class Server:
     def stats(self) -> dict:
         with self._lock:
             lat = np.array(self._latencies) * 1e3
+            wt = np.array(self._waits) * 1e3
             span = (self._t_last - self._t0) if self._t0 is not None and self._t_last is not None else 0.0
             return {
                 "requests": int(lat.size),
@@ -235,6 +279,11 @@ class Server:
                 "requests_per_s": float(lat.size / span) if span > 0 else None,
                 "solves_per_s": float(self._columns / span) if span > 0 else None,
                 "mean_batch_columns": float(np.mean(self._batches)) if self._batches else None,
+                "p50_wait_ms": float(np.percentile(wt, 50)) if wt.size else None,
+                "p99_wait_ms": float(np.percentile(wt, 99)) if wt.size else None,
+                "solves": int(self._sessions),
+                "joined_running_solve": int(self._joined),
+                "arrived_during_solve": int(self._during),
                 "resident_operators": len(self._ops),
             }
 
@@ -253,11 +302,19 @@ class Server:
             nv, nc = r0.verts.shape[0], r0.tris.shape[0]
             if scene in self._ops:
                 self._ops.move_to_end(scene)
-                need = op_footprint(nv, nc, cols, with_factors=True, widest=self._ops[scene][1])
+                foot = lambda w: op_footprint(nv, nc, w, with_factors=True, widest=self._ops[scene][1])  # noqa: E731
             else:
                 shares_mesh = any(s[0] == scene[0] for s in self._ops)
-                need = op_footprint(nv, nc, cols, with_factors=not shares_mesh)
-            if need > 0 and not self._make_room(need, keep=scene):
+                foot = lambda w: op_footprint(nv, nc, w, with_factors=not shares_mesh)  # noqa: E731
+            # a session allocates its column slots up front: open it max_batch_columns wide (beyond
+            # the planes any wide solve builds, that costs only its solve vectors), else, where
+            # that cannot be made to fit, just as wide as the requests taken
+            widths = [self.max_cols, cols] if self.continuous and cols < self.max_cols else [cols]
+            for width in widths:
+                need = foot(width)
+                if need <= 0 or self._make_room(need, keep=scene):
+                    break
+            else:
                 for r in reversed(batch):  # put back: wait for memory
                     queue.appendleft(r)
                 continue
@@ -265,7 +322,7 @@ class Server:
             self._reserved += need
             if not queue:
                 del self._pending[scene]
-            return scene, batch, need
+            return scene, batch, need, width
         return None
 
     def _make_room(self, need: int, keep=None) -> bool:
@@ -310,45 +367,140 @@ class Server:
                         if self._closed and not self._pending:
                             return
                         self._lock.wait(timeout=0.05)
-                scene, batch, need = item
+                scene, batch, need, width = item
                 entry = self._ops.get(scene)
-            try:
-                if entry is None:
-                    entry = (self.backend.create(batch[0]), 1)
-                khat = np.concatenate([r.khat for r in batch])
-                pol = np.concatenate([r.pol for r in batch])
-                tol = min(r.tol for r in batch)
-                jh, rep = self.backend.solve(entry[0], khat, pol, tol, stream)
-                t_done = time.perf_counter()
-                out = []
-                c = 0
+                t_start = time.perf_counter()
                 for r in batch:
-                    sl = slice(c, c + r.nrhs)
-                    c += r.nrhs
-                    res = Result(jh[sl].copy(), [x.residual for x in rep[sl]], [x.iterations for x in rep[sl]],
-                                 t_done - r.t_submit, int(khat.shape[0]))
-                    out.append((r, res))
-                with self._lock:
-                    self._ops[scene] = (entry[0], max(entry[1], int(khat.shape[0])))
-                    self._ops.move_to_end(scene)
-                    self._busy.discard(scene)
-                    self._reserved -= need
-                    for r, res in out:
-                        self._latencies.append(res.latency_s)
-                    self._columns += int(khat.shape[0])
-                    self._batches.append(int(khat.shape[0]))
-                    self._t_last = t_done
-                    self._lock.notify_all()
+                    r.t_start = t_start
+                    self._waits.append(t_start - r.t_submit)
+                self._sessions += 1
+            if self.continuous:
+                self._serve_scene(scene, batch, need, width, entry, stream)
+            else:
+                self._serve_merged(scene, batch, need, entry, stream)
+
+    def _serve_merged(self, scene, batch, need, entry, stream):
+        """One multi-column solve of the merged requests, to the end."""
+        widest = 0
+        try:
+            if entry is None:
+                entry = (self.backend.create(batch[0]), 1)
+            khat = np.concatenate([r.khat for r in batch])
+            pol = np.concatenate([r.pol for r in batch])
+            widest = int(khat.shape[0])
+            jh, rep = self.backend.solve(entry[0], khat, pol, min(r.tol for r in batch), stream)
+            t_done = time.perf_counter()
+            out, c = [], 0
+            for r in batch:
+                sl = slice(c, c + r.nrhs)
+                c += r.nrhs
+                out.append((r, Result(jh[sl].copy(), [x.residual for x in rep[sl]], [x.iterations for x in rep[sl]],
+                                      t_done - r.t_submit, widest)))
+            with self._lock:
                 for r, res in out:
-                    r.future.set_result(res)
-            except Exception as exc:  # a failed batch fails its requests, the server keeps running
+                    self._latencies.append(res.latency_s)
+                self._columns += widest
+                self._batches.append(widest)
+                self._t_last = t_done
+            for r, res in out:
+                r.future.set_result(res)
+        except Exception as exc:  # a failed batch fails its requests, the server keeps running
+            for r in batch:
+                if not r.future.done():
+                    r.future.set_exception(exc)
+        finally:
+            with self._lock:
+                if entry is not None:
+                    self._ops[scene] = (entry[0], max(entry[1], widest))
+                    self._ops.move_to_end(scene)
+                self._busy.discard(scene)
+                self._reserved -= need
+                self._lock.notify_all()
+
+    def _serve_scene(self, scene, batch, need, width, entry, stream):
+        """One batch session on the operator of `scene`: admit, sweep, retire, admit again."""
+        session = None
+        live = {}  # request id -> [request, j rows, residuals, iterations, columns left, widest]
+        slot_of = {}  # slot -> (request id, column)
+        waiting = list(batch)  # taken from the queue, not yet in the session
+        tol = batch[0].tol
+        widest = 0
+        try:
+            if entry is None:
+                entry = (self.backend.create(batch[0]), 1)
+            op = entry[0]
+            session = self.backend.open_batch(op, width, tol, stream)
+            while True:
+                if waiting:  # all newcomers in one admission
+                    slots = self.backend.admit(session, np.concatenate([r.khat for r in waiting]),
+                                               np.concatenate([r.pol for r in waiting]), stream)
+                    q = 0
+                    for r in waiting:
+                        live[r.rid] = [r, [None] * r.nrhs, [None] * r.nrhs, [None] * r.nrhs, r.nrhs, 0]
+                        for c in range(r.nrhs):
+                            slot_of[slots[q]] = (r.rid, c)
+                            q += 1
+                    waiting = []
+                running = len(slot_of)
+                if running == 0:
+                    break
+                widest = max(widest, running)
+                for L in live.values():
+                    L[5] = max(L[5], running)
+                finished = self.backend.step(session, stream)
+                done = []
+                if finished:  # all finished columns in one take
+                    jrows, reps = self.backend.take(session, finished, stream)
+                    for sl, jrow, rep in zip(finished, jrows, reps):
+                        rid, c = slot_of.pop(sl)
+                        L = live[rid]
+                        L[1][c], L[2][c], L[3][c] = jrow, rep.residual, rep.iterations
+                        L[4] -= 1
+                        if L[4] == 0:
+                            done.append(live.pop(rid))
+                t_done = time.perf_counter()
                 with self._lock:
-                    self._busy.discard(scene)
-                    self._reserved -= need
+                    self._batches.append(running)
+                    for L in done:
+                        self._latencies.append(t_done - L[0].t_submit)
+                        self._columns += L[0].nrhs
+                        self._t_last = t_done
+                    # requests that arrived for this operator join the running solve
+                    free = width - len(slot_of)
+                    q = self._pending.get(scene)
+                    while q and q[0].tol == tol and q[0].nrhs <= free:
+                        r = q.popleft()
+                        r.t_start = t_done
+                        self._waits.append(t_done - r.t_submit)
+                        self._joined += 1
+                        waiting.append(r)
+                        free -= r.nrhs
+                    if q is not None and not q:
+                        del self._pending[scene]
                     self._lock.notify_all()
-                for r in batch:
-                    if not r.future.done():
-                        r.future.set_exception(exc)
+                for L in done:
+                    r = L[0]
+                    L[0].future.set_result(Result(np.array(L[1]), L[2], L[3], t_done - r.t_submit, L[5]))
+        except Exception as exc:  # a failed session fails its requests, the server keeps running
+            for L in list(live.values()):
+                if not L[0].future.done():
+                    L[0].future.set_exception(exc)
+            for r in waiting:
+                if not r.future.done():
+                    r.future.set_exception(exc)
+        finally:
+            if session is not None:
+                try:
+                    self.backend.close_batch(session)
+                except Exception:
+                    pass
+            with self._lock:
+                if entry is not None:
+                    self._ops[scene] = (entry[0], max(entry[1], widest))
+                    self._ops.move_to_end(scene)
+                self._busy.discard(scene)
+                self._reserved -= need
+                self._lock.notify_all()
 
 
 class FakeBackend:
@@ -395,6 +547,53 @@ class FakeBackend:
             iterations = 1
 
         return np.zeros((khat.shape[0], op["n"]), np.complex128), [_Rep() for _ in range(khat.shape[0])]
+
+    # batch sessions: a column finishes after `steps_per_column` sweeps
+    steps_per_column = 2
+
+    def open_batch(self, op, capacity: int, tol: float, stream):
+        sess = {"op": op, "cap": capacity, "slots": {}, "steps": 0}
+        self.sessions = getattr(self, "sessions", []) + [sess]
+        return sess
+
+    def admit(self, sess, khat, pol, stream) -> list:
+        n = int(khat.shape[0])
+        free = [s for s in range(sess["cap"]) if s not in sess["slots"]][:n]
+        if len(free) < n:
+            raise RuntimeError("batch full")
+        for s in free:
+            sess["slots"][s] = 0
+        op, w = sess["op"], len(sess["slots"])
+        if w > op["widest"]:
+            grow = op_footprint(op["nv"], op["nc"], w, with_factors=False, widest=op["widest"])
+            with self._lock:
+                op["lazy"] += grow
+                self.in_use += grow
+                self.max_in_use = max(self.max_in_use, self.in_use)
+            op["widest"] = w
+        return free
+
+    def step(self, sess, stream) -> list:
+        time.sleep(self.solve_seconds)
+        sess["steps"] += 1
+        fin = []
+        for s in sess["slots"]:
+            sess["slots"][s] += 1
+            if sess["slots"][s] == self.steps_per_column:
+                fin.append(s)
+        return fin
+
+    def take(self, sess, slots: list, stream):
+        class _Rep:
+            residual = 0.0
+            iterations = 1
+
+        for s in slots:
+            del sess["slots"][s]
+        return np.zeros((len(slots), sess["op"]["n"]), np.complex128), [_Rep() for _ in slots]
+
+    def close_batch(self, sess):
+        pass
 
     def destroy(self, op):
         with self._lock:

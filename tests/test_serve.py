@@ -29,19 +29,51 @@ def test_all_requests_complete_with_their_columns():
     assert st["p50_ms"] is not None and st["p99_ms"] >= st["p50_ms"]
 
 
-def test_waiting_requests_of_one_operator_are_merged():
+def test_requests_join_a_running_solve_between_sweeps():
     be = serve.FakeBackend(solve_seconds=0.05)
+    be.steps_per_column = 3
     srv = serve.Server(be, hbm_budget=0, workers=1, max_batch_columns=64)
     v, t = _mesh(2)
     kh, pol = synth.plane_wave_z()
     first = srv.submit(v, t, 1.0, kh, pol)
-    time.sleep(0.02)  # the first solve is running; these queue behind it
+    time.sleep(0.02)  # the first solve is in its first sweep; these join it at the next sweep
     rest = [srv.submit(v, t, 1.0, kh, pol) for _ in range(5)]
-    first.result(timeout=10)
-    sizes = {f.result(timeout=10).batch_columns for f in rest}
+    r0 = first.result(timeout=10)
+    rr = [f.result(timeout=10) for f in rest]
     srv.close()
-    assert sizes == {5}
+    assert len(be.sessions) == 1  # one running solve took all six requests
+    assert srv.stats()["joined_running_solve"] == 5
+    assert r0.batch_columns == 6 and {r.batch_columns for r in rr} == {6}
+    assert r0.latency_s < min(r.latency_s + 0.02 for r in rr) + 0.06  # the first left before the others
     assert len(be.created) == 1  # the operator stayed resident
+
+
+def test_merged_mode_solves_waiting_requests_together():
+    be = serve.FakeBackend(solve_seconds=0.05)
+    srv = serve.Server(be, hbm_budget=0, workers=1, max_batch_columns=64, continuous=False)
+    v, t = _mesh(2)
+    kh, pol = synth.plane_wave_z()
+    first = srv.submit(v, t, 1.0, kh, pol)
+    time.sleep(0.02)  # the first solve is running; these queue behind it and merge
+    rest = [srv.submit(v, t, 1.0, kh, pol) for _ in range(5)]
+    assert first.result(timeout=10).batch_columns == 1
+    assert {f.result(timeout=10).batch_columns for f in rest} == {5}
+    st = srv.stats()
+    srv.close()
+    assert st["solves"] == 2 and st["joined_running_solve"] == 0
+    assert not getattr(be, "sessions", [])
+
+
+def test_a_full_session_leaves_the_rest_waiting():
+    be = serve.FakeBackend(solve_seconds=0.02)
+    srv = serve.Server(be, hbm_budget=0, workers=1, max_batch_columns=4)
+    v, t = _mesh(2)
+    kh, pol = synth.random_plane_waves(3, seed=1)
+    futs = [srv.submit(v, t, 1.0, kh, pol) for _ in range(4)]  # 12 columns through 4 slots
+    res = [f.result(timeout=10) for f in futs]
+    srv.close()
+    assert all(r.j.shape[0] == 3 for r in res)
+    assert max(srv.stats()["mean_batch_columns"] for _ in [0]) <= 4
 
 
 def test_admission_respects_the_budget_and_evicts_lru():
@@ -61,10 +93,10 @@ def test_admission_respects_the_budget_and_evicts_lru():
 
 def test_a_failing_batch_fails_only_its_requests():
     class Flaky(serve.FakeBackend):
-        def solve(self, op, khat, pol, tol, stream):
-            if op["scene"][1] == 2.0:
+        def admit(self, sess, khat, pol, stream):
+            if sess["op"]["scene"][1] == 2.0:
                 raise RuntimeError("boom")
-            return super().solve(op, khat, pol, tol, stream)
+            return super().admit(sess, khat, pol, stream)
 
     srv = serve.Server(Flaky(), hbm_budget=0, workers=2)
     v, t = _mesh(2)
