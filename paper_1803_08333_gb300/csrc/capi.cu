@@ -496,7 +496,6 @@ int ensure_workspace(rfcmp_op* op, int cols) {
     ws->gs.cap_cols = 4;
     RF_TRY(dalloc(&ws->gs.xh, (size_t)ws->gs.cap_ld * 4, ws->owned));
     RF_TRY(dalloc(&ws->gs.xl, (size_t)ws->gs.cap_ld * 4, ws->owned));
-    RF_TRY(dalloc(&ws->gs.acc, (size_t)capn * 4, ws->owned));
     // one error flag for every bounded device-side wait (streaming GEMV, tensor-core products)
     RF_TRY(dalloc(&ws->ms.err, 1, ws->owned));
     RF_CUDA(cudaMemset(ws->ms.err, 0, sizeof(int)));

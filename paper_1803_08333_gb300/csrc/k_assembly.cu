@@ -31,6 +31,14 @@ constexpr int FAR_THREADS = 256;  // 32 s-cells x 8 t-lanes
 constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI = 0.0795774715459476679;
 
+// 1/sqrt(x) with subnormal inputs and results flushed to zero: the hardware approximation alone,
+// without the rescaling a subnormal operand would need (far-pair distances are far from it)
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // sin and cos of |r| <= pi/4 in FP32: Taylor series of sin to r^9 and of cos to r^8
 // (truncation below 4e-9).
 __device__ __forceinline__ void sincos_quarter(float r, float* s, float* c) {
@@ -192,7 +200,7 @@ __device__ __forceinline__ void far_moments(const TileCells& S, int sl, const So
     for (int j = 0; j < 7; ++j) {
       const float4 q = Q.qn[tl][j];
       const float r2 = fmaf(Dx, q.x, fmaf(Dy, q.y, fmaf(Dz, q.z, A + q.w)));
-      const float rinv = rsqrtf(r2);
+      const float rinv = rsqrt_ftz(r2);
       const float R = r2 * rinv;
       float sn, cs;
       if (SHIFTED == 2) {
@@ -280,18 +288,17 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
   RF_COUNT_LAUNCH();
   __shared__ TileCells S, Tt;
   __shared__ SourceTile Q;
-  // linear tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
-  long long tix = blockIdx.x;
-  int bi = 0;
-  {
-    long long rem = tix;
-    while (rem >= nb - bi) {
-      rem -= nb - bi;
-      ++bi;
-    }
-    tix = rem;
-  }
-  const int bj = bi + (int)tix;
+  // linear tile index -> (bi, bj), bi <= bj, row-major over the upper triangle: row bi starts at
+  // T(bi) = bi (2 nb - bi + 1) / 2, so bi is the root of T(bi) = tix rounded down, corrected by
+  // at most a step either way for the rounding of the square root
+  const long long tix = blockIdx.x;
+  const double b2 = 2.0 * nb + 1.0;
+  int bi = (int)floor(0.5 * (b2 - sqrt(fmax(b2 * b2 - 8.0 * (double)tix, 0.0))));
+  bi = max(0, min(bi, nb - 1));
+  auto row_start = [nb](long long r) { return r * (2LL * nb - r + 1) / 2; };
+  if (row_start(bi) > tix) --bi;
+  else if (bi + 1 < nb && row_start(bi + 1) <= tix) ++bi;
+  const int bj = bi + (int)(tix - row_start(bi));
   load_tiles(S, Tt, Q, g, bi * TILE, bj * TILE);
 
   const int sl = threadIdx.x >> 3;

@@ -77,8 +77,8 @@ __device__ __forceinline__ void ff_acc(float& hi, float& lo, float a, float bh, 
 template <bool CONJ>
 __global__ void __launch_bounds__(STHREADS, FF_NCTA)
 gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
-                      const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr,
-                      int* __restrict__ err) {
+                      const float2* __restrict__ xl, double2* __restrict__ out, double scale, long long units,
+                      int upr, int* __restrict__ err) {
   RF_COUNT_LAUNCH();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -133,8 +133,8 @@ gemv_stream_ff_kernel(const float2* __restrict__ M, int ld, int n, const float2*
     fh[0] = fh[1] = fl[0] = fl[1] = 0.f;
     if (lane == 0 && row < n) {
       double* o = reinterpret_cast<double*>(out + row);
-      atomicAdd(o, re);
-      atomicAdd(o + 1, im);
+      atomicAdd(o, scale * re);
+      atomicAdd(o + 1, scale * im);
     }
   };
   long long cur_rb = -1;
@@ -305,7 +305,7 @@ __device__ __forceinline__ void sym_tile(const uint8_t* st, int qc, int row0, in
 template <int NR, bool REAL, bool CONJ, int NCTA>
 __global__ void __launch_bounds__(STHREADS, NCTA)
 gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __restrict__ xh,
-                double2* __restrict__ out, long long units, int* __restrict__ err) {
+                double2* __restrict__ out, double scale, long long units, int* __restrict__ err) {
   RF_COUNT_LAUNCH();
   constexpr int NST = SymStage<NR, REAL, NCTA>::NST;
   constexpr int STG = SymStage<NR, REAL, NCTA>::BYTES;
@@ -397,8 +397,8 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
       for (int e = 0; e < EPQ; ++e) {
         if (j0 + e < n) {
           double* o = reinterpret_cast<double*>(out + (size_t)r * n + j0 + e);
-          atomicAdd(o, (double)ca[r][e][0] + (double)cc[r][e][0]);
-          atomicAdd(o + 1, (double)ca[r][e][1] + (double)cc[r][e][1]);
+          atomicAdd(o, scale * ((double)ca[r][e][0] + (double)cc[r][e][0]));
+          atomicAdd(o + 1, scale * ((double)ca[r][e][1] + (double)cc[r][e][1]));
         }
         ca[r][e][0] = ca[r][e][1] = cc[r][e][0] = cc[r][e][1] = 0.f;
       }
@@ -472,7 +472,7 @@ gemv_sym_kernel(const void* __restrict__ Mv, int ld, int n, const float2* __rest
         for (int w2 = 0; w2 < SROWS; ++w2) sum += red[w2 * V + lane];
         const int rr = lane / (2 * NR), r = (lane / 2) % NR, z = lane & 1;
         const int row = row0 + rr;
-        if (row < n) atomicAdd(reinterpret_cast<double*>(out + (size_t)r * n + row) + z, (double)sum);
+        if (row < n) atomicAdd(reinterpret_cast<double*>(out + (size_t)r * n + row) + z, scale * (double)sum);
       }
     }
     __syncwarp();
@@ -510,7 +510,7 @@ cudaError_t launch_sym(const void* M, int ld, int n, GemvScratch& w, cudaStream_
   const SymGeom G = sym_geom(n, ld, SEG);
   const long long units = G.off(G.S);
   const int grid = (int)std::max(1LL, std::min<long long>(units, (long long)NCTA * sms));
-  k<<<grid, STHREADS, SMEM, s>>>(M, ld, n, w.xh, w.acc, units, w.err);
+  k<<<grid, STHREADS, SMEM, s>>>(M, ld, n, w.xh, w.out, w.scale, units, w.err);
   return cudaGetLastError();
 }
 
@@ -532,7 +532,7 @@ cudaError_t launch_stream_ff(const float2* M, int ld, int n, GemvScratch& w, cud
   const int upr = (ld + SEG - 1) / SEG;
   const long long units = (long long)((n + SROWS - 1) / SROWS) * upr;
   const int grid = (int)std::max(1LL, std::min<long long>(units, (long long)FF_NCTA * sms));
-  k<<<grid, STHREADS, FF_NST * SSTAGE + 256, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, w.err);
+  k<<<grid, STHREADS, FF_NST * SSTAGE + 256, s>>>(M, ld, n, w.xh, w.xl, w.out, w.scale, units, upr, w.err);
   return cudaGetLastError();
 }
 

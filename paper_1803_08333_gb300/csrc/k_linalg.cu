@@ -57,7 +57,7 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
 
 // x (complex128, n x nr) -> FP32 hi (and lo) copies padded to ld, and zero the accumulator
 __global__ void gemv_prep_kernel(const double2* __restrict__ x, int n, int ld, int nr, float2* __restrict__ xh,
-                                 float2* __restrict__ xl, double2* __restrict__ acc, int acc_n) {
+                                 float2* __restrict__ xl, double2* __restrict__ y) {
   RF_COUNT_LAUNCH();
   const int r = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x) {
@@ -65,31 +65,15 @@ __global__ void gemv_prep_kernel(const double2* __restrict__ x, int n, int ld, i
     const float2 h = make_float2((float)v.x, (float)v.y);
     xh[(size_t)r * ld + i] = h;
     if (xl) xl[(size_t)r * ld + i] = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
-    if (i < acc_n) acc[(size_t)r * acc_n + i] = make_double2(0.0, 0.0);
+    // the product adds into y: a fresh product starts from zero (x is read above, first)
+    if (y && i < n) y[(size_t)r * n + i] = make_double2(0.0, 0.0);
   }
 }
 
-// y = scale * acc (+ y)
-__global__ void gemv_finalize_kernel(const double2* __restrict__ acc, int n, int nr, double2 scale, int accumulate,
-                                     double2* __restrict__ y) {
-  RF_COUNT_LAUNCH();
-  const int r = blockIdx.y;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double2 a = acc[(size_t)r * n + i];
-    double2 o = make_double2(scale.x * a.x - scale.y * a.y, scale.x * a.y + scale.y * a.x);
-    if (accumulate) {
-      const double2 p = y[(size_t)r * n + i];
-      o.x += p.x;
-      o.y += p.y;
-    }
-    y[(size_t)r * n + i] = o;
-  }
-}
-
-// Flushes the per-lane FP64 row sums of one row block into the accumulator.
+// Adds scale times the per-lane FP64 row sums of one row block into the output.
 template <int NR>
 __device__ __forceinline__ void flush_rows(double (&acc)[GEMV_ROWS_PER_WARP][NR][2], int row0, int n, int lane,
-                                           double2* __restrict__ out) {
+                                           double2* __restrict__ out, double scale) {
 #pragma unroll
   for (int a = 0; a < GEMV_ROWS_PER_WARP; ++a)
 #pragma unroll
@@ -99,8 +83,8 @@ __device__ __forceinline__ void flush_rows(double (&acc)[GEMV_ROWS_PER_WARP][NR]
       acc[a][r][0] = acc[a][r][1] = 0.0;
       if (lane == 0 && row0 + a < n) {
         double* o = reinterpret_cast<double*>(out + (size_t)r * n + row0 + a);
-        atomicAdd(o, re);
-        atomicAdd(o + 1, im);
+        atomicAdd(o, scale * re);
+        atomicAdd(o + 1, scale * im);
       }
     }
 }
@@ -111,7 +95,7 @@ __device__ __forceinline__ void flush_rows(double (&acc)[GEMV_ROWS_PER_WARP][NR]
 template <int NR, bool FF, bool CONJ>
 __global__ void __launch_bounds__(GEMV_WARPS * 32)
 gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const float2* __restrict__ xh,
-                const float2* __restrict__ xl, double2* __restrict__ out, long long units, int upr, int chunk) {
+                const float2* __restrict__ xl, double2* __restrict__ out, double scale, long long units, int upr, int chunk) {
   RF_COUNT_LAUNCH();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
@@ -125,7 +109,7 @@ gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const float2* __res
     const int rb = (int)(u / upr), cc = (int)(u % upr);
     const int row0 = rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP;
     if (rb != cur_rb) {
-      if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
+      if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out, scale);
       cur_rb = rb;
     }
     const int cb = cc * chunk;
@@ -192,14 +176,14 @@ gemv_c64_kernel(const float2* __restrict__ M, int ld, int n, const float2* __res
         acc[a][r][1] += (double)fh[a][r][1] + (double)fl[a][r][1];
       }
   }
-  if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
+  if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out, scale);
 }
 
 // ---------------------------------------------------------------- real (hi + lo) GEMV (persistent)
 template <int NR, bool FF>
 __global__ void __launch_bounds__(GEMV_WARPS * 32)
 gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, int ld, int n,
-                const float2* __restrict__ xh, const float2* __restrict__ xl, double2* __restrict__ out,
+                const float2* __restrict__ xh, const float2* __restrict__ xl, double2* __restrict__ out, double scale,
                 long long units, int upr, int chunk) {
   RF_COUNT_LAUNCH();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -214,7 +198,7 @@ gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, in
     const int rb = (int)(u / upr), cc = (int)(u % upr);
     const int row0 = rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP;
     if (rb != cur_rb) {
-      if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
+      if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out, scale);
       cur_rb = rb;
     }
     const int cb = cc * chunk;
@@ -294,7 +278,7 @@ gemv_r32_kernel(const float* __restrict__ Mhi, const float* __restrict__ Mlo, in
         acc[a][r][1] += (double)fh[a][r][1] + (double)fl[a][r][1];
       }
   }
-  if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out);
+  if (cur_rb >= 0) flush_rows<NR>(acc, (int)cur_rb * GEMV_ROWS + warp * GEMV_ROWS_PER_WARP, n, lane, out, scale);
 }
 
 // persistent grid: SMs x resident CTAs of this kernel (cached per kernel and device)
@@ -332,15 +316,14 @@ long long gemv_grid(K kernel, long long units, const GemvScratch& w) {
 
 int gemv_chunk(const GemvScratch& w) { return w.chunk > 0 ? w.chunk : GEMV_CHUNK; }
 
-cudaError_t gemv_prep(const double2* x, int n, int ld, int nr, bool ff, GemvScratch& w, cudaStream_t s) {
+// x -> FP32 hi (and lo) in w.xh / w.xl; y zeroed unless the product accumulates into it; the
+// product that follows adds scale times its partial sums into y
+cudaError_t gemv_prep(const double2* x, double2* y, int n, int ld, int nr, bool ff, bool accumulate, double scale,
+                      GemvScratch& w, cudaStream_t s) {
+  w.out = y;
+  w.scale = scale;
   dim3 grid(std::min((ld + 255) / 256, 4 * 152), nr);
-  gemv_prep_kernel<<<grid, 256, 0, s>>>(x, n, ld, nr, w.xh, ff ? w.xl : nullptr, w.acc, n);
-  return cudaGetLastError();
-}
-
-cudaError_t gemv_finalize(int n, int nr, double2 scale, bool acc, double2* y, GemvScratch& w, cudaStream_t s) {
-  dim3 grid(std::min((n + 255) / 256, 4 * 152), nr);
-  gemv_finalize_kernel<<<grid, 256, 0, s>>>(w.acc, n, nr, scale, acc ? 1 : 0, y);
+  gemv_prep_kernel<<<grid, 256, 0, s>>>(x, n, ld, nr, w.xh, ff ? w.xl : nullptr, accumulate ? nullptr : y);
   return cudaGetLastError();
 }
 
@@ -362,7 +345,7 @@ cudaError_t gemv_c64_dispatch(const float2* M, int ld, int n, bool conj, GemvMod
   {                                                                                               \
     auto k = gemv_c64_kernel<NR, FFV, CJ>;                                                        \
     const int grid = (int)gemv_grid(k, units, w);                                                 \
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, chunk);           \
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.out, w.scale, units, upr, chunk);           \
   }
   if (mode == GEMV_FF) {
     if (conj) RF_LAUNCH_C(true, true) else RF_LAUNCH_C(true, false)
@@ -387,11 +370,11 @@ cudaError_t gemv_r32_dispatch(const float* Mhi, const float* Mlo, int ld, int n,
   if (mode == GEMV_FF) {
     auto k = gemv_r32_kernel<NR, true>;
     const int grid = (int)gemv_grid(k, units, w);
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr, chunk);
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.out, w.scale, units, upr, chunk);
   } else {
     auto k = gemv_r32_kernel<NR, false>;
     const int grid = (int)gemv_grid(k, units, w);
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.acc, units, upr, chunk);
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(Mhi, Mlo, ld, n, w.xh, w.xl, w.out, w.scale, units, upr, chunk);
   }
   return cudaGetLastError();
 }
@@ -442,21 +425,22 @@ void dev_pool_trim() {
   }
 }
 
-// y = scale * op(M) x (+ y): prep (x -> FP32 hi/lo, zero accumulator), persistent GEMV, finalize.
+// y = scale * op(M) x (+ y) for a real scale: prep (x -> FP32 hi/lo, y zeroed unless it
+// accumulates), then the GEMV, whose CTAs add scale times their FP64 partial sums into y.
 cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate, double2 scale,
                      bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s) {
   const int ld = padded_ld(n);
+  if (scale.y != 0.0) return cudaErrorInvalidValue;
   cudaError_t err = cudaSuccess;
   for (int r = 0; r < nrhs && err == cudaSuccess;) {
     const int nr = std::min(4, nrhs - r) >= 4 ? 4 : (nrhs - r >= 2 ? 2 : 1);
     if (n > w.cap_n || ld > w.cap_ld || nr > w.cap_cols) return cudaErrorInvalidValue;
     const double2* xr = x + (size_t)r * n;
     double2* yr = y + (size_t)r * n;
-    if ((err = gemv_prep(xr, n, ld, nr, mode == GEMV_FF, w, s)) != cudaSuccess) break;
+    if ((err = gemv_prep(xr, yr, n, ld, nr, mode == GEMV_FF, accumulate, scale.x, w, s)) != cudaSuccess) break;
     if (nr == 4) err = gemv_c64_dispatch<4>(M, ld, n, conjugate, mode, w, s);
     else if (nr == 2) err = gemv_c64_dispatch<2>(M, ld, n, conjugate, mode, w, s);
     else err = gemv_c64_dispatch<1>(M, ld, n, conjugate, mode, w, s);
-    if (err == cudaSuccess) err = gemv_finalize(n, nr, scale, accumulate, yr, w, s);
     r += nr;
   }
   return err;
@@ -475,7 +459,7 @@ cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y,
     if (n > w.cap_n || ld > w.cap_ld || nr > w.cap_cols) return cudaErrorInvalidValue;
     const double2* xr = x + (size_t)r * n;
     double2* yr = y + (size_t)r * n;
-    if ((err = gemv_prep(xr, n, ld, nr, mode == GEMV_FF, w, s)) != cudaSuccess) break;
+    if ((err = gemv_prep(xr, yr, n, ld, nr, mode == GEMV_FF, false, 1.0, w, s)) != cudaSuccess) break;
     const int rowblocks = (n + GEMV_ROWS - 1) / GEMV_ROWS;
     const int upr = (ld + GEMV_CHUNK - 1) / GEMV_CHUNK;
     const long long units = (long long)rowblocks * upr;
@@ -486,7 +470,7 @@ cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y,
         cudaSuccess)                                                                             \
       break;                                                                                     \
     const int grid = (int)std::min<long long>(units, (long long)sms * std::max(1, per));         \
-    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.acc, units, upr, GEMV_CHUNK);     \
+    k<<<grid, GEMV_WARPS * 32, 0, s>>>(M, ld, n, w.xh, w.xl, w.out, w.scale, units, upr, GEMV_CHUNK);     \
   }
 #define RF_PLAIN_NR(NRV)                                           \
   if (mode == GEMV_FF) {                                           \
@@ -504,7 +488,6 @@ cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y,
 #undef RF_PLAIN_NR
 #undef RF_PLAIN
     if ((err = cudaGetLastError()) != cudaSuccess) break;
-    err = gemv_finalize(n, nr, make_double2(1.0, 0.0), false, yr, w, s);
     r += nr;
   }
   return err;
@@ -519,11 +502,10 @@ cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x
     if (n > w.cap_n || ld > w.cap_ld || nr > w.cap_cols) return cudaErrorInvalidValue;
     const double2* xr = x + (size_t)r * n;
     double2* yr = y + (size_t)r * n;
-    if ((err = gemv_prep(xr, n, ld, nr, mode == GEMV_FF, w, s)) != cudaSuccess) break;
+    if ((err = gemv_prep(xr, yr, n, ld, nr, mode == GEMV_FF, accumulate, scale, w, s)) != cudaSuccess) break;
     if (nr == 4) err = gemv_r32_dispatch<4>(Mhi, Mlo, ld, n, mode, w, s);
     else if (nr == 2) err = gemv_r32_dispatch<2>(Mhi, Mlo, ld, n, mode, w, s);
     else err = gemv_r32_dispatch<1>(Mhi, Mlo, ld, n, mode, w, s);
-    if (err == cudaSuccess) err = gemv_finalize(n, nr, make_double2(scale, 0.0), accumulate, yr, w, s);
     r += nr;
   }
   return err;

@@ -70,8 +70,8 @@ extern "C" int rfcmp_apply_ta_noalloc(const rfcmp_op* op, const rfcmp_c128* x, r
     GemvScratch w;
     w.xh = reinterpret_cast<float2*>(b);
     w.xl = reinterpret_cast<float2*>(b + NOALLOC_MAX * sizeof(float2));
-    w.acc = reinterpret_cast<double2*>(b + 2 * NOALLOC_MAX * sizeof(float2));
-    // the GEMV runs column chunks of at most 4; each chunk uses ld x cols of x and n x cols of acc
+    // the GEMV runs column chunks of at most 4; each chunk uses ld x cols of x (hi and lo) and
+    // adds its partial sums straight into y
     w.cap_cols = (int)nrhs;
     w.cap_ld = (int)(NOALLOC_MAX / nrhs);
     w.cap_n = w.cap_ld;

@@ -242,7 +242,8 @@ enum GemvMode { GEMV_F32 = 0, GEMV_FF = 1 };
 struct GemvScratch {
   float2* xh = nullptr;   // cap_cols x cap_ld
   float2* xl = nullptr;   // cap_cols x cap_ld
-  double2* acc = nullptr; // cap_cols x cap_n
+  double2* out = nullptr; // y of the current product (set per call): CTAs add scale * partial sums
+  double scale = 1.0;     // real factor of the current product
   int cap_n = 0, cap_ld = 0, cap_cols = 0;
   int chunk = 0;          // columns per work unit (multiple of 256; 0 = 1024)
   int ctas_per_sm = 0;    // persistent CTAs per SM (0 = occupancy maximum)
@@ -250,8 +251,8 @@ struct GemvScratch {
   bool symmetric = false; // every matrix this scratch serves is symmetric: read the upper triangle
 };
 // Streaming FP32-mode GEMV of a symmetric matrix (k_gemv_stream.cu; w.symmetric must be set): the
-// prepared x (w.xh) times the complex64 or FP32 matrix into the FP64 accumulator w.acc, the
-// upper triangle streamed by bulk copies; NR = 1 or 2.
+// prepared x (w.xh) times the complex64 or FP32 matrix, w.scale times it added into the FP64
+// output w.out, the upper triangle streamed by bulk copies; NR = 1 or 2.
 template <int NR>
 cudaError_t gemv_stream_c64(const float2* M, int ld, int n, bool conj, GemvScratch& w, cudaStream_t s);
 template <int NR>

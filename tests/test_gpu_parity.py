@@ -323,8 +323,8 @@ def test_multi_rhs_tensor_core_path(ctx, memo, name, k):
 
 
 def test_launch_counter_counts_every_kernel(ctx, memo):
-    """The device launch counter sees each kernel of an application: the split of x, the
-    streaming GEMV and the scaling of the accumulator, at least."""
+    """The device launch counter sees each kernel of an application: the split of x (which also
+    zeroes y) and the streaming GEMV, whose CTAs add their scaled partial sums into y."""
     import torch
 
     m, _, _, _ = _oracle(memo, "l2", 1.0)
@@ -337,5 +337,5 @@ def test_launch_counter_counts_every_kernel(ctx, memo):
     n1 = rf.launch_count()
     op.apply("T_A", x)
     n2 = rf.launch_count()
-    assert n1 - n0 >= 3
+    assert n1 - n0 == 2
     assert n2 - n1 == n1 - n0  # the same call launches the same kernels
