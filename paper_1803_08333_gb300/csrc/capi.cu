@@ -672,7 +672,7 @@ int ensure_digits(rfcmp_op* op, cudaStream_t st) {
 // y = scale * op(M) x (+ y) for M = T_A or V: GEMV, or the tensor-core product for wide FP32 blocks
 // (split-BF16 in the inner iterations, exact digits where float-float accuracy is asked)
 int prod_c(rfcmp_op* op, bool ta, const double2* x, double2* y, int nr, bool conj, double2 scale, bool acc,
-           GemvMode m, cudaStream_t st) {
+           GemvMode m, cudaStream_t st, bool fed = false) {
   if (m == GEMV_FF && nr >= plan_exact(op)) {
     RF_TRY(ensure_digits(op, st));
     RF_K(exact_cplx_gemm(ta ? op->ta_digits : op->v_digits, ta ? (int)op->top.ne : (int)op->top.nc, x, y, nr, conj,
@@ -685,13 +685,13 @@ int prod_c(rfcmp_op* op, bool ta, const double2* x, double2* y, int nr, bool con
     return RFCMP_OK;
   }
   RF_K(gemv_c64(ta ? op->TA : op->V, ta ? (int)op->top.ne : (int)op->top.nc, x, y, nr, conj, scale, acc, m,
-                op->ws->gs, st));
+                op->ws->gs, st, fed));
   return RFCMP_OK;
 }
 
 // y = scale * F x (+ y) for a dense real factor
 int prod_r(rfcmp_op* op, DenseFactor& f, const double2* x, double2* y, int nr, double scale, bool acc, GemvMode m,
-           cudaStream_t st) {
+           cudaStream_t st, bool fed = false) {
   if (m == GEMV_FF && nr >= plan_exact(op)) {
     RF_TRY(ensure_digits(op, st));
     RF_K(exact_real_gemm(f.digits, f.n, x, y, nr, scale, acc, op->ws->ms, st));
@@ -702,8 +702,28 @@ int prod_r(rfcmp_op* op, DenseFactor& f, const double2* x, double2* y, int nr, d
     RF_K(real_gemm(f.planes, x, y, nr, scale, acc, op->ws->ms, st));
     return RFCMP_OK;
   }
-  RF_K(gemv_r32(f.hi, f.lo, f.n, x, y, nr, scale, acc, m, op->ws->gs, st));
+  RF_K(gemv_r32(f.hi, f.lo, f.n, x, y, nr, scale, acc, m, op->ws->gs, st, fed));
   return RFCMP_OK;
+}
+
+// Whether prod_c / prod_r of nr columns in mode m take the GEMV (1, 2 or 4 columns below the
+// tensor-core widths), so that the sparse kernel producing their x can write its split
+// (GemvFeed) and the GEMV skip its own.
+bool gemv_feedable(const rfcmp_op* op, int nr, GemvMode m) {
+  if (nr != 1 && nr != 2 && nr != 4) return false;
+  return m == GEMV_FF ? nr < plan_exact(op) : nr < plan_mrhs(op);
+}
+
+// the feed of a length-n vector whose GEMV writes y (and a second GEMV of it y2); none if !on
+GemvFeed make_feed(rfcmp_op* op, bool on, int n, GemvMode m, double2* y, double2* y2 = nullptr) {
+  GemvFeed f;
+  if (!on) return f;
+  f.xh = op->ws->gs.xh;
+  f.xl = m == GEMV_FF ? op->ws->gs.xl : nullptr;
+  f.ld = padded_ld(n);
+  f.y = y;
+  f.y2 = y2;
+  return f;
 }
 
 // ---- building blocks of the application, nrhs columns, column-major ----
@@ -725,27 +745,30 @@ int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cu
   const DeviceGeometry& g = op->g;
   const double k = op->k, a = op->alpha, b = op->beta, gm = op->gamma;
   const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
-  // s = Sigma^T x, z = L^+ s
-  RF_TRY(star_coeff(op, x, W.s, W.z, nr, m, st));
-  // v = (ik/a) x - (ik/a + k/b) Sigma z      = i k x_L / a - k x_S / b
+  // every sparse kernel below writes the split of its output for the GEMV that reads it next
+  const bool fd = gemv_feedable(op, nr, m);
+  // s = Sigma^T x, z = L^+ s ; w = V Sigma^T x / (k b) (the same split of s)
+  RF_K(sigma_t(g, x, W.s, nr, st, make_feed(op, fd, C, m, W.z, W.w)));
+  RF_TRY(prod_r(op, *op->lplus, W.s, W.z, nr, 1.0, false, m, st, fd));
+  RF_TRY(prod_c(op, false, W.s, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, st, fd));
+  // v = (ik/a) x - (ik/a + k/b) Sigma z      = i k x_L / a - k x_S / b ; u = T_A v
   {
     EdgeCombo c;
     c.x = x;
     c.a = c2(0.0, k / a);
     c.zs = W.z;
     c.b = c2(-k / b, -k / a);
-    RF_K(edge_combo(g, c, W.v, nr, st));
+    RF_K(edge_combo(g, c, W.v, nr, st, make_feed(op, fd, N, m, W.u)));
   }
-  // u = T_A v ; w = V Sigma^T x / (k b)
-  RF_TRY(prod_c(op, true, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, st));
-  RF_TRY(prod_c(op, false, W.s, W.w, nr, false, c2(1.0 / (k * b), 0.0), false, m, st));
+  RF_TRY(prod_c(op, true, W.v, W.u, nr, false, c2(1.0, 0.0), false, m, st, fd));
   // zu = L^+ Sigma^T u ; tg = G_ll^{-1} Lambda^T u
-  RF_TRY(star_coeff(op, W.u, W.s, W.zu, nr, m, st));
-  RF_K(lambda_t(g, W.u, W.t, nr, st));
-  RF_TRY(prod_r(op, *op->gll, W.t, W.tg, nr, 1.0, false, m, st));
+  RF_K(sigma_t(g, W.u, W.s, nr, st, make_feed(op, fd, C, m, W.zu)));
+  RF_TRY(prod_r(op, *op->lplus, W.s, W.zu, nr, 1.0, false, m, st, fd));
+  RF_K(lambda_t(g, W.u, W.t, nr, st, make_feed(op, fd, NV, m, W.tg)));
+  RF_TRY(prod_r(op, *op->gll, W.t, W.tg, nr, 1.0, false, m, st, fd));
   // q = L^+ G_pp^{-1} (zu + w - mean(w)) / b^2
-  RF_K(star_middle(g, W.zu, W.w, 1.0, W.q0, nr, W.mean, st));
-  RF_TRY(prod_r(op, *op->lplus, W.q0, W.q, nr, 1.0 / (b * b), false, m, st));
+  RF_K(star_middle(g, W.zu, W.w, 1.0, W.q0, nr, W.mean, st, make_feed(op, fd, C, m, W.q)));
+  RF_TRY(prod_r(op, *op->lplus, W.q0, W.q, nr, 1.0 / (b * b), false, m, st, fd));
   // y = Lambda tg / a^2 + (u - Sigma zu) / gamma + Sigma q
   {
     EdgeCombo c;
@@ -757,14 +780,15 @@ int apply_A(rfcmp_op* op, const double2* x, double2* out, int nr, GemvMode m, cu
     c.b = c2(-1.0 / gm, 0.0);
     c.zs2 = W.q;
     c.d = c2(1.0, 0.0);
-    RF_K(edge_combo(g, c, W.y, nr, st));
+    RF_K(edge_combo(g, c, W.y, nr, st, make_feed(op, fd, N, m, W.up)));
   }
   // up = conj(T_A) y ; vp = conj(V) (Sigma^T Sigma) q / (k b)
-  RF_TRY(prod_c(op, true, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st));
-  RF_K(lap_apply(g, W.q, W.Lq, nr, st));
-  RF_TRY(prod_c(op, false, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, st));
+  RF_TRY(prod_c(op, true, W.y, W.up, nr, true, c2(1.0, 0.0), false, m, st, fd));
+  RF_K(lap_apply(g, W.q, W.Lq, nr, st, make_feed(op, fd, C, m, W.vp)));
+  RF_TRY(prod_c(op, false, W.Lq, W.vp, nr, true, c2(1.0 / (k * b), 0.0), false, m, st, fd));
   // zp = L^+ Sigma^T up
-  RF_TRY(star_coeff(op, W.up, W.s, W.z, nr, m, st));
+  RF_K(sigma_t(g, W.up, W.s, nr, st, make_feed(op, fd, C, m, W.z)));
+  RF_TRY(prod_r(op, *op->lplus, W.s, W.z, nr, 1.0, false, m, st, fd));
   // out = -(ik/a) up + (ik/a - k/b) Sigma zp + Sigma vp
   {
     EdgeCombo c;

@@ -428,9 +428,19 @@ void dev_pool_trim() {
 // y = scale * op(M) x (+ y) for a real scale: prep (x -> FP32 hi/lo, y zeroed unless it
 // accumulates), then the GEMV, whose CTAs add scale times their FP64 partial sums into y.
 cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate, double2 scale,
-                     bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s) {
+                     bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s, bool fed) {
   const int ld = padded_ld(n);
   if (scale.y != 0.0) return cudaErrorInvalidValue;
+  if (fed) {  // split and zeroed y written by the producer of x
+    if ((nrhs != 1 && nrhs != 2 && nrhs != 4) || n > w.cap_n || ld > w.cap_ld || nrhs > w.cap_cols ||
+        (mode == GEMV_FF && !w.xl))
+      return cudaErrorInvalidValue;
+    w.out = y;
+    w.scale = scale.x;
+    if (nrhs == 4) return gemv_c64_dispatch<4>(M, ld, n, conjugate, mode, w, s);
+    if (nrhs == 2) return gemv_c64_dispatch<2>(M, ld, n, conjugate, mode, w, s);
+    return gemv_c64_dispatch<1>(M, ld, n, conjugate, mode, w, s);
+  }
   cudaError_t err = cudaSuccess;
   for (int r = 0; r < nrhs && err == cudaSuccess;) {
     const int nr = std::min(4, nrhs - r) >= 4 ? 4 : (nrhs - r >= 2 ? 2 : 1);
@@ -494,8 +504,18 @@ cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y,
 }
 
 cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x, double2* y, int nrhs, double scale,
-                     bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s) {
+                     bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s, bool fed) {
   const int ld = padded_ld(n);
+  if (fed) {  // split and zeroed y written by the producer of x
+    if ((nrhs != 1 && nrhs != 2 && nrhs != 4) || n > w.cap_n || ld > w.cap_ld || nrhs > w.cap_cols ||
+        (mode == GEMV_FF && !w.xl))
+      return cudaErrorInvalidValue;
+    w.out = y;
+    w.scale = scale;
+    if (nrhs == 4) return gemv_r32_dispatch<4>(Mhi, Mlo, ld, n, mode, w, s);
+    if (nrhs == 2) return gemv_r32_dispatch<2>(Mhi, Mlo, ld, n, mode, w, s);
+    return gemv_r32_dispatch<1>(Mhi, Mlo, ld, n, mode, w, s);
+  }
   cudaError_t err = cudaSuccess;
   for (int r = 0; r < nrhs && err == cudaSuccess;) {
     const int nr = nrhs - r >= 4 ? 4 : (nrhs - r >= 2 ? 2 : 1);
@@ -518,12 +538,34 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// element i of column r (length n) of a vector a GEMV reads next: its split (as gemv_prep_kernel
+// forms it) and the GEMV's zeroed output
+__device__ __forceinline__ void feed_out(const GemvFeed& f, int r, int i, int n, double2 v) {
+  if (f.xh) {
+    const float2 h = make_float2((float)v.x, (float)v.y);
+    f.xh[(size_t)r * f.ld + i] = h;
+    if (f.xl) f.xl[(size_t)r * f.ld + i] = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+  }
+  if (f.y) f.y[(size_t)r * n + i] = make_double2(0.0, 0.0);
+  if (f.y2) f.y2[(size_t)r * n + i] = make_double2(0.0, 0.0);
+}
+// the split's padding n <= i < ld (the grids cover ld: 256-thread blocks over n, ld = n rounded to 64)
+__device__ __forceinline__ void feed_pad(const GemvFeed& f, int r, int i) {
+  if (f.xh && i < f.ld) {
+    f.xh[(size_t)r * f.ld + i] = make_float2(0.f, 0.f);
+    if (f.xl) f.xl[(size_t)r * f.ld + i] = make_float2(0.f, 0.f);
+  }
+}
+
 __global__ void sigma_t_kernel(const int32_t* __restrict__ cell_edges, const int8_t* __restrict__ cell_sign, int nc,
-                               int ne, const double2* __restrict__ x, double2* __restrict__ out) {
+                               int ne, const double2* __restrict__ x, double2* __restrict__ out, GemvFeed f) {
   RF_COUNT_LAUNCH();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (c >= nc) return;
+  if (c >= nc) {
+    feed_pad(f, r, c);
+    return;
+  }
   const double2* xr = x + (size_t)r * ne;
   double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
@@ -534,15 +576,19 @@ __global__ void sigma_t_kernel(const int32_t* __restrict__ cell_edges, const int
     acc.y += sg * v.y;
   }
   out[(size_t)r * nc + c] = acc;
+  feed_out(f, r, c, nc, acc);
 }
 
 __global__ void lambda_t_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ edge,
                                 const int8_t* __restrict__ sign, int nv, int ne, const double2* __restrict__ x,
-                                double2* __restrict__ out) {
+                                double2* __restrict__ out, GemvFeed f) {
   RF_COUNT_LAUNCH();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (v >= nv) return;
+  if (v >= nv) {
+    feed_pad(f, r, v);
+    return;
+  }
   const double2* xr = x + (size_t)r * ne;
   double2 acc = make_double2(0.0, 0.0);
   for (int q = ptr[v]; q < ptr[v + 1]; ++q) {
@@ -552,15 +598,19 @@ __global__ void lambda_t_kernel(const int32_t* __restrict__ ptr, const int32_t* 
     acc.y += sg * val.y;
   }
   out[(size_t)r * nv + v] = acc;
+  feed_out(f, r, v, nv, acc);
 }
 
 __global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, int nc,
-                           const double2* __restrict__ z, double2* __restrict__ out) {
+                           const double2* __restrict__ z, double2* __restrict__ out, GemvFeed f) {
   RF_COUNT_LAUNCH();
   // Sigma^T Sigma z: 3 z_c - sum over edge-neighbours (values are +-1 and 3 by construction)
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (c >= nc) return;
+  if (c >= nc) {
+    feed_pad(f, r, c);
+    return;
+  }
   const double2* zr = z + (size_t)r * nc;
   double2 acc = make_double2(0.0, 0.0);
   for (int q = ptr[c]; q < ptr[c + 1]; ++q) {
@@ -570,14 +620,18 @@ __global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __res
     acc.y += w * zr[d].y;
   }
   out[(size_t)r * nc + c] = acc;
+  feed_out(f, r, c, nc, acc);
 }
 
 __global__ void edge_combo_kernel(const int32_t* __restrict__ edge_cells, const int32_t* __restrict__ edge_verts,
-                                  int ne, int nc, int nv, EdgeCombo cb, double2* __restrict__ out) {
+                                  int ne, int nc, int nv, EdgeCombo cb, double2* __restrict__ out, GemvFeed f) {
   RF_COUNT_LAUNCH();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (n >= ne) return;
+  if (n >= ne) {
+    feed_pad(f, r, n);
+    return;
+  }
   double2 acc = make_double2(0.0, 0.0);
   const size_t oe = (size_t)r * ne;
   if (cb.x) {
@@ -611,6 +665,7 @@ __global__ void edge_combo_kernel(const int32_t* __restrict__ edge_cells, const 
     acc.y += t.y;
   }
   out[oe + n] = acc;
+  feed_out(f, r, n, ne, acc);
 }
 
 __global__ void column_sum_kernel(const double2* __restrict__ w, int n, double* __restrict__ sums) {
@@ -632,11 +687,14 @@ __global__ void column_sum_kernel(const double2* __restrict__ w, int n, double* 
 
 __global__ void star_middle_kernel(const double* __restrict__ area, int nc, const double2* __restrict__ z,
                                    const double2* __restrict__ w, const double* __restrict__ sums, double scale,
-                                   double2* __restrict__ q) {
+                                   double2* __restrict__ q, GemvFeed f) {
   RF_COUNT_LAUNCH();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (c >= nc) return;
+  if (c >= nc) {
+    feed_pad(f, r, c);
+    return;
+  }
   const size_t o = (size_t)r * nc + c;
   double2 v = z[o];
   if (w) {
@@ -644,8 +702,9 @@ __global__ void star_middle_kernel(const double* __restrict__ area, int nc, cons
     v.x += w[o].x - mx;
     v.y += w[o].y - my;
   }
-  const double f = scale * area[c];
-  q[o] = make_double2(f * v.x, f * v.y);
+  const double fa = scale * area[c];
+  q[o] = make_double2(fa * v.x, fa * v.y);
+  feed_out(f, r, c, nc, q[o]);
 }
 
 __global__ void cell_combo_kernel(int nc, const double2* __restrict__ z, double2 a, const double2* __restrict__ w,
@@ -681,32 +740,36 @@ cudaError_t cell_combo(const DeviceGeometry& g, const double2* z, double2 a, con
   return cudaGetLastError();
 }
 
-cudaError_t sigma_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s) {
+cudaError_t sigma_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s,
+                    const GemvFeed& feed) {
   dim3 grid((g.nc + 255) / 256, nrhs);
-  sigma_t_kernel<<<grid, 256, 0, s>>>(g.cell_edges, g.cell_sign, g.nc, g.ne, x, out);
+  sigma_t_kernel<<<grid, 256, 0, s>>>(g.cell_edges, g.cell_sign, g.nc, g.ne, x, out, feed);
   return cudaGetLastError();
 }
 
-cudaError_t lambda_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s) {
+cudaError_t lambda_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s,
+                     const GemvFeed& feed) {
   dim3 grid((g.nv + 255) / 256, nrhs);
-  lambda_t_kernel<<<grid, 256, 0, s>>>(g.vtx_ptr, g.vtx_edge, g.vtx_sign, g.nv, g.ne, x, out);
+  lambda_t_kernel<<<grid, 256, 0, s>>>(g.vtx_ptr, g.vtx_edge, g.vtx_sign, g.nv, g.ne, x, out, feed);
   return cudaGetLastError();
 }
 
-cudaError_t lap_apply(const DeviceGeometry& g, const double2* z, double2* out, int nrhs, cudaStream_t s) {
+cudaError_t lap_apply(const DeviceGeometry& g, const double2* z, double2* out, int nrhs, cudaStream_t s,
+                      const GemvFeed& feed) {
   dim3 grid((g.nc + 255) / 256, nrhs);
-  lap_kernel<<<grid, 256, 0, s>>>(g.lap_ptr, g.lap_col, g.nc, z, out);
+  lap_kernel<<<grid, 256, 0, s>>>(g.lap_ptr, g.lap_col, g.nc, z, out, feed);
   return cudaGetLastError();
 }
 
-cudaError_t edge_combo(const DeviceGeometry& g, const EdgeCombo& c, double2* out, int nrhs, cudaStream_t s) {
+cudaError_t edge_combo(const DeviceGeometry& g, const EdgeCombo& c, double2* out, int nrhs, cudaStream_t s,
+                       const GemvFeed& feed) {
   dim3 grid((g.ne + 255) / 256, nrhs);
-  edge_combo_kernel<<<grid, 256, 0, s>>>(g.edge_cells, g.edge_verts, g.ne, g.nc, g.nv, c, out);
+  edge_combo_kernel<<<grid, 256, 0, s>>>(g.edge_cells, g.edge_verts, g.ne, g.nc, g.nv, c, out, feed);
   return cudaGetLastError();
 }
 
 cudaError_t star_middle(const DeviceGeometry& g, const double2* z, const double2* w, double scale, double2* q,
-                        int nrhs, double* scratch_mean, cudaStream_t s) {
+                        int nrhs, double* scratch_mean, cudaStream_t s, const GemvFeed& feed) {
   if (w) {
     cudaError_t e = cudaMemsetAsync(scratch_mean, 0, sizeof(double) * 2 * nrhs, s);
     if (e != cudaSuccess) return e;
@@ -714,7 +777,7 @@ cudaError_t star_middle(const DeviceGeometry& g, const double2* z, const double2
     column_sum_kernel<<<grid, 256, 0, s>>>(w, g.nc, scratch_mean);
   }
   dim3 grid((g.nc + 255) / 256, nrhs);
-  star_middle_kernel<<<grid, 256, 0, s>>>(g.area64, g.nc, z, w, scratch_mean, scale, q);
+  star_middle_kernel<<<grid, 256, 0, s>>>(g.area64, g.nc, z, w, scratch_mean, scale, q, feed);
   return cudaGetLastError();
 }
 

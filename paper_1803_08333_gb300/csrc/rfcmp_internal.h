@@ -236,9 +236,9 @@ cudaError_t split_bf16_f64(const double* src, long long ld_src, int rows, int co
 // ---------------------------------------------------------------- kernels (k_linalg.cu)
 enum GemvMode { GEMV_F32 = 0, GEMV_FF = 1 };
 
-// Device scratch of the GEMV: x converted to FP32 hi (and lo) padded to ld, and the FP64
-// accumulator the persistent CTAs add their row sums into.  Calls sharing a scratch must not
-// overlap on the device.
+// Device scratch of the GEMV: x converted to FP32 hi (and lo) padded to ld, and the output the
+// persistent CTAs add their scaled FP64 row sums into.  Calls sharing a scratch must not overlap
+// on the device.
 struct GemvScratch {
   float2* xh = nullptr;   // cap_cols x cap_ld
   float2* xl = nullptr;   // cap_cols x cap_ld
@@ -278,20 +278,39 @@ void dev_pool_trim();
 // y[:, r] = scale * op(M) x[:, r] (+ y[:, r] if accumulate), r < nrhs; M n x n complex64
 // row-major with rows padded to padded_ld(n) (symmetric, so rows are columns); op = conj if
 // conjugate.  x, y complex128 column-major with leading dimension n.
+// fed: the kernel that produced x already wrote its split into w.xh (and w.xl) and zeroed y
+// (GemvFeed), so the split is skipped; nrhs is then 1, 2 or 4.
 cudaError_t gemv_c64(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate,
-                     double2 scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s);
+                     double2 scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s,
+                     bool fed = false);
 // y = op(M) x through the same kernels with no allocation of any kind (no profiling events,
 // no cached launch-grid table).
 cudaError_t gemv_c64_plain(const float2* M, int n, const double2* x, double2* y, int nrhs, bool conjugate,
                            GemvMode mode, GemvScratch& w, cudaStream_t s);
 // y = scale * (Mhi [+ Mlo]) x with a real symmetric n x n matrix in FP32 hi/lo planes.
 cudaError_t gemv_r32(const float* Mhi, const float* Mlo, int n, const double2* x, double2* y, int nrhs,
-                     double scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s);
+                     double scale, bool accumulate, GemvMode mode, GemvScratch& w, cudaStream_t s,
+                     bool fed = false);
+
+// What a sparse kernel writes besides its output when a GEMV reads that output next: the FP32
+// split of each value exactly as the GEMV's own split would form it (hi, and lo for float-float
+// products; zero padding up to ld), and the zeroed output of that GEMV (and of a second GEMV of
+// the same vector).  All null: nothing besides the output.
+struct GemvFeed {
+  float2* xh = nullptr;
+  float2* xl = nullptr;
+  int ld = 0;
+  double2* y = nullptr;
+  double2* y2 = nullptr;
+};
 
 // sparse transforms (Sec. 2, Eq. qHofj); all complex128, nrhs columns
-cudaError_t sigma_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s);   // N_C
-cudaError_t lambda_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s);  // N_V
-cudaError_t lap_apply(const DeviceGeometry& g, const double2* z, double2* out, int nrhs, cudaStream_t s); // Sigma^T Sigma z
+cudaError_t sigma_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s,
+                    const GemvFeed& feed = GemvFeed());  // N_C
+cudaError_t lambda_t(const DeviceGeometry& g, const double2* x, double2* out, int nrhs, cudaStream_t s,
+                     const GemvFeed& feed = GemvFeed());  // N_V
+cudaError_t lap_apply(const DeviceGeometry& g, const double2* z, double2* out, int nrhs, cudaStream_t s,
+                      const GemvFeed& feed = GemvFeed());  // Sigma^T Sigma z
 
 // Fused edge-space combination: out = a*x + b*(Sigma zs) + c*(Lambda zl) + d*(Sigma zs2) + e*w
 // with complex coefficients; any input may be null (its term is dropped).
@@ -302,11 +321,12 @@ struct EdgeCombo {
   const double2* zs2 = nullptr; double2 d{0, 0};   // second N_C vector through Sigma
   const double2* w = nullptr;   double2 e{0, 0};   // second edge vector
 };
-cudaError_t edge_combo(const DeviceGeometry& g, const EdgeCombo& c, double2* out, int nrhs, cudaStream_t s);
+cudaError_t edge_combo(const DeviceGeometry& g, const EdgeCombo& c, double2* out, int nrhs, cudaStream_t s,
+                       const GemvFeed& feed = GemvFeed());
 
 // q = scale * diag(area) (z + w - mean(w)); mean over each column of w (N_C).  w may be null.
 cudaError_t star_middle(const DeviceGeometry& g, const double2* z, const double2* w, double scale, double2* q,
-                        int nrhs, double* scratch_mean, cudaStream_t s);
+                        int nrhs, double* scratch_mean, cudaStream_t s, const GemvFeed& feed = GemvFeed());
 
 // q = a z + b (w - mean(w)) over the cells, per column; z may be null; scratch holds 2 x nrhs doubles
 cudaError_t cell_combo(const DeviceGeometry& g, const double2* z, double2 a, const double2* w, double2 b, double2* q,
