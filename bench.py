@@ -246,6 +246,7 @@ def bench_ours(args):
 
         dist.init_process_group("nccl")
     build.build()
+    rf.set_solve_graphs(args.solve_graphs == "on")
     mesh = _mesh()
     dirs = _cut_dirs()
     kh, pol = synth.plane_wave_z()
@@ -335,6 +336,7 @@ def bench_ours(args):
             "l2": "inputs larger than L2 (T_A complex64 %.2f GB, V %.2f GB)"
                   % (8e-9 * (30 * MESH_N ** 2) ** 2, 8e-9 * (20 * MESH_N ** 2) ** 2),
             "plan": plan,
+            "solve_graphs": args.solve_graphs,
         },
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2), "p99": round(float(np.percentile(lat, 99)), 2)},
         "iterations": iters,
@@ -760,6 +762,9 @@ def main():
                     help="serving: columns join running solves between sweeps, or merged solves run to the end")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--no-tuning", action="store_true", help="ignore the autotuner table (built-in plans)")
+    ap.add_argument("--solve-graphs", default="on", choices=["on", "off"],
+                    help="sweep: solve loops as CUDA graphs (default), or the same kernels launched one by one "
+                         "(every kernel then shows in a profiler's launch list)")
     args = ap.parse_args()
     global MESH_N, KA, WORKLOAD
     if args.mesh_n != 32 or args.ka:
