@@ -8,12 +8,14 @@
 // other three).  Used for the multi-RHS complex products with the resident operator blocks and
 // for the dense products of the factor refinement.
 //
-// Kernel layout: one CTA per 128 x 128 output tile, 128 threads.  Thread 0 issues the TMA loads
-// of a 3-stage ring (each stage: A hi, A lo, B hi, B lo tiles of 128 x 64 BF16 with the 128-byte
-// swizzle), thread 32 issues the MMAs (tcgen05.mma kind::f16, M = 128, N = 128, K = 16 per
-// instruction) and commits them to the stage's "empty" barrier, and all four warps drain the
-// accumulator (tcgen05.ld 32x32b) into D.  Every wait is bounded by a clock limit; on timeout the
-// kernel records an error code, still releases its tensor memory, and returns.
+// Kernel layout: one persistent CTA per SM, 192 threads, 128 x BN output tiles.  Thread 0 issues
+// the TMA loads of a stage ring (each stage: A hi, A lo, B hi, B lo tiles of 128 x 64 BF16 with
+// the 128-byte swizzle) across tile boundaries, thread 32 issues the MMAs (tcgen05.mma kind::f16,
+// M = 128, N = BN, K = 16 per instruction) into one of two tensor-memory accumulators and commits
+// them to the stage's "empty" barrier, and warps 2-5 drain the other accumulator (tcgen05.ld
+// 32x32b) through a shared-memory transpose into D with row-contiguous stores.  Every wait is
+// bounded by a clock limit; on timeout the kernel records an error code, waits (bounded) for its
+// own MMAs and copies, releases its tensor memory, and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -39,8 +41,9 @@ struct TileCfg {
   static constexpr int STAGES = BN >= 128 ? 3 : (BN >= 64 ? 4 : 5);
   static constexpr int TILE_B = BN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;  // a 32 x 33 FP32 transpose buffer per epilogue warp
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr uint32_t TMEM_COLS = 2 * (BN < 32 ? 32 : BN);  // two accumulators
 };
 
 struct GemmMaps {
@@ -48,45 +51,96 @@ struct GemmMaps {
   CUtensorMap b[2][2];
 };
 
+constexpr int GEMM_THREADS = 192;  // warp 0 loads, warp 1 issues MMAs, warps 2-5 drain accumulators
+
+// Output tile of linear index lin: groups of GROUP_M row tiles, the row tile fastest within a
+// group.  The CTAs working at one time then cover a block of about GROUP_M x (SMs / GROUP_M)
+// tiles and share its A and B panels in L2; in plain N-fastest order a wide result (N of many
+// tiles, as in the Newton-Schulz products) has every CTA stream its own B panel from HBM.
+constexpr int GROUP_M = 8;
+__device__ __forceinline__ void tile_of(int lin, int tm, int tn, int& tile_m, int& tile_n) {
+  const int grp = lin / (GROUP_M * tn), first = grp * GROUP_M, gs = min(tm - first, GROUP_M);
+  const int local = lin - grp * GROUP_M * tn;
+  tile_m = first + local % gs;
+  tile_n = local / gs;
+}
+
+// The same order restricted to the tiles on or above the diagonal of a t x t tile grid, numbered
+// without gaps (so that a stride over them gives every CTA the same number of tiles): group g
+// holds rows first .. first + gs - 1; its columns first .. first + gs - 1 hold 1, 2, .., gs tiles
+// (rows up to the column), the columns after them gs tiles each.
+__device__ __forceinline__ void upper_tile_of(int c, int t, int& tile_m, int& tile_n) {
+  int first = 0;
+  for (;;) {
+    const int gs = min(t - first, GROUP_M);
+    const int tri = gs * (gs + 1) / 2;
+    const int cnt = tri + gs * (t - first - gs);
+    if (c < cnt || first + gs >= t) {
+      if (c < tri) {  // column first + j holds rows first .. first + j
+        int j = 0;
+        while ((j + 1) * (j + 2) / 2 <= c) ++j;
+        tile_n = first + j;
+        tile_m = first + (c - j * (j + 1) / 2);
+      } else {
+        c -= tri;
+        tile_n = first + gs + c / gs;
+        tile_m = first + c % gs;
+      }
+      return;
+    }
+    c -= cnt;
+    first += gs;
+  }
+}
+
+// tile i of the kernel's sequence: all tiles, or (upper) those on or above the diagonal
+__device__ __forceinline__ void seq_tile(int i, int tm, int tn, int upper, int& tile_m, int& tile_n) {
+  if (upper) upper_tile_of(i, tn, tile_m, tile_n);
+  else tile_of(i, tm, tn, tile_m, tile_n);
+}
+
+// Persistent kernel: CTA b takes the tiles b, b + G, b + 2G, ... (G CTAs, one per SM).  The
+// producer keeps the stage ring full across tile boundaries; the MMA warp accumulates tile t into
+// tensor-memory buffer t % 2 while the epilogue warps drain buffer (t - 1) % 2, so a tile's
+// epilogue overlaps the next tile's main loop.  The epilogue goes through a shared-memory
+// transpose so that each warp store writes 128 contiguous bytes of one row of D.
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
 gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask, int M, int N, int K,
                    float* __restrict__ D, long long ldd, int accumulate, int* __restrict__ err, int upper) {
   RF_COUNT_LAUNCH();
-  // Tile order: groups of GROUP_M row tiles, the row tile fastest within a group.  The CTAs
-  // resident at one time then cover a block of about GROUP_M x (SMs / GROUP_M) tiles and share
-  // its A and B panels in L2; in plain N-fastest order a wide result (N of many tiles, as in the
-  // Newton-Schulz products) has every resident CTA stream its own B panel from HBM.
-  constexpr int GROUP_M = 8;
-  const int tn = (int)gridDim.x, tm = (int)gridDim.y;
-  const int lin = (int)blockIdx.y * tn + (int)blockIdx.x;
-  const int grp = lin / (GROUP_M * tn), first = grp * GROUP_M, gs = min(tm - first, GROUP_M);
-  const int local = lin - grp * GROUP_M * tn;
-  const int tile_m = first + local % gs, tile_n = local / gs;
-  // upper: only the tiles on or above the diagonal of a symmetric result (BN == BM)
-  if (upper && tile_n < tile_m) return;
   using C = TileCfg<BN>;
   constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, TILE_B = C::TILE_B;
+  constexpr uint32_t ACC_COLS = BN < 32 ? 32 : BN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  float* epi = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + C::EPI_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* acc_full = empty + STAGES;  // [2]: the MMAs of a tile have completed
+  uint64_t* acc_empty = acc_full + 2;   // [2]: the epilogue has read the buffer
+  uint64_t* drained = acc_empty + 2;    // every MMA this CTA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = tile_m * BM, n0 = tile_n * BN;
+  const int tn = (N + BN - 1) / BN, tm = (M + BM - 1) / BM;
+  // upper (BN == BM, tm >= tn): the tn (tn + 1) / 2 tiles on or above the diagonal
+  const int tiles = upper ? tn * (tn + 1) / 2 : tm * tn;
   const int kblocks = (K + BK - 1) / BK;
-  const int total = nseg * kblocks;
+  const int total = nseg * kblocks;  // ring iterations per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(drained, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(C::TMEM_COLS)
                  : "memory");
@@ -99,77 +153,132 @@ gemm_bf16x3_kernel(const __grid_constant__ GemmMaps maps, int nseg, int neg_mask
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: TMA loads into the stage ring
-      for (int it = 0; it < total; ++it) {
-        const int s = it % STAGES, round = it / STAGES;
-        if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
-          atomicExch(err, 1);
-          break;
+      // producer: TMA loads into the stage ring, tile after tile
+      long long it = 0;
+      bool ok = true;
+      for (int lin = blockIdx.x; lin < tiles && ok; lin += gridDim.x) {
+        int tile_m, tile_n;
+        seq_tile(lin, tm, tn, upper, tile_m, tile_n);
+        const int m0 = tile_m * BM, n0 = tile_n * BN;
+        for (int q = 0; q < total; ++q, ++it) {
+          const int s = (int)(it % STAGES);
+          const long long round = it / STAGES;
+          if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1))) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * STAGE_BYTES;
+          const int seg = q / kblocks, kx = (q % kblocks) * BK;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(st, &maps.a[seg][0], &full[s], kx, m0);
+          tma_load_2d(st + TILE_A, &maps.a[seg][1], &full[s], kx, m0);
+          tma_load_2d(st + 2 * TILE_A, &maps.b[seg][0], &full[s], kx, n0);
+          tma_load_2d(st + 2 * TILE_A + TILE_B, &maps.b[seg][1], &full[s], kx, n0);
         }
-        uint8_t* st = smem + s * STAGE_BYTES;
-        const int seg = it / kblocks, kx = (it % kblocks) * BK;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_2d(st, &maps.a[seg][0], &full[s], kx, m0);
-        tma_load_2d(st + TILE_A, &maps.a[seg][1], &full[s], kx, m0);
-        tma_load_2d(st + 2 * TILE_A, &maps.b[seg][0], &full[s], kx, n0);
-        tma_load_2d(st + 2 * TILE_A + TILE_B, &maps.b[seg][1], &full[s], kx, n0);
       }
+      // the copies of the last rounds have landed before the CTA may exit (bounded)
+      for (long long j = it - 1; j >= 0 && j >= it - STAGES; --j)
+        if (!mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1))) atomicExch(err, 4);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
       const uint32_t id_pos = idesc_bf16(BM, BN, false), id_neg = idesc_bf16(BM, BN, true);
-      for (int it = 0; it < total; ++it) {
-        const int s = it % STAGES, round = it / STAGES;
-        if (!mbar_wait(&full[s], round & 1)) {
-          atomicExch(err, 2);
+      long long it = 0;
+      int t = 0;  // tiles of this CTA so far
+      bool ok = true;
+      for (int lin = blockIdx.x; lin < tiles && ok; lin += gridDim.x) {
+        int tile_m, tile_n;
+        seq_tile(lin, tm, tn, upper, tile_m, tile_n);
+        const int b = t & 1, use = t >> 1;
+        if (use > 0 && !mbar_wait(&acc_empty[b], (uint32_t)((use - 1) & 1))) {
+          atomicExch(err, 5);
           break;
         }
         tc_fence_after();
-        const int seg = it / kblocks;
-        const uint32_t idesc = (neg_mask >> seg) & 1 ? id_neg : id_pos;
-        const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + TILE_A;
-        const uint32_t b_hi = a_hi + 2 * TILE_A, b_lo = b_hi + TILE_B;
+        const uint32_t acc = tmem + (uint32_t)b * ACC_COLS;
+        for (int q = 0; q < total; ++q, ++it) {
+          const int s = (int)(it % STAGES);
+          const long long round = it / STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)(round & 1))) {
+            atomicExch(err, 2);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int seg = q / kblocks;
+          const uint32_t idesc = (neg_mask >> seg) & 1 ? id_neg : id_pos;
+          const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + TILE_A;
+          const uint32_t b_hi = a_hi + 2 * TILE_A, b_lo = b_hi + TILE_B;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte swizzled row
-          const uint64_t ah = sw128_desc(a_hi + off), al = sw128_desc(a_lo + off);
-          const uint64_t bh = sw128_desc(b_hi + off), bl = sw128_desc(b_lo + off);
-          mma_bf16(tmem, ah, bh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-          mma_bf16(tmem, ah, bl, idesc, 1u);
-          mma_bf16(tmem, al, bh, idesc, 1u);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte swizzled row
+            const uint64_t ah = sw128_desc(a_hi + off), al = sw128_desc(a_lo + off);
+            const uint64_t bh = sw128_desc(b_hi + off), bl = sw128_desc(b_lo + off);
+            mma_bf16(acc, ah, bh, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(acc, ah, bl, idesc, 1u);
+            mma_bf16(acc, al, bh, idesc, 1u);
+          }
+          mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
         }
-        mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+        if (!ok) break;
+        mma_commit(&acc_full[b]);  // arrives when the tile's MMAs have completed
+        ++t;
       }
-      mma_commit(done);  // arrives when every MMA issued above has completed
+      // every MMA issued above has completed before tensor memory is released (bounded)
+      mma_commit(drained);
+      if (!mbar_wait(drained, 0)) atomicExch(err, 6);
+    }
+  } else {
+    // epilogue: warp w drains accumulator lanes (rows) 32 (w % 4) .. + 31
+    const int quarter = warp & 3;
+    float* tb = epi + (warp - 2) * 32 * 33;
+    int t = 0;
+    for (int lin = blockIdx.x; lin < tiles; lin += gridDim.x) {
+      int tile_m, tile_n;
+      seq_tile(lin, tm, tn, upper, tile_m, tile_n);
+      const int b = t & 1, use = t >> 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)(use & 1)));
+      if (!ok) {
+        if (lane == 0) atomicExch(err, 3);
+        break;
+      }
+      tc_fence_after();
+      const int r0 = tile_m * BM + 32 * quarter, n0 = tile_n * BN;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)b * ACC_COLS + (uint32_t)c0, r);
+        // lane = row of the block; transpose so that lane = column for the stores
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        if (col < N) {
+#pragma unroll 4
+          for (int i = 0; i < 32; ++i) {
+            const int row = r0 + i;
+            if (row >= M) break;
+            float* dst = D + (size_t)row * ldd + col;
+            float v = tb[i * 33 + lane];
+            if (accumulate) v += *dst;
+            *dst = v;
+          }
+        }
+        __syncwarp();
+      }
+      // the buffer's loads have completed (tmem_ld32 waits): hand it back to the MMA warp
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      ++t;
     }
   }
   __syncwarp();
-
-  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));  // warp-uniform: tcgen05.ld is .sync.aligned
-  if (!ok && lane == 0) atomicExch(err, 3);
-  tc_fence_after();
-  const int row = m0 + 32 * warp + lane;
-  if (ok) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
-      if (row < M) {
-        float* dst = D + (size_t)row * ldd + n0 + c0;
-        const int cols = min(32, N - (n0 + c0));
-        for (int j = 0; j < cols; ++j) {
-          float v = __uint_as_float(r[j]);
-          if (accumulate) v += dst[j];
-          dst[j] = v;
-        }
-      }
-    }
-  }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
+  tc_fence_after();
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
@@ -213,15 +322,26 @@ cudaError_t gemm_launch(const SplitOperand* A, const SplitOperand* B, const int*
         cudaFuncSetAttribute(gemm_bf16x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  const long long tnl = (N + BN - 1) / BN, tml = (M + BM - 1) / BM;
+  if (upper && tml < tnl) return cudaErrorInvalidValue;
+  const long long tiles = upper ? tnl * (tnl + 1) / 2 : tnl * tml;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = (int)std::max(1LL, std::min<long long>(tiles, sms));
   double frac = 1.0;  // share of the output tiles computed
   if (upper) {
     const double tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
     frac = std::min(1.0, tn * (tn + 1) / 2.0 / (tm * tn));  // tiles with n-tile >= m-tile (tm >= tn)
   }
   ProfScope prof("gemm_bf16x3", 0.0, 6.0 * (double)M * N * K * nseg * frac, s);
-  gemm_bf16x3_kernel<BN><<<grid, 128, C::SMEM_BYTES, s>>>(maps, nseg, neg_mask, M, N, K, D, ldd, accumulate ? 1 : 0,
-                                                          err_dev, upper ? 1 : 0);
+  gemm_bf16x3_kernel<BN><<<grid, GEMM_THREADS, C::SMEM_BYTES, s>>>(maps, nseg, neg_mask, M, N, K, D, ldd,
+                                                                   accumulate ? 1 : 0, err_dev, upper ? 1 : 0);
   return cudaGetLastError();
 }
 
