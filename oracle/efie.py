@@ -86,8 +86,10 @@ def discretize(verts, tris) -> Discretization:
     rho = qp - cent[:, None, :]
     a_loc = verts[tris] - cent[:, None, :]
     rows = np.arange(3 * top.nc)
+    ce = top.cell_edges.ravel()
+    on = ce >= 0  # boundary edges of an open surface carry no RWG function
     B = sp.csr_matrix(
-        (top.cell_sign.ravel().astype(np.float64), (rows, top.cell_edges.ravel())),
+        (top.cell_sign.ravel()[on].astype(np.float64), (rows[on], ce[on])),
         shape=(3 * top.nc, top.ne),
     )
     # near pairs: cells sharing at least one vertex (including s == t)

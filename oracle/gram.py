@@ -40,6 +40,19 @@ def g_ff(D) -> sp.csr_matrix:
     return (D.B.T @ K @ D.B).tocsr()
 
 
+def g_ll_loops(D) -> sp.csr_matrix:
+    """G_ll over the loop functions: the P1 mass matrix restricted to the interior vertices
+    (all vertices of a closed surface)."""
+    idx = D.top.loop_verts
+    return g_ll(D)[idx][:, idx].tocsr()
+
+
+def stiffness_loops(D) -> sp.csr_matrix:
+    """The P1 stiffness matrix restricted to the interior vertices."""
+    idx = D.top.loop_verts
+    return stiffness(D)[idx][:, idx].tocsr()
+
+
 def stiffness(D) -> sp.csr_matrix:
     """(grad l_m, grad l_n): on a cell, grad l_i = n x e_i / (2A) with e_i the edge opposite i."""
     p = D.verts[D.tris]

@@ -90,11 +90,14 @@ def factors(D) -> Factors:
     nc = D.nc
     J = np.full((nc, nc), 1.0 / nc)
     Lplus = np.linalg.inv(S.T @ S + J) - J  # Sec. 3.2 identity
-    Gll_inv = np.linalg.inv(gram.g_ll(D).toarray())
+    Gll_inv = np.linalg.inv(gram.g_ll_loops(D).toarray())
     Gpp_inv = np.diag(D.area)
     P_S = S @ Lplus @ S.T
-    Gtp_inv = np.linalg.inv(gram.g_lambda_tilde_p(D).toarray())
-    P_gS = S @ Lplus @ Gtp_inv @ S.T
+    if D.top.boundaries == 0:
+        Gtp_inv = np.linalg.inv(gram.g_lambda_tilde_p(D).toarray())
+        P_gS = S @ Lplus @ Gtp_inv @ S.T
+    else:  # the dual functions of Sec. 2 are defined on closed surfaces only
+        Gtp_inv = P_gS = None
     return Factors(S, L, Lplus, Gll_inv, Gpp_inv, P_S, np.eye(D.N) - P_S, Gtp_inv, P_gS)
 
 

@@ -12,6 +12,8 @@ from .meshes import (  # noqa: F401
     ellipsoid,
     cube,
     torus,
+    plate,
+    open_cylinder,
     mesh_for_config,
 )
 from .excitation import (  # noqa: F401

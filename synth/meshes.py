@@ -1,8 +1,8 @@
-"""Seeded surface triangulations of closed PEC bodies.
+"""Seeded surface triangulations of PEC bodies.
 
-Every mesh is a closed, consistently oriented (counter-clockwise about the
-outward normal) triangulation returned as ``verts`` (float64, N_V x 3) and
-``tris`` (int32, N_C x 3).
+Every mesh is a consistently oriented (counter-clockwise about the outward normal)
+triangulation returned as ``verts`` (float64, N_V x 3) and ``tris`` (int32, N_C x 3); all are
+closed except ``plate`` and ``open_cylinder`` (open surfaces).
 
 * ``geodesic_sphere(n)``: the icosahedron with each face cut into n^2
   triangles (frequency-n geodesic grid), projected onto the sphere.
@@ -242,6 +242,66 @@ def torus(nu: int, nv: int, R: float = 1.0, r: float = 0.4, jitter: float = 0.0,
     if vol < 0:
         tris = tris[:, [0, 2, 1]]
     return Mesh(verts, tris.astype(np.int32), f"torus_{nu}x{nv}_R{R}_r{r}")
+
+
+def plate(n: int, side: float = 1.0, bow: float = 0.0, jitter: float = 0.03, seed: int = 7) -> Mesh:
+    """Open square plate (one boundary curve, disk topology): an n x n grid of squares in
+    [-side/2, side/2]^2, each split into two triangles along alternating diagonals, normal +z.
+
+    ``bow`` lifts the plate into a shallow cap z = bow (1 - (x^2 + y^2) / (side^2 / 2)).
+    Jitter moves interior vertices in the (x, y) plane by at most ``jitter`` times the grid step;
+    boundary vertices stay on the square.
+    """
+    if n < 1:
+        raise ValueError("plate grid must be at least 1 x 1")
+    rng = np.random.default_rng(seed)
+    t = (np.arange(n + 1) / n - 0.5) * side
+    xx, yy = np.meshgrid(t, t, indexing="ij")
+    if jitter > 0:
+        inner = np.zeros(xx.shape, bool)
+        inner[1:-1, 1:-1] = True
+        h = side / n
+        xx = xx + np.where(inner, rng.uniform(-1, 1, xx.shape) * jitter * h, 0.0)
+        yy = yy + np.where(inner, rng.uniform(-1, 1, yy.shape) * jitter * h, 0.0)
+    zz = bow * (1.0 - (xx**2 + yy**2) / (side**2 / 2.0))
+    verts = np.stack([xx, yy, zz], axis=-1).reshape(-1, 3)
+    idx = lambda i, j: i * (n + 1) + j  # noqa: E731
+    tris = []
+    for i in range(n):
+        for j in range(n):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            if (i + j) % 2 == 0:
+                tris += [(a, b, c), (a, c, d)]
+            else:
+                tris += [(a, b, d), (b, c, d)]
+    return Mesh(verts, np.array(tris, dtype=np.int32), f"plate_n{n}_side{side}_bow{bow}_j{jitter}_s{seed}")
+
+
+def open_cylinder(nu: int, nz: int, radius: float = 0.5, height: float = 1.0, jitter: float = 0.03,
+                  seed: int = 8) -> Mesh:
+    """Open circular cylinder without end caps (two boundary curves, the topology of an annulus:
+    one harmonic field): an nu x nz grid in (angle, z), each quad split into two triangles,
+    normal pointing outward.  Jitter moves the vertices off the two rims in (angle, z)."""
+    if nu < 3 or nz < 1:
+        raise ValueError("cylinder grid must be at least 3 x 1")
+    rng = np.random.default_rng(seed)
+    u = 2.0 * np.pi * np.arange(nu) / nu
+    z = (np.arange(nz + 1) / nz - 0.5) * height
+    uu, zz = np.meshgrid(u, z, indexing="ij")
+    if jitter > 0:
+        inner = np.zeros(uu.shape, bool)
+        inner[:, 1:-1] = True
+        h = 0.5 * (2.0 * np.pi * radius / nu + height / nz)
+        uu = uu + np.where(inner, rng.uniform(-1, 1, uu.shape) * jitter * h / radius, 0.0)
+        zz = zz + np.where(inner, rng.uniform(-1, 1, zz.shape) * jitter * h, 0.0)
+    verts = np.stack([radius * np.cos(uu), radius * np.sin(uu), zz], axis=-1).reshape(-1, 3)
+    idx = lambda i, j: (i % nu) * (nz + 1) + j  # noqa: E731
+    tris = []
+    for i in range(nu):
+        for j in range(nz):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            tris += [(a, b, c), (a, c, d)]  # (angle, z) is counter-clockwise about the outward normal
+    return Mesh(verts, np.array(tris, dtype=np.int32), f"cylinder_{nu}x{nz}_r{radius}_h{height}_j{jitter}_s{seed}")
 
 
 def mesh_for_config(name: str) -> Mesh:

@@ -129,14 +129,25 @@ def test_quasi_helmholtz_identities(mesh):
     assert abs(np.trace(np.eye(top.ne) - PS - PL) - 2 * g) < 1e-8
 
 
-def test_topology_rejects_open_and_misoriented_meshes():
+def test_topology_open_surfaces_and_invalid_meshes():
     m = synth.geodesic_sphere(2)
-    with pytest.raises(topology.MeshError):
-        topology.build_topology(m.tris[:-1], m.nv)
+    # one cell removed: an open surface (a disk) with one boundary curve of three edges, whose
+    # vertices carry no loop function
+    t = topology.build_topology(m.tris[:-1], m.nv)
+    assert t.boundaries == 1 and t.genus == 0 and t.ne == 30 * 4 - 3 and t.nvl == m.nv - 3
     bad = m.tris.copy()
     bad[0] = bad[0, [0, 2, 1]]
-    with pytest.raises(topology.MeshError):
+    with pytest.raises(topology.MeshError):  # inconsistent orientation
         topology.build_topology(bad, m.nv)
+    junction = np.vstack([m.tris, m.tris[:1, [0, 2, 1]]])  # an edge shared by three cells
+    with pytest.raises(topology.MeshError):
+        topology.build_topology(junction, m.nv)
+    # two holes meeting at one vertex: a boundary vertex with four boundary edges
+    v = int(m.tris[0, 0])
+    around = [c for c in range(m.nc) if v in m.tris[c]]
+    pinched = np.delete(m.tris, [around[0], around[2]], axis=0)
+    with pytest.raises(topology.MeshError):
+        topology.build_topology(pinched, m.nv)
 
 
 # ---------------------------------------------------------------- projectors
