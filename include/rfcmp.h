@@ -4,8 +4,11 @@
  * Adrian, Andriulli, Eibert, "On a refinement-free Calderon multiplicative
  * preconditioner for the electric field integral equation" (arXiv 1803.08333).
  *
- * Problem (Sec. 2): a closed PEC surface Gamma, triangulated; RWG functions
- * f_n (not divided by the edge length, Eq. RWGdef); wavenumber k; e^{-i w t};
+ * Problem (Sec. 2): a PEC surface Gamma, triangulated, closed or open; RWG
+ * functions f_n (not divided by the edge length, Eq. RWGdef) on the edges
+ * shared by two cells (an edge of one cell is a boundary edge of an open
+ * surface and carries none); loop functions on the interior vertices (every
+ * vertex of a closed surface); wavenumber k; e^{-i w t};
  * current j normalised by the wave impedance.  With
  *   [T_A]_mn  = int int f_m(r) . f_n(r') G(r,r'),    G = e^{ikR}/(4 pi R),
  *   V_st      = int int p_s(r) p_t(r') G(r,r'),      p_s = 1/A_s on cell s,
@@ -61,7 +64,8 @@ typedef struct { double re, im; } rfcmp_c128;
 typedef enum {
   RFCMP_OK = 0,
   RFCMP_ERR_INVALID_ARG = -1,
-  RFCMP_ERR_MESH_NOT_MANIFOLD = -2, /* an edge not shared by exactly two cells, or a bad index */
+  RFCMP_ERR_MESH_NOT_MANIFOLD = -2, /* an edge of three or more cells, a pinched boundary vertex, no
+                                       interior vertex, or a bad index */
   RFCMP_ERR_MESH_ORIENTATION = -3,  /* neighbouring cells not consistently oriented */
   RFCMP_ERR_OUT_OF_BUDGET = -4,     /* the op would exceed the context's HBM budget */
   RFCMP_ERR_CUDA = -5,              /* a CUDA call failed (message in rfcmp_last_error) */
@@ -157,9 +161,11 @@ typedef struct {
 } rfcmp_solve_report;
 
 typedef struct {
-  int64_t n_edges, n_vertices, n_cells;
+  int64_t n_edges;     /* RWG functions N: the edges shared by two cells */
+  int64_t n_vertices;  /* loop functions: the interior vertices (all vertices of a closed surface) */
+  int64_t n_cells;
   int32_t genus;
-  int32_t reserved0;
+  int32_t boundaries;  /* boundary curves of an open surface (0: closed) */
   double k, alpha, beta, gamma;
   uint64_t device_bytes;    /* device memory held by the op */
   double ms_assembly;       /* T_A and V assembly (device time) */
@@ -189,12 +195,14 @@ uint64_t rfcmp_ctx_bytes_in_use(const rfcmp_ctx* ctx);
 /* ----------------------------------------------------------------------------
  * Operator: mesh + wavenumber -> resident T_A (N x N) and V (N_C x N_C),
  * complex64, row-major (both complex symmetric); dense (Sigma^T Sigma)^+
- * (N_C x N_C) and G_ll^{-1} (N_V x N_V) as FP32 hi + lo planes; alpha, beta,
+ * (N_C x N_C) and G_ll^{-1} (N_V x N_V, the interior vertices) as FP32 hi + lo planes; alpha, beta,
  * gamma.  Assembly (Sec. 2 definitions): 7 x 7 product of the 7-point rule
  * on far cell pairs in FP32; on near pairs (a shared vertex) closed-form
  * integration of 1/(4 pi R) over the source cell plus the 7-point rule for
  * (e^{ikR} - 1)/(4 pi R), in FP64, averaged over both orders.
- *  verts  N_V x 3 float64 (host), tris N_C x 3 int32 (host).
+ *  verts  nv x 3 float64 (host: every mesh vertex), tris N_C x 3 int32 (host).  Open
+ *         surfaces need at least one interior vertex; the theory variant (opts.outer =
+ *         RFCMP_OUTER_GSIGMA) needs a closed surface (RFCMP_ERR_INVALID_ARG otherwise).
  *  k      wavenumber > 0 (rad/m, c = 1).
  *  opts   NULL for the defaults.
  * All work runs on the context device's legacy default stream; the call

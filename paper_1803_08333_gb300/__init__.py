@@ -95,7 +95,7 @@ class SolveReport(ctypes.Structure):
 class OpInfo(ctypes.Structure):
     _fields_ = [
         ("n_edges", ctypes.c_int64), ("n_vertices", ctypes.c_int64), ("n_cells", ctypes.c_int64),
-        ("genus", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("genus", ctypes.c_int32), ("boundaries", ctypes.c_int32),
         ("k", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
         ("device_bytes", ctypes.c_uint64), ("ms_assembly", ctypes.c_double), ("ms_factors", ctypes.c_double),
         ("ms_scaling", ctypes.c_double), ("factor_iterations_lplus", ctypes.c_int32),

@@ -1292,13 +1292,14 @@ int upload_geometry(const Topology& T, const std::vector<double>& verts, DeviceG
   RF_TRY(upload(&g.cell_edges, T.cell_edges, own));
   RF_TRY(upload(&g.cell_sign, T.cell_sign, own));
   RF_TRY(upload(&g.edge_cells, T.edge_cells, own));
-  RF_TRY(upload(&g.edge_verts, T.edge_verts, own));
+  RF_TRY(upload(&g.edge_loops, T.edge_loops, own));
   RF_TRY(upload(&g.edge_free, T.edge_free, own));
   RF_TRY(upload(&g.vtx_ptr, T.vtx_ptr, own));
   RF_TRY(upload(&g.vtx_edge, T.vtx_edge, own));
   RF_TRY(upload(&g.vtx_sign, T.vtx_sign, own));
   RF_TRY(upload(&g.lap_ptr, T.lap_ptr, own));
   RF_TRY(upload(&g.lap_col, T.lap_col, own));
+  RF_TRY(upload(&g.lap_val, T.lap_val, own));
   RF_TRY(upload(&g.near_pairs, T.near_pairs, own));
   g.n_near = (int32_t)(T.near_pairs.size() / 2);
   return RFCMP_OK;
@@ -1633,7 +1634,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     auto it = ctx->mesh_cache.find(mesh_key);
-    if (it != ctx->mesh_cache.end() && it->second->top.nc == nc && it->second->top.nv == nv &&
+    if (it != ctx->mesh_cache.end() && it->second->top.nc == nc && it->second->top.nv_mesh == nv &&
         std::equal(tris, tris + 3 * nc, it->second->top.tris.begin()) &&
         std::equal(verts, verts + 3 * nv, it->second->verts.begin()))
       me = it->second;
@@ -1657,6 +1658,11 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   op->top = me->top;
   op->verts = me->verts;
   op->g = me->g;
+  if (op->top.nv == 0)
+    return set_error(RFCMP_ERR_MESH_NOT_MANIFOLD, "the open surface has no interior vertex (no loop function)");
+  if (o.outer == RFCMP_OUTER_GSIGMA && op->top.boundaries > 0)
+    return set_error(RFCMP_ERR_INVALID_ARG,
+                     "the theory variant P_gSigma needs a closed surface (its dual functions are defined there)");
   const int N = (int)op->top.ne, C = (int)op->top.nc, NV = (int)op->top.nv;
   op->ldN = padded_ld(N);
   op->ldC = padded_ld(C);
@@ -1761,6 +1767,7 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
   op->info.n_vertices = NV;
   op->info.n_cells = C;
   op->info.genus = op->top.genus;
+  op->info.boundaries = op->top.boundaries;
   op->info.k = k;
   op->info.alpha = op->alpha;
   op->info.beta = op->beta;

@@ -264,6 +264,7 @@ __device__ __forceinline__ void far_store(const TileCells& S, const TileCells& T
     const float pa_r = Mo.Irr_r - (ax * Mo.Ip_r[0] + ay * Mo.Ip_r[1] + az * Mo.Ip_r[2]);
     const float pa_i = Mo.Irr_i - (ax * Mo.Ip_i[0] + ay * Mo.Ip_i[1] + az * Mo.Ip_i[2]);
     const int m = S.edge[sl][a];
+    if (m < 0) continue;  // a boundary edge of an open surface: no RWG function
     const float sa = S.sign[sl][a] * quarter;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -273,6 +274,7 @@ __device__ __forceinline__ void far_store(const TileCells& S, const TileCells& T
       const float vi = pa_i - (bx * Mo.Ir_i[0] + by * Mo.Ir_i[1] + bz * Mo.Ir_i[2]) + ab * Mo.I0i;
       const float f = sa * Tt.sign[tl][b];
       const int n = Tt.edge[tl][b];
+      if (n < 0) continue;
       // T_A is complex symmetric: only the upper triangle is accumulated (m != n on far pairs),
       // the lower one is mirrored afterwards so that both are bit-identical
       atomic_add_c64(&TA[(size_t)min(m, n) * ldN + max(m, n)], f * vr, f * vi);
@@ -532,6 +534,7 @@ near_pairs_kernel(const DeviceGeometry g, double k, float2* __restrict__ TA, flo
       pi -= ai[x] * Iti[x];
     }
     const int m = g.cell_edges[3 * s + a];
+    if (m < 0) continue;  // a boundary edge of an open surface: no RWG function
     const double sa = (double)g.cell_sign[3 * s + a] * 0.25 * inv_aa;
     for (int b = 0; b < 3; ++b) {
       double vr = pr, vi = pi, ab = 0.0;
@@ -545,6 +548,7 @@ near_pairs_kernel(const DeviceGeometry g, double k, float2* __restrict__ TA, flo
       vi += ab * I0i;
       const double f = sa * (double)g.cell_sign[3 * t + b];
       const int n = g.cell_edges[3 * t + b];
+      if (n < 0) continue;
       // upper triangle only: a distinct pair reaches (m, n) and (n, m) once each, which is
       // twice on the diagonal; the self pair lists both (a, b) and (b, a) itself
       double mult = 1.0;
@@ -726,6 +730,7 @@ farfield_kernel(const DeviceGeometry g, double k, const double2* __restrict__ j,
       double sr = 0.0, si = 0.0, tr[3] = {0.0, 0.0, 0.0}, ti[3] = {0.0, 0.0, 0.0};
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
+        if (ed[i] < 0) continue;  // a boundary edge: no current
         const double2 v = jr[ed[i]];
         const double vr = sg[i] * v.x, vi = sg[i] * v.y;
         sr += vr;

@@ -570,8 +570,10 @@ __global__ void sigma_t_kernel(const int32_t* __restrict__ cell_edges, const int
   double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
+    const int e = cell_edges[3 * c + i];
+    if (e < 0) continue;  // a boundary edge of an open surface: no RWG function
     const double sg = (double)cell_sign[3 * c + i];
-    const double2 v = xr[cell_edges[3 * c + i]];
+    const double2 v = xr[e];
     acc.x += sg * v.x;
     acc.y += sg * v.y;
   }
@@ -601,10 +603,11 @@ __global__ void lambda_t_kernel(const int32_t* __restrict__ ptr, const int32_t* 
   feed_out(f, r, v, nv, acc);
 }
 
-__global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, int nc,
-                           const double2* __restrict__ z, double2* __restrict__ out, GemvFeed f) {
+__global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, int nc, const double2* __restrict__ z,
+                           double2* __restrict__ out, GemvFeed f) {
   RF_COUNT_LAUNCH();
-  // Sigma^T Sigma z: 3 z_c - sum over edge-neighbours (values are +-1 and 3 by construction)
+  // Sigma^T Sigma z (CSR: the cell's RWG edge count on the diagonal, -1 per shared edge)
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (c >= nc) {
@@ -615,7 +618,7 @@ __global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __res
   double2 acc = make_double2(0.0, 0.0);
   for (int q = ptr[c]; q < ptr[c + 1]; ++q) {
     const int d = col[q];
-    const double w = d == c ? 3.0 : -1.0;
+    const double w = val[q];
     acc.x += w * zr[d].x;
     acc.y += w * zr[d].y;
   }
@@ -623,7 +626,7 @@ __global__ void lap_kernel(const int32_t* __restrict__ ptr, const int32_t* __res
   feed_out(f, r, c, nc, acc);
 }
 
-__global__ void edge_combo_kernel(const int32_t* __restrict__ edge_cells, const int32_t* __restrict__ edge_verts,
+__global__ void edge_combo_kernel(const int32_t* __restrict__ edge_cells, const int32_t* __restrict__ edge_loops,
                                   int ne, int nc, int nv, EdgeCombo cb, double2* __restrict__ out, GemvFeed f) {
   RF_COUNT_LAUNCH();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -653,8 +656,10 @@ __global__ void edge_combo_kernel(const int32_t* __restrict__ edge_cells, const 
     acc.y += t.y;
   }
   if (cb.zl) {
-    const int v1 = edge_verts[2 * n], v2 = edge_verts[2 * n + 1];
-    const double2 p = cb.zl[(size_t)r * nv + v1], m = cb.zl[(size_t)r * nv + v2];
+    // loop indices of the edge ends; an end on the boundary of an open surface has none
+    const int v1 = edge_loops[2 * n], v2 = edge_loops[2 * n + 1];
+    const double2 zero = make_double2(0.0, 0.0);
+    const double2 p = v1 >= 0 ? cb.zl[(size_t)r * nv + v1] : zero, m = v2 >= 0 ? cb.zl[(size_t)r * nv + v2] : zero;
     const double2 t = cmul(cb.c, make_double2(p.x - m.x, p.y - m.y));
     acc.x += t.x;
     acc.y += t.y;
@@ -757,14 +762,14 @@ cudaError_t lambda_t(const DeviceGeometry& g, const double2* x, double2* out, in
 cudaError_t lap_apply(const DeviceGeometry& g, const double2* z, double2* out, int nrhs, cudaStream_t s,
                       const GemvFeed& feed) {
   dim3 grid((g.nc + 255) / 256, nrhs);
-  lap_kernel<<<grid, 256, 0, s>>>(g.lap_ptr, g.lap_col, g.nc, z, out, feed);
+  lap_kernel<<<grid, 256, 0, s>>>(g.lap_ptr, g.lap_col, g.lap_val, g.nc, z, out, feed);
   return cudaGetLastError();
 }
 
 cudaError_t edge_combo(const DeviceGeometry& g, const EdgeCombo& c, double2* out, int nrhs, cudaStream_t s,
                        const GemvFeed& feed) {
   dim3 grid((g.ne + 255) / 256, nrhs);
-  edge_combo_kernel<<<grid, 256, 0, s>>>(g.edge_cells, g.edge_verts, g.ne, g.nc, g.nv, c, out, feed);
+  edge_combo_kernel<<<grid, 256, 0, s>>>(g.edge_cells, g.edge_loops, g.ne, g.nc, g.nv, c, out, feed);
   return cudaGetLastError();
 }
 

@@ -74,8 +74,13 @@ class ProfScope {
 // ---------------------------------------------------------------- host topology
 // Edge numbering and signs follow include/rfcmp.h (Sec. 2, Eq. RWGdef, Eq. qHofj).
 struct Topology {
-  int64_t nv = 0, nc = 0, ne = 0;
+  int64_t nv = 0, nc = 0, ne = 0;  // nv: loop functions (the interior vertices)
+  int64_t nv_mesh = 0;             // vertices of the mesh
   int genus = 0;
+  int boundaries = 0;                // boundary curves (0: a closed surface)
+  std::vector<int32_t> loop_of;      // nv_mesh: loop index of a vertex, -1 on the boundary
+  std::vector<int32_t> loop_verts;   // nv: mesh vertex of each loop function
+  std::vector<int32_t> edge_loops;   // ne x 2: loop indices of (v1, v2), -1 on the boundary
   std::vector<int32_t> tris;        // nc x 3
   std::vector<int32_t> edge_verts;  // ne x 2 (v1, v2): c^+ traverses v1 -> v2
   std::vector<int32_t> edge_cells;  // ne x 2 (c^+, c^-)
@@ -85,7 +90,8 @@ struct Topology {
   // Lambda^T gather: for vertex v, entries [vtx_ptr[v], vtx_ptr[v+1]) of vtx_edge / vtx_sign
   std::vector<int32_t> vtx_ptr, vtx_edge;
   std::vector<int8_t> vtx_sign;
-  // Sigma^T Sigma as CSR (cell graph Laplacian: 3 on the diagonal, -1 per shared edge)
+  // Sigma^T Sigma as CSR (cell graph Laplacian: the cell's RWG edges on the diagonal, -1 per
+  // shared edge)
   std::vector<int32_t> lap_ptr, lap_col;
   std::vector<double> lap_val;
   // unordered near pairs (s <= t) of cells sharing at least one vertex
@@ -101,7 +107,8 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& out, s
 void gtp_matrix_csr(const Topology& top, std::vector<int32_t>& ptr, std::vector<int32_t>& col,
                     std::vector<double>& val);
 
-// G_ll (P1 mass matrix) as CSR over the vertices, local block A/12 [[2,1,1],[1,2,1],[1,1,2]].
+// G_ll (P1 mass matrix) as CSR over the loop (interior) vertices, local block
+// A/12 [[2,1,1],[1,2,1],[1,1,2]] restricted to them.
 void mass_matrix_csr(const Topology& top, const double* verts, std::vector<int32_t>& ptr,
                      std::vector<int32_t>& col, std::vector<double>& val);
 
@@ -128,13 +135,14 @@ struct DeviceGeometry {
   int32_t* cell_edges = nullptr;  // nc x 3
   int8_t* cell_sign = nullptr;    // nc x 3
   int32_t* edge_cells = nullptr;  // ne x 2
-  int32_t* edge_verts = nullptr;  // ne x 2
+  int32_t* edge_loops = nullptr;  // ne x 2 loop indices of the edge ends (-1 on the boundary)
   int32_t* edge_free = nullptr;   // ne x 2
   int32_t* vtx_ptr = nullptr;     // nv + 1
   int32_t* vtx_edge = nullptr;
   int8_t* vtx_sign = nullptr;
   int32_t* lap_ptr = nullptr;     // nc + 1
   int32_t* lap_col = nullptr;
+  double* lap_val = nullptr;
   int32_t* near_pairs = nullptr;  // n_near x 2
   int32_t n_near = 0;
 };

@@ -4,8 +4,11 @@
 // cells c_n^+ and c_n^- with free vertices r_n^+ and r_n^-.
 // Sec. 2, Eq. qHofj: Sigma (N x N_C) and Lambda (N x N_V) with entries +-1,
 // Lambda^T Sigma = 0.  Sec. 2 (graph Laplacians): Sigma^T Sigma is the cell
-// graph Laplacian, 3 on the diagonal and -1 for each pair of cells sharing an
-// edge.  Numbering and sign conventions: include/rfcmp.h.
+// graph Laplacian, the number of RWG edges of a cell on the diagonal and -1 for
+// each pair of cells sharing an edge.  Open surfaces (Sec. 2: inner vertices only):
+// an edge of one cell is a boundary edge without an RWG function, and the loop
+// functions belong to the interior vertices.  Numbering and sign conventions:
+// include/rfcmp.h.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -40,7 +43,7 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std
   }
   T = Topology();
   T.nc = nc;
-  T.nv = nv;
+  T.nv_mesh = nv;
   T.tris.assign(tris, tris + 3 * nc);
   std::vector<HalfEdge> he;
   he.reserve(3 * nc);
@@ -63,11 +66,26 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std
     if (x.hi != y.hi) return x.hi < y.hi;
     return x.cell < y.cell;
   });
-  if (he.size() % 2 != 0) {
-    err = "odd number of half-edges: the surface is not closed";
+  // groups of equal vertex pairs: two half-edges make an RWG edge, one a boundary edge
+  std::vector<size_t> inner;  // index of the first half-edge of each RWG edge
+  std::vector<std::pair<int32_t, int32_t>> bnd;
+  for (size_t q = 0; q < he.size();) {
+    size_t r = q + 1;
+    while (r < he.size() && he[r].lo == he[q].lo && he[r].hi == he[q].hi) ++r;
+    if (r - q > 2) {
+      err = "edge (" + std::to_string(he[q].lo) + "," + std::to_string(he[q].hi) + ") is shared by " +
+            std::to_string(r - q) + " cells (a junction: not a 2-manifold)";
+      return RFCMP_ERR_MESH_NOT_MANIFOLD;
+    }
+    if (r - q == 2) inner.push_back(q);
+    else bnd.push_back({he[q].lo, he[q].hi});
+    q = r;
+  }
+  const int64_t ne = (int64_t)inner.size();
+  if (ne == 0) {
+    err = "the mesh has no edge shared by two cells";
     return RFCMP_ERR_MESH_NOT_MANIFOLD;
   }
-  const int64_t ne = (int64_t)he.size() / 2;
   T.ne = ne;
   T.edge_verts.resize(2 * ne);
   T.edge_cells.resize(2 * ne);
@@ -75,14 +93,8 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std
   T.cell_edges.assign(3 * nc, -1);
   T.cell_sign.assign(3 * nc, 0);
   for (int64_t n = 0; n < ne; ++n) {
-    const HalfEdge& p = he[2 * n];
-    const HalfEdge& m = he[2 * n + 1];
-    if (p.lo != m.lo || p.hi != m.hi || (2 * n + 2 < (int64_t)he.size() && he[2 * n + 2].lo == p.lo &&
-                                         he[2 * n + 2].hi == p.hi)) {
-      err = "edge (" + std::to_string(p.lo) + "," + std::to_string(p.hi) +
-            ") is not shared by exactly two cells";
-      return RFCMP_ERR_MESH_NOT_MANIFOLD;
-    }
+    const HalfEdge& p = he[inner[n]];
+    const HalfEdge& m = he[inner[n] + 1];
     if (!(p.a == m.b && p.b == m.a)) {
       err = "cells " + std::to_string(p.cell) + " and " + std::to_string(m.cell) +
             " are not consistently oriented";
@@ -99,7 +111,7 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std
     T.cell_edges[3 * m.cell + m.local] = (int32_t)n;
     T.cell_sign[3 * m.cell + m.local] = -1;
   }
-  // every vertex must be used; Euler characteristic of a closed orientable surface
+  // every vertex must be used
   std::vector<int32_t> deg(nv, 0);
   for (int64_t i = 0; i < 3 * nc; ++i) deg[tris[i]]++;
   for (int64_t v = 0; v < nv; ++v)
@@ -107,30 +119,69 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std
       err = "vertex " + std::to_string(v) + " is not used by any cell";
       return RFCMP_ERR_MESH_NOT_MANIFOLD;
     }
-  int64_t chi = nv - ne + nc;
-  if (chi > 2 || (chi % 2) != 0) {
-    err = "Euler characteristic " + std::to_string(chi) + " is not that of a closed orientable surface";
+  // boundary curves: each boundary vertex has exactly two boundary edges; the curves are the
+  // components of the boundary edges (union-find over their vertices)
+  std::vector<int32_t> bdeg(nv, 0), parent(nv);
+  for (int64_t v = 0; v < nv; ++v) parent[v] = (int32_t)v;
+  auto root = [&](int32_t v) {
+    while (parent[v] != v) v = parent[v] = parent[parent[v]];
+    return v;
+  };
+  for (auto& e : bnd) {
+    bdeg[e.first]++;
+    bdeg[e.second]++;
+    parent[root(e.first)] = root(e.second);
+  }
+  int64_t curves = 0;
+  for (int64_t v = 0; v < nv; ++v) {
+    if (bdeg[v] != 0 && bdeg[v] != 2) {
+      err = "vertex " + std::to_string(v) + " has " + std::to_string(bdeg[v]) +
+            " boundary edges (not a 2-manifold)";
+      return RFCMP_ERR_MESH_NOT_MANIFOLD;
+    }
+    if (bdeg[v] == 2 && root((int32_t)v) == v) ++curves;
+  }
+  // Euler characteristic of an orientable surface of genus g with b boundary curves: 2 - 2g - b
+  const int64_t chi = nv - (ne + (int64_t)bnd.size()) + nc;
+  if (2 - chi - curves < 0 || (2 - chi - curves) % 2 != 0) {
+    err = "Euler characteristic " + std::to_string(chi) + " with " + std::to_string(curves) +
+          " boundary curves is not that of an orientable surface";
     return RFCMP_ERR_MESH_NOT_MANIFOLD;
   }
-  T.genus = (int)((2 - chi) / 2);
+  T.genus = (int)((2 - chi - curves) / 2);
+  T.boundaries = (int)curves;
+  // loop functions: the interior vertices (all vertices of a closed surface)
+  T.loop_of.assign(nv, -1);
+  T.loop_verts.clear();
+  for (int64_t v = 0; v < nv; ++v)
+    if (bdeg[v] == 0) {
+      T.loop_of[v] = (int32_t)T.loop_verts.size();
+      T.loop_verts.push_back((int32_t)v);
+    }
+  const int64_t nl = (int64_t)T.loop_verts.size();
+  T.nv = nl;
+  T.edge_loops.resize(2 * ne);
+  for (int64_t i = 0; i < 2 * ne; ++i) T.edge_loops[i] = T.loop_of[T.edge_verts[i]];
 
-  // Lambda^T gather lists
-  T.vtx_ptr.assign(nv + 1, 0);
-  for (int64_t n = 0; n < ne; ++n) {
-    T.vtx_ptr[T.edge_verts[2 * n] + 1]++;
-    T.vtx_ptr[T.edge_verts[2 * n + 1] + 1]++;
-  }
-  for (int64_t v = 0; v < nv; ++v) T.vtx_ptr[v + 1] += T.vtx_ptr[v];
-  T.vtx_edge.resize(2 * ne);
-  T.vtx_sign.resize(2 * ne);
+  // Lambda^T gather lists over the loop vertices
+  T.vtx_ptr.assign(nl + 1, 0);
+  for (int64_t i = 0; i < 2 * ne; ++i)
+    if (T.edge_loops[i] >= 0) T.vtx_ptr[T.edge_loops[i] + 1]++;
+  for (int64_t v = 0; v < nl; ++v) T.vtx_ptr[v + 1] += T.vtx_ptr[v];
+  T.vtx_edge.resize(T.vtx_ptr[nl]);
+  T.vtx_sign.resize(T.vtx_ptr[nl]);
   {
     std::vector<int32_t> fill(T.vtx_ptr.begin(), T.vtx_ptr.end() - 1);
     for (int64_t n = 0; n < ne; ++n) {
-      int32_t v1 = T.edge_verts[2 * n], v2 = T.edge_verts[2 * n + 1];
-      T.vtx_edge[fill[v1]] = (int32_t)n;
-      T.vtx_sign[fill[v1]++] = 1;
-      T.vtx_edge[fill[v2]] = (int32_t)n;
-      T.vtx_sign[fill[v2]++] = -1;
+      const int32_t l1 = T.edge_loops[2 * n], l2 = T.edge_loops[2 * n + 1];
+      if (l1 >= 0) {
+        T.vtx_edge[fill[l1]] = (int32_t)n;
+        T.vtx_sign[fill[l1]++] = 1;
+      }
+      if (l2 >= 0) {
+        T.vtx_edge[fill[l2]] = (int32_t)n;
+        T.vtx_sign[fill[l2]++] = -1;
+      }
     }
   }
   // Sigma^T Sigma (duplicates merged: two cells sharing two edges get -2)
@@ -139,12 +190,15 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std
   T.lap_val.clear();
   for (int64_t c = 0; c < nc; ++c) {
     int32_t nb[3];
+    int ndeg = 0;
     for (int i = 0; i < 3; ++i) {
       int32_t n = T.cell_edges[3 * c + i];
-      nb[i] = T.edge_cells[2 * n] == c ? T.edge_cells[2 * n + 1] : T.edge_cells[2 * n];
+      nb[i] = n < 0 ? -1 : (T.edge_cells[2 * n] == c ? T.edge_cells[2 * n + 1] : T.edge_cells[2 * n]);
+      ndeg += n >= 0;
     }
-    std::vector<std::pair<int32_t, double>> row = {{(int32_t)c, 3.0}};
+    std::vector<std::pair<int32_t, double>> row = {{(int32_t)c, (double)ndeg}};
     for (int i = 0; i < 3; ++i) {
+      if (nb[i] < 0) continue;  // a boundary edge: no RWG function
       bool merged = false;
       for (auto& e : row)
         if (e.first == nb[i]) {
@@ -192,6 +246,7 @@ int build_topology(const int32_t* tris, int64_t nc, int64_t nv, Topology& T, std
 
 void mass_matrix_csr(const Topology& T, const double* verts, std::vector<int32_t>& ptr, std::vector<int32_t>& col,
                      std::vector<double>& val) {
+  // over the loop vertices: the P1 mass matrix restricted to the interior vertices
   const int64_t nv = T.nv, nc = T.nc;
   std::vector<std::vector<std::pair<int32_t, double>>> rows(nv);
   for (int64_t c = 0; c < nc; ++c) {
@@ -203,8 +258,14 @@ void mass_matrix_csr(const Topology& T, const double* verts, std::vector<int32_t
     double w[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
     double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
     double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) rows[t[i]].push_back({t[j], area * (i == j ? 2.0 : 1.0) / 12.0});
+    for (int i = 0; i < 3; ++i) {
+      const int32_t li = T.loop_of[t[i]];
+      if (li < 0) continue;
+      for (int j = 0; j < 3; ++j) {
+        const int32_t lj = T.loop_of[t[j]];
+        if (lj >= 0) rows[li].push_back({lj, area * (i == j ? 2.0 : 1.0) / 12.0});
+      }
+    }
   }
   ptr.assign(nv + 1, 0);
   col.clear();
@@ -229,8 +290,8 @@ void gtp_matrix_csr(const Topology& T, std::vector<int32_t>& ptr, std::vector<in
   //   m = n:                      2/18 (9/2 + sum over the vertices v of m of 1/NoC(v))
   //   cells sharing edge (a, b):  2/18 (1/2 + 1/NoC(a) + 1/NoC(b))
   //   sharing only vertex v:      2/18 (1/NoC(v))
-  // with NoC(v) the number of cells around vertex v.
-  const int64_t nv = T.nv, nc = T.nc;
+  // with NoC(v) the number of cells around vertex v.  (Closed surfaces: the dual functions.)
+  const int64_t nv = T.nv_mesh, nc = T.nc;
   std::vector<int32_t> noc(nv, 0);
   for (int64_t i = 0; i < 3 * nc; ++i) noc[T.tris[i]]++;
   std::vector<std::vector<int32_t>> v2c(nv);

@@ -260,9 +260,13 @@ def test_solve_host_buffers(ctx, memo):
 
 def test_error_codes(ctx):
     m = synth.geodesic_sphere(2)
+    # an edge shared by three cells (a junction) is not a 2-manifold; a missing cell is not an
+    # error (an open surface)
+    junction = np.vstack([m.tris, m.tris[:1, [0, 2, 1]]])
     with pytest.raises(rf.RfcmpError) as ei:
-        rf.Operator(ctx, m.verts, m.tris[:-1], 1.0)
+        rf.Operator(ctx, m.verts, junction, 1.0)
     assert ei.value.status == -2
+    assert rf.Operator(ctx, m.verts, m.tris[:-1], 1.0).info().boundaries == 1
     bad = m.tris.copy()
     bad[0] = bad[0, [0, 2, 1]]
     with pytest.raises(rf.RfcmpError) as ei:
