@@ -60,12 +60,30 @@ def _peaks():
 
 
 MESH_N = 32
+MESH_KIND = "sphere"  # or "plate": the open square plate of MESH_N x MESH_N squares
 
 
 def _mesh():
     import synth
 
+    if MESH_KIND == "plate":
+        return synth.plate(MESH_N, seed=7)
     return synth.geodesic_sphere(MESH_N, seed=2)
+
+
+def _mesh_sizes():
+    """(cells, unknowns) of the bench mesh."""
+    n = MESH_N
+    if MESH_KIND == "plate":
+        return 2 * n * n, 3 * n * n - 2 * n
+    return 20 * n * n, 30 * n * n
+
+
+def _mesh_desc():
+    c, u = _mesh_sizes()
+    if MESH_KIND == "plate":
+        return "open square plate %d x %d squares, %d cells, %d unknowns, jitter 3%%, seed 7" % (MESH_N, MESH_N, c, u)
+    return "geodesic sphere frequency %d, %d cells, %d unknowns, jitter 3%%, seed 2" % (MESH_N, c, u)
 
 
 def _cut_dirs():
@@ -324,17 +342,16 @@ def bench_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "fp32 operator, float-float/fp64 refinement",
-        "data": "synthetic (seeded jittered icosphere, plane wave)",
+        "data": "synthetic (seeded jittered %s, plane wave)" % ("open plate" if MESH_KIND == "plate" else "icosphere"),
         "config": {
             "workload": WORKLOAD,
-            "mesh": "geodesic sphere frequency %d, %d cells, %d unknowns, jitter 3%%, seed 2"
-                    % (MESH_N, 20 * MESH_N * MESH_N, 30 * MESH_N * MESH_N),
+            "mesh": _mesh_desc(),
             "ka": KA,
             "tol": TOL,
             "nrhs": 1,
             "parallelism": "replicas" if ws > 1 else "single",
             "l2": "inputs larger than L2 (T_A complex64 %.2f GB, V %.2f GB)"
-                  % (8e-9 * (30 * MESH_N ** 2) ** 2, 8e-9 * (20 * MESH_N ** 2) ** 2),
+                  % (8e-9 * _mesh_sizes()[1] ** 2, 8e-9 * _mesh_sizes()[0] ** 2),
             "plan": plan,
             "solve_graphs": args.solve_graphs,
         },
@@ -762,12 +779,21 @@ def main():
                     help="serving: columns join running solves between sweeps, or merged solves run to the end")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--no-tuning", action="store_true", help="ignore the autotuner table (built-in plans)")
+    ap.add_argument("--mesh", default="sphere", choices=["sphere", "plate"],
+                    help="sweep: the closed sphere (default) or an open square plate of --mesh-n squares a side "
+                         "(give --mesh-n 100 for the 29800-unknown plate)")
     ap.add_argument("--solve-graphs", default="on", choices=["on", "off"],
                     help="sweep: solve loops as CUDA graphs (default), or the same kernels launched one by one "
                          "(every kernel then shows in a profiler's launch list)")
     args = ap.parse_args()
-    global MESH_N, KA, WORKLOAD
-    if args.mesh_n != 32 or args.ka:
+    global MESH_N, KA, WORKLOAD, METRIC, MESH_KIND
+    if args.mesh == "plate":
+        MESH_KIND = "plate"
+        MESH_N = args.mesh_n
+        KA = args.ka or KA
+        WORKLOAD = "lowfreq_sweep_plate_n%d_N%d" % (MESH_N, _mesh_sizes()[1])
+        METRIC = "RF-CMP EFIE solves/s @1e-6 resid (ka sweep 1..1e-5, open plate)"
+    elif args.mesh_n != 32 or args.ka:
         MESH_N = args.mesh_n
         KA = args.ka or KA
         WORKLOAD = "profiling_case_sphere_f%d" % MESH_N

@@ -145,7 +145,9 @@ typedef struct {
 typedef struct {
   double tol;           /* stop when ||b - A i|| / ||b|| <= tol on the preconditioned system; default 1e-6 */
   int32_t max_iter;     /* total CG iterations per right-hand side, 1..1000000; default 2000 */
-  int32_t max_refine;   /* refinement sweeps (MIXED), 0..1000; default 8 */
+  int32_t max_refine;   /* refinement sweeps (MIXED), 0..1000; default 24 (a column stops at its own
+                           tolerance: 2-3 sweeps at low frequency, 12 for 1024 plane waves at ka = 10
+                           on 90750 unknowns, where split-BF16 inner products meet a harder system) */
   double inner_tol;     /* relative reduction asked of each inner CG (MIXED); default 1e-4 */
   int32_t precision;    /* rfcmp_precision; default RFCMP_PREC_MIXED */
   int32_t fail_on_nonconvergence; /* nonzero: return RFCMP_ERR_NOT_CONVERGED if any column fails */

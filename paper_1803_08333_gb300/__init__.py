@@ -445,7 +445,7 @@ class Operator:
         o.precision = PRECISION[precision]
         return o
 
-    def solve(self, e, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 8, inner_tol: float = 1e-4,
+    def solve(self, e, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 24, inner_tol: float = 1e-4,
               precision: str = "mixed"):
         """j with T j = -e via RF-CMP + CG; returns (j, [Report per column])."""
         import torch
@@ -459,7 +459,7 @@ class Operator:
         _check(lib().rfcmp_solve(self._h, _ptr(e), _ptr(j), nr, ctypes.byref(o), rep, _stream()))
         return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]
 
-    def solve_host(self, e: np.ndarray, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 8,
+    def solve_host(self, e: np.ndarray, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 24,
                    inner_tol: float = 1e-4, precision: str = "mixed", stream=None, out: "np.ndarray | None" = None):
         """Same solve with host arrays (nrhs, N) complex128; copies happen inside the C call.
 
@@ -480,7 +480,7 @@ class Operator:
                                       nr, ctypes.byref(o), rep, _stream(stream)))
         return j, [Report(bool(r.converged), r.iterations, r.refinements, r.residual) for r in rep]
 
-    def batch(self, capacity: int, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 8,
+    def batch(self, capacity: int, tol: float = 1e-6, max_iter: int = 2000, max_refine: int = 24,
               inner_tol: float = 1e-4, precision: str = "mixed") -> "Batch":
         """A batch session on this operator (continuous batching; see Batch)."""
         return Batch(self, capacity, self._solve_opts(tol, max_iter, max_refine, inner_tol, precision))

@@ -1548,7 +1548,7 @@ void rfcmp_solve_opts_default(rfcmp_solve_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->tol = 1e-6;
   o->max_iter = 2000;
-  o->max_refine = 8;
+  o->max_refine = 24;
   o->inner_tol = 1e-4;
   o->precision = RFCMP_PREC_MIXED;
 }

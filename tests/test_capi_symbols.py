@@ -45,7 +45,7 @@ def test_status_strings_and_defaults(libpath):
     assert o.power_steps == 30 and o.scaling == 0 and o.factor_tol == 1e-13 and o.power_rtol == 1e-3
     s = rf.SolveOpts()
     L.rfcmp_solve_opts_default(ctypes.byref(s))
-    assert s.tol == 1e-6 and s.precision == 0 and s.max_refine == 8
+    assert s.tol == 1e-6 and s.precision == 0 and s.max_refine == 24
 
 
 def test_struct_layouts_match_header(libpath):
