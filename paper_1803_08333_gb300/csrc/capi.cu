@@ -1272,6 +1272,14 @@ int upload_geometry(const Topology& T, const std::vector<double>& verts, DeviceG
     for (int i = 0; i < 3; ++i)
       for (int a = 0; a < 3; ++a) aloc[9 * c + 3 * i + a] = (float)(P[i][a] - cen[3 * c + a]);
     inv_area[c] = (float)(1.0 / area[c]);
+    double rc = 0.0;
+    for (int q = 0; q < 7; ++q) {
+      double r2 = 0.0;
+      for (int a = 0; a < 3; ++a) r2 += (qp[21 * c + 3 * q + a] - cen[3 * c + a]) * (qp[21 * c + 3 * q + a] - cen[3 * c + a]);
+      rc = std::max(rc, std::sqrt(r2));
+    }
+    g.rq_max = std::max(g.rq_max, (float)(rc * 1.001));  // margin over the kernel's FP32 radii
+    g.rq_mean += (float)(rc / (double)nc);
   }
   g.nc = (int32_t)nc;
   g.ne = (int32_t)T.ne;

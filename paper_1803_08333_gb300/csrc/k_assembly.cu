@@ -203,7 +203,12 @@ __device__ __forceinline__ void far_moments(const TileCells& S, int sl, const So
       const float rinv = rsqrt_ftz(r2);
       const float R = r2 * rinv;
       float sn, cs;
-      if (SHIFTED == 2) {
+      if (SHIFTED == 3) {
+        // |x| <= 3.4e-4: 1 - cos x <= x^2/2 <= 5.8e-8 and (x - sin x)/x <= x^2/6 <= 1.9e-8, both
+        // below half an FP32 unit in the last place: cos x = 1 and sin x = x exactly in FP32
+        sn = fmaf(k, R, -kref);
+        cs = 1.f;
+      } else if (SHIFTED == 2) {
         const float x = fmaf(k, R, -kref), xx = x * x;
         cs = fmaf(xx, -0.5f, 1.f);
         sn = fmaf(x * xx, -1.0f / 6.0f, x);
@@ -283,8 +288,13 @@ __device__ __forceinline__ void far_store(const TileCells& S, const TileCells& T
 }
 
 // MINB: resident CTAs per SM that the register allocation is sized for (the plan's choice).
+// PATH: the phase treatment, chosen on the host from the quadrature radii.  2: the short series
+// for every pair (k (r_s + r_t) <= 1/20 for the largest radii); 4: chosen per pair among no series
+// (<= 3.4e-4), the short series, the quarter-turn series and the full reduction, for launches
+// where the typical pair needs no series; 0: per pair among the last three (measured on GB300 at
+// 20480 cells: 14.04 / 12.65 / 14.11 ms for a launch at ka = 1 / 1e-3 / either).
 // Thread (sl, l) of a 32 x 32 tile pair takes s-cell sl against t-cells l, l + 8, l + 16, l + 24.
-template <int MINB>
+template <int MINB, int PATH>
 __global__ void __launch_bounds__(FAR_THREADS, MINB)
 far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float2* __restrict__ V, int nb) {
   RF_COUNT_LAUNCH();
@@ -330,15 +340,22 @@ far_pairs_kernel(const DeviceGeometry g, float k, float2* __restrict__ TA, float
     // e^{ikR} = e^{ik Rc} e^{ik (R - Rc)} with Rc the centroid distance: |R - Rc| is at most the
     // sum of the two quadrature radii, so where k times that is within pi/4 the 49 evaluations
     // take sin and cos of k (R - Rc) without a range reduction (a shorter series within 1/20,
-    // the common case at low frequency) and the factor e^{ik Rc} multiplies the eight moments once
+    // the common case at low frequency; none at all within 3.4e-4, where cos = 1 and sin x = x
+    // to FP32 rounding) and the factor e^{ik Rc} multiplies the eight moments once
     const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
     const float kRc = k * (dd * rsqrtf(dd));
     const float span = k * (S.rq[sl] + Tt.rq[tl]);  // bound on |k (R - Rc)|
     FarMoments Mo;
-    if (span <= 0.05f) far_moments<2, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
-    else if (span <= 0.78f) far_moments<1, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
-    else far_moments<0, UNR>(S, sl, Q, tl, d, k, 0.f, Mo);
-    if (span <= 0.78f) Mo.rotate(kRc);
+    if (PATH == 2) {
+      far_moments<2, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
+      Mo.rotate(kRc);
+    } else {
+      if (PATH == 4 && span <= 3.4e-4f) far_moments<3, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
+      else if (span <= 0.05f) far_moments<2, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
+      else if (span <= 0.78f) far_moments<1, UNR>(S, sl, Q, tl, d, k, kRc, Mo);
+      else far_moments<0, UNR>(S, sl, Q, tl, d, k, 0.f, Mo);
+      if (span <= 0.78f) Mo.rotate(kRc);
+    }
     far_store(S, Tt, sl, tl, s, t, Mo, ldN, ldC, TA, V);
   }
 }
@@ -778,23 +795,31 @@ cudaError_t launch_assemble_far(const DeviceGeometry& g, float k, float2* TA, fl
   // far pairs: all unordered pairs minus the near ones (n_near counts s <= t, including s == t)
   const double far = (double)g.nc * (g.nc + 1) / 2.0 - (double)g.n_near;
   ProfScope prof("assemble_far", 8.0 * (double)g.nc * g.nc + 8.0 * (double)g.ne * g.ne, far * 49.0 * 54.0, s);
+  // every pair's phase span k (r_s + r_t) is at most 2 k rq_max; a typical pair's about 2 k rq_mean
+  const double span_max = 2.0 * (double)k * (double)g.rq_max, span_mean = 2.0 * (double)k * (double)g.rq_mean;
+  const int path = span_mean <= 3.4e-4 ? 4 : (span_max <= 0.05 ? 2 : 0);
+#define RF_FAR(MB)                                                                           \
+  if (path == 4) far_pairs_kernel<MB, 4><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb); \
+  else if (path == 2) far_pairs_kernel<MB, 2><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb); \
+  else far_pairs_kernel<MB, 0><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
   switch (min_blocks) {
     case 1:
-      far_pairs_kernel<1><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      RF_FAR(1)
       break;
     case 2:
-      far_pairs_kernel<2><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      RF_FAR(2)
       break;
     case 0:
     case 3:
-      far_pairs_kernel<3><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      RF_FAR(3)
       break;
     case 4:
-      far_pairs_kernel<4><<<(unsigned)tiles, FAR_THREADS, 0, s>>>(g, k, TA, V, nb);
+      RF_FAR(4)
       break;
     default:
       return cudaErrorInvalidValue;
   }
+#undef RF_FAR
   return cudaGetLastError();
 }
 

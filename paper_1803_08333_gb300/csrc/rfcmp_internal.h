@@ -118,6 +118,8 @@ void mass_matrix_csr(const Topology& top, const double* verts, std::vector<int32
 struct DeviceGeometry {
   int32_t nc = 0, ne = 0, nv = 0;
   int32_t ldN = 0, ldC = 0;  // padded row strides (elements) of T_A and V
+  float rq_max = 0.f;        // largest distance of a quadrature point from its cell's centroid (+ margin)
+  float rq_mean = 0.f;       // that distance per cell, averaged over the cells
   // FP32 (far pairs)
   float* cen_hi = nullptr;   // nc x 3 (centroid rounded to FP32)
   float* cen_lo = nullptr;   // nc x 3 (centroid - cen_hi)
