@@ -505,7 +505,7 @@ def bench_serving(args):
 
     build.build()
     torch.cuda.set_device(0)
-    work = serve.poisson_workload(args.requests, args.rate, seed=4, pool=48, mesh_pool=12)
+    work = serve.poisson_workload(args.requests, args.rate, seed=4, pool=args.scene_pool, mesh_pool=args.mesh_pool)
     meshes = {}
     scenes = [(_scene_mesh(sc[0], sc[1], meshes), sc[2], nr) for _, sc, nr in work]
     budget = int(torch.cuda.mem_get_info()[1] * 0.85)
@@ -778,6 +778,8 @@ def main():
     ap.add_argument("--serve-mode", default="continuous", choices=["continuous", "merged"],
                     help="serving: columns join running solves between sweeps, or merged solves run to the end")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--scene-pool", type=int, default=48, help="serving: (mesh, ka) scenes the requests draw from")
+    ap.add_argument("--mesh-pool", type=int, default=12, help="serving: meshes the scenes draw from")
     ap.add_argument("--no-tuning", action="store_true", help="ignore the autotuner table (built-in plans)")
     ap.add_argument("--mesh", default="sphere", choices=["sphere", "plate"],
                     help="sweep: the closed sphere (default) or an open square plate of --mesh-n squares a side "
