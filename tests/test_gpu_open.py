@@ -103,3 +103,16 @@ def test_open_surface_refusals(ctx):
     s = synth.plate(1)  # two cells: every vertex on the boundary, no loop function
     with pytest.raises(rf.RfcmpError):
         rf.Operator(ctx, s.verts, s.tris, 1.0)
+
+
+def test_large_plate_factor_build_and_solve(ctx):
+    """The 100 x 100 plate (20000 cells, 29800 unknowns): the Newton-Schulz refinement of
+    (Sigma^T Sigma)^+ floors near a 1e-12 residual on this open surface and must be kept there
+    (not fall back or fail), and the solve converges at ka = 1 and 1e-4."""
+    m = synth.plate(100, seed=7)
+    for k in (1.0, 1e-4):
+        op = rf.Operator(ctx, m.verts, m.tris, k)
+        assert op.N == 29800 and op.info().boundaries == 1
+        j, rep = op.solve(op.rhs_planewave(*synth.plane_wave_z()), tol=1e-6)
+        assert rep[0].converged and rep[0].residual <= 1e-6, rep
+        op.close()
