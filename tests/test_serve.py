@@ -170,3 +170,39 @@ def test_idle_operators_are_trimmed_before_they_are_evicted():
     assert getattr(be, "trims", 0) >= 1  # the first operator gave its planes back ...
     assert be.destroyed == [(serve.mesh_key(v, t), 1.0), (serve.mesh_key(v, t), 2.0)]  # ... and stayed until close
     assert be.in_use == 0
+
+
+def test_a_request_wider_than_a_session_gets_its_own():
+    be = serve.FakeBackend(solve_seconds=0.01)
+    srv = serve.Server(be, hbm_budget=0, workers=1, max_batch_columns=4)
+    v, t = _mesh(2)
+    kh, pol = synth.random_plane_waves(6, seed=3)
+    r = srv.submit(v, t, 1.0, kh, pol).result(timeout=10)
+    srv.close()
+    assert r.j.shape == (6, 3 * t.shape[0] // 2)
+    assert be.sessions[0]["cap"] == 6  # opened as wide as the request
+
+
+def test_reservations_are_released_after_sessions_and_failures():
+    class Flaky(serve.FakeBackend):
+        def step(self, sess, stream):
+            if sess["op"]["scene"][1] == 3.0:
+                raise RuntimeError("boom")
+            return super().step(sess, stream)
+
+    be = Flaky(solve_seconds=0.005)
+    srv = serve.Server(be, hbm_budget=10**12, workers=2, max_batch_columns=8)
+    v, t = _mesh(2)
+    kh, pol = synth.random_plane_waves(3, seed=5)
+    futs = [srv.submit(v, t, 1.0 + (i % 3), kh, pol) for i in range(12)]
+    ok = [f for i, f in enumerate(futs) if 1.0 + (i % 3) != 3.0]
+    bad = [f for i, f in enumerate(futs) if 1.0 + (i % 3) == 3.0]
+    for f in ok:
+        assert f.result(timeout=10).j.shape[0] == 3
+    for f in bad:
+        with pytest.raises(RuntimeError):
+            f.result(timeout=10)
+    srv.close()
+    assert srv._reserved == 0 and not srv._busy
+    st = srv.stats()
+    assert st["requests"] == len(ok) and st["solves"] >= 3
