@@ -326,13 +326,16 @@ cudaError_t gemm_launch(const SplitOperand* A, const SplitOperand* B, const int*
   if (upper && tml < tnl) return cudaErrorInvalidValue;
   const long long tiles = upper ? tnl * (tnl + 1) / 2 : tnl * tml;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  // the SM count, read once (launches may come from several host threads)
+  static std::once_flag sms_once;
   static int sms = 0;
-  if (sms == 0) {
+  static cudaError_t sms_err = cudaSuccess;
+  std::call_once(sms_once, [] {
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+    sms_err = cudaGetDevice(&dev);
+    if (sms_err == cudaSuccess) sms_err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  if (sms_err != cudaSuccess || sms <= 0) return sms_err != cudaSuccess ? sms_err : cudaErrorInvalidValue;
   const int grid = (int)std::max(1LL, std::min<long long>(tiles, sms));
   double frac = 1.0;  // share of the output tiles computed
   if (upper) {
