@@ -57,6 +57,12 @@
 extern "C" {
 #endif
 
+/* Largest k times the diagonal of the vertices' bounding box that rfcmp_op_create accepts.  The
+ * far-pair assembly (FP32) reduces k R by whole multiples of pi/2 with a product that stays exact
+ * below 2^16 multiples (k R < 1.029e5); beyond this bound the phase would be silently wrong.  The
+ * FP32 phase error itself grows as k R * 2^-24 (6e-3 rad at the bound). */
+#define RFCMP_MAX_K_EXTENT 1.0e5
+
 typedef struct rfcmp_ctx rfcmp_ctx;
 typedef struct rfcmp_op rfcmp_op;
 typedef struct { double re, im; } rfcmp_c128;
@@ -205,7 +211,8 @@ uint64_t rfcmp_ctx_bytes_in_use(const rfcmp_ctx* ctx);
  *  verts  nv x 3 float64 (host: every mesh vertex), tris N_C x 3 int32 (host).  Open
  *         surfaces need at least one interior vertex; the theory variant (opts.outer =
  *         RFCMP_OUTER_GSIGMA) needs a closed surface (RFCMP_ERR_INVALID_ARG otherwise).
- *  k      wavenumber > 0 (rad/m, c = 1).
+ *  k      wavenumber > 0 (rad/m, c = 1); k times the diagonal of the bounding box of verts at
+ *         most RFCMP_MAX_K_EXTENT (RFCMP_ERR_INVALID_ARG otherwise).
  *  opts   NULL for the defaults.
  * All work runs on the context device's legacy default stream; the call
  * returns when the op is ready.

@@ -26,6 +26,7 @@ OUTER = {"sigma": 0, "gsigma": 1}
 SCALING = {"power": 0, "k": 1, "fixed": 2}
 PRECISION = {"mixed": 0, "ff": 1}
 EXPORT = {"T_A": 0, "V": 1, "LPLUS": 2, "GLL_INV": 3, "GTP_INV": 4}
+MAX_K_EXTENT = 1.0e5  # RFCMP_MAX_K_EXTENT: largest k x (bounding-box diagonal) an op accepts
 
 # every symbol include/rfcmp.h declares
 EXPORTED_SYMBOLS = [

@@ -1622,6 +1622,25 @@ int rfcmp_op_create(rfcmp_ctx* ctx, const double* verts, int64_t nv, const int32
     return set_error(RFCMP_ERR_INVALID_ARG, "fixed scaling needs positive alpha, beta, gamma");
   for (int64_t i = 0; i < 3 * nv; ++i)
     if (!std::isfinite(verts[i])) return set_error(RFCMP_ERR_INVALID_ARG, "non-finite vertex coordinate");
+  {
+    // the far-pair kernel reduces k R by multiples of pi/2 whose leading part (8 bits) times the
+    // multiple stays exact below 2^16 multiples, k R < 1.029e5; R is at most the diagonal of the
+    // vertices' bounding box
+    double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+    for (int64_t i = 0; i < nv; ++i)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], verts[3 * i + a]);
+        hi[a] = std::max(hi[a], verts[3 * i + a]);
+      }
+    double d2 = 0.0;
+    for (int a = 0; a < 3 && nv > 0; ++a) d2 += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+    if (k * std::sqrt(d2) > RFCMP_MAX_K_EXTENT) {
+      char msg[160];
+      snprintf(msg, sizeof msg, "k times the mesh extent (%.4g) exceeds %.4g, the phase range of the FP32 assembly",
+               k * std::sqrt(d2), (double)RFCMP_MAX_K_EXTENT);
+      return set_error(RFCMP_ERR_INVALID_ARG, msg);
+    }
+  }
   RF_CUDA(cudaSetDevice(ctx->device));
   auto op = std::make_unique<rfcmp_op>();
   op->ctx = ctx;

@@ -176,15 +176,9 @@ struct FarMoments {
 // and R^2 = |D|^2 + |rho'_j|^2 + D.(-2 rho'_j): four operations per evaluation for R^2, the
 // source data read from shared memory where they are used.  SHIFTED > 0: the phase of each
 // evaluation is k R - k Rc with |k R - k Rc| <= pi/4 (SHIFTED 1, series to r^9 / r^8) or <= 1/20
-// (SHIFTED 2: sin to r^3, cos to r^2, truncation below 3e-7), no range reduction; 0: sin and cos
-// of k R with the reduction.  The rho' moments come out of the loop against -2 rho' and are
-// scaled back at the end.
-// 7 x 7 product rule over the pair (s outer, t source).  For outer point i, D = c_s + rho_i - c_t
-// and R^2 = |D|^2 + |rho'_j|^2 + D.(-2 rho'_j): four operations per evaluation for R^2, the
-// source data read from shared memory where they are used.  SHIFTED > 0: the phase of each
-// evaluation is k R - k Rc with |k R - k Rc| <= pi/4 (SHIFTED 1, series to r^9 / r^8) or <= 1/20
-// (SHIFTED 2: sin to r^3, cos to r^2, truncation below 3e-7), no range reduction; 0: sin and cos
-// of k R with the reduction.  The rho' moments come out of the loop against -2 rho' and are
+// (SHIFTED 2: sin to r^3, cos to r^2, truncation below 3e-7) or <= 3.4e-4 (SHIFTED 3: sin x = x,
+// cos x = 1), no range reduction; 0: sin and cos of k R with the reduction (k R < 1.029e5, which
+// the host checks at op creation).  The rho' moments come out of the loop against -2 rho' and are
 // scaled back at the end.
 template <int SHIFTED, int UNROLL>
 __device__ __forceinline__ void far_moments(const TileCells& S, int sl, const SourceTile& Q, int tl, const float (&d)[3],

@@ -48,6 +48,16 @@ def test_status_strings_and_defaults(libpath):
     assert s.tol == 1e-6 and s.precision == 0 and s.max_refine == 24
 
 
+def test_phase_range_bound_matches_header():
+    txt = open(os.path.join(ROOT, "include", "rfcmp.h")).read()
+    (val,) = re.findall(r"#define RFCMP_MAX_K_EXTENT\s+([0-9.eE+-]+)", txt)
+    assert float(val) == rf.MAX_K_EXTENT
+    # the reduction's leading part of pi/2 has 8 significant bits (1.5703125 = 201 / 128), so q
+    # times it is exact in FP32 while q < 2^16; the bound keeps q = rint(k R 2/pi) below that
+    assert 1.5703125 * 128 == 201 and 201 < 2**8
+    assert rf.MAX_K_EXTENT * 2 / 3.141592653589793 + 0.5 < 2**16
+
+
 def test_struct_layouts_match_header(libpath):
     # sizes implied by include/rfcmp.h on LP64
     assert ctypes.sizeof(rf.OpOpts) == 4 + 4 + 8 * 5 + 8 + 4 * 8

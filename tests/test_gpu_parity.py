@@ -275,6 +275,11 @@ def test_error_codes(ctx):
     with pytest.raises(rf.RfcmpError) as ei:
         rf.Operator(ctx, m.verts, m.tris, -1.0)
     assert ei.value.status == -1
+    # k times the bounding-box diagonal beyond the exact range of the FP32 phase reduction
+    diag = float(np.linalg.norm(m.verts.max(0) - m.verts.min(0)))
+    with pytest.raises(rf.RfcmpError) as ei:
+        rf.Operator(ctx, m.verts, m.tris, 1.01 * rf.MAX_K_EXTENT / diag)
+    assert ei.value.status == -1 and "extent" in str(ei.value)
     small = rf.Context(0, hbm_budget_bytes=1 << 16)  # the level-1 sphere needs about 300 KB
     with pytest.raises(rf.RfcmpError) as ei:
         rf.Operator(small, m.verts, m.tris, 1.0)
