@@ -17,8 +17,10 @@ Readings (the paper names the method and its tolerance only):
     cells; a cell: its three vertices); a cluster's box is the union of its items' supports.
   * admissibility: a block (row cluster a, column cluster b) is stored in low rank when
     min(diam a, diam b) <= eta * dist(a, b), diam the box diagonal and dist the distance
-    between the two boxes (zero when they touch or overlap).  Since the supports are inside
-    the boxes, an admissible block couples only cells that share no vertex.
+    between the two boxes (zero when they touch or overlap), and only when dist > 0: boxes
+    that touch never form a low-rank block, boxes of zero extent included.  Since the
+    supports are inside the boxes, an admissible block couples only cells that share no
+    vertex.
   * block tree: a pair that is not admissible is split into the children of whichever
     clusters have children (both when both do); a pair of two leaves that is not admissible
     is a dense block.
@@ -115,7 +117,8 @@ def box_distance(a: Cluster, b: Cluster) -> float:
 
 
 def admissible(a: Cluster, b: Cluster, eta: float) -> bool:
-    return min(a.diam, b.diam) <= eta * box_distance(a, b)
+    d = box_distance(a, b)
+    return d > 0.0 and min(a.diam, b.diam) <= eta * d
 
 
 @dataclass
