@@ -444,6 +444,81 @@ const char* rfcmp_last_error(void);
 void rfcmp_op_opts_default(rfcmp_op_opts* opts);
 void rfcmp_solve_opts_default(rfcmp_solve_opts* opts);
 
+/* ----------------------------------------------------------------------------
+ * Compressed operators (Sec. 4: the system matrix compressed by an adaptive cross
+ * approximation at tolerance 1e-4; at extremely low frequency the vector potential stored and
+ * compressed apart from the scalar potential).  T_A (RWG functions) and V (cells) each become a
+ * symmetric hierarchical matrix: a cluster tree of the index set (recursive bisection at the
+ * middle position of the items sorted along the largest extent of their centres; an item's
+ * support box spans the vertices of its cells), the blocks of the block tree on and above the
+ * block diagonal, an admissible block (min(diam a, diam b) <= eta * dist(a, b) > 0 for the two
+ * clusters' boxes, which couples only cells that share no vertex) stored as rank-r crosses
+ * U^T Vt found by ACA with partial pivoting on the device (stop after the cross whose size
+ * ||u|| ||v|| is at most eps ||S_r||_F), every other block dense.  A block off the diagonal also
+ * stands for its transpose below it, so the compressed T_A and V stay exactly complex symmetric.
+ * The compressed form is built from an op's resident dense T_A and V (the op remains valid and
+ * unchanged); assembling the compressed form without the dense matrices is not provided.
+ */
+typedef struct rfcmp_hm rfcmp_hm;
+
+typedef enum {
+  RFCMP_HM_T_A = 0, /* the vector-potential block T_A (N x N) */
+  RFCMP_HM_V = 1    /* the scalar-potential block V (N_C x N_C) */
+} rfcmp_hm_which;
+
+typedef struct {
+  double eps;        /* ACA stopping tolerance per block, in (0, 1) (default 1e-4, the paper's) */
+  double eta;        /* admissibility parameter > 0 (default 1) */
+  int32_t leaf;      /* largest cluster that is not split, in [8, 1024] (default 32) */
+  int32_t max_rank;  /* crosses per block, in [1, 256] (default 64); an admissible block whose
+                        crosses reach it without meeting the stopping rule is stored dense */
+  int32_t reserved[6];  /* must be zero */
+} rfcmp_hm_opts;
+
+typedef struct {
+  int64_t n[2];               /* rows of T_A (N) and V (N_C), indexed by rfcmp_hm_which */
+  int64_t lowrank_blocks[2];  /* blocks stored as crosses (on and above the block diagonal) */
+  int64_t dense_blocks[2];    /* blocks stored dense, capped ones included */
+  int64_t capped_blocks[2];   /* admissible blocks the rank cap left dense */
+  int64_t bytes[2];           /* device bytes of each compressed matrix */
+  int32_t max_rank[2];        /* largest rank of a low-rank block */
+  int32_t reserved[6];
+} rfcmp_hm_info;
+
+void rfcmp_hm_opts_default(rfcmp_hm_opts* opts);
+
+/* Host only (no device work): the cluster tree and the symmetric block list of n items.
+ *  centres, sup_lo, sup_hi  n x 3 float64 each (host): item centres and support boxes.
+ *  leaf, eta                as in rfcmp_hm_opts (leaf in [1, 65536], eta >= 0).
+ *  perm       n int32 (host, caller-owned): cluster order -> item index.
+ *  blocks     5 int32 per block (host, caller-owned) or NULL to query the count: r0, r1, c0, c1
+ *             (half-open ranges of the cluster order, r0 <= c0) and 1 if admissible else 0,
+ *             ordered by (r0, c0); capacity = blocks the array holds.
+ *  n_blocks   receives the number of blocks.
+ * Errors: RFCMP_ERR_INVALID_ARG (NULL, non-finite coordinates, argument out of range, capacity
+ * too small). */
+int rfcmp_hm_partition(const double* centres, const double* sup_lo, const double* sup_hi, int64_t n, int32_t leaf,
+                       double eta, int32_t* perm, int32_t* blocks, int64_t capacity, int64_t* n_blocks);
+
+/* Compresses op's T_A and V (opts NULL for the defaults).  Runs on the context device's legacy
+ * default stream and returns when the compressed form is ready.  Its bytes count against the
+ * context's budget; destroy it before the context.
+ * Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_OUT_OF_BUDGET (the build's peak: the crosses' slots
+ * and, at worst, every block dense), RFCMP_ERR_CUDA. */
+int rfcmp_hm_create(rfcmp_op* op, const rfcmp_hm_opts* opts, rfcmp_hm** out);
+
+/* y = H x for nrhs columns, H the compressed T_A or V (which), FP32 factors with FP64
+ * accumulation.  x, y DEVICE, n x nrhs complex128 column-major (n = N or N_C), not aliased;
+ * nrhs in [1, 65535]; stream NULL for the legacy default stream.  Several streams may run
+ * products of one hm at once.  Errors: RFCMP_ERR_INVALID_ARG, RFCMP_ERR_CUDA. */
+int rfcmp_hm_apply(rfcmp_hm* hm, int which, const rfcmp_c128* x, rfcmp_c128* y, int64_t nrhs, void* stream);
+
+/* Block counts, ranks and bytes of both compressed matrices.  Errors: RFCMP_ERR_INVALID_ARG. */
+int rfcmp_hm_info_get(const rfcmp_hm* hm, rfcmp_hm_info* out);
+
+/* Frees the compressed form after the products queued on its streams. */
+int rfcmp_hm_destroy(rfcmp_hm* hm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,10 @@ EXPORTED_SYMBOLS = [
     "rfcmp_op_trim", "rfcmp_launch_count", "rfcmp_set_solve_graphs", "rfcmp_rhs_voltage_gap",
     "rfcmp_pool_stats", "rfcmp_pool_reset_high", "rfcmp_pool_trim", "rfcmp_batch_create", "rfcmp_batch_destroy",
     "rfcmp_batch_admit", "rfcmp_batch_step", "rfcmp_batch_take", "rfcmp_batch_counts",
+    "rfcmp_hm_opts_default", "rfcmp_hm_partition", "rfcmp_hm_create", "rfcmp_hm_apply", "rfcmp_hm_info_get",
+    "rfcmp_hm_destroy",
 ]
+HM = {"T_A": 0, "V": 1}
 
 
 class C128(ctypes.Structure):
@@ -111,6 +114,21 @@ class ProfileEntry(ctypes.Structure):
     ]
 
 
+class HmOpts(ctypes.Structure):
+    _fields_ = [
+        ("eps", ctypes.c_double), ("eta", ctypes.c_double), ("leaf", ctypes.c_int32), ("max_rank", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
+    ]
+
+
+class HmInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64 * 2), ("lowrank_blocks", ctypes.c_int64 * 2), ("dense_blocks", ctypes.c_int64 * 2),
+        ("capped_blocks", ctypes.c_int64 * 2), ("bytes", ctypes.c_int64 * 2), ("max_rank", ctypes.c_int32 * 2),
+        ("reserved", ctypes.c_int32 * 6),
+    ]
+
+
 class RfcmpError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("rfcmp status %d: %s" % (status, msg))
@@ -173,6 +191,13 @@ def lib():
         L.rfcmp_batch_step.argtypes = [vp, i32p, i32p, vp]
         L.rfcmp_batch_take.argtypes = [vp, i32p, i32, vp, ctypes.POINTER(SolveReport), vp]
         L.rfcmp_batch_counts.argtypes = [vp, i32p, i32p, i32p]
+        L.rfcmp_hm_opts_default.argtypes = [ctypes.POINTER(HmOpts)]
+        L.rfcmp_hm_opts_default.restype = None
+        L.rfcmp_hm_partition.argtypes = [vp, vp, vp, i64, i32, dbl, vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.rfcmp_hm_create.argtypes = [vp, ctypes.POINTER(HmOpts), ctypes.POINTER(vp)]
+        L.rfcmp_hm_apply.argtypes = [vp, i32, vp, vp, i64, vp]
+        L.rfcmp_hm_info_get.argtypes = [vp, ctypes.POINTER(HmInfo)]
+        L.rfcmp_hm_destroy.argtypes = [vp]
         _LIB = L
     return _LIB
 
@@ -504,6 +529,77 @@ class Operator:
         try:
             if self._h:
                 lib().rfcmp_op_destroy(self._h)
+        except Exception:
+            pass
+
+
+def hm_partition(centres, sup_lo, sup_hi, leaf: int = 32, eta: float = 1.0):
+    """Cluster order (n,) and symmetric block list (B, 5: r0, r1, c0, c1, admissible) of n items
+    with centres and support boxes (n x 3 each), computed by the library on the host."""
+    c = np.ascontiguousarray(centres, dtype=np.float64)
+    lo = np.ascontiguousarray(sup_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(sup_hi, dtype=np.float64)
+    n = c.shape[0]
+    if lo.shape != c.shape or hi.shape != c.shape or (n and c.shape[1] != 3):
+        raise ValueError("centres, sup_lo and sup_hi must all be n x 3")
+    perm = np.empty(n, dtype=np.int32)
+    nb = ctypes.c_int64()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().rfcmp_hm_partition(vp(c), vp(lo), vp(hi), n, int(leaf), float(eta), vp(perm), None, 0,
+                                    ctypes.byref(nb)))
+    blocks = np.empty((nb.value, 5), dtype=np.int32)
+    _check(lib().rfcmp_hm_partition(vp(c), vp(lo), vp(hi), n, int(leaf), float(eta), vp(perm), vp(blocks),
+                                    nb.value, ctypes.byref(nb)))
+    return perm, blocks
+
+
+class Compressed:
+    """T_A and V of an operator compressed apart (rfcmp_hm_*): symmetric hierarchical matrices
+    with ACA crosses on the admissible blocks (Sec. 4)."""
+
+    def __init__(self, op: "Operator", eps: float = 1e-4, eta: float = 1.0, leaf: int = 32, max_rank: int = 64):
+        self.op = op
+        o = HmOpts()
+        lib().rfcmp_hm_opts_default(ctypes.byref(o))
+        o.eps, o.eta, o.leaf, o.max_rank = float(eps), float(eta), int(leaf), int(max_rank)
+        self._h = ctypes.c_void_p()
+        _check(lib().rfcmp_hm_create(op._h, ctypes.byref(o), ctypes.byref(self._h)))
+
+    def apply(self, which: str, x, out=None, stream=None):
+        """y = H x for H the compressed "T_A" or "V"; x (nrhs, n) or (n,) on the device."""
+        import torch
+
+        x = x.to(device="cuda", dtype=torch.complex128)
+        if x.dim() == 1:
+            x = x[None]
+        x = x.contiguous()
+        n = self.op.N if which == "T_A" else self.op.nc
+        if x.shape[1] != n:
+            raise ValueError("x has %d rows, the compressed %s has %d" % (x.shape[1], which, n))
+        y = torch.empty_like(x) if out is None else out
+        _check(lib().rfcmp_hm_apply(self._h, HM[which], _ptr(x), _ptr(y), x.shape[0], _stream(stream)))
+        return y
+
+    def info(self) -> dict:
+        i = HmInfo()
+        _check(lib().rfcmp_hm_info_get(self._h, ctypes.byref(i)))
+        out = {}
+        for w, name in enumerate(("T_A", "V")):
+            out[name] = {
+                "n": i.n[w], "lowrank_blocks": i.lowrank_blocks[w], "dense_blocks": i.dense_blocks[w],
+                "capped_blocks": i.capped_blocks[w], "bytes": i.bytes[w], "max_rank": i.max_rank[w],
+            }
+        return out
+
+    def close(self):
+        if self._h:
+            _check(lib().rfcmp_hm_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().rfcmp_hm_destroy(self._h)
         except Exception:
             pass
 

@@ -19,6 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librfcmp.so")
 SOURCES = [
     "k_assembly.cu", "k_linalg.cu", "k_gemv_stream.cu", "k_gemm.cu", "k_exact.cu", "k_factor.cu", "k_krylov.cu",
+    "k_hmatrix.cu",
     "capi.cu",
     "noalloc.cu", "topology.cpp", "amg.cpp",
 ]

@@ -1443,6 +1443,23 @@ bool op_ta_view(const rfcmp_op* op, OpTaView* out) {
   out->device = op->ctx->device;
   return true;
 }
+
+bool op_dense_view(rfcmp_op* op, OpDenseView* out) {
+  if (!op || !out || !op->TA || !op->V) return false;
+  out->TA = op->TA;
+  out->V = op->V;
+  out->n = (int)op->top.ne;
+  out->nc = (int)op->top.nc;
+  out->ldN = op->ldN;
+  out->ldC = op->ldC;
+  out->device = op->ctx->device;
+  out->top = &op->top;
+  out->verts = op->verts.data();
+  out->ctx_bytes = &op->ctx->bytes;
+  out->ctx_live = &op->ctx->live_ops;
+  out->budget = op->ctx->budget;
+  return true;
+}
 }  // namespace rfcmp
 
 // ============================================================================ C ABI
@@ -1451,7 +1468,7 @@ extern "C" {
 int rfcmp_launch_count(uint64_t* out) {
   if (!out) return set_error(RFCMP_ERR_INVALID_ARG, "invalid argument");
   *out = launches_assembly() + launches_exact() + launches_factor() + launches_gemm() + launches_gemv_stream() +
-         launches_linalg() + launches_krylov();
+         launches_linalg() + launches_krylov() + launches_hmatrix();
   return RFCMP_OK;
 }
 

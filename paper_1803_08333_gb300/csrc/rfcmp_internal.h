@@ -3,6 +3,7 @@
 // C ABI (capi.cu).  Nothing here is part of the public interface.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -39,6 +40,7 @@ unsigned long long launches_gemm();
 unsigned long long launches_gemv_stream();
 unsigned long long launches_linalg();
 unsigned long long launches_krylov();
+unsigned long long launches_hmatrix();
 
 // ---------------------------------------------------------------- op accessors
 // Read-only view of an operator's T_A for translation units outside capi.cu.
@@ -48,6 +50,22 @@ struct OpTaView {
   int device = 0;
 };
 bool op_ta_view(const rfcmp_op* op, OpTaView* out);
+struct Topology;
+// Read-only view of an operator's dense T_A and V, its mesh and its context's accounting, for the
+// compressed form (k_hmatrix.cu).
+struct OpDenseView {
+  const float2* TA = nullptr;
+  const float2* V = nullptr;
+  int n = 0, nc = 0;      // rows of T_A (RWG functions) and V (cells)
+  int ldN = 0, ldC = 0;   // their row strides (elements); both triangles are stored
+  int device = 0;
+  const Topology* top = nullptr;
+  const double* verts = nullptr;        // mesh vertices, 3 per vertex
+  std::atomic<uint64_t>* ctx_bytes = nullptr;
+  std::atomic<int>* ctx_live = nullptr;  // objects that must be destroyed before the context
+  uint64_t budget = 0;                   // the context's HBM budget (0: none)
+};
+bool op_dense_view(rfcmp_op* op, OpDenseView* out);
 // Records the message returned by rfcmp_last_error() for the calling thread; returns code.
 int set_error(int code, const std::string& msg);
 
