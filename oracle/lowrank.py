@@ -34,6 +34,8 @@ Readings (the paper names the method and its tolerance only):
     its inner products with the earlier ones.
   * recompression: the ACA factors of a block are orthogonalised (QR of both sides) and
     the small core is cut by its SVD at eps relative to its largest singular value.
+  * storage: an admissible block whose crosses would take at least its own entries
+    (rank (m + n) >= m n) is stored dense.
 
 Parity status: pinned by tests/test_oracle_lowrank.py: exact recovery of a matrix of known
 rank, the interpolation property of the crosses, the Frobenius-norm update against a direct
@@ -301,6 +303,10 @@ def compress(entries, rows: ClusterTree, cols: ClusterTree, eta: float, eps: flo
                     ri.size, ci.size, eps)
         if recompress_blocks:
             U, Vt = recompress(U, Vt, eps)
+        if U.shape[1] * (ri.size + ci.size) >= ri.size * ci.size:
+            # the crosses would take at least the block's own entries: stored dense
+            blocks.append(Block(a.start, a.stop, b.start, b.stop, D=np.asarray(entries(ri, ci), np.complex128)))
+            continue
         blocks.append(Block(a.start, a.stop, b.start, b.stop, U=U, Vt=Vt))
     return HMatrix((m, n), rows.perm, cols.perm, blocks, symmetric)
 
