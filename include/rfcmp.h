@@ -454,7 +454,7 @@ void rfcmp_solve_opts_default(rfcmp_solve_opts* opts);
  * block diagonal, an admissible block (min(diam a, diam b) <= eta * dist(a, b) > 0 for the two
  * clusters' boxes, which couples only cells that share no vertex) stored as rank-r crosses
  * U^T Vt found by ACA with partial pivoting on the device (stop after the cross whose size
- * ||u|| ||v|| is at most eps ||S_r||_F), every other block dense.  A block off the diagonal also
+ * ||u|| ||v|| is at most eps ||S_r||_F) when r (m + n) < m n, every other block dense.  A block off the diagonal also
  * stands for its transpose below it, so the compressed T_A and V stay exactly complex symmetric.
  * The compressed form is built from an op's resident dense T_A and V (the op remains valid and
  * unchanged); assembling the compressed form without the dense matrices is not provided.
@@ -480,6 +480,8 @@ typedef struct {
   int64_t lowrank_blocks[2];  /* blocks stored as crosses (on and above the block diagonal) */
   int64_t dense_blocks[2];    /* blocks stored dense, capped ones included */
   int64_t capped_blocks[2];   /* admissible blocks the rank cap left dense */
+  int64_t small_blocks[2];    /* admissible blocks stored dense because their crosses would take
+                                 at least the block's own entries (rank (m + n) >= m n) */
   int64_t bytes[2];           /* device bytes of each compressed matrix */
   int32_t max_rank[2];        /* largest rank of a low-rank block */
   int32_t reserved[6];

@@ -124,7 +124,8 @@ class HmOpts(ctypes.Structure):
 class HmInfo(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int64 * 2), ("lowrank_blocks", ctypes.c_int64 * 2), ("dense_blocks", ctypes.c_int64 * 2),
-        ("capped_blocks", ctypes.c_int64 * 2), ("bytes", ctypes.c_int64 * 2), ("max_rank", ctypes.c_int32 * 2),
+        ("capped_blocks", ctypes.c_int64 * 2), ("small_blocks", ctypes.c_int64 * 2), ("bytes", ctypes.c_int64 * 2),
+        ("max_rank", ctypes.c_int32 * 2),
         ("reserved", ctypes.c_int32 * 6),
     ]
 
@@ -587,7 +588,8 @@ class Compressed:
         for w, name in enumerate(("T_A", "V")):
             out[name] = {
                 "n": i.n[w], "lowrank_blocks": i.lowrank_blocks[w], "dense_blocks": i.dense_blocks[w],
-                "capped_blocks": i.capped_blocks[w], "bytes": i.bytes[w], "max_rank": i.max_rank[w],
+                "capped_blocks": i.capped_blocks[w], "small_blocks": i.small_blocks[w], "bytes": i.bytes[w],
+                "max_rank": i.max_rank[w],
             }
         return out
 

@@ -10,7 +10,7 @@
 // carrying support boxes), the admissibility test min(diam a, diam b) <= eta dist(a, b) on
 // boxes that do not touch (dist > 0), the block list.  Device: one CTA per admissible block runs the cross approximation on the
 // resident dense matrix (rows and columns gathered through the cluster permutation), blocks whose
-// crosses reach the rank cap stay dense, and the factors and dense blocks are packed into one
+// crosses reach the rank cap, or would take at least the block's own entries, stay dense, and the factors and dense blocks are packed into one
 // buffer per matrix.  The product y = H x gathers x into cluster order, runs one CTA per (block,
 // column) with FP64 accumulation and FP64 atomics into y, and scatters back.
 #include <cuda_runtime.h>
@@ -519,7 +519,7 @@ struct HmPart {
   HmBlockDev* blocks = nullptr;  // (device)
   float2* data = nullptr;        // dense blocks and crosses (device)
   long long elems = 0;
-  int64_t n_lowrank = 0, n_dense = 0, n_capped = 0;
+  int64_t n_lowrank = 0, n_dense = 0, n_capped = 0, n_small = 0;
   int max_rank = 0;
   uint64_t bytes = 0;
 };
@@ -613,13 +613,15 @@ int build_part(const float2* A, int ld, int n, const std::vector<double>& cen, c
     long long s = 0;
     if (b.admissible) {
       const size_t c = ci++;
-      if (status[c] == 0 && rank[c] >= 0 && rank[c] <= cap) {
+      if (status[c] != 0 || rank[c] < 0 || rank[c] > cap) {
+        ++out.n_capped;
+      } else if ((long long)rank[c] * (m + nn) >= m * nn) {
+        ++out.n_small;  // the crosses would take at least the block's own entries
+      } else {
         d.rank = rank[c];
         s = slot[c];
         ++out.n_lowrank;
         out.max_rank = std::max(out.max_rank, rank[c]);
-      } else {
-        ++out.n_capped;
       }
     }
     if (d.rank < 0) ++out.n_dense;
@@ -835,6 +837,7 @@ int rfcmp_hm_info_get(const rfcmp_hm* hm, rfcmp_hm_info* out) {
     out->lowrank_blocks[w] = P.n_lowrank;
     out->dense_blocks[w] = P.n_dense;
     out->capped_blocks[w] = P.n_capped;
+    out->small_blocks[w] = P.n_small;
     out->bytes[w] = P.bytes;
     out->max_rank[w] = P.max_rank;
   }

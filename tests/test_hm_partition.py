@@ -103,4 +103,4 @@ def test_hm_opts_defaults_and_layout():
     rf.lib().rfcmp_hm_opts_default(ctypes.byref(o))
     assert o.eps == 1e-4 and o.eta == 1.0 and o.leaf == 32 and o.max_rank == 64
     assert ctypes.sizeof(rf.HmOpts) == 8 + 8 + 4 + 4 + 6 * 4
-    assert ctypes.sizeof(rf.HmInfo) == 5 * 2 * 8 + 2 * 4 + 6 * 4
+    assert ctypes.sizeof(rf.HmInfo) == 6 * 2 * 8 + 2 * 4 + 6 * 4
