@@ -104,3 +104,14 @@ def test_hm_opts_defaults_and_layout():
     assert o.eps == 1e-4 and o.eta == 1.0 and o.leaf == 32 and o.max_rank == 64
     assert ctypes.sizeof(rf.HmOpts) == 8 + 8 + 4 + 4 + 6 * 4
     assert ctypes.sizeof(rf.HmInfo) == 6 * 2 * 8 + 2 * 4 + 6 * 4
+
+
+def test_compressed_entry_points_refuse_null_handles():
+    import ctypes
+
+    L_ = rf.lib()
+    out = ctypes.c_void_p()
+    assert L_.rfcmp_hm_create(None, None, ctypes.byref(out)) == -1
+    assert L_.rfcmp_hm_apply(None, 0, None, None, 1, None) == -1
+    assert L_.rfcmp_hm_info_get(None, ctypes.byref(rf.HmInfo())) == -1
+    assert L_.rfcmp_hm_destroy(None) == 0
